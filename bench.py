@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""Throughput of the randomly shifted rank-1 lattice rule on one GB300.
+
+Workload (the metric's single-sector configuration): d = 6 sector integrand
+U^-2 F^-1 with U = c0 + 6 degree-1 and F = c0 + 12 degree-2 monomials
+(coefficients U(0.1, 2), seed 0x5EED0002), baker transform, prime
+n = 16777213, m = 32 shifts, FP32 evaluation with FP64 sums; the generating
+vector comes from the library's CBC search (untimed).
+
+One step = one full rule (all kernels of qmc_plan_execute: lattice kernel +
+final pass, Eq. 2 and Eq. 3) with inputs resident on the device.  `value` is
+lattice-point evaluations (n * m per step, all ranks) per second.  `e2e` is
+the same metric through qmc_integrate with host inputs and a host result.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lattice-point evals/sec & % FP pipe peak; time to 1e-8 rel err vs plain QMC"
+UNIT = "evals/s"
+WORKLOAD = "sector U^-2 F^-1, d=6, T_U=6, T_F=12, baker, n=16777213, m=32, FP32 eval / FP64 sums"
+
+# Algorithmic FP32 flops per evaluation of this workload (FMA = 2): baker
+# 2 per coordinate (12), U 2 per term (12), F 3 per degree-2 term (36),
+# U^2 F 2, accumulate 1 -> 63, plus one reciprocal on the MUFU unit.
+FLOPS_PER_EVAL = 63
+# FP32 FMA peak of a GB300 at its maximum SM clock: 152 SMs x 128 lanes x
+# 2 flops x 2070 MHz.
+SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+# DRAM traffic of the lattice kernel from one ncu capture of this workload;
+# valid only while the kernel sources hash to KERNEL_SHA (else reported null).
+NCU_TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1811_11722_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def workload(rank: int, n=None):
+    from paper_1811_11722_gb300 import inputs as I
+    p = I.config2() if n is None else I.config2(n=n)
+    if rank > 0:  # weak scaling: every rank integrates its own independent shifts
+        p = I.with_shifts(p, p.m, I.SEED_BASE + 0x100 + rank)
+    return p
+
+
+def config_dict(world: int, n: int = 16777213):
+    return {"workload": WORKLOAD if n == 16777213 else WORKLOAD.replace("16777213", str(n)) + " (profiling size)",
+            "d": 6, "n": n, "m": 32, "transform": "baker",
+            "integrand": "U^-2 F^-1 (T_U=6 deg-1, T_F=12 deg-2, + constants)", "precision": "FP32 eval, FP64 sums",
+            "evals_per_step_per_gpu": n * 32, "parallelism": f"replicas x{world} (independent shifts)",
+            "l2": "flushed between timed steps (256 MiB write); inputs are KB-sized descriptors in kernel "
+                  "parameters, no HBM reads on the hot path"}
+
+
+def cpu_baseline(p, g, budget_s: float = 12.0):
+    """The oracle as it stands on all host cores over a leading run of lattice points."""
+    import oracle
+    threads = host_cores()
+    S = 1 << 16
+    t = time.perf_counter()
+    oracle.rule_sums(p, g, 0, S, nthreads=threads)
+    dt = time.perf_counter() - t
+    S2 = int(min(p.n, max(S, S * budget_s / max(dt, 1e-3))))
+    t = time.perf_counter()
+    oracle.rule_sums(p, g, 0, S2, nthreads=threads)
+    dt = time.perf_counter() - t
+    return {"value": S2 * p.m / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"j in [0, {S2}) of n={p.n}, all m={p.m} shifts ({S2 * p.m} evals, FP64, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle (plain FP64 definition) on the same workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    from oracle.cbc import cbc_fast
+    from paper_1811_11722_gb300 import inputs as I
+    p = workload(0)
+    lat = os.path.join(ROOT, "tests", "golden", "lattices.json")
+    table = json.load(open(lat))["g"] if os.path.exists(lat) else {}
+    g = table.get(str(p.n), None)
+    g = (g[: p.d] if g else list(cbc_fast(p.d, p.n, p.gamma)))
+    threads = host_cores()
+    S = 1 << 20
+    for _ in range(args.warmup):
+        oracle.rule_sums(p, g, 0, 1 << 14, nthreads=threads)
+    times = []
+    for s in range(args.steps):
+        j0 = (s * S) % (p.n - S)
+        t = time.perf_counter()
+        oracle.rule_sums(p, g, j0, j0 + S, nthreads=threads)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    val = S * p.m * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(world),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step: {S} consecutive lattice points x {p.m} shifts of the workload"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None,
+                    help="smaller prime lattice size, for profiler captures only (changes the workload)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1811_11722_gb300 import build, qmc
+    build.build_library()
+    p = workload(rank, args.n)
+    g = qmc.qmc_make_lattice(p.d, p.n, p.gamma)          # host CBC, untimed
+    f = qmc.integrand_from_problem(p, "fp32")
+    t = qmc.transform(p.transform, p.alpha)
+    plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
+    launches_per_step = plan.launches()
+
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    out = torch.zeros(qmc.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    per = torch.zeros(2 * p.m, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        plan.execute(out=out, per_shift=per, stream=sh)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(K):
+            flush.zero_()                                    # L2 flush between steps, outside the events
+            e_step0, e_rule0, e_rule1, e_step1 = ev[s]
+            plan.record_events(e_rule0.cuda_event, e_rule1.cuda_event)
+            e_step0.record(stream)
+            plan.execute(out=out, per_shift=per, stream=sh)
+            e_step1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    plan.record_events(None, None)
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    rule_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        tt = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+    evals = p.n * p.m
+    value = world * evals * K / total_s
+
+    res = qmc.qmc_result.from_buffer_copy(out.cpu().numpy().tobytes()).as_dict()
+    assert res["status"] == 0 and np.isfinite(res["mean"][0]), res
+
+    # end to end: public C-ABI call with host inputs and a host result
+    e2e_times = []
+    for s in range(args.warmup + K):
+        t0 = time.perf_counter()
+        r, _ = qmc.qmc_integrate(p.d, p.n, p.m, g, p.shifts, t, f, stream=sh)
+        if s >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_times)
+    if dist:
+        tt = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    h2d = int(g.nbytes + p.shifts.nbytes + p.U.coef.nbytes + p.U.expo.nbytes + p.F.coef.nbytes + p.F.expo.nbytes)
+
+    rule_avg_s = statistics.mean(rule_ms) / 1e3
+    achieved = FLOPS_PER_EVAL * evals / rule_avg_s / 1e12
+    clocks = clk.summary()
+    sha = kernel_sha()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel_sha"] == sha else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": config_dict(world, p.n),
+        "e2e": {"value": world * evals * K / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": qmc.RESULT_BYTES},
+        "gpu_launches": launches_per_step * K,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "sector_kernel<float, D=6, MC=32, baker, U deg 1, F deg 2>",
+                     "kernel_ms": 1e3 * rule_avg_s, "flops_per_eval": FLOPS_PER_EVAL,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (nominal max clock)",
+                     "frac_at_observed_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)
+                                                if clocks.get("sm_mhz") else None)},
+        "clocks": clocks,
+        "result": {"mean": res["mean"][0], "err": res["err"][0]},
+        "kernel_sha": sha,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, g)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * qmc.h - C ABI of the GB300 (sm_103a) randomly shifted rank-1 lattice rule.
+ *
+ * The library evaluates, on one GPU,
+ *   Qbar = (1/m) sum_{k=1}^{m} Q^(k),  Q^(k) = (1/n) sum_{j=1}^{n} f({(j-1) g / n + Delta_k})
+ * (Eq. 2 of "Numerical evaluation of multi-loop integrals", Sec. 2) and the
+ * error estimate
+ *   sigma^2 = 1/(m(m-1)) sum_k (Q^(k) - Qbar)^2
+ * (Eq. 3), for integrands f of the sector-decomposed class of Eq. (7) after a
+ * periodizing transform (Korobov, Eq. 5, or baker, Eq. 6).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a qmc_status; QMC_OK is 0.  No exception or
+ *     longjmp crosses the ABI.
+ *   - Input arrays (g, shifts, polynomial tables, weights, c, b, h) are HOST
+ *     memory owned by the caller; the library reads them during the call and
+ *     keeps no pointer to them afterwards.
+ *   - Result arrays (qmc_result, per_shift) may be host or device memory; the
+ *     library tells them apart with cudaPointerGetAttributes.  When a result
+ *     lives in host memory the call synchronises `stream`; when every result
+ *     lives in device memory the call is asynchronous on `stream`.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  All device work of a call is ordered on it.
+ *   - Complex results are reported as two real estimates (real part and
+ *     imaginary part), each by Eq. (3); index [0] is the real part, [1] the
+ *     imaginary part.  Real integrands report 0 for [1].
+ */
+#ifndef QMC_H
+#define QMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QMC_DMAX 16 /* largest supported dimension d */
+
+typedef enum {
+  QMC_OK = 0,
+  QMC_EINVAL = -1,       /* an argument is out of range or inconsistent */
+  QMC_ENOMEM = -2,       /* a device or host allocation failed */
+  QMC_ECUDA = -3,        /* a CUDA runtime call failed (no GPU, launch error, ...) */
+  QMC_ENONFINITE = -4,   /* some f values were NaN/Inf; they were left out and counted */
+  QMC_ETIMEOUT = -5,     /* a bounded device wait ran out */
+  QMC_EDEFORM = -6,      /* deformed F had Im F > 0 at some points (counted) */
+  QMC_EUNSUPPORTED = -7  /* a valid request this build has no kernel for */
+} qmc_status;
+
+/* Periodizing transform applied to every coordinate before f.
+ * KOROBOV (Eq. 5): z = int_0^x w(u) du with w(u) = u^a (1-u)^a / B(a+1, a+1),
+ *   alpha = a in [1, 6]; the rule integrates f(z(x)) prod_i w(x_i).
+ * BAKER (Eq. 6): z = 1 - |2x - 1|, weight 1.
+ * NONE: z = x. */
+enum { QMC_TRANSFORM_NONE = 0, QMC_TRANSFORM_KOROBOV = 1, QMC_TRANSFORM_BAKER = 2 };
+typedef struct {
+  int32_t kind;
+  int32_t alpha;
+} qmc_transform;
+
+/* Polynomial in d variables as a term table:
+ *   P(z) = sum_{t < nterms} coef[t] * prod_{i < d} z_i ^ expo[t * d + i].
+ * Total degree at most 3.  Repeated monomials are summed. */
+typedef struct {
+  int32_t nterms;
+  const double* coef; /* [nterms] */
+  const uint8_t* expo; /* [nterms * d], row-major */
+} qmc_poly;
+
+/* Integrand families.
+ * CONST          f = 1                                 (Sec. 2 / Fig. 3 study)
+ * SEPARABLE_EXP  f = prod_i (1 + c_i z_i) exp(b_i z_i)  (closed-form test integrand)
+ * SECTOR         f = U(z)^aU F(z)^aF                   (Eq. 7 at eps = 0)
+ * SECTOR_DEFORMED f = U(w)^aU F(w)^aF det(dw/dz), with the contour
+ *                w_k = z_k - i lambda z_k (1 - z_k) dF/dz_k (Sec. 3 Feynman
+ *                prescription; vanishes at z_k in {0, 1}); F of degree <= 2
+ * TRIG           f = cos(2 pi h . z)                   (dual-lattice check) */
+enum {
+  QMC_F_CONST = 0,
+  QMC_F_SEPARABLE_EXP = 1,
+  QMC_F_SECTOR = 2,
+  QMC_F_SECTOR_DEFORMED = 3,
+  QMC_F_TRIG = 4
+};
+
+/* Arithmetic of the per-point evaluation.  Per-shift sums, Q^(k), Qbar and
+ * sigma^2 are FP64 on the device in both modes.
+ * FP64: coordinates, transform and f in double.
+ * FP32EVAL: coordinates from 32-bit fixed point, transform and f in float,
+ *   compensated float run sums promoted to double per thread. */
+enum { QMC_FP64 = 0, QMC_FP32EVAL = 1 };
+
+typedef struct {
+  int32_t kind;      /* QMC_F_* */
+  int32_t d;         /* dimension, 1 <= d <= QMC_DMAX; must equal the rule's d */
+  int32_t precision; /* QMC_FP64 or QMC_FP32EVAL */
+  qmc_poly U, F;     /* SECTOR / SECTOR_DEFORMED */
+  int32_t aU, aF;    /* integer powers in [-8, 8] */
+  double lambda;     /* SECTOR_DEFORMED deformation parameter */
+  const double* c;   /* SEPARABLE_EXP: [d] */
+  const double* b;   /* SEPARABLE_EXP: [d] */
+  const int32_t* h;  /* TRIG: [d] */
+} qmc_integrand;
+
+typedef struct {
+  double mean[2]; /* Qbar (Eq. 2), real and imaginary part */
+  double var[2];  /* sigma^2 (Eq. 3) */
+  double err[2];  /* sqrt(var) */
+  uint64_t nonfinite;         /* points whose f was NaN/Inf (left out of the sums) */
+  uint64_t deform_violations; /* SECTOR_DEFORMED points with Im F(w) > 0 */
+  int32_t status;             /* qmc_status of this problem */
+  int32_t reserved;
+} qmc_result;
+
+/* Generating vector by component-by-component search (the paper takes g as
+ * given, Eq. 2; the construction follows the review it cites for QMC):
+ * minimises, one component at a time with g_1 = 1, the shift-averaged
+ * worst-case error in the unanchored weighted Sobolev space with product
+ * weights,
+ *   e^2(g) = -1 + (1/n) sum_{k=0}^{n-1} prod_i (1 + gamma_i B2({k g_i / n})),
+ *   B2(t) = t^2 - t + 1/6,
+ * over candidates 1 <= z <= (n-1)/2 (ties to the smallest z).
+ *   d      1 <= d <= QMC_DMAX
+ *   n      prime, 5 <= n < 2^31
+ *   gamma  [d] positive weights (host)
+ *   g_out  [d] result (host)
+ * Host precompute: runs on the host cores (FFT-based cyclic convolution,
+ * O(d n log n)); it touches no GPU.  Returns QMC_EINVAL for a composite or
+ * out-of-range n. */
+int qmc_make_lattice(int32_t d, uint64_t n, const double* gamma, uint64_t* g_out);
+
+/* The shifted rank-1 lattice rule, Eq. (2) and (3), on the GPU.
+ *   d, n, m     dimension (1..QMC_DMAX), points (2 <= n < 2^31), shifts (2..1024)
+ *   g           [d] generating vector, 1 <= g_i < n (host)
+ *   shifts      [m * d] row-major shift table Delta_k in [0, 1) (host)
+ *   t           transform
+ *   f           integrand; f->d must equal d
+ *   out         result (host or device)
+ *   per_shift   optional [m * 2] array receiving Q^(k) (re, im), host or device
+ *   stream      cudaStream_t
+ * Returns QMC_EINVAL for bad arguments (m < 2, g_i outside [1, n), ...),
+ * QMC_ECUDA if no GPU is usable, QMC_ENONFINITE / QMC_EDEFORM as warnings
+ * (the estimate is still written) when `out` is host memory; with a device
+ * `out` those two are reported in out->status only. */
+int qmc_integrate(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                  qmc_transform t, const qmc_integrand* f, qmc_result* out, double* per_shift,
+                  void* stream);
+
+/* A planned rule: the same arguments as qmc_integrate, validated and packed
+ * once into launch descriptors and a device workspace owned by the plan, so
+ * that qmc_plan_execute only launches kernels (no host staging, no
+ * allocation). */
+typedef struct qmc_plan_s* qmc_plan;
+int qmc_plan_create(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                    qmc_transform t, const qmc_integrand* f, qmc_plan* plan_out);
+/* out / per_shift as for qmc_integrate.  Device memory keeps execute fully
+ * asynchronous. */
+int qmc_plan_execute(qmc_plan plan, qmc_result* out, double* per_shift, void* stream);
+int qmc_plan_destroy(qmc_plan plan);
+/* Number of kernel launches one qmc_plan_execute issues. */
+int qmc_plan_launches(qmc_plan plan, int32_t* launches_out);
+/* Timing hook: when set (non-NULL cudaEvent_t handles passed as void*), every
+ * later qmc_plan_execute records `before_rule` on its stream just before the
+ * rule kernels and `after_rule` just after them (before the final pass), so a
+ * caller can time the lattice kernels alone.  NULL, NULL clears the hook. */
+int qmc_plan_record_events(qmc_plan plan, void* before_rule, void* after_rule);
+
+/* One problem of a batch: the arguments of qmc_integrate. */
+typedef struct {
+  int32_t d;
+  int32_t m;
+  uint64_t n;
+  const uint64_t* g;
+  const double* shifts;
+  qmc_transform t;
+  const qmc_integrand* f;
+} qmc_problem;
+
+/* Many independent rules in one persistent launch (sectors of uneven d, n).
+ *   count      number of problems (1..65536)
+ *   problems   [count] descriptors (host)
+ *   out        [count] results (host or device); out[i].status per problem
+ *   per_shift  optional; problem i writes 2*m_i doubles at offset 2*sum_{p<i} m_p
+ * Supported: SECTOR integrands with U of degree <= 1, F of degree <= 2,
+ * d <= 8, FP32EVAL, all problems with the same transform.  Other batches
+ * return QMC_EUNSUPPORTED. */
+int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* out,
+                        double* per_shift, void* stream);
+
+/* Planned batch: packs once, captures the persistent launch and the final
+ * reduction into a CUDA graph on first execute, replays it afterwards. */
+typedef struct qmc_batch_plan_s* qmc_batch_plan;
+int qmc_batch_plan_create(int32_t count, const qmc_problem* problems, qmc_batch_plan* plan_out);
+int qmc_batch_plan_execute(qmc_batch_plan plan, qmc_result* out, double* per_shift, void* stream);
+int qmc_batch_plan_destroy(qmc_batch_plan plan);
+
+/* Single terms of Eq. (2), evaluated by the same device code the rule uses:
+ * for each sample s, the weighted value f(z(x)) prod_i w(x_i) at point
+ * j[s] (0-based, the paper's j-1) and shift k[s].
+ *   values  [count * 2] (re, im), host
+ *   idx     optional [count * d] lattice indices (j g_i) mod n, host
+ *   coord   optional [count * d] the coordinate x the kernel used, as double, host
+ * Synchronises `stream`. */
+int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                      qmc_transform t, const qmc_integrand* f, int32_t count, const uint64_t* j,
+                      const int32_t* k, double* values, uint64_t* idx, double* coord, void* stream);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* qmc_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t qmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMC_H */

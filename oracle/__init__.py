@@ -78,6 +78,8 @@ def lib():
             L.orc_cbc_error.argtypes = [i32, u64, vp, vp]
             L.orc_cbc_error.restype = dbl
             L.orc_cbc_plain.argtypes = [i32, u64, vp, vp]
+            L.orc_cbc_candidate.argtypes = [u64, vp, u64]
+            L.orc_cbc_candidate.restype = dbl
             _lib = L
     return _lib
 
@@ -220,6 +222,12 @@ def cbc_error(d: int, n: int, g, gamma) -> float:
     g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
     gamma = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
     return float(lib().orc_cbc_error(d, n, _ptr(g), _ptr(gamma)))
+
+
+def cbc_candidate(n: int, p, z: int) -> float:
+    """T(z) = sum_k p[k] B2({k z / n}) (Neumaier, k ascending)."""
+    p = np.ascontiguousarray(np.asarray(p, dtype=np.float64))
+    return float(lib().orc_cbc_candidate(n, _ptr(p), z))
 
 
 def cbc_plain(d: int, n: int, gamma) -> np.ndarray:

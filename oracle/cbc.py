@@ -11,8 +11,11 @@ For prime n the candidate-by-point matrix B2({k z / n}) becomes circulant once
 z and k are ordered by powers of a primitive root, so all candidates of one
 dimension come from one cyclic convolution (Nuyens and Cools, Math. Comp. 2006).
 numpy's FFT serves as that convolution; nothing else is reordered.
-Ties (which a floating-point convolution only resolves to ~1e-13) go to the
-smallest candidate z within a relative window of 1e-12 of the minimum.
+The FFT's rounding noise (~1e-16 n) can exceed the gaps between the best
+candidates at large n, so the RERANK candidates with the smallest convolution
+values are re-evaluated exactly, T(z) = sum_k p[k] B2({k z / n}) by the
+oracle's compensated sum (the plain search's own criterion), and the smallest
+T wins, ties to the smallest z.
 """
 from __future__ import annotations
 
@@ -66,6 +69,9 @@ def _b2(t):
     return t * t - t + 1.0 / 6.0
 
 
+RERANK = 32
+
+
 def cbc_fast(d: int, n: int, gamma) -> np.ndarray:
     """CBC generating vector for prime n < 2^31 (g_1 = 1)."""
     gamma = np.asarray(gamma, dtype=np.float64)
@@ -94,10 +100,15 @@ def cbc_fast(d: int, n: int, gamma) -> np.ndarray:
         lin = np.fft.irfft(c_hat * np.fft.rfft(qf, M), M)
         T = lin[:h].copy()
         T[: M - h if M - h < h else h] += lin[h:2 * h][: min(h, M - h)]
-        best = T.min()
-        window = np.abs(best) * 1e-12 + 1e-300
-        ok = np.nonzero(T <= best + window)[0]
-        z = int(cand[ok].min())
+        K = min(RERANK, h)
+        top = np.argpartition(T, K - 1)[:K]
+        from . import cbc_candidate
+        pc = np.ascontiguousarray(p)
+        best_t, z = None, None
+        for zc in sorted(set(int(v) for v in cand[top])):
+            tz = cbc_candidate(n, pc, zc)
+            if best_t is None or tz < best_t:
+                best_t, z = tz, zc
         g.append(z)
         p = p * (1.0 + gamma[s] * _b2(((k * z) % n) / n))
     return np.array(g, dtype=np.uint64)

@@ -27,7 +27,8 @@
  *   e^2(g) = -1 + (1/n) sum_{k=0}^{n-1} prod_i (1 + gamma_i B2({k g_i / n})),
  *   B2(t) = t^2 - t + 1/6,
  * plain O(n^2) per dimension, g_1 = 1, candidates 1 <= z <= (n-1)/2, ties to
- * the smallest z.
+ * the smallest z.  The candidate criterion T(z) = sum_k p[k] B2({k z/n}) is
+ * also what the FFT-based search (cbc.py) re-ranks its best candidates by.
  */
 #include <complex.h>
 #include <math.h>
@@ -500,23 +501,39 @@ int orc_gauss_legendre(const orc_problem* p, int q, const double* nodes, const d
 
 static double bern2(double t) { return t * t - t + 1.0 / 6.0; }
 
-/* e^2(g) = -1 + (1/n) sum_{k=0}^{n-1} prod_i (1 + gamma_i B2({k g_i / n})) */
+/* e^2(g) = -1 + (1/n) sum_{k=0}^{n-1} prod_i (1 + gamma_i B2({k g_i / n})),
+ * summed as (1/n) sum_k [prod_i (1 + a_i) - 1] with the bracket built up as
+ * t <- t + a_i (1 + t), which avoids cancelling against the -1 when e^2 is
+ * far below double resolution of 1. */
 double orc_cbc_error(int d, uint64_t n, const uint64_t* g, const double* gamma) {
   neum_t s = {0, 0};
   for (uint64_t k = 0; k < n; ++k) {
-    double p = 1.0;
+    double t = 0.0;
     for (int i = 0; i < d; ++i) {
       uint64_t r = orc_index(k, g[i], n);
-      p *= 1.0 + gamma[i] * bern2((double)r / (double)n);
+      double a = gamma[i] * bern2((double)r / (double)n);
+      t = t + a * (1.0 + t);
     }
-    neum_add(&s, p);
+    neum_add(&s, t);
   }
-  return neum_get(&s) / (double)n - 1.0;
+  return neum_get(&s) / (double)n;
+}
+
+/* The part of e^2 that depends on the next component z, given the running
+ * products p[k] = prod_{i<s} (1 + gamma_i B2({k g_i / n})):
+ *   T(z) = sum_{k=0}^{n-1} p[k] B2({k z / n})   (Neumaier, k ascending).
+ * e^2 with z appended = -1 + (1/n) sum_k p[k] + (gamma_s / n) T(z), so the
+ * search minimises T. */
+double orc_cbc_candidate(uint64_t n, const double* p, uint64_t z) {
+  neum_t s = {0, 0};
+  for (uint64_t k = 0; k < n; ++k) neum_add(&s, p[k] * bern2((double)orc_index(k, z, n) / (double)n));
+  return neum_get(&s);
 }
 
 /* Plain component-by-component construction: g_1 = 1, then for each next
- * dimension the candidate z in [1, (n-1)/2] minimising e^2 given the earlier
- * components (strict <, ascending z: ties go to the smallest z). */
+ * dimension the candidate z in [1, (n-1)/2] minimising T(z) (equivalently
+ * e^2) given the earlier components (strict <, ascending z: ties go to the
+ * smallest z). */
 int orc_cbc_plain(int d, uint64_t n, const double* gamma, uint64_t* g) {
   if (d < 1 || n < 2) return -1;
   double* prodk = (double*)malloc(sizeof(double) * n);
@@ -528,12 +545,9 @@ int orc_cbc_plain(int d, uint64_t n, const double* gamma, uint64_t* g) {
     uint64_t zmax = (n - 1) / 2;
     if (zmax < 1) zmax = 1;
     for (uint64_t z = 1; z <= zmax; ++z) {
-      neum_t acc = {0, 0};
-      for (uint64_t k = 0; k < n; ++k)
-        neum_add(&acc, prodk[k] * (1.0 + gamma[s] * bern2((double)orc_index(k, z, n) / (double)n)));
-      double e2 = neum_get(&acc) / (double)n - 1.0;
-      if (e2 < best) {
-        best = e2;
+      double t = orc_cbc_candidate(n, prodk, z);
+      if (t < best) {
+        best = t;
         best_z = z;
       }
     }

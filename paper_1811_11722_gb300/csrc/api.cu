@@ -1,0 +1,708 @@
+// C ABI of the lattice-rule library: argument validation, packing of the
+// problem into launch descriptors, plans, kernel dispatch and the final pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernel_table.h"
+#include "plan.h"
+
+namespace qmc {
+
+// ------------------------------------------------------------------ errors --
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(QMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define QMC_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+bool is_device_pointer(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------- validation --
+
+static bool is_prime_u64(uint64_t n) {
+  if (n < 2) return false;
+  for (uint64_t p : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 17ull, 19ull, 23ull, 29ull, 31ull, 37ull}) {
+    if (n % p == 0) return n == p;
+  }
+  uint64_t d = n - 1;
+  int s = 0;
+  while ((d & 1) == 0) {
+    d >>= 1;
+    ++s;
+  }
+  auto mulmod = [&](uint64_t a, uint64_t b) { return (uint64_t)((unsigned __int128)a * b % n); };
+  auto powmod = [&](uint64_t a, uint64_t e) {
+    uint64_t r = 1;
+    while (e) {
+      if (e & 1) r = mulmod(r, a);
+      a = mulmod(a, a);
+      e >>= 1;
+    }
+    return r;
+  };
+  for (uint64_t a : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 17ull, 19ull, 23ull, 29ull, 31ull, 37ull}) {
+    uint64_t x = powmod(a, d);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int r = 1; r < s; ++r) {
+      x = mulmod(x, x);
+      if (x == n - 1) {
+        comp = false;
+        break;
+      }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+bool prime_check(uint64_t n) { return is_prime_u64(n); }
+
+static int validate_poly(const qmc_poly& p, int d, const char* name) {
+  if (p.nterms < 1 || p.nterms > kTermsMax)
+    return fail(QMC_EINVAL, "%s: nterms=%d outside [1, %d]", name, p.nterms, kTermsMax);
+  if (!p.coef || !p.expo) return fail(QMC_EINVAL, "%s: null coefficient or exponent table", name);
+  for (int t = 0; t < p.nterms; ++t) {
+    if (!std::isfinite(p.coef[t])) return fail(QMC_EINVAL, "%s: coefficient %d not finite", name, t);
+    int deg = 0;
+    for (int i = 0; i < d; ++i) deg += p.expo[(size_t)t * d + i];
+    if (deg > 3) return fail(QMC_EINVAL, "%s: term %d has degree %d > 3", name, t, deg);
+  }
+  return QMC_OK;
+}
+
+int validate_problem(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                     const qmc_transform& t, const qmc_integrand* f) {
+  if (d < 1 || d > QMC_DMAX) return fail(QMC_EINVAL, "d=%d outside [1, %d]", d, QMC_DMAX);
+  if (n < 2 || n >= (1ull << 31)) return fail(QMC_EINVAL, "n=%llu outside [2, 2^31)", (unsigned long long)n);
+  if (m < 2 || m > 1024) return fail(QMC_EINVAL, "m=%d outside [2, 1024] (Eq. 3 needs m >= 2)", m);
+  if (!g || !shifts || !f) return fail(QMC_EINVAL, "null g, shifts or integrand");
+  for (int i = 0; i < d; ++i)
+    if (g[i] < 1 || g[i] >= n) return fail(QMC_EINVAL, "g[%d]=%llu outside [1, n)", i, (unsigned long long)g[i]);
+  for (int k = 0; k < m * d; ++k)
+    if (!(shifts[k] >= 0.0 && shifts[k] < 1.0)) return fail(QMC_EINVAL, "shift entry %d outside [0, 1)", k);
+  if (t.kind != QMC_TRANSFORM_NONE && t.kind != QMC_TRANSFORM_KOROBOV && t.kind != QMC_TRANSFORM_BAKER)
+    return fail(QMC_EINVAL, "unknown transform %d", t.kind);
+  if (t.kind == QMC_TRANSFORM_KOROBOV && (t.alpha < 1 || t.alpha > 6))
+    return fail(QMC_EINVAL, "Korobov weight %d outside [1, 6]", t.alpha);
+  if (f->d != d) return fail(QMC_EINVAL, "integrand d=%d differs from rule d=%d", f->d, d);
+  if (f->precision != QMC_FP64 && f->precision != QMC_FP32EVAL)
+    return fail(QMC_EINVAL, "unknown precision %d", f->precision);
+  switch (f->kind) {
+    case QMC_F_CONST:
+      break;
+    case QMC_F_SEPARABLE_EXP:
+      if (!f->c || !f->b) return fail(QMC_EINVAL, "separable integrand needs c and b");
+      for (int i = 0; i < d; ++i)
+        if (!std::isfinite(f->c[i]) || !std::isfinite(f->b[i]))
+          return fail(QMC_EINVAL, "separable coefficient %d not finite", i);
+      break;
+    case QMC_F_TRIG:
+      if (!f->h) return fail(QMC_EINVAL, "trig integrand needs h");
+      break;
+    case QMC_F_SECTOR:
+    case QMC_F_SECTOR_DEFORMED: {
+      int rc = validate_poly(f->U, d, "U");
+      if (rc) return rc;
+      rc = validate_poly(f->F, d, "F");
+      if (rc) return rc;
+      if (f->aU < -8 || f->aU > 8 || f->aF < -8 || f->aF > 8)
+        return fail(QMC_EINVAL, "powers aU=%d aF=%d outside [-8, 8]", f->aU, f->aF);
+      if (f->kind == QMC_F_SECTOR_DEFORMED) {
+        if (!std::isfinite(f->lambda) || f->lambda < 0.0)
+          return fail(QMC_EINVAL, "deformation lambda must be finite and >= 0");
+        for (int t2 = 0; t2 < f->F.nterms; ++t2) {
+          int deg = 0;
+          for (int i = 0; i < d; ++i) deg += f->F.expo[(size_t)t2 * d + i];
+          if (deg > 2) return fail(QMC_EINVAL, "deformed F must have degree <= 2");
+        }
+        for (int t2 = 0; t2 < f->U.nterms; ++t2) {
+          int deg = 0;
+          for (int i = 0; i < d; ++i) deg += f->U.expo[(size_t)t2 * d + i];
+          if (deg > 2) return fail(QMC_EINVAL, "deformed U must have degree <= 2");
+        }
+      }
+      break;
+    }
+    default:
+      return fail(QMC_EINVAL, "unknown integrand kind %d", f->kind);
+  }
+  return QMC_OK;
+}
+
+// ---------------------------------------------------------------- packing --
+
+int poly_degree(const qmc_poly& p, int d) {
+  int deg = 0;
+  for (int t = 0; t < p.nterms; ++t) {
+    int s = 0;
+    for (int i = 0; i < d; ++i) s += p.expo[(size_t)t * d + i];
+    deg = std::max(deg, s);
+  }
+  return deg;
+}
+
+// Coefficient of every monomial (sorted variable list, repeated monomials summed).
+static std::map<std::vector<int>, double> monomials(const qmc_poly& p, int d) {
+  std::map<std::vector<int>, double> out;
+  for (int t = 0; t < p.nterms; ++t) {
+    std::vector<int> vars;
+    for (int i = 0; i < d; ++i)
+      for (int e = 0; e < p.expo[(size_t)t * d + i]; ++e) vars.push_back(i);
+    out[vars] += p.coef[t];
+  }
+  return out;
+}
+
+// Nested-Horner slots of a degree-K polynomial in D variables (order matches
+// poly_dense): c0; for i: l_i, [K>=2: for j>=i: q_ij, [K=3: c_ijk for k>=j]].
+std::vector<double> pack_dense(const qmc_poly& p, int D, int K) {
+  auto mono = monomials(p, D);
+  auto get = [&](std::vector<int> v) {
+    auto it = mono.find(v);
+    return it == mono.end() ? 0.0 : it->second;
+  };
+  std::vector<double> c;
+  c.push_back(get({}));
+  if (K == 1) {
+    for (int i = 0; i < D; ++i) c.push_back(get({i}));
+  } else if (K == 2) {
+    for (int i = 0; i < D; ++i) {
+      c.push_back(get({i}));
+      for (int j = i; j < D; ++j) c.push_back(get({i, j}));
+    }
+  } else if (K == 3) {
+    for (int i = 0; i < D; ++i) {
+      c.push_back(get({i}));
+      for (int j = i; j < D; ++j) {
+        c.push_back(get({i, j}));
+        for (int k = j; k < D; ++k) c.push_back(get({i, j, k}));
+      }
+    }
+  }
+  return c;
+}
+
+// 2^128 / n = rhi 2^64 + rlo + frac
+Recip reciprocal(uint64_t n) {
+  unsigned __int128 one64 = (unsigned __int128)1 << 64;
+  Recip r;
+  r.rhi = (uint64_t)(one64 / n);
+  uint64_t rem = (uint64_t)(one64 % n);
+  r.rlo = (uint64_t)(((unsigned __int128)rem << 64) / n);
+  return r;
+}
+
+// Korobov z(s) = C sum_k binom(a,k) (-1)^k s^(a+k+1)/(a+k+1), C = (2a+1)!/(a!)^2.
+void korobov_coefs(int alpha, double* kor /*8*/) {
+  double C = 1.0;
+  for (int i = 1; i <= 2 * alpha + 1; ++i) C *= (double)i;
+  double f = 1.0;
+  for (int i = 1; i <= alpha; ++i) f *= (double)i;
+  C /= f * f;
+  for (int k = 0; k < 8; ++k) kor[k] = 0.0;
+  for (int k = 0; k <= alpha; ++k) {
+    double b = 1.0;
+    for (int i = 1; i <= k; ++i) b = b * (double)(alpha - k + i) / (double)i;
+    kor[k] = ((k & 1) ? -1.0 : 1.0) * C * b / (double)(alpha + k + 1);
+  }
+  kor[7] = C;
+}
+
+uint64_t shift_fixed64(double delta) {
+  // delta in [0, 1): delta * 2^64, floor
+  long double v = std::ldexp((long double)delta, 64);
+  if (v >= 18446744073709551615.0L) return ~0ull;
+  return (uint64_t)v;
+}
+
+static bool poly_positive(const qmc_poly& p, int d) {
+  bool has_const = false;
+  for (int t = 0; t < p.nterms; ++t) {
+    int deg = 0;
+    for (int i = 0; i < d; ++i) deg += p.expo[(size_t)t * d + i];
+    if (p.coef[t] < 0.0) return false;
+    if (deg == 0 && p.coef[t] > 0.0) has_const = true;
+  }
+  return has_const;
+}
+
+template <typename R>
+void fill_common(RuleParams<R>& P, int32_t d, uint64_t n, const uint64_t* g, const qmc_transform& t,
+                 const qmc_integrand* f) {
+  std::memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.d = d;
+  P.alpha = t.kind == QMC_TRANSFORM_KOROBOV ? t.alpha : 0;
+  P.tr = t.kind == QMC_TRANSFORM_KOROBOV ? TR_KOROBOV : (t.kind == QMC_TRANSFORM_BAKER ? TR_BAKER : TR_NONE);
+  P.aU = f->aU;
+  P.aF = f->aF;
+  P.lam = (R)f->lambda;
+  P.value_scale = 1.0;
+  P.rc = reciprocal(n);
+  for (int i = 0; i < d; ++i) {
+    P.g[i] = (uint32_t)g[i];
+    P.gstep[i] = (uint32_t)(((uint64_t)kThreads * g[i]) % n);
+  }
+  double kor[8];
+  korobov_coefs(P.alpha > 0 ? P.alpha : 1, kor);
+  for (int k = 0; k < 8; ++k) P.kor[k] = (R)kor[k];
+  if (f->kind == QMC_F_SEPARABLE_EXP) {
+    for (int i = 0; i < d; ++i) {
+      P.sep_c[i] = (R)f->c[i];
+      P.sep_b[i] = (R)f->b[i];
+    }
+  } else if (f->kind == QMC_F_TRIG) {
+    for (int i = 0; i < d; ++i) P.sep_c[i] = (R)f->h[i];
+  }
+  P.check_finite = 1;
+  if (f->kind == QMC_F_CONST) P.check_finite = 0;
+  if (f->kind == QMC_F_SECTOR && f->aU <= 0 && f->aF <= 0 && poly_positive(f->U, d) && poly_positive(f->F, d))
+    P.check_finite = 0;
+}
+
+// ------------------------------------------------------------------- plan --
+
+static int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  return sms;
+}
+
+// Grid: one resident wave (SMs x CTAs per SM), each CTA one tile of
+// kThreads * L points, L from the point count.
+int choose_grid(const void* func, size_t smem, uint64_t n, int& nblk, int& L, uint64_t& tiles,
+                int occupancy_override) {
+  int sms = device_sm_count();
+  if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
+  int occ = 0;
+  QMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, kThreads, smem));
+  if (occ < 1) occ = 1;
+  if (occupancy_override > 0) occ = std::min(occ, occupancy_override);
+  uint64_t want = (uint64_t)sms * occ;
+  uint64_t per = (n + want * kThreads - 1) / (want * kThreads);
+  const uint64_t Lmax = 512;
+  L = (int)std::max<uint64_t>(1, std::min(per, Lmax));
+  tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
+  nblk = (int)std::min<uint64_t>(want, tiles);
+  return QMC_OK;
+}
+
+static int pick_mc(int m, bool fp32) {
+  if (!fp32) return 16;
+  int mm = std::min(m, kMcMax);
+  if (mm <= 8) return 8;
+  if (mm <= 16) return 16;
+  return 32;
+}
+
+template <typename R>
+static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                           const qmc_transform& t, const qmc_integrand* f, const TuneChoice& tune) {
+  const bool fp32 = sizeof(R) == 4;
+  RuleParams<R> base;
+  fill_common(base, d, n, g, t, f);
+  const void* func = nullptr;
+  size_t pbytes = sizeof(RuleParams<R>);
+  std::vector<uint8_t> blob;
+  int mc = tune.mc > 0 ? tune.mc : pick_mc(m, fp32);
+  bool general = false;
+
+  if (f->kind == QMC_F_SECTOR) {
+    int ku = poly_degree(f->U, d), kf = poly_degree(f->F, d);
+    int KU = -1, KF = -1;
+    if (ku <= 1 && kf <= 2) {
+      KU = 1;
+      KF = 2;
+    } else if (ku <= 2 && kf <= 3 && fp32) {
+      KU = 2;
+      KF = 3;
+      mc = 16;
+    }
+    if (KU > 0 && d <= kDFast && !tune.force_general) {
+      switch (d) {
+#define QMC_D_CASE(DD) \
+  case DD:             \
+    func = sector_ptr<R, DD>(mc, base.tr, base.alpha, KU, KF); \
+    break;
+        QMC_D_CASE(1) QMC_D_CASE(2) QMC_D_CASE(3) QMC_D_CASE(4) QMC_D_CASE(5) QMC_D_CASE(6)
+        QMC_D_CASE(7) QMC_D_CASE(8)
+#undef QMC_D_CASE
+        default: break;
+      }
+    }
+    if (func) {
+      auto cu = pack_dense(f->U, d, KU);
+      auto cf = pack_dense(f->F, d, KF);
+      for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
+      for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
+      if (base.tr == TR_KOROBOV) base.value_scale = std::pow((double)base.kor[7], (double)d);
+    } else {
+      general = true;
+    }
+  } else if (f->kind == QMC_F_SECTOR_DEFORMED) {
+    return fail(QMC_EUNSUPPORTED, "deformed sector integrands are served by the complex kernels");
+  } else {
+    int fk = f->kind == QMC_F_CONST ? FK_CONST : (f->kind == QMC_F_SEPARABLE_EXP ? FK_SEPEXP : FK_TRIG);
+    mc = 8;
+    func = separable_ptr(fp32, base.tr, fk);
+    if (!func) return fail(QMC_EUNSUPPORTED, "no separable kernel for this transform");
+  }
+
+  GeneralParams<R> gp;
+  if (general) {
+    mc = 8;
+    std::memset(&gp, 0, sizeof(gp));
+    func = general_ptr(fp32);
+    pbytes = sizeof(GeneralParams<R>);
+    auto fill_sparse = [&](SparsePoly<R>& S, const qmc_poly& p) {
+      S.nterms = p.nterms;
+      for (int tt = 0; tt < p.nterms; ++tt) {
+        S.coef[tt] = (R)p.coef[tt];
+        for (int i = 0; i < d; ++i) S.expo[tt][i] = p.expo[(size_t)tt * d + i];
+      }
+    };
+    fill_sparse(gp.U, f->U);
+    fill_sparse(gp.F, f->F);
+  }
+
+  int nblk = 0, L = 0;
+  uint64_t tiles = 0;
+  int rc = choose_grid(func, 0, n, nblk, L, tiles, tune.occupancy);
+  if (rc) return rc;
+  if (tune.L > 0) {
+    L = tune.L;
+    tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
+    nblk = (int)std::min<uint64_t>((uint64_t)nblk, tiles);
+  }
+  base.L = L;
+  base.tiles = tiles;
+  base.nblk = nblk;
+  pl->nblk = nblk;
+  pl->func = func;
+  pl->mc = mc;
+  pl->value_scale = 1.0;  // applied per value inside the kernels' sums via finalize
+  pl->final_scale = base.value_scale;
+  for (int k0 = 0; k0 < m; k0 += mc) {
+    int mk = std::min(mc, m - k0);
+    RuleParams<R> P = base;
+    P.m_launch = mk;
+    P.k_base = k0;
+    for (int kk = 0; kk < mk; ++kk)
+      for (int i = 0; i < d; ++i) {
+        uint64_t s64 = shift_fixed64(shifts[(size_t)(k0 + kk) * d + i]);
+        P.shift64[kk][i] = s64;
+        P.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
+      }
+    Launch ln;
+    ln.func = func;
+    ln.grid = dim3(nblk);
+    ln.params.resize(pbytes);
+    if (general) {
+      gp.base = P;
+      std::memcpy(ln.params.data(), &gp, pbytes);
+    } else {
+      std::memcpy(ln.params.data(), &P, pbytes);
+    }
+    pl->launches.push_back(std::move(ln));
+  }
+  return QMC_OK;
+}
+
+int plan_build(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+               qmc_transform t, const qmc_integrand* f, const TuneChoice& tune) {
+  int rc = validate_problem(d, n, m, g, shifts, t, f);
+  if (rc) return rc;
+  pl->d = d;
+  pl->n = n;
+  pl->m = m;
+  pl->is_complex = f->kind == QMC_F_SECTOR_DEFORMED;
+  if (f->kind == QMC_F_SECTOR_DEFORMED) {
+    rc = build_deformed_plan(pl, d, n, m, g, shifts, t, f, tune);
+  } else if (f->precision == QMC_FP32EVAL) {
+    rc = build_rule_plan<float>(pl, d, n, m, g, shifts, t, f, tune);
+  } else {
+    rc = build_rule_plan<double>(pl, d, n, m, g, shifts, t, f, tune);
+  }
+  return rc;
+}
+
+int plan_alloc(Plan* pl, cudaStream_t stream, bool async) {
+  size_t partial_bytes = (size_t)pl->m * pl->nblk * 2 * sizeof(double);
+  size_t total = partial_bytes + 2 * sizeof(unsigned long long) + sizeof(qmc_result) + (size_t)pl->m * 2 * sizeof(double) + 256;
+  void* p = nullptr;
+  cudaError_t e = async ? cudaMallocAsync(&p, total, stream) : cudaMalloc(&p, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QMC_ENOMEM, "device workspace of %zu bytes: %s", total, cudaGetErrorString(e));
+  }
+  pl->ws_base = p;
+  pl->ws_async = async;
+  char* c = (char*)p;
+  pl->ws.partial = (double*)c;
+  c += partial_bytes;
+  pl->ws.counters = (unsigned long long*)c;
+  c += 2 * sizeof(unsigned long long);
+  pl->ws.result = (qmc_result*)c;
+  c += sizeof(qmc_result);
+  c = (char*)(((uintptr_t)c + 15) & ~(uintptr_t)15);
+  pl->ws.per_shift = (double*)c;
+  e = async ? cudaMemsetAsync(pl->ws.counters, 0, 2 * sizeof(unsigned long long), stream)
+            : cudaMemset(pl->ws.counters, 0, 2 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(e, "clear counters");
+  return QMC_OK;
+}
+
+void plan_free(Plan* pl, cudaStream_t stream) {
+  if (!pl->ws_base) return;
+  if (pl->ws_async) cudaFreeAsync(pl->ws_base, stream);
+  else cudaFree(pl->ws_base);
+  pl->ws_base = nullptr;
+}
+
+int launch_rule(const Plan* pl, const Workspace& ws, cudaStream_t stream, const SampleIO& sio) {
+  for (const Launch& ln : pl->launches) {
+    void* args[4];
+    args[0] = (void*)ln.params.data();
+    double* partial = ws.partial;
+    unsigned long long* counters = ws.counters;
+    args[1] = &partial;
+    args[2] = &counters;
+    args[3] = (void*)&sio;
+    QMC_CUDA(cudaLaunchKernel(ln.func, ln.grid, dim3(kThreads), args, 0, stream));
+  }
+  return QMC_OK;
+}
+
+int launch_finalize(const Plan* pl, const Workspace& ws, qmc_result* res_dev, double* per_shift_dev,
+                    cudaStream_t stream) {
+  FinalizeArgs A;
+  A.partial = ws.partial;
+  A.nblk = pl->nblk;
+  A.m = pl->m;
+  A.is_complex = pl->is_complex;
+  A.pad = 0;
+  A.dn = (double)pl->n;
+  A.value_scale = pl->final_scale;
+  A.counters = ws.counters;
+  A.result = res_dev;
+  A.per_shift = per_shift_dev;
+  void* args[1] = {&A};
+  size_t smem = (size_t)pl->m * 2 * sizeof(double);
+  QMC_CUDA(cudaLaunchKernel(finalize_ptr(), dim3(1), dim3(256), args, smem, stream));
+  return QMC_OK;
+}
+
+int plan_execute(Plan* pl, qmc_result* out, double* per_shift, cudaStream_t stream) {
+  if (!out) return fail(QMC_EINVAL, "null result pointer");
+  const bool out_dev = is_device_pointer(out);
+  const bool ps_dev = per_shift ? is_device_pointer(per_shift) : true;
+  SampleIO none;
+  std::memset(&none, 0, sizeof(none));
+  if (pl->ev_before) QMC_CUDA(cudaEventRecord(pl->ev_before, stream));
+  int rc = launch_rule(pl, pl->ws, stream, none);
+  if (rc) return rc;
+  if (pl->ev_after) QMC_CUDA(cudaEventRecord(pl->ev_after, stream));
+  rc = launch_finalize(pl, pl->ws, out_dev ? out : pl->ws.result,
+                       (per_shift && ps_dev) ? per_shift : (per_shift ? pl->ws.per_shift : nullptr), stream);
+  if (rc) return rc;
+  if (!out_dev) QMC_CUDA(cudaMemcpyAsync(out, pl->ws.result, sizeof(qmc_result), cudaMemcpyDeviceToHost, stream));
+  if (per_shift && !ps_dev)
+    QMC_CUDA(cudaMemcpyAsync(per_shift, pl->ws.per_shift, (size_t)pl->m * 2 * sizeof(double),
+                             cudaMemcpyDeviceToHost, stream));
+  if (!out_dev || (per_shift && !ps_dev)) {
+    QMC_CUDA(cudaStreamSynchronize(stream));
+    if (!out_dev) return out->status;
+  }
+  return QMC_OK;
+}
+
+}  // namespace qmc
+
+using namespace qmc;
+
+// ------------------------------------------------------------------ C ABI --
+
+extern "C" {
+
+const char* qmc_last_error(void) { return g_last_error.c_str(); }
+
+int32_t qmc_version(void) { return 100; }
+
+int qmc_plan_create(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts, qmc_transform t,
+                    const qmc_integrand* f, qmc_plan* plan_out) {
+  if (!plan_out) return fail(QMC_EINVAL, "null plan_out");
+  *plan_out = nullptr;
+  std::unique_ptr<Plan> pl(new Plan());
+  int rc = plan_build(pl.get(), d, n, m, g, shifts, t, f, TuneChoice{});
+  if (rc) return rc;
+  rc = plan_alloc(pl.get(), nullptr, false);
+  if (rc) return rc;
+  *plan_out = reinterpret_cast<qmc_plan>(pl.release());
+  return QMC_OK;
+}
+
+int qmc_plan_execute(qmc_plan plan, qmc_result* out, double* per_shift, void* stream) {
+  if (!plan) return fail(QMC_EINVAL, "null plan");
+  return plan_execute(reinterpret_cast<Plan*>(plan), out, per_shift, (cudaStream_t)stream);
+}
+
+int qmc_plan_destroy(qmc_plan plan) {
+  if (!plan) return QMC_OK;
+  Plan* pl = reinterpret_cast<Plan*>(plan);
+  cudaDeviceSynchronize();
+  plan_free(pl, nullptr);
+  delete pl;
+  return QMC_OK;
+}
+
+int qmc_plan_launches(qmc_plan plan, int32_t* launches_out) {
+  if (!plan || !launches_out) return fail(QMC_EINVAL, "null argument");
+  *launches_out = (int32_t)reinterpret_cast<Plan*>(plan)->launches.size() + 1;
+  return QMC_OK;
+}
+
+int qmc_plan_record_events(qmc_plan plan, void* before_rule, void* after_rule) {
+  if (!plan) return fail(QMC_EINVAL, "null plan");
+  Plan* pl = reinterpret_cast<Plan*>(plan);
+  pl->ev_before = (cudaEvent_t)before_rule;
+  pl->ev_after = (cudaEvent_t)after_rule;
+  return QMC_OK;
+}
+
+int qmc_integrate(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts, qmc_transform t,
+                  const qmc_integrand* f, qmc_result* out, double* per_shift, void* stream) {
+  Plan pl;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = plan_build(&pl, d, n, m, g, shifts, t, f, TuneChoice{});
+  if (rc) return rc;
+  rc = plan_alloc(&pl, s, true);
+  if (rc) return rc;
+  rc = plan_execute(&pl, out, per_shift, s);
+  plan_free(&pl, s);
+  return rc;
+}
+
+int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts, qmc_transform t,
+                      const qmc_integrand* f, int32_t count, const uint64_t* j, const int32_t* k, double* values,
+                      uint64_t* idx, double* coord, void* stream) {
+  if (count < 0 || (count > 0 && (!j || !k || !values))) return fail(QMC_EINVAL, "bad sample arrays");
+  if (count == 0) return QMC_OK;
+  for (int s = 0; s < count; ++s) {
+    if (j[s] >= n) return fail(QMC_EINVAL, "sample %d: j=%llu >= n", s, (unsigned long long)j[s]);
+    if (k[s] < 0 || k[s] >= m) return fail(QMC_EINVAL, "sample %d: k=%d outside [0, m)", s, k[s]);
+  }
+  Plan pl;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = plan_build(&pl, d, n, m, g, shifts, t, f, TuneChoice{});
+  if (rc) return rc;
+  const int dd = d;
+  const int comps = pl.is_complex ? 2 : 1;
+  (void)comps;
+  // group samples by shift chunk (each launch holds mc shifts)
+  std::vector<std::vector<int>> by_chunk(pl.launches.size());
+  for (int s = 0; s < count; ++s) by_chunk[k[s] / pl.mc].push_back(s);
+  size_t bytes = (size_t)count * (8 + 4 + 16 + 8 * dd + 8 * dd) + 64;
+  char* dbuf = nullptr;
+  QMC_CUDA(cudaMallocAsync((void**)&dbuf, bytes, st));
+  uint64_t* dj = (uint64_t*)dbuf;
+  int32_t* dk = (int32_t*)(dj + count);
+  double* dv = (double*)(((uintptr_t)(dk + count) + 15) & ~(uintptr_t)15);
+  uint64_t* di = (uint64_t*)(dv + 2 * (size_t)count);
+  double* dc = (double*)(di + (size_t)count * dd);
+  std::vector<uint64_t> hj(count);
+  std::vector<int32_t> hk(count);
+  std::vector<int> order;
+  for (size_t c = 0; c < by_chunk.size(); ++c)
+    for (int s : by_chunk[c]) order.push_back(s);
+  for (int q = 0; q < count; ++q) {
+    hj[q] = j[order[q]];
+    hk[q] = k[order[q]] % pl.mc;
+  }
+  QMC_CUDA(cudaMemcpyAsync(dj, hj.data(), 8 * (size_t)count, cudaMemcpyHostToDevice, st));
+  QMC_CUDA(cudaMemcpyAsync(dk, hk.data(), 4 * (size_t)count, cudaMemcpyHostToDevice, st));
+  int off = 0;
+  for (size_t c = 0; c < by_chunk.size(); ++c) {
+    int cnt = (int)by_chunk[c].size();
+    if (!cnt) continue;
+    SampleIO sio;
+    sio.count = cnt;
+    sio.pad = 0;
+    sio.j = dj + off;
+    sio.k = dk + off;
+    sio.values = dv + 2 * (size_t)off;
+    sio.idx = di + (size_t)off * dd;
+    sio.coord = dc + (size_t)off * dd;
+    const Launch& ln = pl.launches[c];
+    void* args[4];
+    double* partial = nullptr;
+    unsigned long long* counters = nullptr;
+    args[0] = (void*)ln.params.data();
+    args[1] = &partial;
+    args[2] = &counters;
+    args[3] = &sio;
+    QMC_CUDA(cudaLaunchKernel(ln.func, dim3((cnt + 255) / 256), dim3(kThreads), args, 0, st));
+    off += cnt;
+  }
+  std::vector<double> hv(2 * (size_t)count), hc((size_t)count * dd);
+  std::vector<uint64_t> hi((size_t)count * dd);
+  QMC_CUDA(cudaMemcpyAsync(hv.data(), dv, 16 * (size_t)count, cudaMemcpyDeviceToHost, st));
+  QMC_CUDA(cudaMemcpyAsync(hi.data(), di, 8 * (size_t)count * dd, cudaMemcpyDeviceToHost, st));
+  QMC_CUDA(cudaMemcpyAsync(hc.data(), dc, 8 * (size_t)count * dd, cudaMemcpyDeviceToHost, st));
+  QMC_CUDA(cudaFreeAsync(dbuf, st));
+  QMC_CUDA(cudaStreamSynchronize(st));
+  for (int q = 0; q < count; ++q) {
+    int s = order[q];
+    values[2 * (size_t)s] = hv[2 * (size_t)q];
+    values[2 * (size_t)s + 1] = hv[2 * (size_t)q + 1];
+    for (int i = 0; i < dd; ++i) {
+      if (idx) idx[(size_t)s * dd + i] = hi[(size_t)q * dd + i];
+      if (coord) coord[(size_t)s * dd + i] = hc[(size_t)q * dd + i];
+    }
+  }
+  return QMC_OK;
+}
+
+}  // extern "C"
+
+namespace qmc {
+template void fill_common<float>(RuleParams<float>&, int32_t, uint64_t, const uint64_t*, const qmc_transform&,
+                                 const qmc_integrand*);
+template void fill_common<double>(RuleParams<double>&, int32_t, uint64_t, const uint64_t*, const qmc_transform&,
+                                  const qmc_integrand*);
+}  // namespace qmc

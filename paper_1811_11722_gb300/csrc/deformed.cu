@@ -1,0 +1,79 @@
+// Plan builder for contour-deformed (complex) sector integrands.
+#include <cmath>
+#include <cstring>
+
+#include "plan.h"
+
+namespace qmc {
+
+constexpr int kMcDef = 8;  // shifts per launch (matches the kernel's shared accumulators)
+
+template <typename R>
+static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                     const qmc_transform& t, const qmc_integrand* f, const TuneChoice& tune) {
+  if (d > kDFast) return fail(QMC_EUNSUPPORTED, "deformed sector integrands need d <= %d", kDFast);
+  RuleParams<R> base;
+  fill_common(base, d, n, g, t, f);
+  const void* func = nullptr;
+  switch (d) {
+#define QMC_D_CASE(DD) \
+  case DD:             \
+    func = deformed_ptr<R, DD>(); \
+    break;
+    QMC_D_CASE(1) QMC_D_CASE(2) QMC_D_CASE(3) QMC_D_CASE(4) QMC_D_CASE(5) QMC_D_CASE(6) QMC_D_CASE(7)
+    QMC_D_CASE(8)
+#undef QMC_D_CASE
+    default: break;
+  }
+  if (!func) return fail(QMC_EUNSUPPORTED, "no deformed kernel for d=%d", d);
+  auto cu = pack_dense(f->U, d, 2);
+  auto cf = pack_dense(f->F, d, 2);
+  for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
+  for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
+  base.value_scale = 1.0;  // transform weights normalised per factor in this kernel
+  base.check_finite = 1;
+  int nblk = 0, L = 0;
+  uint64_t tiles = 0;
+  int rc = choose_grid(func, 0, n, nblk, L, tiles, tune.occupancy);
+  if (rc) return rc;
+  if (tune.L > 0) {
+    L = tune.L;
+    tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
+    nblk = (int)std::min<uint64_t>((uint64_t)nblk, tiles);
+  }
+  base.L = L;
+  base.tiles = tiles;
+  base.nblk = nblk;
+  pl->nblk = nblk;
+  pl->func = func;
+  pl->mc = kMcDef;
+  pl->final_scale = 1.0;
+  pl->is_complex = 1;
+  for (int k0 = 0; k0 < m; k0 += kMcDef) {
+    const int mk = std::min(kMcDef, m - k0);
+    RuleParams<R> P = base;
+    P.m_launch = mk;
+    P.k_base = k0;
+    for (int kk = 0; kk < mk; ++kk)
+      for (int i = 0; i < d; ++i) {
+        uint64_t s64 = shift_fixed64(shifts[(size_t)(k0 + kk) * d + i]);
+        P.shift64[kk][i] = s64;
+        P.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
+      }
+    Launch ln;
+    ln.func = func;
+    ln.grid = dim3(nblk);
+    ln.params.resize(sizeof(P));
+    std::memcpy(ln.params.data(), &P, sizeof(P));
+    pl->launches.push_back(std::move(ln));
+  }
+  return QMC_OK;
+}
+
+int build_deformed_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                        const qmc_transform& t, const qmc_integrand* f, const TuneChoice& tune) {
+  if (f->precision == QMC_FP32EVAL) return build_def<float>(pl, d, n, m, g, shifts, t, f, tune);
+  return build_def<double>(pl, d, n, m, g, shifts, t, f, tune);
+}
+
+}  // namespace qmc

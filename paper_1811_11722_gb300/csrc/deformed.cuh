@@ -1,0 +1,287 @@
+// Contour-deformed (complex) sector integrands (Sec. 3: the Feynman
+// prescription as a deformation of the integration contour into the complex
+// plane, vanishing at the endpoints).
+//
+// After the periodizing transform y = z(x):
+//   w_k  = y_k - i lambda y_k (1 - y_k) dF/dy_k (y)
+//   J_kl = dw_k/dy_l = delta_kl - i lambda [delta_kl (1 - 2 y_k) dF/dy_k
+//                                           + y_k (1 - y_k) d2F/dy_k dy_l]
+//   f    = U(w)^aU F(w)^aF det J,   value = f * prod_i (transform weight)
+// F (and U) are dense polynomials of degree <= 2 in nested Horner form, so
+// dF/dy is a linear form and d2F a constant symmetric matrix read from the
+// same coefficients at compile-time offsets.  J = I + i M with M real; its
+// determinant comes from LU factorisation with partial pivoting done by
+// conditional row swaps in registers (no dynamic register indexing).
+//
+// One thread evaluates one shift at a time (the per-point work, ~700 flops,
+// dwarfs the index work it would share), keeping one complex matrix live.
+#pragma once
+
+#include "rule_kernels.cuh"
+
+namespace qmc {
+
+template <typename R>
+struct Cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return {fma_(a.re, b.re, -a.im * b.im), fma_(a.re, b.im, a.im * b.re)};
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> crecip(Cx<R> a) {
+  R den = fma_(a.re, a.re, a.im * a.im);
+  R r = recip(den);
+  return {a.re * r, -a.im * r};
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cpow_int(Cx<R> z, int a) {
+  Cx<R> p{R(1), R(0)};
+  int k = a < 0 ? -a : a;
+  for (int q = 0; q < k; ++q) p = cmul(p, z);
+  return a < 0 ? crecip(p) : p;
+}
+
+// Offset of q_ij (i <= j) in the nested degree-2 layout.
+__host__ __device__ constexpr int q_off(int D, int i, int j) {
+  int off = 1;
+  for (int a = 0; a < i; ++a) off += 1 + (D - a);
+  return off + 1 + (j - i);
+}
+__host__ __device__ constexpr int l_off(int D, int i) {
+  int off = 1;
+  for (int a = 0; a < i; ++a) off += 1 + (D - a);
+  return off;
+}
+
+// Complex evaluation of a dense degree-2 polynomial with real coefficients.
+template <int D, typename R>
+__device__ __forceinline__ Cx<R> poly2_complex(const R* c, const Cx<R>* z) {
+  Cx<R> acc{c[0], R(0)};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Cx<R> r{c[l_off(D, i)], R(0)};
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      const R q = c[q_off(D, i, j)];
+      r.re = fma_(q, z[j].re, r.re);
+      r.im = fma_(q, z[j].im, r.im);
+    }
+    Cx<R> t = cmul(z[i], r);
+    acc.re += t.re;
+    acc.im += t.im;
+  }
+  return acc;
+}
+
+template <typename R>
+__device__ __forceinline__ R cmag1(R re, R im) {
+  return fabs(re) + fabs(im);
+}
+
+// det(J) for J = I + i M (M real, D x D) by LU with partial pivoting.
+template <int D, typename R>
+__device__ __forceinline__ Cx<R> det_ipm(R (&M)[D][D]) {
+  R ar[D][D], ai[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      ar[r][q] = (r == q) ? R(1) : R(0);
+      ai[r][q] = M[r][q];
+    }
+  Cx<R> det{R(1), R(0)};
+  bool neg = false;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+#pragma unroll
+    for (int r = c + 1; r < D; ++r) {
+      const bool sw = cmag1(ar[r][c], ai[r][c]) > cmag1(ar[c][c], ai[c][c]);
+      neg ^= sw;
+#pragma unroll
+      for (int q = c; q < D; ++q) {
+        R tr = ar[c][q], ti = ai[c][q];
+        ar[c][q] = sw ? ar[r][q] : tr;
+        ai[c][q] = sw ? ai[r][q] : ti;
+        ar[r][q] = sw ? tr : ar[r][q];
+        ai[r][q] = sw ? ti : ai[r][q];
+      }
+    }
+    const Cx<R> piv{ar[c][c], ai[c][c]};
+    det = cmul(det, piv);
+    const Cx<R> inv = crecip(piv);
+#pragma unroll
+    for (int r = c + 1; r < D; ++r) {
+      const Cx<R> f = cmul(Cx<R>{ar[r][c], ai[r][c]}, inv);
+#pragma unroll
+      for (int q = c + 1; q < D; ++q) {
+        const Cx<R> t = cmul(f, Cx<R>{ar[c][q], ai[c][q]});
+        ar[r][q] -= t.re;
+        ai[r][q] -= t.im;
+      }
+    }
+  }
+  if (neg) {
+    det.re = -det.re;
+    det.im = -det.im;
+  }
+  return det;
+}
+
+// Weighted complex value at one point and shift; *bad set when Im F(w) > 0.
+template <typename R, int D>
+__device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const typename FixT<R>::T* base, int k,
+                                                bool& bad) {
+  R y[D];
+  R wt = R(1);
+#pragma unroll
+  for (int i = 0; i < D; ++i) y[i] = coord_general<R>(P, base[i] + shift_of(P, k, i), wt);
+  const R* cF = P.cF;
+  // gradient of F (linear form) and the contour
+  R gr[D];
+#pragma unroll
+  for (int kk = 0; kk < D; ++kk) {
+    R s = cF[l_off(D, kk)];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int a = kk < j ? kk : j, b = kk < j ? j : kk;
+      const R q = cF[q_off(D, a, b)];
+      s = fma_(j == kk ? R(2) * q : q, y[j], s);
+    }
+    gr[kk] = s;
+  }
+  const R lam = P.lam;
+  Cx<R> z[D];
+  R M[D][D];
+#pragma unroll
+  for (int kk = 0; kk < D; ++kk) {
+    const R a = fma_(-y[kk], y[kk], y[kk]);  // y (1 - y)
+    z[kk] = {y[kk], -lam * a * gr[kk]};
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      const int lo = kk < l ? kk : l, hi = kk < l ? l : kk;
+      const R q = cF[q_off(D, lo, hi)];
+      const R h2 = (kk == l) ? R(2) * q : q;
+      R v = a * h2;
+      if (kk == l) v = fma_(fma_(R(-2), y[kk], R(1)), gr[kk], v);
+      M[kk][l] = -lam * v;
+    }
+  }
+  const Cx<R> dJ = det_ipm<D, R>(M);
+  const Cx<R> U = poly2_complex<D, R>(P.cU, z);
+  const Cx<R> F = poly2_complex<D, R>(cF, z);
+  bad = F.im > R(0);
+  Cx<R> v;
+  if (P.aU == -2 && P.aF == -1) v = cmul(dJ, crecip(cmul(cmul(U, U), F)));
+  else v = cmul(dJ, cmul(cpow_int(U, P.aU), cpow_int(F, P.aF)));
+  v.re *= wt;
+  v.im *= wt;
+  return v;
+}
+
+constexpr int kMcDeformed = 8;
+
+template <typename R, int D>
+__global__ void __launch_bounds__(kThreads)
+    deformed_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
+                    unsigned long long* __restrict__ counters, const SampleIO sio) {
+  using FT = typename FixT<R>::T;
+  if (sio.count > 0) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sio.count) return;
+    const uint64_t j = sio.j[s];
+    const int k = sio.k[s];
+    FT base[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      uint32_t idx = lattice_index(j, P.g[i], P.n);
+      base[i] = fix_base<R>(idx, P.rc);
+      if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
+      if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<R>(base[i] + shift_of(P, k, i));
+    }
+    bool bad;
+    Cx<R> v = deformed_value<R, D>(P, base, k, bad);
+    sio.values[2 * (size_t)s] = (double)v.re * P.value_scale;
+    sio.values[2 * (size_t)s + 1] = (double)v.im * P.value_scale;
+    return;
+  }
+  __shared__ double accs[2][kMcDeformed][kThreads];
+  const uint32_t n = (uint32_t)P.n;
+  const int mk = P.m_launch;
+  for (int kk = 0; kk < kMcDeformed; ++kk) {
+    accs[0][kk][threadIdx.x] = 0.0;
+    accs[1][kk][threadIdx.x] = 0.0;
+  }
+  unsigned nbad = 0, ndef = 0;
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+#pragma unroll 1
+    for (int kk = 0; kk < mk; ++kk) {
+      uint32_t idx[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
+      Acc<R> are, aim;
+      are.init();
+      aim.init();
+#pragma unroll 1
+      for (int s = 0; s < steps; ++s) {
+        FT base[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) base[i] = fix_base<R>(idx[i], P.rc);
+        bool bad;
+        Cx<R> v = deformed_value<R, D>(P, base, kk, bad);
+        ndef += bad ? 1u : 0u;
+        if (P.check_finite) {
+          const bool ok = finite_(v.re) && finite_(v.im);
+          nbad += ok ? 0u : 1u;
+          v.re = ok ? v.re : R(0);
+          v.im = ok ? v.im : R(0);
+        }
+        are.add(v.re);
+        aim.add(v.im);
+#pragma unroll
+        for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
+        if constexpr (sizeof(R) == 4) {
+          if ((s & (kFoldG - 1)) == kFoldG - 1) {
+            are.fold();
+            aim.fold();
+          }
+        }
+      }
+      accs[0][kk][threadIdx.x] += are.thread_total();
+      accs[1][kk][threadIdx.x] += aim.thread_total();
+    }
+  }
+  __shared__ double red[kThreads / 32][kMcDeformed][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int kk = 0; kk < mk; ++kk) {
+    const double tr = warp_sum_d(accs[0][kk][threadIdx.x]);
+    const double ti = warp_sum_d(accs[1][kk][threadIdx.x]);
+    if (lane == 0) {
+      red[warp][kk][0] = tr;
+      red[warp][kk][1] = ti;
+    }
+  }
+  unsigned long long b1 = warp_sum_u64((unsigned long long)nbad);
+  unsigned long long b2 = warp_sum_u64((unsigned long long)ndef);
+  if (lane == 0 && b1) atomicAdd(&counters[0], b1);
+  if (lane == 0 && b2) atomicAdd(&counters[1], b2);
+  __syncthreads();
+  if (threadIdx.x < 2 * mk) {
+    const int kk = threadIdx.x >> 1, part = threadIdx.x & 1;
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][kk][part];
+    partial[((size_t)(P.k_base + kk) * P.nblk + blockIdx.x) * 2 + part] = s;
+  }
+}
+
+}  // namespace qmc

@@ -1,0 +1,67 @@
+// Lookup of kernel instantiations by their runtime description.  Each getter
+// returns the address of a __global__ function (for cudaLaunchKernel) or null
+// when no specialisation exists for the request.
+#pragma once
+
+#include <cstdint>
+
+#include "qmc_internal.h"
+
+namespace qmc {
+
+// Dense sector kernel, U of degree ku, F of degree kf, d = D <= kDFast.
+// One explicit specialisation per (precision, D), each in its own unit.
+template <typename R, int D>
+const void* sector_ptr(int mc, int tr, int alpha, int ku, int kf);
+#define QMC_DECL_SECTOR(R, D) template <> const void* sector_ptr<R, D>(int, int, int, int, int);
+QMC_DECL_SECTOR(float, 1) QMC_DECL_SECTOR(float, 2) QMC_DECL_SECTOR(float, 3) QMC_DECL_SECTOR(float, 4)
+QMC_DECL_SECTOR(float, 5) QMC_DECL_SECTOR(float, 6) QMC_DECL_SECTOR(float, 7) QMC_DECL_SECTOR(float, 8)
+QMC_DECL_SECTOR(double, 1) QMC_DECL_SECTOR(double, 2) QMC_DECL_SECTOR(double, 3) QMC_DECL_SECTOR(double, 4)
+QMC_DECL_SECTOR(double, 5) QMC_DECL_SECTOR(double, 6) QMC_DECL_SECTOR(double, 7) QMC_DECL_SECTOR(double, 8)
+#undef QMC_DECL_SECTOR
+
+// Contour-deformed complex sector kernel, d = D <= kDFast (runtime transform).
+template <typename R, int D>
+const void* deformed_ptr();
+#define QMC_DECL_DEF(R, D) template <> const void* deformed_ptr<R, D>();
+QMC_DECL_DEF(float, 1) QMC_DECL_DEF(float, 2) QMC_DECL_DEF(float, 3) QMC_DECL_DEF(float, 4)
+QMC_DECL_DEF(float, 5) QMC_DECL_DEF(float, 6) QMC_DECL_DEF(float, 7) QMC_DECL_DEF(float, 8)
+QMC_DECL_DEF(double, 1) QMC_DECL_DEF(double, 2) QMC_DECL_DEF(double, 3) QMC_DECL_DEF(double, 4)
+QMC_DECL_DEF(double, 5) QMC_DECL_DEF(double, 6) QMC_DECL_DEF(double, 7) QMC_DECL_DEF(double, 8)
+#undef QMC_DECL_DEF
+
+// Separable integrands (const / separable exp / trig), runtime d and
+// Korobov weight (factors normalised, value scale 1).
+template <typename R>
+const void* separable_ptr_t(int tr, int fk);
+template <> const void* separable_ptr_t<float>(int tr, int fk);
+template <> const void* separable_ptr_t<double>(int tr, int fk);
+inline const void* separable_ptr(bool fp32, int tr, int fk) {
+  return fp32 ? separable_ptr_t<float>(tr, fk) : separable_ptr_t<double>(tr, fk);
+}
+
+// General sparse-polynomial sector kernel, runtime d, transform and powers.
+template <typename R>
+const void* general_ptr_t();
+template <> const void* general_ptr_t<float>();
+template <> const void* general_ptr_t<double>();
+inline const void* general_ptr(bool fp32) { return fp32 ? general_ptr_t<float>() : general_ptr_t<double>(); }
+
+// Final deterministic pass: per-shift sums -> Q^(k), Qbar, sigma^2.
+const void* finalize_ptr();
+
+// Arguments of the final pass.
+struct FinalizeArgs {
+  const double* partial;   // [m][nblk][2]
+  int32_t nblk;
+  int32_t m;
+  int32_t is_complex;
+  int32_t pad;
+  double dn;      // n as a double
+  double value_scale;
+  unsigned long long* counters;  // [2], reset to zero after reading
+  qmc_result* result;            // device
+  double* per_shift;             // device [m][2] or null
+};
+
+}  // namespace qmc

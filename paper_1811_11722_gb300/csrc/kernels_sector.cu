@@ -1,0 +1,50 @@
+// Instantiations of the specialised sector and deformed kernels for one
+// (precision, d).
+// Compiled once per pair with -DQMC_REAL=float|double -DQMC_D=1..8 so the
+// build spreads the template work over parallel nvcc processes.
+#include "kernel_table.h"
+#include "deformed.cuh"
+#include "rule_kernels.cuh"
+
+#ifndef QMC_REAL
+#error "QMC_REAL must be float or double"
+#endif
+#ifndef QMC_D
+#error "QMC_D must be 1..8"
+#endif
+
+namespace qmc {
+
+#define QMC_SECTOR_TR(R, MC, KU, KF)                                                    \
+  do {                                                                                  \
+    if (tr == TR_NONE) return (const void*)&sector_kernel<R, QMC_D, MC, TR_NONE, 0, KU, KF>; \
+    if (tr == TR_BAKER) return (const void*)&sector_kernel<R, QMC_D, MC, TR_BAKER, 0, KU, KF>; \
+    if (tr == TR_KOROBOV && alpha == 3)                                                 \
+      return (const void*)&sector_kernel<R, QMC_D, MC, TR_KOROBOV, 3, KU, KF>;         \
+  } while (0)
+
+template <>
+const void* sector_ptr<QMC_REAL, QMC_D>(int mc, int tr, int alpha, int ku, int kf) {
+  // FP32 is FMA-pipe bound: shift-chunk sizes 8/16/32 trade registers for
+  // reuse of the per-point index work.  FP64 is DP-pipe bound on this part
+  // and takes one chunk size.
+  constexpr bool kF32 = sizeof(QMC_REAL) == 4;
+  if (ku == 1 && kf == 2) {
+    if constexpr (kF32) {
+      if (mc == 8) QMC_SECTOR_TR(QMC_REAL, 8, 1, 2);
+      if (mc == 32) QMC_SECTOR_TR(QMC_REAL, 32, 1, 2);
+    }
+    if (mc == 16) QMC_SECTOR_TR(QMC_REAL, 16, 1, 2);
+  }
+  if constexpr (kF32) {
+    if (ku == 2 && kf == 3 && mc == 16) QMC_SECTOR_TR(QMC_REAL, 16, 2, 3);
+  }
+  return nullptr;
+}
+
+template <>
+const void* deformed_ptr<QMC_REAL, QMC_D>() {
+  return (const void*)&deformed_kernel<QMC_REAL, QMC_D>;
+}
+
+}  // namespace qmc

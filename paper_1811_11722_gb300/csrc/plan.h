@@ -1,0 +1,80 @@
+// Host-side plan of one rule: validated, packed launch descriptors plus the
+// device workspace (per-CTA slots, counters, result staging).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "kernel_table.h"
+#include "qmc_internal.h"
+
+namespace qmc {
+
+struct SampleIO;
+
+struct Launch {
+  const void* func = nullptr;
+  dim3 grid;
+  size_t smem = 0;
+  std::vector<uint8_t> params;  // kernel parameter struct, passed as args[0]
+};
+
+// Launch-shape overrides (autotuner); zero fields mean "library default".
+struct TuneChoice {
+  int mc = 0;          // shifts per launch chunk (8, 16, 32)
+  int L = 0;           // points per thread per tile
+  int occupancy = 0;   // cap on CTAs per SM
+  bool force_general = false;
+};
+
+struct Plan {
+  int d = 0;
+  uint64_t n = 0;
+  int m = 0;
+  int is_complex = 0;
+  int nblk = 0;
+  int mc = 0;
+  const void* func = nullptr;
+  double value_scale = 1.0;
+  double final_scale = 1.0;
+  std::vector<Launch> launches;
+  Workspace ws{};
+  void* ws_base = nullptr;
+  bool ws_async = false;
+  cudaEvent_t ev_before = nullptr;  // optional timing hook
+  cudaEvent_t ev_after = nullptr;
+};
+
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+bool is_device_pointer(const void* p);
+bool prime_check(uint64_t n);
+
+int validate_problem(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                     const qmc_transform& t, const qmc_integrand* f);
+int poly_degree(const qmc_poly& p, int d);
+std::vector<double> pack_dense(const qmc_poly& p, int D, int K);
+Recip reciprocal(uint64_t n);
+void korobov_coefs(int alpha, double* kor);
+uint64_t shift_fixed64(double delta);
+int choose_grid(const void* func, size_t smem, uint64_t n, int& nblk, int& L, uint64_t& tiles,
+                int occupancy_override);
+
+template <typename R>
+void fill_common(RuleParams<R>& P, int32_t d, uint64_t n, const uint64_t* g, const qmc_transform& t,
+                 const qmc_integrand* f);
+
+int plan_build(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+               qmc_transform t, const qmc_integrand* f, const TuneChoice& tune);
+int build_deformed_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                        const qmc_transform& t, const qmc_integrand* f, const TuneChoice& tune);
+int plan_alloc(Plan* pl, cudaStream_t stream, bool async);
+void plan_free(Plan* pl, cudaStream_t stream);
+int launch_rule(const Plan* pl, const Workspace& ws, cudaStream_t stream, const SampleIO& sio);
+int launch_finalize(const Plan* pl, const Workspace& ws, qmc_result* res_dev, double* per_shift_dev,
+                    cudaStream_t stream);
+int plan_execute(Plan* pl, qmc_result* out, double* per_shift, cudaStream_t stream);
+
+}  // namespace qmc

@@ -1,0 +1,104 @@
+// Internal launch descriptors shared by the host launchers and the sm_103a
+// kernels.  Everything a kernel needs per launch travels in one struct passed
+// as a __grid_constant__ kernel parameter, so the inner loops read shifts and
+// polynomial coefficients as constant-bank operands (no shared-memory or
+// global loads on the hot path).
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/qmc.h"
+
+namespace qmc {
+
+constexpr int kMcMax = 32;      // shifts handled by one launch
+constexpr int kDFast = 8;       // largest d with a specialised sector kernel
+constexpr int kPolyCoefMax = 168;  // nested-Horner slots: d=8 degree 3 needs 165
+constexpr int kTermsMax = 64;   // sparse monomials per polynomial (general kernel)
+constexpr int kThreads = 256;   // threads per CTA of the rule kernels
+
+enum TransformCode { TR_NONE = 0, TR_BAKER = 1, TR_KOROBOV = 2 };
+
+// Integrand code inside kernels.
+enum FKind { FK_CONST = 0, FK_SEPEXP = 1, FK_SECTOR = 2, FK_DEFORMED = 3, FK_TRIG = 4 };
+
+// Number of nested-Horner coefficients of a degree-K polynomial in D variables:
+//   K=1: 1 + D; K=2: 1 + D + D(D+1)/2; K=3: adds D(D+1)(D+2)/6.
+__host__ __device__ constexpr int poly_slots(int D, int K) {
+  return 1 + (K >= 1 ? D : 0) + (K >= 2 ? D * (D + 1) / 2 : 0) + (K >= 3 ? D * (D + 1) * (D + 2) / 6 : 0);
+}
+
+// Fixed point: the fractional part of idx/n is held as P = floor(idx 2^64 / n)
+// (64-bit), from the 128-bit reciprocal 2^128/n = rhi 2^64 + rlo.
+struct Recip {
+  uint64_t rhi;
+  uint64_t rlo;
+};
+
+// Parameters of the per-point rule kernels (single problem).  R = float for
+// FP32EVAL, double for FP64.  Shifts are fixed point: u32 (FP32 path, the
+// 2^-24 rounding offset of the float conversion folded in) or u64.
+template <typename R>
+struct RuleParams {
+  uint64_t n;
+  uint64_t tiles;          // number of point tiles of kThreads * L points
+  int32_t L;               // points per thread per tile
+  int32_t d;
+  int32_t m_launch;        // shifts in this launch (<= kMcMax)
+  int32_t k_base;          // global index of this launch's first shift
+  int32_t nblk;            // CTAs per shift chunk (partial slots per shift)
+  int32_t alpha;           // Korobov weight (transform code TR_KOROBOV)
+  int32_t aU, aF;          // integer powers
+  int32_t check_finite;    // 1: left out and count NaN/Inf values
+  int32_t tr;              // transform code (general kernel)
+  R lam;                   // deformation parameter
+  double value_scale;      // constant factor of every weighted value (applied in FP64)
+  Recip rc;
+  uint32_t g[QMC_DMAX];
+  uint32_t gstep[QMC_DMAX];     // (kThreads * g_i) mod n
+  uint64_t shift64[kMcMax][QMC_DMAX];
+  uint32_t shift32[kMcMax][QMC_DMAX];
+  R kor[8];                // Korobov z(s) = s^(a+1) sum_k kor[k] s^k on s <= 1/2;
+                           // kor[7] = (2a+1)!/(a!)^2 (general kernel weight)
+  R cU[kPolyCoefMax];      // nested-Horner U (dense kernels)
+  R cF[kPolyCoefMax];      // nested-Horner F
+  R sep_c[QMC_DMAX];       // separable: (1 + c z) exp(b z), trig: h as R
+  R sep_b[QMC_DMAX];
+};
+
+// Sparse monomial table for the general kernel (any degree, d <= QMC_DMAX).
+template <typename R>
+struct SparsePoly {
+  int32_t nterms;
+  int32_t pad;
+  R coef[kTermsMax];
+  uint8_t expo[kTermsMax][QMC_DMAX];
+};
+
+template <typename R>
+struct GeneralParams {
+  RuleParams<R> base;
+  SparsePoly<R> U;
+  SparsePoly<R> F;
+};
+
+// Sampling mode: the rule kernels evaluate listed (j, k) terms instead of the rule.
+struct SampleIO {
+  int32_t count;
+  int32_t pad;
+  const uint64_t* j;
+  const int32_t* k;    // chunk-local shift index
+  double* values;      // [count][2]
+  uint64_t* idx;       // [count][d] or null
+  double* coord;       // [count][d] or null
+};
+
+// Device workspace layout of one planned rule.
+struct Workspace {
+  double* partial;               // [m][nblk][2]
+  unsigned long long* counters;  // [0] non-finite, [1] deformation violations
+  qmc_result* result;            // device copy of the result
+  double* per_shift;             // [m][2]
+};
+
+}  // namespace qmc

@@ -1,0 +1,435 @@
+// Kernels of the shifted rank-1 lattice rule, Eq. (2), for one problem.
+//
+// Work layout.  The n points are cut into tiles of kThreads * L points; CTA b
+// takes tiles b, b + gridDim.x, ...  Inside a tile, thread t takes points
+// j = tile_start + t + s * kThreads, s = 0..L-1, so each warp walks a
+// contiguous run of 32 points at every step, and a thread advances its d
+// lattice indices by a precomputed step (kThreads g_i mod n) with one add and
+// one conditional subtract per dimension.  All MC shifts of the launch are
+// evaluated for a point before moving on (shift loop unrolled, one register
+// accumulator per shift), so the index and fixed-point work of a point is
+// shared by MC evaluations.
+//
+// Sums.  FP64: double accumulators.  FP32: a float run over G = 8 points is
+// folded into a (hi, lo) float pair by Fast2Sum; at the end the pairs are
+// reduced across the warp in float-float and across warps in double.  Each
+// CTA writes its per-shift sum into a fixed slot; finalize_kernel adds the
+// slots in a fixed order, so results are bit-reproducible for a given launch
+// configuration.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace qmc {
+
+constexpr int kFoldG = 8;
+
+template <typename R>
+struct Acc;
+
+template <>
+struct Acc<float> {
+  float run, hi, lo;
+  __device__ __forceinline__ void init() { run = hi = lo = 0.0f; }
+  __device__ __forceinline__ void add(float v) { run += v; }
+  __device__ __forceinline__ void fold() {
+    fast2sum_add(hi, lo, run);
+    run = 0.0f;
+  }
+  // warp-reduced total (valid in lane 0)
+  __device__ __forceinline__ double warp_total() {
+    fold();
+    warp_sum_ff(hi, lo);
+    return (double)hi + (double)lo;
+  }
+  // this thread's total
+  __device__ __forceinline__ double thread_total() {
+    fold();
+    return (double)hi + (double)lo;
+  }
+};
+
+template <>
+struct Acc<double> {
+  double run;
+  __device__ __forceinline__ void init() { run = 0.0; }
+  __device__ __forceinline__ void add(double v) { run += v; }
+  __device__ __forceinline__ void fold() {}
+  __device__ __forceinline__ double warp_total() { return warp_sum_d(run); }
+  __device__ __forceinline__ double thread_total() { return run; }
+};
+
+// Fixed-point base of a coordinate for the precision at hand.
+template <typename R>
+struct FixT;
+template <>
+struct FixT<float> {
+  using T = uint32_t;
+};
+template <>
+struct FixT<double> {
+  using T = uint64_t;
+};
+
+template <typename R>
+__device__ __forceinline__ typename FixT<R>::T fix_base(uint32_t idx, const Recip& rc) {
+  if constexpr (sizeof(R) == 4) return frac32(frac64(idx, rc));
+  else return frac64(idx, rc);
+}
+
+template <typename R>
+__device__ __forceinline__ typename FixT<R>::T shift_of(const RuleParams<R>& P, int k, int i) {
+  if constexpr (sizeof(R) == 4) return P.shift32[k][i];
+  else return P.shift64[k][i];
+}
+
+template <typename R, int TR, int ALPHA>
+__device__ __forceinline__ R coord(typename FixT<R>::T X, const R* kor, int alpha, R& w) {
+  if constexpr (sizeof(R) == 4) return coord_f32<TR, ALPHA>(X, kor, alpha, w);
+  else return coord_f64<TR, ALPHA>(X, kor, alpha, w);
+}
+
+// The coordinate a kernel used, as a double in [0, 1) (sampling output).
+template <typename R>
+__device__ __forceinline__ double coord_used(typename FixT<R>::T X) {
+  if constexpr (sizeof(R) == 4) return (double)(unit_f32(X) - 1.0f);
+  else return (double)(X >> 11) * 0x1p-53;
+}
+
+// --------------------------------------------------- sector, dense, fast --
+
+// f = U^aU F^aF with U, F dense of degrees KU, KF, times the transform weight.
+template <typename R, int D, int TR, int ALPHA, int KU, int KF>
+__device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename FixT<R>::T* base, int k,
+                                          R* zout = nullptr) {
+  R z[D];
+  R w = R(1);
+#pragma unroll
+  for (int i = 0; i < D; ++i) z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
+  if (zout) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) zout[i] = z[i];
+  }
+  R U = poly_dense<D, KU>(P.cU, z);
+  R F = poly_dense<D, KF>(P.cF, z);
+  R v;
+  if (P.aU == -2 && P.aF == -1) v = recip(U * U * F);
+  else v = ipow(U, P.aU) * ipow(F, P.aF);
+  if constexpr (TR == TR_KOROBOV) v *= w;
+  return v;
+}
+
+template <typename R, int D, int TR, int ALPHA, int KU, int KF>
+__device__ void sector_sample(const RuleParams<R>& P, const SampleIO& sio) {
+  using FT = typename FixT<R>::T;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= sio.count) return;
+  uint64_t j = sio.j[s];
+  int k = sio.k[s];
+  FT base[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    uint32_t idx = lattice_index(j, P.g[i], P.n);
+    base[i] = fix_base<R>(idx, P.rc);
+    if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
+    if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<R>(base[i] + shift_of(P, k, i));
+  }
+  R v = sector_value<R, D, TR, ALPHA, KU, KF>(P, base, k);
+  sio.values[2 * (size_t)s] = (double)v * (double)P.value_scale;
+  sio.values[2 * (size_t)s + 1] = 0.0;
+}
+
+// Block-level epilogue: per-shift warp totals -> fixed CTA slot.
+template <typename R, int MC>
+__device__ __forceinline__ void block_epilogue(Acc<R>* acc, int mk, unsigned nbad, const RuleParams<R>& P,
+                                               double* __restrict__ partial,
+                                               unsigned long long* __restrict__ counters) {
+  __shared__ double red[kThreads / 32][MC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int kk = 0; kk < MC; ++kk) {
+    double t = acc[kk].warp_total();
+    if (lane == 0) red[warp][kk] = t;
+  }
+  unsigned long long bad = warp_sum_u64((unsigned long long)nbad);
+  if (lane == 0 && bad) atomicAdd(&counters[0], bad);
+  __syncthreads();
+  if (threadIdx.x < mk) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+    size_t slot = ((size_t)(P.k_base + threadIdx.x) * P.nblk + blockIdx.x) * 2;
+    partial[slot] = s;
+    partial[slot + 1] = 0.0;
+  }
+}
+
+template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF>
+__global__ void __launch_bounds__(kThreads)
+    sector_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
+                  unsigned long long* __restrict__ counters, const SampleIO sio) {
+  using FT = typename FixT<R>::T;
+  if (sio.count > 0) {
+    sector_sample<R, D, TR, ALPHA, KU, KF>(P, sio);
+    return;
+  }
+  const uint32_t n = (uint32_t)P.n;
+  const int mk = P.m_launch;
+  Acc<R> acc[MC];
+#pragma unroll
+  for (int kk = 0; kk < MC; ++kk) acc[kk].init();
+  unsigned nbad = 0;
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+    uint32_t idx[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
+    for (int s = 0; s < steps; ++s) {
+      FT base[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) base[i] = fix_base<R>(idx[i], P.rc);
+#pragma unroll
+      for (int kk = 0; kk < MC; ++kk) {
+        if (kk < mk) {
+          R v = sector_value<R, D, TR, ALPHA, KU, KF>(P, base, kk);
+          if (P.check_finite) {
+            bool ok = finite_(v);
+            nbad += ok ? 0u : 1u;
+            v = ok ? v : R(0);
+          }
+          acc[kk].add(v);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
+      if constexpr (sizeof(R) == 4) {
+        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+#pragma unroll
+          for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
+        }
+      }
+    }
+  }
+  block_epilogue<R, MC>(acc, mk, nbad, P, partial, counters);
+}
+
+// ------------------------------------------------ separable integrands --
+
+// f = 1, prod (1 + c_i z_i) exp(b_i z_i) or cos(2 pi h.z), runtime d.  The
+// dimension loop is not unrolled: per point and dimension the index comes
+// straight from (j g_i) mod n, shared by the MC shifts of the launch.
+template <typename R, int MC, int TR, int FK>
+struct SepState {
+  R w[MC], prod[MC], lin[MC];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) {
+      w[kk] = R(1);
+      prod[kk] = R(1);
+      lin[kk] = R(0);
+    }
+  }
+  __device__ __forceinline__ void dim(const RuleParams<R>& P, typename FixT<R>::T base, int i, int kk) {
+    R z = coord<R, TR, 0>(base + shift_of(P, kk, i), P.kor, P.alpha, w[kk]);
+    if constexpr (FK == FK_SEPEXP) {
+      prod[kk] *= fma_(P.sep_c[i], z, R(1));
+      lin[kk] = fma_(P.sep_b[i], z, lin[kk]);
+    } else if constexpr (FK == FK_TRIG) {
+      lin[kk] = fma_(P.sep_c[i], z, lin[kk]);
+    }
+  }
+  __device__ __forceinline__ R value(int kk) const {
+    R v;
+    if constexpr (FK == FK_SEPEXP) v = prod[kk] * exp(lin[kk]);
+    else if constexpr (FK == FK_TRIG) v = cospi(R(2) * lin[kk]);
+    else v = R(1);
+    if constexpr (TR == TR_KOROBOV) v *= w[kk];
+    return v;
+  }
+};
+
+template <typename R, int MC, int TR, int FK>
+__global__ void __launch_bounds__(kThreads)
+    separable_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
+                     unsigned long long* __restrict__ counters, const SampleIO sio) {
+  using FT = typename FixT<R>::T;
+  if (sio.count > 0) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sio.count) return;
+    const uint64_t j = sio.j[s];
+    const int k = sio.k[s];
+    R w = R(1), prod = R(1), lin = R(0);
+#pragma unroll 1
+    for (int i = 0; i < P.d; ++i) {
+      uint32_t idx = lattice_index(j, P.g[i], P.n);
+      FT X = fix_base<R>(idx, P.rc) + shift_of(P, k, i);
+      if (sio.idx) sio.idx[(size_t)s * P.d + i] = idx;
+      if (sio.coord) sio.coord[(size_t)s * P.d + i] = coord_used<R>(X);
+      R z = coord<R, TR, 0>(X, P.kor, P.alpha, w);
+      if constexpr (FK == FK_SEPEXP) {
+        prod *= fma_(P.sep_c[i], z, R(1));
+        lin = fma_(P.sep_b[i], z, lin);
+      } else if constexpr (FK == FK_TRIG) {
+        lin = fma_(P.sep_c[i], z, lin);
+      }
+    }
+    R v;
+    if constexpr (FK == FK_SEPEXP) v = prod * exp(lin);
+    else if constexpr (FK == FK_TRIG) v = cospi(R(2) * lin);
+    else v = R(1);
+    if constexpr (TR == TR_KOROBOV) v *= w;
+    sio.values[2 * (size_t)s] = (double)v * P.value_scale;
+    sio.values[2 * (size_t)s + 1] = 0.0;
+    return;
+  }
+  const int mk = P.m_launch;
+  Acc<R> acc[MC];
+#pragma unroll
+  for (int kk = 0; kk < MC; ++kk) acc[kk].init();
+  unsigned nbad = 0;
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+    for (int s = 0; s < steps; ++s) {
+      const uint64_t j = j0 + (uint64_t)s * kThreads;
+      SepState<R, MC, TR, FK> st;
+      st.init();
+#pragma unroll 1
+      for (int i = 0; i < P.d; ++i) {
+        const FT base = fix_base<R>(lattice_index(j, P.g[i], P.n), P.rc);
+#pragma unroll
+        for (int kk = 0; kk < MC; ++kk)
+          if (kk < mk) st.dim(P, base, i, kk);
+      }
+#pragma unroll
+      for (int kk = 0; kk < MC; ++kk) {
+        if (kk < mk) {
+          R v = st.value(kk);
+          if (P.check_finite) {
+            bool ok = finite_(v);
+            nbad += ok ? 0u : 1u;
+            v = ok ? v : R(0);
+          }
+          acc[kk].add(v);
+        }
+      }
+      if constexpr (sizeof(R) == 4) {
+        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+#pragma unroll
+          for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
+        }
+      }
+    }
+  }
+  block_epilogue<R, MC>(acc, mk, nbad, P, partial, counters);
+}
+
+// --------------------------------------------------- general (sparse) --
+
+// Runtime transform for the general kernel (Korobov weight from the params,
+// normalised per factor).
+template <typename R>
+__device__ __forceinline__ R coord_general(const RuleParams<R>& P, typename FixT<R>::T X, R& w) {
+  if (P.tr == TR_BAKER) return coord<R, TR_BAKER, 0>(X, P.kor, 0, w);
+  if (P.tr == TR_KOROBOV) return coord<R, TR_KOROBOV, 0>(X, P.kor, P.alpha, w);
+  return coord<R, TR_NONE, 0>(X, P.kor, 0, w);
+}
+
+// Sparse monomial sum with the point's coordinates in shared memory
+// (z[i * kThreads + threadIdx.x]).
+template <typename R>
+__device__ __forceinline__ R sparse_eval(const SparsePoly<R>& Q, const R* z, int d) {
+  R acc = R(0);
+#pragma unroll 1
+  for (int t = 0; t < Q.nterms; ++t) {
+    R p = Q.coef[t];
+#pragma unroll 1
+    for (int i = 0; i < d; ++i) {
+      const int e = Q.expo[t][i];
+      const R zi = z[i * kThreads + threadIdx.x];
+      for (int q = 0; q < e; ++q) p *= zi;
+    }
+    acc += p;
+  }
+  return acc;
+}
+
+// U^aU F^aF for any degree and d <= QMC_DMAX, everything at run time; the
+// per-thread coordinates and per-shift accumulators live in shared memory.
+template <typename R>
+__device__ __forceinline__ R general_value(const GeneralParams<R>& G, uint64_t j, int k, R* zsh,
+                                           uint64_t* idx_out, double* coord_out) {
+  const RuleParams<R>& P = G.base;
+  R w = R(1);
+#pragma unroll 1
+  for (int i = 0; i < P.d; ++i) {
+    uint32_t idx = lattice_index(j, P.g[i], P.n);
+    typename FixT<R>::T X = fix_base<R>(idx, P.rc) + shift_of(P, k, i);
+    if (idx_out) idx_out[i] = idx;
+    if (coord_out) coord_out[i] = coord_used<R>(X);
+    zsh[i * kThreads + threadIdx.x] = coord_general<R>(P, X, w);
+  }
+  R U = sparse_eval(G.U, zsh, P.d);
+  R F = sparse_eval(G.F, zsh, P.d);
+  return ipow(U, P.aU) * ipow(F, P.aF) * w;
+}
+
+template <typename R, int MC>
+__global__ void __launch_bounds__(kThreads)
+    general_kernel(const __grid_constant__ GeneralParams<R> G, double* __restrict__ partial,
+                   unsigned long long* __restrict__ counters, const SampleIO sio) {
+  __shared__ R zsh[QMC_DMAX * kThreads];
+  const RuleParams<R>& P = G.base;
+  if (sio.count > 0) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sio.count) return;
+    R v = general_value<R>(G, sio.j[s], sio.k[s], zsh, sio.idx ? sio.idx + (size_t)s * P.d : nullptr,
+                           sio.coord ? sio.coord + (size_t)s * P.d : nullptr);
+    sio.values[2 * (size_t)s] = (double)v * P.value_scale;
+    sio.values[2 * (size_t)s + 1] = 0.0;
+    return;
+  }
+  const int mk = P.m_launch;
+  Acc<R> acc[MC];
+#pragma unroll
+  for (int kk = 0; kk < MC; ++kk) acc[kk].init();
+  unsigned nbad = 0;
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+    for (int s = 0; s < steps; ++s) {
+      const uint64_t j = j0 + (uint64_t)s * kThreads;
+#pragma unroll
+      for (int kk = 0; kk < MC; ++kk) {
+        if (kk < mk) {
+          R v = general_value<R>(G, j, kk, zsh, nullptr, nullptr);
+          if (P.check_finite) {
+            bool ok = finite_(v);
+            nbad += ok ? 0u : 1u;
+            v = ok ? v : R(0);
+          }
+          acc[kk].add(v);
+        }
+      }
+      if constexpr (sizeof(R) == 4) {
+        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+#pragma unroll
+          for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
+        }
+      }
+    }
+  }
+  block_epilogue<R, MC>(acc, mk, nbad, P, partial, counters);
+}
+
+}  // namespace qmc

@@ -15,6 +15,10 @@ Readings of the workloads (the paper fixes none of these draws):
     polynomials keep a nonzero constant after the monomial factors are pulled
     out (Sec. 2: sector functions are smooth on the closed cube), hence c0.
   * Draw order per problem: sizes, coefficients, variable indices, shifts.
+  * Polynomial coefficients are rounded to the nearest float32 when drawn, so
+    an FP32 evaluation and an FP64 evaluation integrate the identical
+    integrand (rounding coefficients inside an FP32 kernel would otherwise
+    move the integral by ~1e-7 relative).
 """
 from __future__ import annotations
 
@@ -46,6 +50,10 @@ class SplitMix64:
 
     def uniform_in(self, lo: float, hi: float) -> float:
         return lo + (hi - lo) * self.uniform()
+
+    def uniform_f32(self, lo: float, hi: float) -> float:
+        """uniform_in rounded to the nearest float32 (exactly representable in both precisions)."""
+        return float(np.float32(self.uniform_in(lo, hi)))
 
     def randint(self, lo: int, hi: int) -> int:
         """Integer uniform on [lo, hi] inclusive."""
@@ -169,9 +177,9 @@ def random_poly(rng: SplitMix64, d: int, n_lin: int, n_quad: int, coef_lo=0.1, c
                 neg_quad: int = 0, neg_lo=-2.0, neg_hi=-0.5) -> Poly:
     """c0 + n_lin degree-1 monomials + n_quad degree-2 monomials.  The first
     `neg_quad` degree-2 coefficients are drawn from U(neg_lo, neg_hi)."""
-    c0 = rng.uniform_in(coef_lo, coef_hi)
-    lin_c = [rng.uniform_in(coef_lo, coef_hi) for _ in range(n_lin)]
-    quad_c = [rng.uniform_in(neg_lo, neg_hi) if t < neg_quad else rng.uniform_in(coef_lo, coef_hi)
+    c0 = rng.uniform_f32(coef_lo, coef_hi)
+    lin_c = [rng.uniform_f32(coef_lo, coef_hi) for _ in range(n_lin)]
+    quad_c = [rng.uniform_f32(neg_lo, neg_hi) if t < neg_quad else rng.uniform_f32(coef_lo, coef_hi)
               for t in range(n_quad)]
     lin_v = draw_indices(rng, d, n_lin)
     pairs = pair_list(d)

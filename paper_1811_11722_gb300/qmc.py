@@ -1,0 +1,345 @@
+"""ctypes binding of libqmc_gb300.so (include/qmc.h), argument marshalling only.
+
+Every function keeps the C name and forwards to the library; all arithmetic of
+the rule runs in the CUDA library.  Loading fails loudly when the library has
+not been built (``python -m paper_1811_11722_gb300.build``): there is no CPU
+fallback.
+
+Host inputs are numpy arrays.  Results may go to host memory (a qmc_result
+returned here) or to device memory given as an integer address, e.g. a torch
+CUDA tensor's ``data_ptr()``; streams are passed as integer handles, e.g.
+``torch.cuda.current_stream().cuda_stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqmc_gb300.so")
+
+QMC_DMAX = 16
+QMC_OK, QMC_EINVAL, QMC_ENOMEM, QMC_ECUDA = 0, -1, -2, -3
+QMC_ENONFINITE, QMC_ETIMEOUT, QMC_EDEFORM, QMC_EUNSUPPORTED = -4, -5, -6, -7
+QMC_TRANSFORM_NONE, QMC_TRANSFORM_KOROBOV, QMC_TRANSFORM_BAKER = 0, 1, 2
+QMC_F_CONST, QMC_F_SEPARABLE_EXP, QMC_F_SECTOR, QMC_F_SECTOR_DEFORMED, QMC_F_TRIG = 0, 1, 2, 3, 4
+QMC_FP64, QMC_FP32EVAL = 0, 1
+
+STATUS_NAMES = {0: "QMC_OK", -1: "QMC_EINVAL", -2: "QMC_ENOMEM", -3: "QMC_ECUDA", -4: "QMC_ENONFINITE",
+                -5: "QMC_ETIMEOUT", -6: "QMC_EDEFORM", -7: "QMC_EUNSUPPORTED"}
+WARNINGS = (QMC_ENONFINITE, QMC_EDEFORM)
+
+
+class QmcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class qmc_transform(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("alpha", ctypes.c_int32)]
+
+
+class qmc_poly(ctypes.Structure):
+    _fields_ = [("nterms", ctypes.c_int32), ("coef", ctypes.c_void_p), ("expo", ctypes.c_void_p)]
+
+
+class qmc_integrand(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("d", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("U", qmc_poly), ("F", qmc_poly), ("aU", ctypes.c_int32), ("aF", ctypes.c_int32),
+                ("lam", ctypes.c_double), ("c", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("h", ctypes.c_void_p)]
+
+
+class qmc_result(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double * 2), ("var", ctypes.c_double * 2), ("err", ctypes.c_double * 2),
+                ("nonfinite", ctypes.c_uint64), ("deform_violations", ctypes.c_uint64),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"mean": np.array(self.mean[:]), "var": np.array(self.var[:]), "err": np.array(self.err[:]),
+                "nonfinite": int(self.nonfinite), "deform_violations": int(self.deform_violations),
+                "status": int(self.status)}
+
+
+class qmc_problem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("m", ctypes.c_int32), ("n", ctypes.c_uint64), ("g", ctypes.c_void_p),
+                ("shifts", ctypes.c_void_p), ("t", qmc_transform), ("f", ctypes.POINTER(qmc_integrand))]
+
+
+RESULT_BYTES = ctypes.sizeof(qmc_result)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libqmc_gb300.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1811_11722_gb300.build` "
+                                  "(the rule has no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+            P_int = ctypes.POINTER(qmc_integrand)
+            L.qmc_make_lattice.argtypes = [i32, u64, vp, vp]
+            L.qmc_integrate.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, vp, vp, vp]
+            L.qmc_plan_create.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, ctypes.POINTER(vp)]
+            L.qmc_plan_execute.argtypes = [vp, vp, vp, vp]
+            L.qmc_plan_destroy.argtypes = [vp]
+            L.qmc_plan_launches.argtypes = [vp, ctypes.POINTER(i32)]
+            L.qmc_plan_record_events.argtypes = [vp, vp, vp]
+            L.qmc_integrate_batch.argtypes = [i32, vp, vp, vp, vp]
+            L.qmc_batch_plan_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
+            L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
+            L.qmc_batch_plan_destroy.argtypes = [vp]
+            L.qmc_sample_points.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, i32, vp, vp, vp, vp, vp, vp]
+            L.qmc_last_error.restype = ctypes.c_char_p
+            L.qmc_version.restype = i32
+            for name in ("qmc_make_lattice", "qmc_integrate", "qmc_plan_create", "qmc_plan_execute",
+                         "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_integrate_batch", "qmc_batch_plan_create",
+                         "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_sample_points"):
+                getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def qmc_last_error() -> str:
+    return lib().qmc_last_error().decode()
+
+
+def qmc_version() -> int:
+    return int(lib().qmc_version())
+
+
+def _check(rc: int, allow_warnings: bool = False) -> int:
+    if rc == QMC_OK or (allow_warnings and rc in WARNINGS):
+        return rc
+    raise QmcError(rc, qmc_last_error())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _addr(x):
+    """Device/host address: an int, a numpy array, or an object with data_ptr()."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return _ptr(x)
+
+
+# ------------------------------------------------------------- descriptors --
+
+class Integrand:
+    """Owns the numpy arrays behind a qmc_integrand (keep it alive across calls)."""
+
+    def __init__(self, kind: int, d: int, precision: int = QMC_FP64, U=None, F=None, aU: int = -2, aF: int = -1,
+                 lam: float = 0.0, c=None, b=None, h=None):
+        self._keep = []
+        s = qmc_integrand()
+        s.kind, s.d, s.precision = kind, d, precision
+        s.aU, s.aF, s.lam = aU, aF, float(lam)
+
+        def arr(x, dt):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+            self._keep.append(a)
+            return a
+
+        for name, poly in (("U", U), ("F", F)):
+            if poly is not None:
+                coef, expo = poly
+                ca, ea = arr(coef, np.float64), arr(expo, np.uint8)
+                setattr(s, name, qmc_poly(ca.shape[0], _ptr(ca), _ptr(ea)))
+        s.c = _ptr(arr(c, np.float64))
+        s.b = _ptr(arr(b, np.float64))
+        s.h = _ptr(arr(h, np.int32))
+        self.s = s
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def transform(kind: str, alpha: int = 0) -> qmc_transform:
+    k = {"none": QMC_TRANSFORM_NONE, "korobov": QMC_TRANSFORM_KOROBOV, "baker": QMC_TRANSFORM_BAKER}[kind]
+    return qmc_transform(k, alpha)
+
+
+def integrand_from_problem(p, precision: str | None = None) -> Integrand:
+    """Integrand descriptor from a paper_1811_11722_gb300.inputs.Problem."""
+    prec = {"fp64": QMC_FP64, "fp32": QMC_FP32EVAL}[precision or p.precision]
+    kind = {"const": QMC_F_CONST, "separable_exp": QMC_F_SEPARABLE_EXP, "sector": QMC_F_SECTOR,
+            "sector_deformed": QMC_F_SECTOR_DEFORMED, "trig": QMC_F_TRIG}[p.kind]
+    U = (p.U.coef, p.U.expo) if p.U is not None else None
+    F = (p.F.coef, p.F.expo) if p.F is not None else None
+    return Integrand(kind, p.d, prec, U, F, p.aU, p.aF, p.lam, p.c, p.b, p.h)
+
+
+# --------------------------------------------------------------- functions --
+
+def qmc_make_lattice(d: int, n: int, gamma) -> np.ndarray:
+    gamma = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+    g = np.zeros(d, dtype=np.uint64)
+    _check(lib().qmc_make_lattice(d, n, _ptr(gamma), _ptr(g)))
+    return g
+
+
+def qmc_integrate(d, n, m, g, shifts, t: qmc_transform, f: Integrand, out=None, per_shift=None, stream=0,
+                  want_per_shift=False):
+    """Returns (qmc_result, per_shift ndarray or None) for host outputs; with a
+    device `out` address the call is asynchronous and returns (None, None)."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    if out is None:
+        res = qmc_result()
+        ps = np.zeros(2 * m) if (want_per_shift and per_shift is None) else per_shift
+        rc = lib().qmc_integrate(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(res), _addr(ps),
+                                 ctypes.c_void_p(stream))
+        _check(rc, allow_warnings=True)
+        return res, (ps.reshape(m, 2) if isinstance(ps, np.ndarray) else None)
+    rc = lib().qmc_integrate(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, _addr(out), _addr(per_shift),
+                             ctypes.c_void_p(stream))
+    _check(rc, allow_warnings=True)
+    return None, None
+
+
+class Plan:
+    """qmc_plan_create / qmc_plan_execute / qmc_plan_destroy."""
+
+    def __init__(self, d, n, m, g, shifts, t: qmc_transform, f: Integrand):
+        self.m = m
+        self._f = f
+        g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+        shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+        h = ctypes.c_void_p()
+        _check(lib().qmc_plan_create(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(h)))
+        self.h = h
+
+    def execute(self, out=None, per_shift=None, stream=0):
+        if out is None:
+            res = qmc_result()
+            rc = lib().qmc_plan_execute(self.h, ctypes.byref(res), _addr(per_shift), ctypes.c_void_p(stream))
+            _check(rc, allow_warnings=True)
+            return res
+        _check(lib().qmc_plan_execute(self.h, _addr(out), _addr(per_shift), ctypes.c_void_p(stream)),
+               allow_warnings=True)
+        return None
+
+    def record_events(self, before_rule=None, after_rule=None):
+        """cudaEvent_t handles (ints) recorded around the rule kernels of later executes."""
+        _check(lib().qmc_plan_record_events(self.h, ctypes.c_void_p(before_rule or 0),
+                                            ctypes.c_void_p(after_rule or 0)))
+
+    def launches(self) -> int:
+        v = ctypes.c_int32(0)
+        _check(lib().qmc_plan_launches(self.h, ctypes.byref(v)))
+        return int(v.value)
+
+    def destroy(self):
+        if self.h:
+            lib().qmc_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def qmc_plan_create(d, n, m, g, shifts, t, f) -> Plan:
+    return Plan(d, n, m, g, shifts, t, f)
+
+
+def qmc_plan_execute(plan: Plan, out=None, per_shift=None, stream=0):
+    return plan.execute(out, per_shift, stream)
+
+
+def qmc_plan_destroy(plan: Plan):
+    plan.destroy()
+
+
+class _Batch:
+    """Marshalled qmc_problem array (keeps every referenced array alive)."""
+
+    def __init__(self, problems):
+        """problems: list of (d, n, m, g, shifts, qmc_transform, Integrand)."""
+        self.keep = []
+        self.arr = (qmc_problem * len(problems))()
+        self.total_m = 0
+        for i, (d, n, m, g, shifts, t, f) in enumerate(problems):
+            g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+            sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+            self.keep += [g, sh, f]
+            self.arr[i] = qmc_problem(d, m, n, _ptr(g), _ptr(sh), t, ctypes.pointer(f.s))
+            self.total_m += m
+        self.count = len(problems)
+
+
+def qmc_integrate_batch(problems, stream=0, want_per_shift=False):
+    b = _Batch(problems)
+    res = (qmc_result * b.count)()
+    ps = np.zeros(2 * b.total_m) if want_per_shift else None
+    rc = lib().qmc_integrate_batch(b.count, ctypes.cast(b.arr, ctypes.c_void_p), ctypes.cast(res, ctypes.c_void_p),
+                                   _ptr(ps), ctypes.c_void_p(stream))
+    _check(rc, allow_warnings=True)
+    return list(res), ps
+
+
+class BatchPlan:
+    """qmc_batch_plan_create / _execute / _destroy."""
+
+    def __init__(self, problems):
+        self.b = _Batch(problems)
+        h = ctypes.c_void_p()
+        _check(lib().qmc_batch_plan_create(self.b.count, ctypes.cast(self.b.arr, ctypes.c_void_p), ctypes.byref(h)))
+        self.h = h
+
+    def execute(self, out=None, per_shift=None, stream=0):
+        if out is None:
+            res = (qmc_result * self.b.count)()
+            rc = lib().qmc_batch_plan_execute(self.h, ctypes.cast(res, ctypes.c_void_p), _addr(per_shift),
+                                              ctypes.c_void_p(stream))
+            _check(rc, allow_warnings=True)
+            return list(res)
+        _check(lib().qmc_batch_plan_execute(self.h, _addr(out), _addr(per_shift), ctypes.c_void_p(stream)),
+               allow_warnings=True)
+        return None
+
+    def destroy(self):
+        if self.h:
+            lib().qmc_batch_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def qmc_sample_points(d, n, m, g, shifts, t, f: Integrand, j, k, want_idx=True, want_coord=True, stream=0):
+    """Returns (values[count, 2], idx[count, d] or None, coord[count, d] or None)."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    j = np.ascontiguousarray(np.asarray(j, dtype=np.uint64))
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.int32))
+    cnt = j.shape[0]
+    vals = np.zeros((cnt, 2))
+    idx = np.zeros((cnt, d), dtype=np.uint64) if want_idx else None
+    crd = np.zeros((cnt, d)) if want_coord else None
+    _check(lib().qmc_sample_points(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, cnt, _ptr(j), _ptr(k), _ptr(vals),
+                                   _ptr(idx), _ptr(crd), ctypes.c_void_p(stream)))
+    return vals, idx, crd

@@ -1,0 +1,125 @@
+"""Host-only checks of the C ABI: the library loads, exports every function
+include/qmc.h declares, the binding's structs match the header's sizes, and
+argument validation rejects bad input before any device work.  The CBC
+generating-vector search is host code and is compared with the oracle here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1811_11722_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qmc.h")
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_1811_11722_gb300 import build, qmc
+    build.build_library()
+    qmc.lib()
+    return qmc
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(qmc_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("qmc_make_lattice", "qmc_integrate", "qmc_integrate_batch", "qmc_plan_create", "qmc_plan_execute",
+              "qmc_plan_destroy", "qmc_sample_points", "qmc_last_error", "qmc_version"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(Q):
+    L = Q.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    # the symbol table itself (not only dlsym through ctypes)
+    out = os.popen(f"nm -D --defined-only {Q.LIB_PATH}").read()
+    for name in declared_functions():
+        assert re.search(rf"\bT {name}\b", out), name
+
+
+def test_struct_layouts(Q):
+    assert ctypes.sizeof(Q.qmc_transform) == 8
+    assert ctypes.sizeof(Q.qmc_poly) == 24
+    assert ctypes.sizeof(Q.qmc_result) == 72
+    assert ctypes.sizeof(Q.qmc_integrand) == 4 * 3 + 4 + 2 * 24 + 8 + 8 + 3 * 8
+    assert Q.qmc_version() >= 100
+
+
+def _sector(Q, d=3, n=101, m=4):
+    p = I.config2(n=n, m=m)
+    return p
+
+
+@pytest.mark.parametrize("case", ["m1", "g0", "gn", "shift1", "d0", "d17", "nbig", "dmismatch", "alpha7",
+                                  "kind", "nterms0", "deg4"])
+def test_validation_rejects_bad_arguments(Q, case):
+    """Bad arguments return QMC_EINVAL without touching the GPU."""
+    d, n, m = 3, 101, 4
+    g = np.array([1, 5, 7], dtype=np.uint64)
+    shifts = np.full((m, d), 0.25)
+    t = Q.transform("baker")
+    coef = np.array([1.0, 0.5])
+    expo = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.uint8)
+    f = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP64, (coef, expo), (coef, expo))
+    if case == "m1":
+        m, shifts = 1, shifts[:1]
+    elif case == "g0":
+        g[1] = 0
+    elif case == "gn":
+        g[2] = n
+    elif case == "shift1":
+        shifts[2, 1] = 1.0
+    elif case == "d0":
+        d = 0
+    elif case == "d17":
+        d = 17
+    elif case == "nbig":
+        n = 1 << 31
+    elif case == "dmismatch":
+        f = Q.Integrand(Q.QMC_F_SECTOR, 2, Q.QMC_FP64, (coef, expo[:, :2]), (coef, expo[:, :2]))
+    elif case == "alpha7":
+        t = Q.transform("korobov", 7)
+    elif case == "kind":
+        f = Q.Integrand(9, d)
+    elif case == "nterms0":
+        f = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP64, (coef[:0], expo[:0]), (coef, expo))
+    elif case == "deg4":
+        f = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP64, (coef, np.array([[0, 0, 0], [4, 0, 0]], np.uint8)),
+                        (coef, expo))
+    with pytest.raises(Q.QmcError) as ei:
+        Q.qmc_integrate(d, n, m, g, shifts, t, f)
+    assert ei.value.status == Q.QMC_EINVAL
+    assert Q.qmc_last_error() != ""
+
+
+def test_make_lattice_rejects_composite(Q):
+    with pytest.raises(Q.QmcError):
+        Q.qmc_make_lattice(3, 1001, [1.0, 0.25, 1 / 9])
+    with pytest.raises(Q.QmcError):
+        Q.qmc_make_lattice(0, 101, [1.0])
+
+
+@pytest.mark.parametrize("n", [31, 101, 1009, 10007, 65537])
+def test_make_lattice_matches_oracle_cbc(Q, oracle_lib, n):
+    """Host CBC of the library against the oracle's plain CBC (n <= 1e4) or the
+    oracle's numpy fast CBC, judged by the worst-case error they reach."""
+    from oracle.cbc import cbc_fast
+    d = 6
+    gam = I.product_weights(d)
+    g = Q.qmc_make_lattice(d, n, gam)
+    ref = oracle_lib.cbc_plain(d, n, gam) if n <= 10007 else cbc_fast(d, n, gam)
+    assert g[0] == 1 and np.all((g >= 1) & (g <= (n - 1) // 2))
+    e_lib = oracle_lib.cbc_error(d, n, g, gam)
+    e_ref = oracle_lib.cbc_error(d, n, ref, gam)
+    assert abs(e_lib - e_ref) <= 1e-12 * e_ref
+    if n >= 101:
+        assert np.array_equal(g, ref)

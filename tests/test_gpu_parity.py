@@ -1,0 +1,369 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Tolerances
+  * lattice indices: bit-exact.
+  * FP64 path: per-shift Q^(k) and Qbar within 1e-12 relative; the error
+    estimate within 2e-12 |Qbar| absolute (sigma is a difference of nearly
+    equal numbers, so its own relative error is not meaningful).
+  * FP32EVAL path: the per-point value carries O(10) float roundings
+    (coordinate 2^-24, transform, polynomial, reciprocal), bounded here by
+    64 * 2^-24 ~ 4e-6 relative per point; the per-shift sums are compensated
+    and promoted to FP64, so Q^(k) differs from the oracle by the average of
+    those per-point errors, bounded (worst case, fully correlated) by the same
+    4e-6 and typically ~1e-7/sqrt(n).  Tests use 4e-6 for single points and
+    2e-7 relative for Q^(k) at n >= 1e4.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1811_11722_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_1811_11722_gb300 import build, qmc
+    build.build_library()
+    return qmc
+
+
+@pytest.fixture(scope="module")
+def lattices():
+    import json
+    return {int(k): np.array(v, dtype=np.uint64) for k, v in
+            json.load(open(os.path.join(HERE, "golden", "lattices.json")))["g"].items()}
+
+
+def gvec(lattices, p):
+    if p.n in lattices and p.d <= len(lattices[p.n]):
+        return lattices[p.n][: p.d]
+    return I.random_generating_vector(I.SplitMix64(p.n + p.d), p.d, p.n)
+
+
+def gpu_run(Q, p, g, precision=None):
+    f = Q.integrand_from_problem(p, precision)
+    t = Q.transform(p.transform, p.alpha)
+    res, ps = Q.qmc_integrate(p.d, p.n, p.m, g, p.shifts, t, f, want_per_shift=True)
+    return res.as_dict(), ps
+
+
+def assert_fp64_parity(gpu, ps, ref):
+    q_ref = ref["q"]
+    scale = np.max(np.abs(q_ref[:, 0])) + 1e-300
+    assert np.all(np.abs(ps[:, 0] - q_ref[:, 0]) <= 1e-12 * np.abs(q_ref[:, 0]) + 1e-15 * scale)
+    assert abs(gpu["mean"][0] - ref["mean"][0]) <= 1e-12 * abs(ref["mean"][0]) + 1e-300
+    assert abs(gpu["err"][0] - ref["err"][0]) <= 2e-12 * abs(ref["mean"][0]) + 1e-300
+
+
+# ------------------------------------------------------------ single points --
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("transform,alpha", [("baker", 0), ("korobov", 3), ("none", 0)])
+def test_points_sector_d6(Q, oracle_lib, lattices, precision, transform, alpha):
+    """Indices bit-exact; coordinates within 2^-52 (FP64) or 2^-23 (FP32) of
+    the oracle's; weighted values within 1e-13 / 4e-6 relative, plus, for the
+    Korobov weight prod (s_i (1 - s_i))^3 with s_i = min(x_i, 1 - x_i), the
+    propagated coordinate error 3 * 2 * dx / s_i per dimension (the weight's
+    relative sensitivity near the cube's boundary)."""
+    p = I.config2(n=16777213, m=32)
+    p.transform, p.alpha = transform, alpha
+    g = gvec(lattices, p)
+    rng = np.random.default_rng(3)
+    js = np.concatenate([[0, 1, 2, p.n - 1, p.n - 2], rng.integers(0, p.n, 200)]).astype(np.uint64)
+    ks = np.concatenate([[0, 31, 5, 17, 31], rng.integers(0, p.m, 200)]).astype(np.int32)
+    vals, idx, crd = Q.qmc_sample_points(p.d, p.n, p.m, g, p.shifts, Q.transform(transform, alpha),
+                                         Q.integrand_from_problem(p, precision), js, ks)
+    ctol = 2.0 ** -52 if precision == "fp64" else 2.0 ** -23
+    vtol = 1e-13 if precision == "fp64" else 4e-6
+    for s in range(len(js)):
+        v, oi, ox, _, _ = oracle_lib.point(p, g, int(ks[s]), int(js[s]))
+        assert np.array_equal(idx[s], oi)
+        dx = np.abs(crd[s] - ox)
+        dx = np.minimum(dx, 1.0 - dx)  # coordinates live on the torus
+        assert np.all(dx <= ctol), (s, crd[s], ox)
+        rel = vtol
+        if transform == "korobov":
+            sdist = np.minimum(ox, 1.0 - ox)
+            rel += float(np.sum(6.0 * ctol / np.maximum(sdist, 1e-300)))
+        assert abs(vals[s, 0] - v[0]) <= rel * abs(v[0]) + 1e-300, (s, vals[s, 0], v[0])
+
+
+def test_points_general_kernel_degree3(Q, oracle_lib):
+    """Degree-3 F (the Zbb vertex polynomial of Eq. 11 plus a constant) in d = 6
+    goes through the general sparse kernel; values match the oracle."""
+    F = I.zbb_vertex_F()
+    F = I.Poly(np.concatenate([[4.0], F.coef]), np.vstack([np.zeros((1, 6), np.uint8), F.expo]))
+    U = I.random_poly(I.SplitMix64(5), 6, 6, 0)
+    rng = I.SplitMix64(6)
+    p = I.Problem("zbb", 6, 100003, 4, I.make_shifts(rng, 4, 6), "korobov", alpha=2, kind="sector", U=U, F=F)
+    g = I.random_generating_vector(rng, 6, p.n)
+    js = np.arange(0, 100003, 997, dtype=np.uint64)
+    ks = (np.arange(len(js)) % 4).astype(np.int32)
+    vals, idx, _ = Q.qmc_sample_points(p.d, p.n, p.m, g, p.shifts, Q.transform("korobov", 2),
+                                       Q.integrand_from_problem(p, "fp64"), js, ks)
+    for s in range(len(js)):
+        v, oi, _, _, _ = oracle_lib.point(p, g, int(ks[s]), int(js[s]))
+        assert np.array_equal(idx[s], oi)
+        assert abs(vals[s, 0] - v[0]) <= 1e-12 * abs(v[0]) + 1e-14
+
+
+# --------------------------------------------------------------- whole rule --
+
+def test_config1_fp64(Q, oracle_lib, lattices):
+    """Configuration 1 as specified: d=3 separable exp, Korobov 3, n=10007, m=10."""
+    p = I.config1()
+    g = gvec(lattices, p)
+    gpu, ps = gpu_run(Q, p, g)
+    ref = oracle_lib.integrate(p, g)
+    assert gpu["status"] == 0
+    assert_fp64_parity(gpu, ps, ref)
+
+
+@pytest.mark.parametrize("transform,alpha", [("baker", 0), ("korobov", 3), ("none", 0)])
+def test_sector_d6_fp64_several_tiles(Q, oracle_lib, nthreads, transform, alpha):
+    """d=6 sector, n = 100003 (many tiles, ragged tail), m = 20 (two shift chunks)."""
+    p = I.config2(n=100003, m=20, precision="fp64")
+    p.transform, p.alpha = transform, alpha
+    g = I.random_generating_vector(I.SplitMix64(7), 6, p.n)
+    gpu, ps = gpu_run(Q, p, g)
+    ref = oracle_lib.integrate(p, g, nthreads=nthreads)
+    assert_fp64_parity(gpu, ps, ref)
+
+
+@pytest.mark.parametrize("transform,alpha", [("baker", 0), ("korobov", 3)])
+def test_sector_d6_fp32(Q, oracle_lib, nthreads, transform, alpha):
+    p = I.config2(n=100003, m=32)
+    p.transform, p.alpha = transform, alpha
+    g = I.random_generating_vector(I.SplitMix64(8), 6, p.n)
+    gpu, ps = gpu_run(Q, p, g, "fp32")
+    ref = oracle_lib.integrate(p, g, nthreads=nthreads)
+    assert np.all(np.abs(ps[:, 0] - ref["q"][:, 0]) <= 2e-7 * np.abs(ref["q"][:, 0]))
+    assert abs(gpu["mean"][0] - ref["mean"][0]) <= 2e-7 * abs(ref["mean"][0])
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 7, 8])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sector_all_dims(Q, oracle_lib, d, precision):
+    """Every specialised dimension, with both shift-chunk paths (m = 10)."""
+    rng = I.SplitMix64(100 + d)
+    U = I.random_poly(rng, d, d, 0)
+    F = I.random_poly(rng, d, 0, d * (d + 1) // 2)
+    p = I.Problem("sec", d, 20011, 10, I.make_shifts(rng, 10, d), "korobov", alpha=3, kind="sector", U=U, F=F)
+    g = I.random_generating_vector(rng, d, p.n)
+    gpu, ps = gpu_run(Q, p, g, precision)
+    ref = oracle_lib.integrate(p, g)
+    if precision == "fp64":
+        assert_fp64_parity(gpu, ps, ref)
+    else:
+        assert np.all(np.abs(ps[:, 0] - ref["q"][:, 0]) <= 4e-7 * np.abs(ref["q"][:, 0]))
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 4, 5, 6])
+def test_korobov_weights_general(Q, oracle_lib, alpha):
+    """Korobov weights other than 3 (general kernel for sectors, runtime weight
+    for separable integrands)."""
+    p = I.config2(n=30011, m=6, precision="fp64")
+    p.transform, p.alpha = "korobov", alpha
+    g = I.random_generating_vector(I.SplitMix64(alpha), 6, p.n)
+    gpu, ps = gpu_run(Q, p, g)
+    ref = oracle_lib.integrate(p, g, nthreads=4)
+    assert_fp64_parity(gpu, ps, ref)
+    c = I.config1(n=30011, m=6)
+    c.alpha = alpha
+    gpu, ps = gpu_run(Q, c, g[:3])
+    assert_fp64_parity(gpu, ps, oracle_lib.integrate(c, g[:3]))
+
+
+def test_large_d_general_kernel(Q, oracle_lib):
+    """d = 12 > 8 sector (general kernel) and d = 16 separable."""
+    rng = I.SplitMix64(12)
+    U = I.random_poly(rng, 12, 12, 0)
+    F = I.random_poly(rng, 12, 0, 20)
+    p = I.Problem("d12", 12, 10007, 3, I.make_shifts(rng, 3, 12), "baker", kind="sector", U=U, F=F)
+    g = I.random_generating_vector(rng, 12, p.n)
+    for prec in ("fp64", "fp32"):
+        gpu, ps = gpu_run(Q, p, g, prec)
+        ref = oracle_lib.integrate(p, g)
+        if prec == "fp64":
+            assert_fp64_parity(gpu, ps, ref)
+        else:
+            assert np.all(np.abs(ps[:, 0] - ref["q"][:, 0]) <= 4e-7 * np.abs(ref["q"][:, 0]))
+    c = I.Problem("sep16", 16, 10007, 4, I.make_shifts(rng, 4, 16), "korobov", alpha=6, kind="separable_exp",
+                  c=np.linspace(0.1, 0.9, 16), b=np.linspace(0.9, 0.1, 16))
+    g16 = I.random_generating_vector(rng, 16, c.n)
+    gpu, ps = gpu_run(Q, c, g16)
+    assert_fp64_parity(gpu, ps, oracle_lib.integrate(c, g16))
+
+
+# ------------------------------------------------------------- pinned cases --
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_constant_baker_exact_on_gpu(Q, precision):
+    """Sec. 2 / Fig. 3 text: baker on the constant has zero error for any lattice."""
+    for d in (6, 9, 10):
+        rng = I.SplitMix64(d)
+        p = I.Problem("c", d, 100003, 5, I.make_shifts(rng, 5, d), "baker", kind="const")
+        g = I.random_generating_vector(rng, d, p.n)
+        gpu, ps = gpu_run(Q, p, g, precision)
+        assert np.all(ps[:, 0] == 1.0) and gpu["var"][0] == 0.0
+
+
+def test_dual_lattice_trig_on_gpu(Q):
+    """Eq. (2) on cos(2 pi h.x): cos(2 pi h.Delta_k) on the dual lattice, else 0."""
+    n, g = 101, np.array([1, 39, 17], dtype=np.uint64)
+    sh = I.make_shifts(I.SplitMix64(9), 4, 3)
+    for h in ([-39, 1, 0], [17, 0, -1], [1, 1, 0], [3, -2, 5]):
+        h = np.array(h, dtype=np.int32)
+        p = I.Problem("trig", 3, n, 4, sh, "none", kind="trig", h=h)
+        gpu, ps = gpu_run(Q, p, g)
+        dual = int(np.dot(h.astype(np.int64), g.astype(np.int64))) % n == 0
+        want = np.array([math.cos(2 * math.pi * float(np.dot(h, sh[k]))) if dual else 0.0 for k in range(4)])
+        assert np.all(np.abs(ps[:, 0] - want) < 1e-13)
+
+
+# ---------------------------------------------------------------- edge cases --
+
+@pytest.mark.parametrize("n,d,m", [(2, 1, 2), (3, 2, 2), (257, 3, 33), (65537, 2, 40), (1021, 8, 64)])
+def test_edge_sizes(Q, oracle_lib, n, d, m):
+    """Smallest lattices, m = 2, m above one launch chunk, ragged tails."""
+    rng = I.SplitMix64(n + d + m)
+    U = I.random_poly(rng, d, d, 0)
+    F = I.random_poly(rng, d, 0, max(1, d))
+    p = I.Problem("edge", d, n, m, I.make_shifts(rng, m, d), "baker", kind="sector", U=U, F=F)
+    g = np.array([1] + [rng.randint(1, n - 1) for _ in range(d - 1)], dtype=np.uint64)
+    gpu, ps = gpu_run(Q, p, g, "fp64")
+    assert_fp64_parity(gpu, ps, oracle_lib.integrate(p, g))
+
+
+def test_nonfinite_values_counted(Q, oracle_lib):
+    """F without a constant term vanishes at z = 0: 1/F is infinite there.  Both
+    sides leave those points out and count them."""
+    d, n, m = 2, 1009, 3
+    U = I.Poly(np.array([1.0]), np.zeros((1, d), np.uint8))
+    F = I.Poly(np.array([1.0, 1.0]), np.array([[1, 0], [0, 1]], np.uint8))
+    sh = np.zeros((m, d))
+    sh[1] = [0.5, 0.25]
+    p = I.Problem("nf", d, n, m, sh, "baker", kind="sector", U=U, F=F, aU=-2, aF=-1)
+    g = np.array([1, 17], dtype=np.uint64)
+    gpu, ps = gpu_run(Q, p, g, "fp64")
+    ref = oracle_lib.integrate(p, g)
+    assert int(ref["nonfinite"].sum()) > 0
+    assert gpu["nonfinite"] == int(ref["nonfinite"].sum())
+    assert gpu["status"] == Q.QMC_ENONFINITE
+    assert np.allclose(ps[:, 0], ref["q"][:, 0], rtol=1e-12)
+
+
+def test_bit_reproducible(Q, lattices):
+    p = I.config2(n=1000003, m=32)
+    g = I.random_generating_vector(I.SplitMix64(1), 6, p.n)
+    a, pa = gpu_run(Q, p, g, "fp32")
+    b, pb = gpu_run(Q, p, g, "fp32")
+    assert np.array_equal(pa, pb) and a["mean"][0] == b["mean"][0] and a["var"][0] == b["var"][0]
+
+
+def test_plan_device_output_matches_host(Q):
+    torch = pytest.importorskip("torch")
+    p = I.config2(n=1000003, m=32)
+    g = I.random_generating_vector(I.SplitMix64(2), 6, p.n)
+    f = Q.integrand_from_problem(p, "fp32")
+    t = Q.transform("baker")
+    plan = Q.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
+    host = plan.execute().as_dict()
+    out = torch.zeros(Q.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    per = torch.zeros(2 * p.m, dtype=torch.float64, device="cuda")
+    plan.execute(out=out, per_shift=per, stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    r = Q.qmc_result.from_buffer_copy(out.cpu().numpy().tobytes()).as_dict()
+    assert r["mean"][0] == host["mean"][0] and r["var"][0] == host["var"][0]
+    assert plan.launches() == 2
+    plan.destroy()
+
+
+# ------------------------------------------------------------------ full size --
+
+def test_config2_full_size_fp32_vs_oracle(Q, oracle_lib, lattices, nthreads):
+    """The benchmark workload (d=6, n=16777213, m=32, baker, FP32EVAL) against the
+    oracle over the whole lattice on all host cores."""
+    p = I.config2()
+    g = gvec(lattices, p)
+    gpu, ps = gpu_run(Q, p, g, "fp32")
+    ref = oracle_lib.integrate(p, g, nthreads=nthreads)
+    assert np.all(np.abs(ps[:, 0] - ref["q"][:, 0]) <= 2e-7 * np.abs(ref["q"][:, 0]))
+    assert abs(gpu["mean"][0] - ref["mean"][0]) <= 2e-7 * abs(ref["mean"][0])
+    g64, ps64 = gpu_run(Q, p, g, "fp64")
+    assert_fp64_parity(g64, ps64, ref)
+
+
+# -------------------------------------------------------- deformed (complex) --
+
+def _c4(n=100003, m=20, lam=0.1):
+    return I.config4(n=n, m=m, lam=lam)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_points_deformed_d5(Q, oracle_lib, precision):
+    """Configuration 4 terms: complex values (contour, Jacobian determinant,
+    U^-2 F^-1) against the oracle's LU-with-pivoting evaluation."""
+    p = _c4(n=4194301)
+    g = I.random_generating_vector(I.SplitMix64(41), 5, p.n)
+    rng = np.random.default_rng(4)
+    js = np.concatenate([[0, 1, p.n - 1], rng.integers(0, p.n, 150)]).astype(np.uint64)
+    ks = np.concatenate([[0, 19, 7], rng.integers(0, p.m, 150)]).astype(np.int32)
+    vals, idx, _ = Q.qmc_sample_points(p.d, p.n, p.m, g, p.shifts, Q.transform("korobov", 3),
+                                       Q.integrand_from_problem(p, precision), js, ks, want_coord=False)
+    ctol = 2.0 ** -52 if precision == "fp64" else 2.0 ** -23
+    vtol = 1e-12 if precision == "fp64" else 3e-5
+    for s in range(len(js)):
+        v, oi, ox, _, _ = oracle_lib.point(p, g, int(ks[s]), int(js[s]))
+        assert np.array_equal(idx[s], oi)
+        sdist = np.minimum(ox, 1.0 - ox)
+        rel = vtol + float(np.sum(6.0 * ctol / np.maximum(sdist, 1e-300)))
+        mag = abs(complex(v[0], v[1]))
+        assert abs(complex(*vals[s]) - complex(v[0], v[1])) <= rel * mag + 1e-300, (s, vals[s], v)
+
+
+def test_config4_deformed_fp64(Q, oracle_lib, nthreads):
+    """Configuration 4 rule (d=5, F with 3 negative coefficients, lambda=0.1,
+    Korobov 3, m=20): per-shift complex Q^(k), Qbar, sigma per part, and the
+    count of points with Im F(w) > 0, against the oracle."""
+    p = _c4()
+    g = I.random_generating_vector(I.SplitMix64(42), 5, p.n)
+    gpu, ps = gpu_run(Q, p, g)
+    ref = oracle_lib.integrate(p, g, nthreads=nthreads)
+    scale = np.abs(ref["q"][:, 0] + 1j * ref["q"][:, 1])
+    assert np.all(np.abs((ps[:, 0] + 1j * ps[:, 1]) - (ref["q"][:, 0] + 1j * ref["q"][:, 1])) <= 1e-12 * scale)
+    mag = abs(complex(*ref["mean"]))
+    assert abs(complex(*gpu["mean"]) - complex(*ref["mean"])) <= 1e-12 * mag
+    assert np.all(np.abs(gpu["err"] - ref["err"]) <= 2e-12 * mag)
+    assert gpu["deform_violations"] == ref["deform_bad"]
+
+
+def test_config4_deformed_fp32(Q, oracle_lib, nthreads):
+    p = _c4()
+    g = I.random_generating_vector(I.SplitMix64(43), 5, p.n)
+    gpu, ps = gpu_run(Q, p, g, "fp32")
+    ref = oracle_lib.integrate(p, g, nthreads=nthreads)
+    scale = np.abs(ref["q"][:, 0] + 1j * ref["q"][:, 1])
+    assert np.all(np.abs((ps[:, 0] + 1j * ps[:, 1]) - (ref["q"][:, 0] + 1j * ref["q"][:, 1])) <= 2e-6 * scale)
+
+
+def test_deformed_lambda_zero_equals_real_kernel(Q):
+    """With lambda = 0 the contour is the real cube and J = I: the complex
+    kernel reproduces the real sector kernel (positive F) to rounding."""
+    rng = I.SplitMix64(44)
+    U = I.random_poly(rng, 4, 4, 0)
+    F = I.random_poly(rng, 4, 0, 6)
+    sh = I.make_shifts(rng, 6, 4)
+    g = I.random_generating_vector(rng, 4, 50021)
+    real = I.Problem("r", 4, 50021, 6, sh, "korobov", alpha=3, kind="sector", U=U, F=F)
+    cplx = I.Problem("c", 4, 50021, 6, sh, "korobov", alpha=3, kind="sector_deformed", U=U, F=F, lam=0.0)
+    a, pa = gpu_run(Q, real, g, "fp64")
+    b, pb = gpu_run(Q, cplx, g, "fp64")
+    assert np.allclose(pa[:, 0], pb[:, 0], rtol=1e-13, atol=0) and np.all(pb[:, 1] == 0.0)
