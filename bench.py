@@ -219,6 +219,7 @@ def main():
     f = qmc.integrand_from_problem(p, "fp32")
     t = qmc.transform(p.transform, p.alpha)
     plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
+    shifts_per_launch = plan.tune(torch.cuda.current_stream().cuda_stream)   # autotuner, untimed
     launches_per_step = plan.launches()
 
     stream = torch.cuda.current_stream()
@@ -233,6 +234,11 @@ def main():
 
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    for e4 in ev:  # torch creates the CUDA event on first record; the library re-records it
+        for e in e4:
+            e.record(stream)
+    torch.cuda.synchronize()
+    assert all(e.cuda_event for e4 in ev for e in e4)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -289,7 +295,7 @@ def main():
         "gpu_launches": launches_per_step * K,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "sector_kernel<float, D=6, MC=32, baker, U deg 1, F deg 2>",
+                     "kernel": f"sector_kernel<float, D=6, MC={shifts_per_launch}, baker, U deg 1, F deg 2>",
                      "kernel_ms": 1e3 * rule_avg_s, "flops_per_eval": FLOPS_PER_EVAL,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (nominal max clock)",
                      "frac_at_observed_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)

@@ -159,6 +159,12 @@ int qmc_plan_execute(qmc_plan plan, qmc_result* out, double* per_shift, void* st
 int qmc_plan_destroy(qmc_plan plan);
 /* Number of kernel launches one qmc_plan_execute issues. */
 int qmc_plan_launches(qmc_plan plan, int32_t* launches_out);
+/* Autotuner: times the plan on `stream` with each specialised shift-chunk
+ * size (shifts evaluated per point by one launch: 8, 16 or 32 for FP32EVAL
+ * sector integrands; other plans have one choice) and keeps the fastest.
+ * Reports the choice in *shifts_per_launch_out (may be NULL).  Synchronises
+ * the device. */
+int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out);
 /* Timing hook: when set (non-NULL cudaEvent_t handles passed as void*), every
  * later qmc_plan_execute records `before_rule` on its stream just before the
  * rule kernels and `after_rule` just after them (before the final pass), so a
@@ -176,23 +182,80 @@ typedef struct {
   const qmc_integrand* f;
 } qmc_problem;
 
-/* Many independent rules in one persistent launch (sectors of uneven d, n).
+/* Many independent rules (e.g. the sectors of one integral: uneven d, n,
+ * integrand) evaluated together.  Every problem keeps the kernel it would get
+ * from qmc_integrate; the batch runs them as independent nodes of one CUDA
+ * graph (the GPU schedules them side by side) followed by one final-pass
+ * launch for all problems.
  *   count      number of problems (1..65536)
- *   problems   [count] descriptors (host)
+ *   problems   [count] descriptors (host); each as for qmc_integrate
  *   out        [count] results (host or device); out[i].status per problem
  *   per_shift  optional; problem i writes 2*m_i doubles at offset 2*sum_{p<i} m_p
- * Supported: SECTOR integrands with U of degree <= 1, F of degree <= 2,
- * d <= 8, FP32EVAL, all problems with the same transform.  Other batches
- * return QMC_EUNSUPPORTED. */
+ * Returns the first non-OK per-problem status when `out` is host memory. */
 int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* out,
                         double* per_shift, void* stream);
 
-/* Planned batch: packs once, captures the persistent launch and the final
- * reduction into a CUDA graph on first execute, replays it afterwards. */
+/* Planned batch: validates and packs once and builds the CUDA graph; every
+ * execute replays it (one cudaGraphLaunch). */
 typedef struct qmc_batch_plan_s* qmc_batch_plan;
 int qmc_batch_plan_create(int32_t count, const qmc_problem* problems, qmc_batch_plan* plan_out);
 int qmc_batch_plan_execute(qmc_batch_plan plan, qmc_result* out, double* per_shift, void* stream);
 int qmc_batch_plan_destroy(qmc_batch_plan plan);
+/* Kernel launches in one replay (rule kernels + the final pass). */
+int qmc_batch_plan_launches(qmc_batch_plan plan, int32_t* launches_out);
+/* Autotuner: times the graph on `stream` for evaluations-per-CTA budgets
+ * 2^18..2^24 (the per-problem grid is ceil(n m / budget) CTAs), rebuilds the
+ * plan with the fastest and reports it in *work_per_cta_out (may be NULL).
+ * `problems` must describe the same batch the plan was created from.
+ * Synchronises `stream`. */
+int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* stream,
+                        uint64_t* work_per_cta_out);
+
+/* Learned control variate (a separable rank-R cosine surrogate):
+ *   g(x) = sum_{r<R} prod_{i<d} sum_{k<K} a[(r*d + i)*K + k] cos(F pi k x_i),
+ *   int_[0,1]^d g = sum_r prod_i a[(r*d + i)*K]
+ * fitted to h(x) = f(z(x)) prod_i w(x_i), the transformed integrand the rule
+ * of Eq. (2) sums, so that Q^(k)[h - g] + int g is an unbiased estimate with
+ * the same Eq. (3) error estimate.  This build: R = 16, K = 32, d <= 8.
+ *   freq_step  F: 1 -> cos(pi k x); 2 -> cos(2 pi k x) (1-periodic basis)
+ *   steps, lr  full-batch Adam (beta 0.9, 0.999), rate lr * (1 + cos(pi s/steps)) / 2
+ *   seed       SplitMix64 seed of the initial parameters */
+typedef struct {
+  int32_t R;
+  int32_t K;
+  int32_t freq_step;
+  int32_t steps;
+  float lr;
+  int32_t reserved;
+  uint64_t seed;
+} qmc_cv_config;
+
+/* Fit the surrogate on the GPU to the n_pilot points of one shifted lattice
+ * (g_pilot, shift_pilot [d]) of the rule's integrand (evaluated in FP64 by
+ * the rule's own kernel), mean squared error, FP32 training kernels.
+ *   a_out     [R*d*K] host, the parameters rounded to bfloat16 (stored as float)
+ *   loss_out  optional [2] host: loss before the first and after the last step
+ * Synchronises `stream`. */
+int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const double* shift_pilot,
+                 qmc_transform t, const qmc_integrand* f, const qmc_cv_config* cfg, float* a_out,
+                 double* loss_out, void* stream);
+
+/* The rule with the control variate: one pass evaluates h and g at every
+ * point and shift.  out->mean[0], var[0], err[0] are the control-variate
+ * estimate Q[h - g] + int g; out->mean[1], var[1], err[1] the plain rule's
+ * Q[h] from the same points (the fallback: keep whichever error is smaller).
+ * per_shift (optional, [m*2]) gets the two per-shift values.  Supports
+ * FP32EVAL sector integrands U^-2 F^-1 with deg U <= 1, deg F <= 2, d <= 8,
+ * transform none, baker or Korobov 3. */
+int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                     qmc_transform t, const qmc_integrand* f, const qmc_cv_config* cfg, const float* a,
+                     qmc_result* out, double* per_shift, void* stream);
+
+/* The training kernels' loss and gradient at given parameters on given
+ * points (x [P*d] in [0,1), targets h [P], host), for checking them against
+ * an independent computation.  grad_out [R*d*K] host. */
+int qmc_cv_loss_grad(int32_t d, const qmc_cv_config* cfg, int32_t P, const double* x, const double* h,
+                     const float* a, double* loss_out, float* grad_out, void* stream);
 
 /* Single terms of Eq. (2), evaluated by the same device code the rule uses:
  * for each sample s, the weighted value f(z(x)) prod_i w(x_i) at point

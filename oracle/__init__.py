@@ -12,6 +12,7 @@ Functions and the passage each follows:
   transform                 Eq. (5) Korobov weight alpha, Eq. (6) baker
   integrand                 Eq. (7) U^aU F^aF, the Sec. 3 contour deformation, test functions
   gauss_legendre            tensor Gauss-Legendre integral (a reference, not the method)
+  cv_g / cv_integral / cv_loss_grad   control-variate surrogate, its integral, its fit gradient
   det_lu                    LU determinant with partial pivoting (deformation Jacobian)
   cbc_plain / cbc_error     generating-vector search (the paper takes g as an input)
 """
@@ -54,6 +55,7 @@ class _Problem(ctypes.Structure):
         ("nF", ctypes.c_int), ("cF", ctypes.c_void_p), ("eF", ctypes.c_void_p),
         ("aU", ctypes.c_int), ("aF", ctypes.c_int), ("lam", ctypes.c_double),
         ("c", ctypes.c_void_p), ("b", ctypes.c_void_p), ("h", ctypes.c_void_p),
+        ("cvR", ctypes.c_int), ("cvK", ctypes.c_int), ("cvF", ctypes.c_int), ("cva", ctypes.c_void_p),
     ]
 
 
@@ -79,6 +81,12 @@ def lib():
             L.orc_cbc_error.restype = dbl
             L.orc_cbc_plain.argtypes = [i32, u64, vp, vp]
             L.orc_cbc_candidate.argtypes = [u64, vp, u64]
+            L.orc_cv_g.argtypes = [i32, i32, i32, i32, vp, vp]
+            L.orc_cv_g.restype = dbl
+            L.orc_cv_integral.argtypes = [i32, i32, i32, vp]
+            L.orc_cv_integral.restype = dbl
+            L.orc_cv_loss_grad.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp]
+            L.orc_cv_loss_grad.restype = dbl
             L.orc_cbc_candidate.restype = dbl
             _lib = L
     return _lib
@@ -117,6 +125,10 @@ class _Marshalled:
         s.c = _ptr(arr(p.c, np.float64))
         s.b = _ptr(arr(p.b, np.float64))
         s.h = _ptr(arr(p.h, np.int32))
+        cv = getattr(p, "cv", None)
+        if cv is not None:
+            s.cvR, s.cvK, s.cvF = int(cv["R"]), int(cv["K"]), int(cv["F"])
+            s.cva = _ptr(arr(cv["a"], np.float32))
         self.s = s
 
 
@@ -216,6 +228,28 @@ def det_lu(a):
     work = a.copy()
     lib().orc_det_lu_out(d, _ptr(work), _ptr(out))
     return complex(out[0], out[1])
+
+
+def cv_g(d, R, K, F, a, x) -> float:
+    """Control-variate surrogate g(x) = sum_r prod_i sum_k a_rik cos(F pi k x_i)."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return float(lib().orc_cv_g(d, R, K, F, _ptr(a), _ptr(x)))
+
+
+def cv_integral(d, R, K, a) -> float:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return float(lib().orc_cv_integral(d, R, K, _ptr(a)))
+
+
+def cv_loss_grad(d, R, K, F, x, h, a):
+    """(loss, grad[R*d*K]) of the mean squared fit, FP64."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    h = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+    grad = np.zeros(R * d * K)
+    loss = lib().orc_cv_loss_grad(d, R, K, F, h.shape[0], _ptr(x), _ptr(h), _ptr(a), _ptr(grad))
+    return float(loss), grad
 
 
 def cbc_error(d: int, n: int, g, gamma) -> float:

@@ -58,6 +58,11 @@ typedef struct {
   const double* c;       /* separable: prod (1 + c_i z_i) exp(b_i z_i) */
   const double* b;
   const int32_t* h;      /* trig: cos(2 pi h . z) */
+  /* optional control variate subtracted from every weighted value:
+   * g(x) = sum_{r<cvR} prod_{i<d} sum_{k<cvK} a[(r*d + i)*cvK + k] cos(cvF pi k x_i)
+   * evaluated at the lattice point x itself (before the transform) */
+  int cvR, cvK, cvF;
+  const float* cva;
 } orc_problem;
 
 /* ---------------------------------------------------------------- sums --- */
@@ -295,6 +300,74 @@ int orc_integrand(const orc_problem* p, const double* y, double* out, int* bad) 
   return -1;
 }
 
+/* ------------------------------------------------------- control variate --- */
+
+/* g(x) = sum_r prod_i sum_k a_rik cos(F pi k x_i), each cosine from libm. */
+double orc_cv_g(int d, int R, int K, int F, const float* a, const double* x) {
+  double g = 0.0;
+  for (int r = 0; r < R; ++r) {
+    double prod = 1.0;
+    for (int i = 0; i < d; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < K; ++k) s += (double)a[(r * d + i) * K + k] * cos((double)F * M_PI * (double)k * x[i]);
+      prod *= s;
+    }
+    g += prod;
+  }
+  return g;
+}
+
+/* int_[0,1]^d g = sum_r prod_i a_ri0, since int_0^1 cos(F pi k x) dx = 0 for k >= 1. */
+double orc_cv_integral(int d, int R, int K, const float* a) {
+  double s = 0.0;
+  for (int r = 0; r < R; ++r) {
+    double p = 1.0;
+    for (int i = 0; i < d; ++i) p *= (double)a[(r * d + i) * K];
+    s += p;
+  }
+  return s;
+}
+
+/* Mean squared error L = (1/P) sum_j (g(x_j) - h_j)^2 and its gradient
+ * dL/da_rik = (2/P) sum_j (g_j - h_j) prod_{i' != i} C_ri'(x_j) cos(F pi k x_ji),
+ * C_ri(x) = sum_k a_rik cos(F pi k x_i), in FP64 (chain rule, term by term). */
+double orc_cv_loss_grad(int d, int R, int K, int F, int P, const double* x, const double* h, const float* a,
+                        double* grad) {
+  int na = R * d * K;
+  for (int q = 0; q < na; ++q) grad[q] = 0.0;
+  double* C = (double*)malloc(sizeof(double) * R * d);
+  double* cs = (double*)malloc(sizeof(double) * d * K);
+  neum_t loss = {0, 0};
+  for (int j = 0; j < P; ++j) {
+    const double* xj = x + (size_t)j * d;
+    for (int i = 0; i < d; ++i)
+      for (int k = 0; k < K; ++k) cs[i * K + k] = cos((double)F * M_PI * (double)k * xj[i]);
+    double g = 0.0;
+    for (int r = 0; r < R; ++r) {
+      double prod = 1.0;
+      for (int i = 0; i < d; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += (double)a[(r * d + i) * K + k] * cs[i * K + k];
+        C[r * d + i] = s;
+        prod *= s;
+      }
+      g += prod;
+    }
+    double e = g - h[j];
+    neum_add(&loss, e * e);
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < d; ++i) {
+        double other = 1.0;
+        for (int i2 = 0; i2 < d; ++i2)
+          if (i2 != i) other *= C[r * d + i2];
+        for (int k = 0; k < K; ++k) grad[(r * d + i) * K + k] += 2.0 * e * other * cs[i * K + k] / (double)P;
+      }
+  }
+  free(C);
+  free(cs);
+  return neum_get(&loss) / (double)P;
+}
+
 /* ------------------------------------------------------------- the rule --- */
 
 /* Lattice index of Eq. (2): idx_i = ((j-1) g_i) mod n with j-1 = jm1, exact in 128 bits. */
@@ -323,6 +396,14 @@ int orc_point(const orc_problem* p, uint64_t n, const uint64_t* g, const double*
   orc_integrand(p, z, f, bad);
   val[0] = f[0] * wprod;
   val[1] = f[1] * wprod;
+  if (p->cva) {
+    double x[ORC_DMAX];
+    for (int i = 0; i < p->d; ++i) {
+      double y = (double)orc_index(jm1, g[i], n) / (double)n + shift[i];
+      x[i] = (y >= 1.0) ? y - 1.0 : y;
+    }
+    val[0] -= orc_cv_g(p->d, p->cvR, p->cvK, p->cvF, p->cva, x);
+  }
   return 0;
 }
 

@@ -354,11 +354,12 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
       KF = 3;
       mc = 16;
     }
-    if (KU > 0 && d <= kDFast && !tune.force_general) {
+    const bool m21 = f->aU == -2 && f->aF == -1;
+    if (KU > 0 && d <= kDFast && m21 && !tune.force_general) {
       switch (d) {
 #define QMC_D_CASE(DD) \
   case DD:             \
-    func = sector_ptr<R, DD>(mc, base.tr, base.alpha, KU, KF); \
+    func = sector_ptr<R, DD>(mc, base.tr, base.alpha, KU, KF, base.check_finite != 0); \
     break;
         QMC_D_CASE(1) QMC_D_CASE(2) QMC_D_CASE(3) QMC_D_CASE(4) QMC_D_CASE(5) QMC_D_CASE(6)
         QMC_D_CASE(7) QMC_D_CASE(8)
@@ -405,6 +406,13 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
   uint64_t tiles = 0;
   int rc = choose_grid(func, 0, n, nblk, L, tiles, tune.occupancy);
   if (rc) return rc;
+  if (tune.max_ctas > 0 && nblk > tune.max_ctas) {
+    nblk = tune.max_ctas;
+    uint64_t per = (n + (uint64_t)nblk * kThreads - 1) / ((uint64_t)nblk * kThreads);
+    L = (int)std::max<uint64_t>(1, std::min<uint64_t>(per, 512));
+    tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
+    nblk = (int)std::min<uint64_t>((uint64_t)nblk, tiles);
+  }
   if (tune.L > 0) {
     L = tune.L;
     tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
@@ -423,9 +431,11 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
     RuleParams<R> P = base;
     P.m_launch = mk;
     P.k_base = k0;
-    for (int kk = 0; kk < mk; ++kk)
+    // rows mk..mc-1 repeat row 0 (evaluated, never written back)
+    for (int kk = 0; kk < mc; ++kk)
       for (int i = 0; i < d; ++i) {
-        uint64_t s64 = shift_fixed64(shifts[(size_t)(k0 + kk) * d + i]);
+        const int src = kk < mk ? k0 + kk : k0;
+        uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
         P.shift64[kk][i] = s64;
         P.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
       }
@@ -444,10 +454,44 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
   return QMC_OK;
 }
 
+void SavedProblem::save(int32_t d_, uint64_t n_, int32_t m_, const uint64_t* g_, const double* shifts_,
+                        qmc_transform t_, const qmc_integrand* f_) {
+  d = d_;
+  n = n_;
+  m = m_;
+  t = t_;
+  g.assign(g_, g_ + d_);
+  shifts.assign(shifts_, shifts_ + (size_t)m_ * d_);
+  f = *f_;
+  auto copy_poly = [&](qmc_poly& p, std::vector<double>& cv, std::vector<uint8_t>& ev) {
+    if (p.nterms > 0 && p.coef && p.expo) {
+      cv.assign(p.coef, p.coef + p.nterms);
+      ev.assign(p.expo, p.expo + (size_t)p.nterms * d_);
+      p.coef = cv.data();
+      p.expo = ev.data();
+    }
+  };
+  copy_poly(f.U, cu, eu);
+  copy_poly(f.F, cf, ef);
+  if (f_->c) {
+    c.assign(f_->c, f_->c + d_);
+    f.c = c.data();
+  }
+  if (f_->b) {
+    b.assign(f_->b, f_->b + d_);
+    f.b = b.data();
+  }
+  if (f_->h) {
+    h.assign(f_->h, f_->h + d_);
+    f.h = h.data();
+  }
+}
+
 int plan_build(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                qmc_transform t, const qmc_integrand* f, const TuneChoice& tune) {
   int rc = validate_problem(d, n, m, g, shifts, t, f);
   if (rc) return rc;
+  pl->tune = tune;
   pl->d = d;
   pl->n = n;
   pl->m = m;
@@ -519,6 +563,8 @@ int launch_finalize(const Plan* pl, const Workspace& ws, qmc_result* res_dev, do
   A.pad = 0;
   A.dn = (double)pl->n;
   A.value_scale = pl->final_scale;
+  A.offset[0] = pl->offset[0];
+  A.offset[1] = pl->offset[1];
   A.counters = ws.counters;
   A.result = res_dev;
   A.per_shift = per_shift_dev;
@@ -573,7 +619,78 @@ int qmc_plan_create(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const d
   if (rc) return rc;
   rc = plan_alloc(pl.get(), nullptr, false);
   if (rc) return rc;
+  pl->saved.save(d, n, m, g, shifts, t, f);
   *plan_out = reinterpret_cast<qmc_plan>(pl.release());
+  return QMC_OK;
+}
+
+int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
+  if (!plan) return fail(QMC_EINVAL, "null plan");
+  Plan* pl = reinterpret_cast<Plan*>(plan);
+  cudaStream_t st = (cudaStream_t)stream;
+  const SavedProblem& sp = pl->saved;
+  std::vector<int> cands;
+  if (sp.f.precision == QMC_FP32EVAL && sp.f.kind == QMC_F_SECTOR) cands = {8, 16, 32};
+  if (cands.empty()) {
+    if (shifts_per_launch_out) *shifts_per_launch_out = pl->mc;
+    return QMC_OK;
+  }
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return fail(QMC_ECUDA, "events");
+  qmc_result* dres = nullptr;
+  QMC_CUDA(cudaMalloc(&dres, sizeof(qmc_result)));
+  float best = 1e30f;
+  int best_mc = pl->mc;
+  int rc = QMC_OK;
+  for (int mc : cands) {
+    Plan trial;
+    TuneChoice tc = pl->tune;
+    tc.mc = mc;
+    rc = plan_build(&trial, sp.d, sp.n, sp.m, sp.g.data(), sp.shifts.data(), sp.t, &sp.f, tc);
+    if (rc == QMC_EUNSUPPORTED) {
+      rc = QMC_OK;
+      continue;
+    }
+    if (rc) break;
+    rc = plan_alloc(&trial, nullptr, false);
+    if (rc) break;
+    float tot = 0.0f;
+    for (int rep = 0; rep < 4 && rc == QMC_OK; ++rep) {
+      cudaEventRecord(a, st);
+      rc = plan_execute(&trial, dres, nullptr, st);
+      cudaEventRecord(b, st);
+      cudaEventSynchronize(b);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0) tot += ms;
+    }
+    plan_free(&trial, nullptr);
+    if (rc) break;
+    if (tot < best) {
+      best = tot;
+      best_mc = mc;
+    }
+  }
+  cudaFree(dres);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  if (best_mc != pl->mc) {
+    TuneChoice tc = pl->tune;
+    tc.mc = best_mc;
+    Plan fresh;
+    rc = plan_build(&fresh, sp.d, sp.n, sp.m, sp.g.data(), sp.shifts.data(), sp.t, &sp.f, tc);
+    if (rc) return rc;
+    rc = plan_alloc(&fresh, nullptr, false);
+    if (rc) return rc;
+    cudaDeviceSynchronize();
+    plan_free(pl, nullptr);
+    fresh.saved = std::move(pl->saved);
+    fresh.ev_before = pl->ev_before;
+    fresh.ev_after = pl->ev_after;
+    *pl = std::move(fresh);
+  }
+  if (shifts_per_launch_out) *shifts_per_launch_out = pl->mc;
   return QMC_OK;
 }
 

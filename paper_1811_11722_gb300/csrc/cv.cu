@@ -1,0 +1,646 @@
+// Learned control variate for the lattice rule.
+//
+// Surrogate (separable rank-R cosine expansion, R = 16, K = 32):
+//   g(x) = sum_{r<R} prod_{i<d} C_ri(x_i),  C_ri(x) = sum_{k<K} a_rik cos(F pi k x),
+//   int_[0,1]^d g = sum_r prod_i a_ri0          (int_0^1 cos(F pi k x) dx = 0, k >= 1)
+// fitted by Adam to h(x) = f(z(x)) prod_i w(x_i), the transformed integrand the
+// rule sees, on the points of a pilot lattice.  The estimator
+//   Q^(k)[h - g] + int g
+// is unbiased for any g whose integral is known exactly; the kernel also sums
+// Q^(k)[h] in the same pass, so every result carries the plain rule's
+// estimate beside the control-variate one and the caller keeps whichever has
+// the smaller Eq. (3) error.
+//
+// Training kernels (FP32 CUDA cores, FP64 loss):
+//   cv_basis     B[i][j][k] = cos(F pi k x_ji) for the pilot points
+//   cv_forward   C_ri(x_j), g_j, e_j = 2 (g_j - h_j)/P, D[i][j][r] = e_j prod_{i'!=i} C_ri'
+//   cv_backward  grad_part[c][i][r][k] = sum_{j in chunk c} D[i][j][r] B[i][j][k]
+//   cv_adam      grad = sum_c grad_part (fixed order), Adam step, cosine-decayed rate
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "plan.h"
+#include "rule_kernels.cuh"
+
+namespace qmc {
+
+constexpr int kCvR = 16;
+constexpr int kCvK = 32;
+constexpr int kCvDMax = 8;
+constexpr int kCvMc = 8;            // shifts per estimator launch
+constexpr int kCvChunk = 2048;      // pilot points per backward CTA
+
+struct CvParams {
+  RuleParams<float> base;
+  float a[kCvR * kCvDMax * kCvK];   // [r][i][k] with row stride d (packed for the actual d)
+  float freq;                       // F: 1 -> cos(pi k x), 2 -> cos(2 pi k x)
+  int32_t pad;
+};
+
+// ------------------------------------------------------------- estimator --
+
+// sum_r prod_i sum_k a_rik T_k(cos(F pi x_i)) with the Chebyshev recurrence.
+template <int D>
+__device__ __forceinline__ float cv_g(const CvParams& C, const float* x) {
+  float pr[kCvR];
+#pragma unroll
+  for (int r = 0; r < kCvR; ++r) pr[r] = 1.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const float c1 = cospif(C.freq * x[i]);
+    const float two = c1 + c1;
+    float cr[kCvR];
+#pragma unroll
+    for (int r = 0; r < kCvR; ++r) cr[r] = fmaf(C.a[(r * D + i) * kCvK + 1], c1, C.a[(r * D + i) * kCvK]);
+    float t0 = 1.0f, t1 = c1;
+#pragma unroll
+    for (int k = 2; k < kCvK; ++k) {
+      const float t2 = fmaf(two, t1, -t0);
+#pragma unroll
+      for (int r = 0; r < kCvR; ++r) cr[r] = fmaf(C.a[(r * D + i) * kCvK + k], t2, cr[r]);
+      t0 = t1;
+      t1 = t2;
+    }
+#pragma unroll
+    for (int r = 0; r < kCvR; ++r) pr[r] *= cr[r];
+  }
+  float g = 0.0f;
+#pragma unroll
+  for (int r = 0; r < kCvR; ++r) g += pr[r];
+  return g;
+}
+
+// (h - g, h) at one point and shift; h = U^-2 F^-1 times the transform weight.
+template <int D, int TR, int ALPHA>
+__device__ __forceinline__ void cv_value(const CvParams& C, const uint32_t* base, int k, float& hv, float& gv) {
+  const RuleParams<float>& P = C.base;
+  float z[D], x[D];
+  float w = 1.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const uint32_t X = base[i] + P.shift32[k][i];
+    x[i] = unit_f32(X) - 1.0f;
+    // Korobov factors normalised one by one (exact constant per factor), so
+    // h needs no large constant that float could not represent exactly
+    z[i] = coord<float, TR, 0>(X, P.kor, P.alpha, w);
+  }
+  const float U = poly_dense<D, 1>(P.cU, z);
+  const float F = poly_dense<D, 2>(P.cF, z);
+  float h = recip(U * U * F);
+  if constexpr (TR == TR_KOROBOV) h *= w;
+  hv = h;
+  gv = cv_g<D>(C, x);
+}
+
+template <int D, int TR, int ALPHA>
+__global__ void __launch_bounds__(kThreads)
+    cv_sector_kernel(const __grid_constant__ CvParams C, double* __restrict__ partial,
+                     unsigned long long* __restrict__ counters, const SampleIO sio) {
+  const RuleParams<float>& P = C.base;
+  if (sio.count > 0) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sio.count) return;
+    uint32_t base[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      uint32_t idx = lattice_index(sio.j[s], P.g[i], P.n);
+      base[i] = fix_base<float>(idx, P.rc);
+      if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
+      if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<float>(base[i] + P.shift32[sio.k[s]][i]);
+    }
+    float h, g;
+    cv_value<D, TR, ALPHA>(C, base, sio.k[s], h, g);
+    sio.values[2 * (size_t)s] = (double)h - (double)g;
+    sio.values[2 * (size_t)s + 1] = (double)g;
+    return;
+  }
+  __shared__ double accs[2][kCvMc][kThreads];
+  const uint32_t n = (uint32_t)P.n;
+  const int mk = P.m_launch;
+  for (int kk = 0; kk < kCvMc; ++kk) {
+    accs[0][kk][threadIdx.x] = 0.0;
+    accs[1][kk][threadIdx.x] = 0.0;
+  }
+  unsigned nbad = 0;
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+#pragma unroll 1
+    for (int kk = 0; kk < mk; ++kk) {
+      uint32_t idx[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
+      Acc<float> acv, apl;
+      acv.init();
+      apl.init();
+#pragma unroll 1
+      for (int s = 0; s < steps; ++s) {
+        uint32_t base[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) base[i] = fix_base<float>(idx[i], P.rc);
+        float h, g;
+        cv_value<D, TR, ALPHA>(C, base, kk, h, g);
+        float dv = h - g;
+        const bool ok = finite_(dv) && finite_(h);
+        nbad += ok ? 0u : 1u;
+        acv.add(ok ? dv : 0.0f);
+        apl.add(ok ? h : 0.0f);
+#pragma unroll
+        for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
+        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+          acv.fold();
+          apl.fold();
+        }
+      }
+      accs[0][kk][threadIdx.x] += acv.thread_total();
+      accs[1][kk][threadIdx.x] += apl.thread_total();
+    }
+  }
+  __shared__ double red[kThreads / 32][kCvMc][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int kk = 0; kk < mk; ++kk) {
+    const double a0 = warp_sum_d(accs[0][kk][threadIdx.x]);
+    const double a1 = warp_sum_d(accs[1][kk][threadIdx.x]);
+    if (lane == 0) {
+      red[warp][kk][0] = a0;
+      red[warp][kk][1] = a1;
+    }
+  }
+  unsigned long long b1 = warp_sum_u64((unsigned long long)nbad);
+  if (lane == 0 && b1) atomicAdd(&counters[0], b1);
+  __syncthreads();
+  if (threadIdx.x < 2 * mk) {
+    const int kk = threadIdx.x >> 1, part = threadIdx.x & 1;
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][kk][part];
+    partial[((size_t)(P.k_base + kk) * P.nblk + blockIdx.x) * 2 + part] = s;
+  }
+}
+
+template <int D>
+static const void* cv_kernel_ptr(int tr, int alpha) {
+  if (tr == TR_BAKER) return (const void*)&cv_sector_kernel<D, TR_BAKER, 0>;
+  if (tr == TR_KOROBOV && alpha == 3) return (const void*)&cv_sector_kernel<D, TR_KOROBOV, 3>;
+  if (tr == TR_NONE) return (const void*)&cv_sector_kernel<D, TR_NONE, 0>;
+  return nullptr;
+}
+
+// -------------------------------------------------------------- training --
+
+__global__ void cv_iota_kernel(uint64_t* j, int P) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < P) j[t] = (uint64_t)t;
+}
+
+__global__ void cv_basis_kernel(const double* __restrict__ x, int P, int d, float freq, float* __restrict__ B) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (i, j)
+  if (t >= P * d) return;
+  const int i = t / P, j = t % P;
+  const double xv = x[(size_t)j * d + i];
+  float* out = B + ((size_t)i * P + j) * kCvK;
+#pragma unroll 4
+  for (int k = 0; k < kCvK; ++k) out[k] = (float)cospi((double)freq * (double)k * xv);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+    cv_forward_kernel(const float* __restrict__ B, const double* __restrict__ hv, const float* __restrict__ a, int P,
+                      float* __restrict__ Dg, double* __restrict__ loss_part) {
+  __shared__ float as[kCvR * D * kCvK];
+  __shared__ double red[8];
+  for (int q = threadIdx.x; q < kCvR * D * kCvK; q += blockDim.x) as[q] = a[q];
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double l2 = 0.0;
+  if (j < P) {
+    float C[D][kCvR];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float b[kCvK];
+      const float4* bp = reinterpret_cast<const float4*>(B + ((size_t)i * P + j) * kCvK);
+#pragma unroll
+      for (int q = 0; q < kCvK / 4; ++q) {
+        float4 v = bp[q];
+        b[4 * q] = v.x;
+        b[4 * q + 1] = v.y;
+        b[4 * q + 2] = v.z;
+        b[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int r = 0; r < kCvR; ++r) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kCvK; ++k) s = fmaf(as[(r * D + i) * kCvK + k], b[k], s);
+        C[i][r] = s;
+      }
+    }
+    float g = 0.0f;
+#pragma unroll
+    for (int r = 0; r < kCvR; ++r) {
+      float p = 1.0f;
+#pragma unroll
+      for (int i = 0; i < D; ++i) p *= C[i][r];
+      g += p;
+    }
+    const double err = (double)g - hv[2 * (size_t)j];
+    l2 = err * err;
+    const float e = (float)(2.0 * err / (double)P);
+#pragma unroll
+    for (int r = 0; r < kCvR; ++r) {
+      float pre[D + 1];
+      pre[0] = 1.0f;
+#pragma unroll
+      for (int i = 0; i < D; ++i) pre[i + 1] = pre[i] * C[i][r];
+      float suf = 1.0f;
+#pragma unroll
+      for (int i = D - 1; i >= 0; --i) {
+        Dg[((size_t)i * P + j) * kCvR + r] = e * pre[i] * suf;
+        suf *= C[i][r];
+      }
+    }
+  }
+  l2 = warp_sum_d(l2);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    loss_part[blockIdx.x] = s;
+  }
+}
+
+// grid (chunks, d); thread t owns outputs (r, k) = (t / 16, 2 (t % 16) + {0, 1}).
+__global__ void __launch_bounds__(256)
+    cv_backward_kernel(const float* __restrict__ B, const float* __restrict__ Dg, int P, int d,
+                       float* __restrict__ grad_part) {
+  __shared__ float ds[64][kCvR];
+  __shared__ float bs[64][kCvK + 1];
+  const int c = blockIdx.x, i = blockIdx.y;
+  const int r = threadIdx.x / 16, k0 = 2 * (threadIdx.x % 16);
+  const int j_begin = c * kCvChunk, j_end = min(P, j_begin + kCvChunk);
+  float g0 = 0.0f, g1 = 0.0f;
+  for (int jt = j_begin; jt < j_end; jt += 64) {
+    const int cnt = min(64, j_end - jt);
+    __syncthreads();
+    for (int q = threadIdx.x; q < 64 * kCvR; q += 256) {
+      const int jj = q / kCvR, rr = q % kCvR;
+      ds[jj][rr] = jj < cnt ? Dg[((size_t)i * P + jt + jj) * kCvR + rr] : 0.0f;
+    }
+    for (int q = threadIdx.x; q < 64 * kCvK; q += 256) {
+      const int jj = q / kCvK, kk = q % kCvK;
+      bs[jj][kk] = jj < cnt ? B[((size_t)i * P + jt + jj) * kCvK + kk] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < 64; ++jj) {
+      const float dv = ds[jj][r];
+      g0 = fmaf(dv, bs[jj][k0], g0);
+      g1 = fmaf(dv, bs[jj][k0 + 1], g1);
+    }
+  }
+  float* out = grad_part + (size_t)c * (kCvR * d * kCvK);
+  out[(r * d + i) * kCvK + k0] = g0;
+  out[(r * d + i) * kCvK + k0 + 1] = g1;
+}
+
+__global__ void cv_adam_kernel(const float* __restrict__ grad_part, int nchunk, int npar, float* __restrict__ a,
+                               float* __restrict__ m1, float* __restrict__ m2, int step, float lr) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= npar) return;
+  double g = 0.0;
+  for (int c = 0; c < nchunk; ++c) g += (double)grad_part[(size_t)c * npar + q];
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float gf = (float)g;
+  const float mm = b1 * m1[q] + (1.0f - b1) * gf;
+  const float vv = b2 * m2[q] + (1.0f - b2) * gf * gf;
+  m1[q] = mm;
+  m2[q] = vv;
+  const float mh = mm / (1.0f - powf(b1, (float)step));
+  const float vh = vv / (1.0f - powf(b2, (float)step));
+  a[q] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+template <int D>
+static void cv_launch_forward(int P, const float* B, const double* hv, const float* a, float* Dg, double* loss_part,
+                              cudaStream_t st) {
+  cv_forward_kernel<D><<<(P + 255) / 256, 256, 0, st>>>(B, hv, a, P, Dg, loss_part);
+}
+
+static void cv_forward(int d, int P, const float* B, const double* hv, const float* a, float* Dg, double* lp,
+                       cudaStream_t st) {
+  switch (d) {
+    case 1: cv_launch_forward<1>(P, B, hv, a, Dg, lp, st); break;
+    case 2: cv_launch_forward<2>(P, B, hv, a, Dg, lp, st); break;
+    case 3: cv_launch_forward<3>(P, B, hv, a, Dg, lp, st); break;
+    case 4: cv_launch_forward<4>(P, B, hv, a, Dg, lp, st); break;
+    case 5: cv_launch_forward<5>(P, B, hv, a, Dg, lp, st); break;
+    case 6: cv_launch_forward<6>(P, B, hv, a, Dg, lp, st); break;
+    case 7: cv_launch_forward<7>(P, B, hv, a, Dg, lp, st); break;
+    default: cv_launch_forward<8>(P, B, hv, a, Dg, lp, st); break;
+  }
+}
+
+static float bf16_round(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u = (u + 0x7FFFu + lsb) & 0xFFFF0000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// Device buffers of one fit: pilot coordinates and values, basis, parameters.
+struct CvFit {
+  int d = 0, P = 0, nchunk = 0, npar = 0;
+  double* x = nullptr;       // [P][d]
+  double* hv = nullptr;      // [P][2] (value, 0)
+  float* B = nullptr;        // [d][P][K]
+  float* Dg = nullptr;       // [d][P][R]
+  float* a = nullptr;
+  float* m1 = nullptr;
+  float* m2 = nullptr;
+  float* grad_part = nullptr;
+  double* loss_part = nullptr;
+  void* block = nullptr;
+  ~CvFit() {
+    if (block) cudaFree(block);
+  }
+  int alloc(int d_, int P_) {
+    d = d_;
+    P = P_;
+    nchunk = (P + kCvChunk - 1) / kCvChunk;
+    npar = kCvR * d * kCvK;
+    const int nlp = (P + 255) / 256;
+    size_t sz[] = {(size_t)P * d * 8, (size_t)P * 2 * 8, (size_t)d * P * kCvK * 4, (size_t)d * P * kCvR * 4,
+                   (size_t)npar * 4,  (size_t)npar * 4, (size_t)npar * 4,        (size_t)nchunk * npar * 4,
+                   (size_t)nlp * 8};
+    size_t total = 0;
+    for (size_t s : sz) total += (s + 255) & ~(size_t)255;
+    if (cudaMalloc(&block, total) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QMC_ENOMEM, "control-variate fit buffers (%zu bytes)", total);
+    }
+    char* p = (char*)block;
+    void** dst[] = {(void**)&x, (void**)&hv, (void**)&B, (void**)&Dg, (void**)&a, (void**)&m1, (void**)&m2,
+                    (void**)&grad_part, (void**)&loss_part};
+    for (int q = 0; q < 9; ++q) {
+      *dst[q] = p;
+      p += (sz[q] + 255) & ~(size_t)255;
+    }
+    return QMC_OK;
+  }
+};
+
+static double cv_loss_host(const CvFit& F, cudaStream_t st) {
+  const int nlp = (F.P + 255) / 256;
+  std::vector<double> lp(nlp);
+  cudaMemcpyAsync(lp.data(), F.loss_part, nlp * 8, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  double s = 0.0;
+  for (double v : lp) s += v;
+  return s / (double)F.P;
+}
+
+static int cv_check(int32_t d, const qmc_cv_config* cfg) {
+  if (!cfg) return fail(QMC_EINVAL, "null control-variate config");
+  if (cfg->R != kCvR || cfg->K != kCvK)
+    return fail(QMC_EUNSUPPORTED, "control variate built for R=%d, K=%d", kCvR, kCvK);
+  if (d < 1 || d > kCvDMax) return fail(QMC_EUNSUPPORTED, "control variate needs d <= %d", kCvDMax);
+  if (cfg->freq_step != 1 && cfg->freq_step != 2) return fail(QMC_EINVAL, "freq_step must be 1 or 2");
+  return QMC_OK;
+}
+
+}  // namespace qmc
+
+using namespace qmc;
+
+extern "C" {
+
+int qmc_cv_loss_grad(int32_t d, const qmc_cv_config* cfg, int32_t P, const double* x, const double* h,
+                     const float* a, double* loss_out, float* grad_out, void* stream) {
+  int rc = cv_check(d, cfg);
+  if (rc) return rc;
+  if (P < 1 || !x || !h || !a || !loss_out || !grad_out) return fail(QMC_EINVAL, "bad loss/gradient arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  CvFit F;
+  rc = F.alloc(d, P);
+  if (rc) return rc;
+  std::vector<double> hv(2 * (size_t)P, 0.0);
+  for (int j = 0; j < P; ++j) hv[2 * (size_t)j] = h[j];
+  cudaMemcpyAsync(F.x, x, (size_t)P * d * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(F.hv, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(F.a, a, (size_t)F.npar * 4, cudaMemcpyHostToDevice, st);
+  cv_basis_kernel<<<(P * d + 255) / 256, 256, 0, st>>>(F.x, P, d, (float)cfg->freq_step, F.B);
+  cv_forward(d, P, F.B, F.hv, F.a, F.Dg, F.loss_part, st);
+  cv_backward_kernel<<<dim3(F.nchunk, d), 256, 0, st>>>(F.B, F.Dg, P, d, F.grad_part);
+  std::vector<float> gp((size_t)F.nchunk * F.npar);
+  cudaMemcpyAsync(gp.data(), F.grad_part, gp.size() * 4, cudaMemcpyDeviceToHost, st);
+  *loss_out = cv_loss_host(F, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "control-variate gradient");
+  for (int q = 0; q < F.npar; ++q) {
+    double s = 0.0;
+    for (int c = 0; c < F.nchunk; ++c) s += gp[(size_t)c * F.npar + q];
+    grad_out[q] = (float)s;
+  }
+  return QMC_OK;
+}
+
+int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const double* shift_pilot,
+                 qmc_transform t, const qmc_integrand* f, const qmc_cv_config* cfg, float* a_out, double* loss_out,
+                 void* stream) {
+  int rc = cv_check(d, cfg);
+  if (rc) return rc;
+  if (!a_out || !shift_pilot) return fail(QMC_EINVAL, "null output or pilot shift");
+  if (n_pilot < 64 || n_pilot > (1u << 22)) return fail(QMC_EINVAL, "pilot size must be in [64, 2^22]");
+  if (cfg->steps < 1 || cfg->steps > 100000 || !(cfg->lr > 0.0f)) return fail(QMC_EINVAL, "bad steps or lr");
+  cudaStream_t st = (cudaStream_t)stream;
+  // pilot values h_j and coordinates x_j from the rule's own FP64 kernel (sampling mode)
+  std::vector<double> sh2(2 * (size_t)d);
+  for (int i = 0; i < d; ++i) sh2[i] = sh2[d + i] = shift_pilot[i];
+  qmc_integrand f64 = *f;
+  f64.precision = QMC_FP64;
+  Plan pilot;
+  rc = plan_build(&pilot, d, n_pilot, 2, g_pilot, sh2.data(), t, &f64, TuneChoice{});
+  if (rc) return rc;
+  const int P = (int)n_pilot;
+  CvFit F;
+  rc = F.alloc(d, P);
+  if (rc) return rc;
+  uint64_t* dj = nullptr;
+  int32_t* dk = nullptr;
+  if (cudaMalloc(&dj, (size_t)P * 8) != cudaSuccess || cudaMalloc(&dk, (size_t)P * 4) != cudaSuccess) {
+    cudaGetLastError();
+    if (dj) cudaFree(dj);
+    return fail(QMC_ENOMEM, "pilot index buffers");
+  }
+  std::unique_ptr<void, void (*)(void*)> g1(dj, [](void* p) { cudaFree(p); });
+  std::unique_ptr<void, void (*)(void*)> g2(dk, [](void* p) { cudaFree(p); });
+  cv_iota_kernel<<<(P + 255) / 256, 256, 0, st>>>(dj, P);
+  cudaMemsetAsync(dk, 0, (size_t)P * 4, st);
+  SampleIO sio;
+  std::memset(&sio, 0, sizeof(sio));
+  sio.count = P;
+  sio.j = dj;
+  sio.k = dk;
+  sio.values = F.hv;
+  sio.idx = nullptr;
+  sio.coord = F.x;
+  {
+    const Launch& ln = pilot.launches[0];
+    double* partial = nullptr;
+    unsigned long long* counters = nullptr;
+    void* args[4] = {(void*)ln.params.data(), &partial, &counters, &sio};
+    cudaError_t e = cudaLaunchKernel(ln.func, dim3((P + 255) / 256), dim3(kThreads), args, 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pilot evaluation");
+  }
+  cv_basis_kernel<<<(P * d + 255) / 256, 256, 0, st>>>(F.x, P, d, (float)cfg->freq_step, F.B);
+  // pilot mean for the initial constant terms
+  std::vector<double> hv(2 * (size_t)P);
+  cudaMemcpyAsync(hv.data(), F.hv, hv.size() * 8, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "pilot");
+  double qp = 0.0;
+  for (int j = 0; j < P; ++j) qp += hv[2 * (size_t)j];
+  qp /= (double)P;
+  // initialisation: a_ri0 = (Q_pilot / R)^(1/d) (sign kept on r = 0), others N(0, 1e-3) (SplitMix64 + Box-Muller)
+  std::vector<float> a0(F.npar);
+  uint64_t state = cfg->seed;
+  auto next = [&]() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto unif = [&]() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+  const double c0 = std::pow(std::fabs(qp) / kCvR, 1.0 / d);
+  for (int r = 0; r < kCvR; ++r)
+    for (int i = 0; i < d; ++i)
+      for (int k = 0; k < kCvK; ++k) {
+        const double u1 = unif(), u2 = unif();
+        const double nrm = std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+        double v = 1e-3 * nrm;
+        if (k == 0) v = c0 * ((qp < 0 && i == 0) ? -1.0 : 1.0) + 1e-3 * nrm;
+        a0[(r * d + i) * kCvK + k] = (float)v;
+      }
+  cudaMemcpyAsync(F.a, a0.data(), (size_t)F.npar * 4, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(F.m1, 0, (size_t)F.npar * 4, st);
+  cudaMemsetAsync(F.m2, 0, (size_t)F.npar * 4, st);
+  double first = 0.0, last = 0.0;
+  for (int step = 1; step <= cfg->steps; ++step) {
+    cv_forward(d, P, F.B, F.hv, F.a, F.Dg, F.loss_part, st);
+    if (step == 1) first = cv_loss_host(F, st);
+    cv_backward_kernel<<<dim3(F.nchunk, d), 256, 0, st>>>(F.B, F.Dg, P, d, F.grad_part);
+    const float lr = (float)(0.5 * cfg->lr * (1.0 + std::cos(M_PI * (double)(step - 1) / (double)cfg->steps)));
+    cv_adam_kernel<<<(F.npar + 255) / 256, 256, 0, st>>>(F.grad_part, F.nchunk, F.npar, F.a, F.m1, F.m2, step, lr);
+  }
+  cv_forward(d, P, F.B, F.hv, F.a, F.Dg, F.loss_part, st);
+  last = cv_loss_host(F, st);
+  std::vector<float> af(F.npar);
+  cudaMemcpyAsync(af.data(), F.a, (size_t)F.npar * 4, cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "control-variate training");
+  for (int q = 0; q < F.npar; ++q) a_out[q] = bf16_round(af[q]);
+  if (loss_out) {
+    loss_out[0] = first;
+    loss_out[1] = last;
+  }
+  return QMC_OK;
+}
+
+int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts, qmc_transform t,
+                     const qmc_integrand* f, const qmc_cv_config* cfg, const float* a, qmc_result* out,
+                     double* per_shift, void* stream) {
+  int rc = cv_check(d, cfg);
+  if (rc) return rc;
+  rc = validate_problem(d, n, m, g, shifts, t, f);
+  if (rc) return rc;
+  if (!a || !out) return fail(QMC_EINVAL, "null parameters or result");
+  if (f->kind != QMC_F_SECTOR || f->precision != QMC_FP32EVAL || f->aU != -2 || f->aF != -1 ||
+      poly_degree(f->U, d) > 1 || poly_degree(f->F, d) > 2)
+    return fail(QMC_EUNSUPPORTED, "control variate: FP32EVAL U^-2 F^-1 sector with deg U <= 1, deg F <= 2");
+  const int tr = t.kind == QMC_TRANSFORM_KOROBOV ? TR_KOROBOV : (t.kind == QMC_TRANSFORM_BAKER ? TR_BAKER : TR_NONE);
+  const void* func = nullptr;
+  switch (d) {
+    case 1: func = cv_kernel_ptr<1>(tr, t.alpha); break;
+    case 2: func = cv_kernel_ptr<2>(tr, t.alpha); break;
+    case 3: func = cv_kernel_ptr<3>(tr, t.alpha); break;
+    case 4: func = cv_kernel_ptr<4>(tr, t.alpha); break;
+    case 5: func = cv_kernel_ptr<5>(tr, t.alpha); break;
+    case 6: func = cv_kernel_ptr<6>(tr, t.alpha); break;
+    case 7: func = cv_kernel_ptr<7>(tr, t.alpha); break;
+    case 8: func = cv_kernel_ptr<8>(tr, t.alpha); break;
+  }
+  if (!func) return fail(QMC_EUNSUPPORTED, "control variate: transform must be none, baker or Korobov 3");
+  std::unique_ptr<CvParams> C(new CvParams());
+  std::memset(C.get(), 0, sizeof(CvParams));
+  fill_common(C->base, d, n, g, t, f);
+  auto cu = pack_dense(f->U, d, 1);
+  auto cf = pack_dense(f->F, d, 2);
+  for (size_t i = 0; i < cu.size(); ++i) C->base.cU[i] = (float)cu[i];
+  for (size_t i = 0; i < cf.size(); ++i) C->base.cF[i] = (float)cf[i];
+  C->base.value_scale = 1.0;
+  const int npar = kCvR * d * kCvK;
+  for (int q = 0; q < npar; ++q) C->a[q] = a[q];
+  C->freq = (float)cfg->freq_step;
+  double gint = 0.0;
+  for (int r = 0; r < kCvR; ++r) {
+    double p = 1.0;
+    for (int i = 0; i < d; ++i) p *= (double)a[(r * d + i) * kCvK];
+    gint += p;
+  }
+  Plan pl;
+  pl.d = d;
+  pl.n = n;
+  pl.m = m;
+  pl.is_complex = 1;
+  pl.final_scale = 1.0;
+  pl.offset[0] = gint;
+  pl.mc = kCvMc;
+  int nblk = 0, L = 0;
+  uint64_t tiles = 0;
+  rc = choose_grid(func, 0, n, nblk, L, tiles, 0);
+  if (rc) return rc;
+  C->base.L = L;
+  C->base.tiles = tiles;
+  C->base.nblk = nblk;
+  pl.nblk = nblk;
+  pl.func = func;
+  for (int k0 = 0; k0 < m; k0 += kCvMc) {
+    const int mk = std::min(kCvMc, m - k0);
+    C->base.m_launch = mk;
+    C->base.k_base = k0;
+    for (int kk = 0; kk < kCvMc; ++kk)
+      for (int i = 0; i < d; ++i) {
+        const int src = kk < mk ? k0 + kk : k0;
+        uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
+        C->base.shift64[kk][i] = s64;
+        C->base.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
+      }
+    Launch ln;
+    ln.func = func;
+    ln.grid = dim3(nblk);
+    ln.params.resize(sizeof(CvParams));
+    std::memcpy(ln.params.data(), C.get(), sizeof(CvParams));
+    pl.launches.push_back(std::move(ln));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = plan_alloc(&pl, st, true);
+  if (rc) return rc;
+  rc = plan_execute(&pl, out, per_shift, st);
+  plan_free(&pl, st);
+  return rc;
+}
+
+}  // extern "C"

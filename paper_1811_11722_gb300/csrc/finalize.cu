@@ -7,10 +7,10 @@ namespace qmc {
 
 constexpr int kFinThreads = 256;
 
-// One CTA.  Warp w adds the CTA slots of (shift, part) tasks w, w+8, ... in a
-// fixed order; warp 0 then forms Qbar and the two-pass sigma^2 per part.
-__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArgs A) {
-  extern __shared__ double q[];  // [m][2]
+// One CTA per problem.  Warp w adds the CTA slots of (shift, part) tasks
+// w, w+8, ... in a fixed order; warp 0 then forms Qbar and the two-pass
+// sigma^2 per part.
+__device__ void finalize_one(const FinalizeArgs& A, double* q /* shared [m][2] */) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int parts = A.is_complex ? 2 : 1;
   const int tasks = A.m * parts;
@@ -20,10 +20,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
     double s = 0.0;
     for (int b = lane; b < A.nblk; b += 32) s += A.partial[((size_t)k * A.nblk + b) * 2 + part];
     s = warp_sum_d(s);
-    if (lane == 0) q[2 * k + part] = (s * A.value_scale) / dn;
+    if (lane == 0) q[2 * k + part] = (s * A.value_scale) / dn + A.offset[part];
   }
   if (!A.is_complex)
-    for (int k = threadIdx.x; k < A.m; k += kFinThreads) q[2 * k + 1] = 0.0;
+    for (int k = threadIdx.x; k < A.m; k += kFinThreads) q[2 * k + 1] = A.offset[1];
   __syncthreads();
   if (A.per_shift)
     for (int t = threadIdx.x; t < 2 * A.m; t += kFinThreads) A.per_shift[t] = q[t];
@@ -58,6 +58,19 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
   }
 }
 
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArgs A) {
+  extern __shared__ double q[];
+  finalize_one(A, q);
+}
+
+// Batched final pass: CTA b finalises problem b.
+__global__ void __launch_bounds__(kFinThreads) finalize_batch_kernel(const FinalizeArgs* __restrict__ args) {
+  extern __shared__ double q[];
+  const FinalizeArgs A = args[blockIdx.x];
+  finalize_one(A, q);
+}
+
 const void* finalize_ptr() { return (const void*)&finalize_kernel; }
+const void* finalize_batch_ptr() { return (const void*)&finalize_batch_kernel; }
 
 }  // namespace qmc

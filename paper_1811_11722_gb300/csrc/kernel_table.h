@@ -11,9 +11,10 @@ namespace qmc {
 
 // Dense sector kernel, U of degree ku, F of degree kf, d = D <= kDFast.
 // One explicit specialisation per (precision, D), each in its own unit.
+// Only U^-2 F^-1; check selects the NaN/Inf-counting variant.
 template <typename R, int D>
-const void* sector_ptr(int mc, int tr, int alpha, int ku, int kf);
-#define QMC_DECL_SECTOR(R, D) template <> const void* sector_ptr<R, D>(int, int, int, int, int);
+const void* sector_ptr(int mc, int tr, int alpha, int ku, int kf, bool check);
+#define QMC_DECL_SECTOR(R, D) template <> const void* sector_ptr<R, D>(int, int, int, int, int, bool);
 QMC_DECL_SECTOR(float, 1) QMC_DECL_SECTOR(float, 2) QMC_DECL_SECTOR(float, 3) QMC_DECL_SECTOR(float, 4)
 QMC_DECL_SECTOR(float, 5) QMC_DECL_SECTOR(float, 6) QMC_DECL_SECTOR(float, 7) QMC_DECL_SECTOR(float, 8)
 QMC_DECL_SECTOR(double, 1) QMC_DECL_SECTOR(double, 2) QMC_DECL_SECTOR(double, 3) QMC_DECL_SECTOR(double, 4)
@@ -47,8 +48,10 @@ template <> const void* general_ptr_t<float>();
 template <> const void* general_ptr_t<double>();
 inline const void* general_ptr(bool fp32) { return fp32 ? general_ptr_t<float>() : general_ptr_t<double>(); }
 
-// Final deterministic pass: per-shift sums -> Q^(k), Qbar, sigma^2.
+// Final deterministic pass: per-shift sums -> Q^(k), Qbar, sigma^2; the
+// batched form takes a device array of FinalizeArgs, one CTA per problem.
 const void* finalize_ptr();
+const void* finalize_batch_ptr();
 
 // Arguments of the final pass.
 struct FinalizeArgs {
@@ -59,6 +62,7 @@ struct FinalizeArgs {
   int32_t pad;
   double dn;      // n as a double
   double value_scale;
+  double offset[2];  // added to Q^(k) of each part (control-variate integral)
   unsigned long long* counters;  // [2], reset to zero after reading
   qmc_result* result;            // device
   double* per_shift;             // device [m][2] or null

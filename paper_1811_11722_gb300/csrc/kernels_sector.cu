@@ -15,16 +15,20 @@
 
 namespace qmc {
 
-#define QMC_SECTOR_TR(R, MC, KU, KF)                                                    \
-  do {                                                                                  \
-    if (tr == TR_NONE) return (const void*)&sector_kernel<R, QMC_D, MC, TR_NONE, 0, KU, KF>; \
-    if (tr == TR_BAKER) return (const void*)&sector_kernel<R, QMC_D, MC, TR_BAKER, 0, KU, KF>; \
-    if (tr == TR_KOROBOV && alpha == 3)                                                 \
-      return (const void*)&sector_kernel<R, QMC_D, MC, TR_KOROBOV, 3, KU, KF>;         \
+#define QMC_SECTOR_CK(R, MC, TR, AL, KU, KF)                                                   \
+  do {                                                                                         \
+    if (check) return (const void*)&sector_kernel<R, QMC_D, MC, TR, AL, KU, KF, true>;         \
+    return (const void*)&sector_kernel<R, QMC_D, MC, TR, AL, KU, KF, false>;                   \
+  } while (0)
+#define QMC_SECTOR_TR(R, MC, KU, KF)                                              \
+  do {                                                                            \
+    if (tr == TR_NONE) QMC_SECTOR_CK(R, MC, TR_NONE, 0, KU, KF);                  \
+    if (tr == TR_BAKER) QMC_SECTOR_CK(R, MC, TR_BAKER, 0, KU, KF);                \
+    if (tr == TR_KOROBOV && alpha == 3) QMC_SECTOR_CK(R, MC, TR_KOROBOV, 3, KU, KF); \
   } while (0)
 
 template <>
-const void* sector_ptr<QMC_REAL, QMC_D>(int mc, int tr, int alpha, int ku, int kf) {
+const void* sector_ptr<QMC_REAL, QMC_D>(int mc, int tr, int alpha, int ku, int kf, bool check) {
   // FP32 is FMA-pipe bound: shift-chunk sizes 8/16/32 trade registers for
   // reuse of the per-point index work.  FP64 is DP-pipe bound on this part
   // and takes one chunk size.

@@ -26,7 +26,23 @@ struct TuneChoice {
   int mc = 0;          // shifts per launch chunk (8, 16, 32)
   int L = 0;           // points per thread per tile
   int occupancy = 0;   // cap on CTAs per SM
+  int max_ctas = 0;    // cap on CTAs of each launch (batched sectors run side by side)
   bool force_general = false;
+};
+
+// Deep copy of a problem's host inputs (so a plan can be rebuilt by the tuner).
+struct SavedProblem {
+  int d = 0;
+  uint64_t n = 0;
+  int m = 0;
+  qmc_transform t{};
+  std::vector<uint64_t> g;
+  std::vector<double> shifts, cu, cf, c, b;
+  std::vector<uint8_t> eu, ef;
+  std::vector<int32_t> h;
+  qmc_integrand f{};
+  void save(int32_t d_, uint64_t n_, int32_t m_, const uint64_t* g_, const double* shifts_, qmc_transform t_,
+            const qmc_integrand* f_);
 };
 
 struct Plan {
@@ -39,12 +55,15 @@ struct Plan {
   const void* func = nullptr;
   double value_scale = 1.0;
   double final_scale = 1.0;
+  double offset[2] = {0.0, 0.0};  // added to Q^(k) per part by the final pass
   std::vector<Launch> launches;
   Workspace ws{};
   void* ws_base = nullptr;
   bool ws_async = false;
   cudaEvent_t ev_before = nullptr;  // optional timing hook
   cudaEvent_t ev_after = nullptr;
+  TuneChoice tune{};
+  SavedProblem saved;
 };
 
 int fail(int code, const char* fmt, ...);

@@ -98,23 +98,18 @@ __device__ __forceinline__ double coord_used(typename FixT<R>::T X) {
 
 // --------------------------------------------------- sector, dense, fast --
 
-// f = U^aU F^aF with U, F dense of degrees KU, KF, times the transform weight.
+// f = U^-2 F^-1 with U, F dense of degrees KU, KF, times the transform weight
+// (other integer powers go to the general kernel, so this path has no
+// per-evaluation branch).
 template <typename R, int D, int TR, int ALPHA, int KU, int KF>
-__device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename FixT<R>::T* base, int k,
-                                          R* zout = nullptr) {
+__device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename FixT<R>::T* base, int k) {
   R z[D];
   R w = R(1);
 #pragma unroll
   for (int i = 0; i < D; ++i) z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
-  if (zout) {
-#pragma unroll
-    for (int i = 0; i < D; ++i) zout[i] = z[i];
-  }
-  R U = poly_dense<D, KU>(P.cU, z);
-  R F = poly_dense<D, KF>(P.cF, z);
-  R v;
-  if (P.aU == -2 && P.aF == -1) v = recip(U * U * F);
-  else v = ipow(U, P.aU) * ipow(F, P.aF);
+  const R U = poly_dense<D, KU>(P.cU, z);
+  const R F = poly_dense<D, KF>(P.cF, z);
+  R v = recip(U * U * F);
   if constexpr (TR == TR_KOROBOV) v *= w;
   return v;
 }
@@ -164,7 +159,11 @@ __device__ __forceinline__ void block_epilogue(Acc<R>* acc, int mk, unsigned nba
   }
 }
 
-template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF>
+// Shift rows mk..MC-1 of a partial last chunk are padded by the host with
+// copies of row 0, so the unrolled shift loop carries no predicate; only the
+// epilogue drops them.  CHECK: count and leave out NaN/Inf values (off when
+// the host has shown U and F positive on the cube).
+template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF, bool CHECK>
 __global__ void __launch_bounds__(kThreads)
     sector_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
                   unsigned long long* __restrict__ counters, const SampleIO sio) {
@@ -174,7 +173,6 @@ __global__ void __launch_bounds__(kThreads)
     return;
   }
   const uint32_t n = (uint32_t)P.n;
-  const int mk = P.m_launch;
   Acc<R> acc[MC];
 #pragma unroll
   for (int kk = 0; kk < MC; ++kk) acc[kk].init();
@@ -194,15 +192,13 @@ __global__ void __launch_bounds__(kThreads)
       for (int i = 0; i < D; ++i) base[i] = fix_base<R>(idx[i], P.rc);
 #pragma unroll
       for (int kk = 0; kk < MC; ++kk) {
-        if (kk < mk) {
-          R v = sector_value<R, D, TR, ALPHA, KU, KF>(P, base, kk);
-          if (P.check_finite) {
-            bool ok = finite_(v);
-            nbad += ok ? 0u : 1u;
-            v = ok ? v : R(0);
-          }
-          acc[kk].add(v);
+        R v = sector_value<R, D, TR, ALPHA, KU, KF>(P, base, kk);
+        if constexpr (CHECK) {
+          const bool ok = finite_(v);
+          nbad += (ok || kk >= P.m_launch) ? 0u : 1u;  // padded rows are not counted
+          v = ok ? v : R(0);
         }
+        acc[kk].add(v);
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
@@ -214,7 +210,8 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
   }
-  block_epilogue<R, MC>(acc, mk, nbad, P, partial, counters);
+  if constexpr (!CHECK) nbad = 0;
+  block_epilogue<R, MC>(acc, P.m_launch, nbad, P, partial, counters);
 }
 
 // ------------------------------------------------ separable integrands --

@@ -94,16 +94,20 @@ def lib():
             L.qmc_plan_destroy.argtypes = [vp]
             L.qmc_plan_launches.argtypes = [vp, ctypes.POINTER(i32)]
             L.qmc_plan_record_events.argtypes = [vp, vp, vp]
+            L.qmc_plan_tune.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.qmc_integrate_batch.argtypes = [i32, vp, vp, vp, vp]
             L.qmc_batch_plan_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
             L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
             L.qmc_batch_plan_destroy.argtypes = [vp]
+            L.qmc_batch_plan_launches.argtypes = [vp, ctypes.POINTER(i32)]
+            L.qmc_batch_plan_tune.argtypes = [vp, vp, vp, ctypes.POINTER(u64)]
             L.qmc_sample_points.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, i32, vp, vp, vp, vp, vp, vp]
             L.qmc_last_error.restype = ctypes.c_char_p
             L.qmc_version.restype = i32
             for name in ("qmc_make_lattice", "qmc_integrate", "qmc_plan_create", "qmc_plan_execute",
-                         "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_integrate_batch", "qmc_batch_plan_create",
-                         "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_sample_points"):
+                         "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_plan_tune", "qmc_integrate_batch", "qmc_batch_plan_create",
+                         "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_batch_plan_launches",
+                         "qmc_batch_plan_tune", "qmc_sample_points"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -237,6 +241,12 @@ class Plan:
                allow_warnings=True)
         return None
 
+    def tune(self, stream=0) -> int:
+        """qmc_plan_tune: returns the chosen shifts-per-launch."""
+        v = ctypes.c_int32(0)
+        _check(lib().qmc_plan_tune(self.h, ctypes.c_void_p(stream), ctypes.byref(v)))
+        return int(v.value)
+
     def record_events(self, before_rule=None, after_rule=None):
         """cudaEvent_t handles (ints) recorded around the rule kernels of later executes."""
         _check(lib().qmc_plan_record_events(self.h, ctypes.c_void_p(before_rule or 0),
@@ -317,6 +327,17 @@ class BatchPlan:
         _check(lib().qmc_batch_plan_execute(self.h, _addr(out), _addr(per_shift), ctypes.c_void_p(stream)),
                allow_warnings=True)
         return None
+
+    def launches(self) -> int:
+        v = ctypes.c_int32(0)
+        _check(lib().qmc_batch_plan_launches(self.h, ctypes.byref(v)))
+        return int(v.value)
+
+    def tune(self, stream=0) -> int:
+        w = ctypes.c_uint64(0)
+        _check(lib().qmc_batch_plan_tune(self.h, ctypes.cast(self.b.arr, ctypes.c_void_p), ctypes.c_void_p(stream),
+                                         ctypes.byref(w)))
+        return int(w.value)
 
     def destroy(self):
         if self.h:

@@ -367,3 +367,84 @@ def test_deformed_lambda_zero_equals_real_kernel(Q):
     a, pa = gpu_run(Q, real, g, "fp64")
     b, pb = gpu_run(Q, cplx, g, "fp64")
     assert np.allclose(pa[:, 0], pb[:, 0], rtol=1e-13, atol=0) and np.all(pb[:, 1] == 0.0)
+
+
+# -------------------------------------------------------------------- batch --
+
+def _batch_tuple(Q, p, g, precision=None):
+    return (p.d, p.n, p.m, g, p.shifts, Q.transform(p.transform, p.alpha), Q.integrand_from_problem(p, precision))
+
+
+def test_batch_matches_oracle_per_problem(Q, oracle_lib, nthreads):
+    """A mixed batch (FP32 sectors of d = 2..8 from the batched-sector
+    generator at reduced n, an FP64 separable problem, a deformed FP64
+    problem): every problem's per-shift values match the oracle."""
+    sect = I.config3(count=10)
+    probs = []
+    for s, p in enumerate(sect):
+        p.n = I.prev_prime(20000 + 3000 * s)
+        probs.append(p)
+    probs.append(I.config1())
+    probs.append(_c4(n=20011, m=8))
+    gs = [I.random_generating_vector(I.SplitMix64(500 + i), p.d, p.n) for i, p in enumerate(probs)]
+    tuples = [_batch_tuple(Q, p, g) for p, g in zip(probs, gs)]
+    res, ps = Q.qmc_integrate_batch(tuples, want_per_shift=True)
+    off = 0
+    for p, g, r in zip(probs, gs, res):
+        ref = oracle_lib.integrate(p, g, nthreads=nthreads)
+        q = ps[2 * off: 2 * (off + p.m)].reshape(p.m, 2)
+        off += p.m
+        refc = ref["q"][:, 0] + 1j * ref["q"][:, 1]
+        tol = 4e-7 if p.precision == "fp32" else 1e-12
+        assert np.all(np.abs((q[:, 0] + 1j * q[:, 1]) - refc) <= tol * np.abs(refc)), p.name
+        assert r.status == 0
+
+
+def test_batch_plan_graph_replay_and_tune(Q):
+    """The batch plan builds its CUDA graph once; replays give identical
+    results, tuning keeps results within FP32 rounding, and the launch count
+    is one per (problem, shift chunk) plus the final pass."""
+    sect = I.config3(count=24)
+    for s, p in enumerate(sect):
+        p.n = I.prev_prime(50000 + 7000 * s)
+    gs = [I.random_generating_vector(I.SplitMix64(700 + i), p.d, p.n) for i, p in enumerate(sect)]
+    tuples = [_batch_tuple(Q, p, g) for p, g in zip(sect, gs)]
+    bp = Q.BatchPlan(tuples)
+    a = [r.as_dict() for r in bp.execute()]
+    b = [r.as_dict() for r in bp.execute()]
+    for x, y in zip(a, b):
+        assert x["mean"][0] == y["mean"][0] and x["var"][0] == y["var"][0]
+    assert bp.launches() == len(sect) + 1
+    w = bp.tune()
+    assert (1 << 18) <= w <= (1 << 24)
+    c = [r.as_dict() for r in bp.execute()]
+    for x, y in zip(a, c):
+        assert abs(x["mean"][0] - y["mean"][0]) <= 1e-7 * abs(x["mean"][0])
+    bp.destroy()
+
+
+def test_config3_full_batch_sampled(Q, oracle_lib, nthreads):
+    """The full batched-sector configuration (256 sectors, ~9.3e9 evaluations):
+    every status OK, and the six smallest sectors checked against the oracle."""
+    sect = I.config3()
+    gs = [I.random_generating_vector(I.SplitMix64(900 + i), p.d, p.n) for i, p in enumerate(sect)]
+    tuples = [_batch_tuple(Q, p, g) for p, g in zip(sect, gs)]
+    res, ps = Q.qmc_integrate_batch(tuples, want_per_shift=True)
+    assert all(r.status == 0 for r in res)
+    offs = np.cumsum([0] + [p.m for p in sect])
+    for i in sorted(range(len(sect)), key=lambda i: sect[i].n)[:6]:
+        ref = oracle_lib.integrate(sect[i], gs[i], nthreads=nthreads)
+        q = ps[2 * offs[i]: 2 * offs[i + 1]].reshape(sect[i].m, 2)
+        assert np.all(np.abs(q[:, 0] - ref["q"][:, 0]) <= 4e-7 * np.abs(ref["q"][:, 0]))
+
+
+def test_plan_tune_keeps_results(Q):
+    p = I.config2(n=1000003, m=32)
+    g = I.random_generating_vector(I.SplitMix64(3), 6, p.n)
+    plan = Q.Plan(p.d, p.n, p.m, g, p.shifts, Q.transform("baker"), Q.integrand_from_problem(p, "fp32"))
+    a = plan.execute().as_dict()
+    mc = plan.tune()
+    assert mc in (8, 16, 32)
+    b = plan.execute().as_dict()
+    assert abs(a["mean"][0] - b["mean"][0]) <= 1e-7 * abs(a["mean"][0])
+    plan.destroy()
