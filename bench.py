@@ -186,6 +186,63 @@ def run_reference(args, rank, world):
     return 0
 
 
+def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
+    """Wall time until err/|Qbar| <= tol walking the lattice ladder (largest prime
+    <= 2^(e/2)), each level a fresh rule with its CBC vector; lattice
+    construction is a precompute and is not timed, everything else is.
+    Compares the plain rule, the control variate (training included) and the
+    batched sectors."""
+    out = {}
+    ladder = [n for n in I.ladder_primes() if n >= 65521]
+    sh = torch.cuda.current_stream().cuda_stream
+
+    def lattices(d, gamma):
+        return {n: qmc.qmc_make_lattice(d, n, gamma) for n in ladder}
+
+    # plain rule on the single-sector workload and on the d=8 Korobov-3 sector
+    for name, p in (("sector_d6_baker_fp32", I.config2()), ("sector_d8_korobov3_fp32", I.config5())):
+        lat = lattices(p.d, p.gamma)
+        f = qmc.integrand_from_problem(p, "fp32")
+        t = qmc.transform(p.transform, p.alpha)
+        wall, rec = 0.0, None
+        for n in ladder:
+            t0 = time.perf_counter()
+            r, _ = qmc.qmc_integrate(p.d, n, p.m, lat[n], p.shifts, t, f, stream=sh)
+            wall += time.perf_counter() - t0
+            rel = r.err[0] / abs(r.mean[0])
+            rec = {"n": n, "rel_err": rel, "mean": r.mean[0], "wall_s": wall}
+            if rel <= tol or wall > budget_s:
+                break
+        rec["reached"] = rec["rel_err"] <= tol
+        out[name] = rec
+    # control variate on the d=8 sector (pilot n=65537, 2000 Adam steps), both bases
+    p = I.config5()
+    lat = lattices(p.d, p.gamma)
+    gp = qmc.qmc_make_lattice(p.d, I.N_PILOT, p.gamma)
+    f = qmc.integrand_from_problem(p, "fp32")
+    t = qmc.transform(p.transform, p.alpha)
+    for freq in (1, 2):
+        cfg = qmc.qmc_cv_config()
+        cfg.R, cfg.K, cfg.freq_step, cfg.steps, cfg.lr, cfg.seed = 16, 32, freq, 2000, 1e-2, 7
+        t0 = time.perf_counter()
+        a, losses = qmc.qmc_cv_train(p.d, I.N_PILOT, gp, I.make_shifts(I.SplitMix64(54), 1, p.d)[0], t, f, cfg)
+        wall = time.perf_counter() - t0
+        train_s = wall
+        rec = None
+        for n in ladder:
+            t0 = time.perf_counter()
+            r, _ = qmc.qmc_integrate_cv(p.d, n, p.m, lat[n], p.shifts, t, f, cfg, a, stream=sh)
+            wall += time.perf_counter() - t0
+            rel = r.err[0] / abs(r.mean[0])
+            rec = {"n": n, "rel_err": rel, "plain_rel_err_same_points": r.err[1] / abs(r.mean[1]), "mean": r.mean[0],
+                   "wall_s": wall, "train_s": train_s, "loss": [float(losses[0]), float(losses[1])]}
+            if rel <= tol or wall > budget_s:
+                break
+        rec["reached"] = rec["rel_err"] <= tol
+        out[f"sector_d8_korobov3_cv_freq{freq}"] = rec
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +250,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner (profiler captures)")
+    ap.add_argument("--time-to-tol", action="store_true",
+                    help="also measure wall time to 1e-8 relative error (plain vs control variate)")
     ap.add_argument("--n", type=int, default=None,
                     help="smaller prime lattice size, for profiler captures only (changes the workload)")
     args = ap.parse_args()
@@ -219,7 +279,7 @@ def main():
     f = qmc.integrand_from_problem(p, "fp32")
     t = qmc.transform(p.transform, p.alpha)
     plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
-    shifts_per_launch = plan.tune(torch.cuda.current_stream().cuda_stream)   # autotuner, untimed
+    shifts_per_launch = 32 if args.no_tune else plan.tune(torch.cuda.current_stream().cuda_stream)  # untimed
     launches_per_step = plan.launches()
 
     stream = torch.cuda.current_stream()
@@ -306,6 +366,9 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, g)
+    if args.time_to_tol and rank == 0:
+        from paper_1811_11722_gb300 import inputs as I
+        line["time_to_1e-8"] = time_to_tolerance(qmc, I, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.destroy()

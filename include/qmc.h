@@ -212,11 +212,11 @@ int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* 
                         uint64_t* work_per_cta_out);
 
 /* Learned control variate (a separable rank-R cosine surrogate):
- *   g(x) = sum_{r<R} prod_{i<d} sum_{k<K} a[(r*d + i)*K + k] cos(F pi k x_i),
+ *   g(z) = sum_{r<R} prod_{i<d} sum_{k<K} a[(r*d + i)*K + k] cos(F pi k z_i),
  *   int_[0,1]^d g = sum_r prod_i a[(r*d + i)*K]
- * fitted to h(x) = f(z(x)) prod_i w(x_i), the transformed integrand the rule
- * of Eq. (2) sums, so that Q^(k)[h - g] + int g is an unbiased estimate with
- * the same Eq. (3) error estimate.  This build: R = 16, K = 32, d <= 8.
+ * fitted to the integrand f, so that Q^(k)[f - g] + int g, the rule of Eq. (2)
+ * applied to f - g after the periodizing transform, is an unbiased estimate
+ * with the same Eq. (3) error estimate.  This build: R = 16, K = 32, d <= 8.
  *   freq_step  F: 1 -> cos(pi k x); 2 -> cos(2 pi k x) (1-periodic basis)
  *   steps, lr  full-batch Adam (beta 0.9, 0.999), rate lr * (1 + cos(pi s/steps)) / 2
  *   seed       SplitMix64 seed of the initial parameters */
@@ -230,9 +230,10 @@ typedef struct {
   uint64_t seed;
 } qmc_cv_config;
 
-/* Fit the surrogate on the GPU to the n_pilot points of one shifted lattice
- * (g_pilot, shift_pilot [d]) of the rule's integrand (evaluated in FP64 by
- * the rule's own kernel), mean squared error, FP32 training kernels.
+/* Fit the surrogate on the GPU to f at the n_pilot points of one shifted
+ * lattice (g_pilot, shift_pilot [d]) on the untransformed cube (f evaluated in
+ * FP64 by the rule's own kernel; t is not used here), mean squared error,
+ * FP32 training kernels.
  *   a_out     [R*d*K] host, the parameters rounded to bfloat16 (stored as float)
  *   loss_out  optional [2] host: loss before the first and after the last step
  * Synchronises `stream`. */
@@ -240,10 +241,11 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
                  qmc_transform t, const qmc_integrand* f, const qmc_cv_config* cfg, float* a_out,
                  double* loss_out, void* stream);
 
-/* The rule with the control variate: one pass evaluates h and g at every
- * point and shift.  out->mean[0], var[0], err[0] are the control-variate
- * estimate Q[h - g] + int g; out->mean[1], var[1], err[1] the plain rule's
- * Q[h] from the same points (the fallback: keep whichever error is smaller).
+/* The rule with the control variate: one pass evaluates f and g at every
+ * transformed point z(x) and sums both times the transform weight.
+ * out->mean[0], var[0], err[0] are the control-variate estimate
+ * Q[f - g] + int g; out->mean[1], var[1], err[1] the plain rule's Q[f] from
+ * the same points (the fallback: keep whichever error is smaller).
  * per_shift (optional, [m*2]) gets the two per-shift values.  Supports
  * FP32EVAL sector integrands U^-2 F^-1 with deg U <= 1, deg F <= 2, d <= 8,
  * transform none, baker or Korobov 3. */

@@ -58,9 +58,9 @@ typedef struct {
   const double* c;       /* separable: prod (1 + c_i z_i) exp(b_i z_i) */
   const double* b;
   const int32_t* h;      /* trig: cos(2 pi h . z) */
-  /* optional control variate subtracted from every weighted value:
-   * g(x) = sum_{r<cvR} prod_{i<d} sum_{k<cvK} a[(r*d + i)*cvK + k] cos(cvF pi k x_i)
-   * evaluated at the lattice point x itself (before the transform) */
+  /* optional control variate g(z) = sum_{r<cvR} prod_{i<d} sum_{k<cvK}
+   * a[(r*d + i)*cvK + k] cos(cvF pi k z_i), subtracted from f at the
+   * transformed point z (so the value becomes (f - g)(z) prod_i w_i) */
   int cvR, cvK, cvF;
   const float* cva;
 } orc_problem;
@@ -397,12 +397,9 @@ int orc_point(const orc_problem* p, uint64_t n, const uint64_t* g, const double*
   val[0] = f[0] * wprod;
   val[1] = f[1] * wprod;
   if (p->cva) {
-    double x[ORC_DMAX];
-    for (int i = 0; i < p->d; ++i) {
-      double y = (double)orc_index(jm1, g[i], n) / (double)n + shift[i];
-      x[i] = (y >= 1.0) ? y - 1.0 : y;
-    }
-    val[0] -= orc_cv_g(p->d, p->cvR, p->cvK, p->cvF, p->cva, x);
+    /* Q[f - g] + int g: the surrogate is subtracted from f before the
+     * transform, so the rule sums (f - g)(z(x)) prod_i w(x_i) */
+    val[0] -= orc_cv_g(p->d, p->cvR, p->cvK, p->cvF, p->cva, z) * wprod;
   }
   return 0;
 }

@@ -41,6 +41,8 @@ def _units():
             units.append((f"sector_{real}_{d}.o", "kernels_sector.cu", [f"-DQMC_REAL={real}", f"-DQMC_D={d}"]))
     for real in ("float", "double"):
         units.append((f"misc_{real}.o", "kernels_misc.cu", [f"-DQMC_REAL={real}"]))
+    for d in SECTOR_DIMS:
+        units.append((f"cv_{d}.o", "cv_inst.cu", [f"-DQMC_D={d}"]))
     for src in ("finalize.cu", "api.cu", "deformed.cu", "batch.cu", "cbc.cpp", "cv.cu", "noalloc.cu"):
         if os.path.exists(os.path.join(CSRC, src)):
             units.append((os.path.splitext(src)[0] + ".o", src, []))

@@ -1,15 +1,19 @@
 // Learned control variate for the lattice rule.
 //
 // Surrogate (separable rank-R cosine expansion, R = 16, K = 32):
-//   g(x) = sum_{r<R} prod_{i<d} C_ri(x_i),  C_ri(x) = sum_{k<K} a_rik cos(F pi k x),
-//   int_[0,1]^d g = sum_r prod_i a_ri0          (int_0^1 cos(F pi k x) dx = 0, k >= 1)
-// fitted by Adam to h(x) = f(z(x)) prod_i w(x_i), the transformed integrand the
-// rule sees, on the points of a pilot lattice.  The estimator
-//   Q^(k)[h - g] + int g
-// is unbiased for any g whose integral is known exactly; the kernel also sums
-// Q^(k)[h] in the same pass, so every result carries the plain rule's
-// estimate beside the control-variate one and the caller keeps whichever has
-// the smaller Eq. (3) error.
+//   g(z) = sum_{r<R} prod_{i<d} C_ri(z_i),  C_ri(z) = sum_{k<K} a_rik cos(F pi k z),
+//   int_[0,1]^d g = sum_r prod_i a_ri0          (int_0^1 cos(F pi k z) dz = 0, k >= 1)
+// fitted by Adam to the integrand f itself (untransformed variables) on the
+// points of a pilot lattice.  The estimator is Q^(k)[f - g] + int g: the rule
+// sums (f - g)(z(x)) prod_i w(x_i), and since the substitution z(x) keeps the
+// integral, int (g o z) prod w = int g.  Subtracting g before the transform
+// keeps the smoothness and periodicity the Korobov transform gives the
+// summand; a surrogate fitted to the transformed integrand instead breaks
+// them and loses the lattice rule's fast convergence.  The estimator is
+// unbiased for any g whose integral is known exactly; the kernel also sums
+// the plain Q^(k)[f] in the same pass, so every result carries the plain
+// rule's estimate beside the control-variate one and the caller keeps
+// whichever has the smaller Eq. (3) error.
 //
 // Training kernels (FP32 CUDA cores, FP64 loss):
 //   cv_basis     B[i][j][k] = cos(F pi k x_ji) for the pilot points
@@ -24,175 +28,10 @@
 #include <memory>
 #include <vector>
 
+#include "cv_device.cuh"
 #include "plan.h"
-#include "rule_kernels.cuh"
 
 namespace qmc {
-
-constexpr int kCvR = 16;
-constexpr int kCvK = 32;
-constexpr int kCvDMax = 8;
-constexpr int kCvMc = 8;            // shifts per estimator launch
-constexpr int kCvChunk = 2048;      // pilot points per backward CTA
-
-struct CvParams {
-  RuleParams<float> base;
-  float a[kCvR * kCvDMax * kCvK];   // [r][i][k] with row stride d (packed for the actual d)
-  float freq;                       // F: 1 -> cos(pi k x), 2 -> cos(2 pi k x)
-  int32_t pad;
-};
-
-// ------------------------------------------------------------- estimator --
-
-// sum_r prod_i sum_k a_rik T_k(cos(F pi x_i)) with the Chebyshev recurrence.
-template <int D>
-__device__ __forceinline__ float cv_g(const CvParams& C, const float* x) {
-  float pr[kCvR];
-#pragma unroll
-  for (int r = 0; r < kCvR; ++r) pr[r] = 1.0f;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    const float c1 = cospif(C.freq * x[i]);
-    const float two = c1 + c1;
-    float cr[kCvR];
-#pragma unroll
-    for (int r = 0; r < kCvR; ++r) cr[r] = fmaf(C.a[(r * D + i) * kCvK + 1], c1, C.a[(r * D + i) * kCvK]);
-    float t0 = 1.0f, t1 = c1;
-#pragma unroll
-    for (int k = 2; k < kCvK; ++k) {
-      const float t2 = fmaf(two, t1, -t0);
-#pragma unroll
-      for (int r = 0; r < kCvR; ++r) cr[r] = fmaf(C.a[(r * D + i) * kCvK + k], t2, cr[r]);
-      t0 = t1;
-      t1 = t2;
-    }
-#pragma unroll
-    for (int r = 0; r < kCvR; ++r) pr[r] *= cr[r];
-  }
-  float g = 0.0f;
-#pragma unroll
-  for (int r = 0; r < kCvR; ++r) g += pr[r];
-  return g;
-}
-
-// (h - g, h) at one point and shift; h = U^-2 F^-1 times the transform weight.
-template <int D, int TR, int ALPHA>
-__device__ __forceinline__ void cv_value(const CvParams& C, const uint32_t* base, int k, float& hv, float& gv) {
-  const RuleParams<float>& P = C.base;
-  float z[D], x[D];
-  float w = 1.0f;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    const uint32_t X = base[i] + P.shift32[k][i];
-    x[i] = unit_f32(X) - 1.0f;
-    // Korobov factors normalised one by one (exact constant per factor), so
-    // h needs no large constant that float could not represent exactly
-    z[i] = coord<float, TR, 0>(X, P.kor, P.alpha, w);
-  }
-  const float U = poly_dense<D, 1>(P.cU, z);
-  const float F = poly_dense<D, 2>(P.cF, z);
-  float h = recip(U * U * F);
-  if constexpr (TR == TR_KOROBOV) h *= w;
-  hv = h;
-  gv = cv_g<D>(C, x);
-}
-
-template <int D, int TR, int ALPHA>
-__global__ void __launch_bounds__(kThreads)
-    cv_sector_kernel(const __grid_constant__ CvParams C, double* __restrict__ partial,
-                     unsigned long long* __restrict__ counters, const SampleIO sio) {
-  const RuleParams<float>& P = C.base;
-  if (sio.count > 0) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= sio.count) return;
-    uint32_t base[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      uint32_t idx = lattice_index(sio.j[s], P.g[i], P.n);
-      base[i] = fix_base<float>(idx, P.rc);
-      if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
-      if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<float>(base[i] + P.shift32[sio.k[s]][i]);
-    }
-    float h, g;
-    cv_value<D, TR, ALPHA>(C, base, sio.k[s], h, g);
-    sio.values[2 * (size_t)s] = (double)h - (double)g;
-    sio.values[2 * (size_t)s + 1] = (double)g;
-    return;
-  }
-  __shared__ double accs[2][kCvMc][kThreads];
-  const uint32_t n = (uint32_t)P.n;
-  const int mk = P.m_launch;
-  for (int kk = 0; kk < kCvMc; ++kk) {
-    accs[0][kk][threadIdx.x] = 0.0;
-    accs[1][kk][threadIdx.x] = 0.0;
-  }
-  unsigned nbad = 0;
-  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
-  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
-    const uint64_t j0 = tile * tile_pts + threadIdx.x;
-    if (j0 >= P.n) continue;
-    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
-    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
-#pragma unroll 1
-    for (int kk = 0; kk < mk; ++kk) {
-      uint32_t idx[D];
-#pragma unroll
-      for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
-      Acc<float> acv, apl;
-      acv.init();
-      apl.init();
-#pragma unroll 1
-      for (int s = 0; s < steps; ++s) {
-        uint32_t base[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) base[i] = fix_base<float>(idx[i], P.rc);
-        float h, g;
-        cv_value<D, TR, ALPHA>(C, base, kk, h, g);
-        float dv = h - g;
-        const bool ok = finite_(dv) && finite_(h);
-        nbad += ok ? 0u : 1u;
-        acv.add(ok ? dv : 0.0f);
-        apl.add(ok ? h : 0.0f);
-#pragma unroll
-        for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-        if ((s & (kFoldG - 1)) == kFoldG - 1) {
-          acv.fold();
-          apl.fold();
-        }
-      }
-      accs[0][kk][threadIdx.x] += acv.thread_total();
-      accs[1][kk][threadIdx.x] += apl.thread_total();
-    }
-  }
-  __shared__ double red[kThreads / 32][kCvMc][2];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int kk = 0; kk < mk; ++kk) {
-    const double a0 = warp_sum_d(accs[0][kk][threadIdx.x]);
-    const double a1 = warp_sum_d(accs[1][kk][threadIdx.x]);
-    if (lane == 0) {
-      red[warp][kk][0] = a0;
-      red[warp][kk][1] = a1;
-    }
-  }
-  unsigned long long b1 = warp_sum_u64((unsigned long long)nbad);
-  if (lane == 0 && b1) atomicAdd(&counters[0], b1);
-  __syncthreads();
-  if (threadIdx.x < 2 * mk) {
-    const int kk = threadIdx.x >> 1, part = threadIdx.x & 1;
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) s += red[w][kk][part];
-    partial[((size_t)(P.k_base + kk) * P.nblk + blockIdx.x) * 2 + part] = s;
-  }
-}
-
-template <int D>
-static const void* cv_kernel_ptr(int tr, int alpha) {
-  if (tr == TR_BAKER) return (const void*)&cv_sector_kernel<D, TR_BAKER, 0>;
-  if (tr == TR_KOROBOV && alpha == 3) return (const void*)&cv_sector_kernel<D, TR_KOROBOV, 3>;
-  if (tr == TR_NONE) return (const void*)&cv_sector_kernel<D, TR_NONE, 0>;
-  return nullptr;
-}
 
 // -------------------------------------------------------------- training --
 
@@ -209,73 +48,6 @@ __global__ void cv_basis_kernel(const double* __restrict__ x, int P, int d, floa
   float* out = B + ((size_t)i * P + j) * kCvK;
 #pragma unroll 4
   for (int k = 0; k < kCvK; ++k) out[k] = (float)cospi((double)freq * (double)k * xv);
-}
-
-template <int D>
-__global__ void __launch_bounds__(256)
-    cv_forward_kernel(const float* __restrict__ B, const double* __restrict__ hv, const float* __restrict__ a, int P,
-                      float* __restrict__ Dg, double* __restrict__ loss_part) {
-  __shared__ float as[kCvR * D * kCvK];
-  __shared__ double red[8];
-  for (int q = threadIdx.x; q < kCvR * D * kCvK; q += blockDim.x) as[q] = a[q];
-  __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  double l2 = 0.0;
-  if (j < P) {
-    float C[D][kCvR];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      float b[kCvK];
-      const float4* bp = reinterpret_cast<const float4*>(B + ((size_t)i * P + j) * kCvK);
-#pragma unroll
-      for (int q = 0; q < kCvK / 4; ++q) {
-        float4 v = bp[q];
-        b[4 * q] = v.x;
-        b[4 * q + 1] = v.y;
-        b[4 * q + 2] = v.z;
-        b[4 * q + 3] = v.w;
-      }
-#pragma unroll
-      for (int r = 0; r < kCvR; ++r) {
-        float s = 0.0f;
-#pragma unroll
-        for (int k = 0; k < kCvK; ++k) s = fmaf(as[(r * D + i) * kCvK + k], b[k], s);
-        C[i][r] = s;
-      }
-    }
-    float g = 0.0f;
-#pragma unroll
-    for (int r = 0; r < kCvR; ++r) {
-      float p = 1.0f;
-#pragma unroll
-      for (int i = 0; i < D; ++i) p *= C[i][r];
-      g += p;
-    }
-    const double err = (double)g - hv[2 * (size_t)j];
-    l2 = err * err;
-    const float e = (float)(2.0 * err / (double)P);
-#pragma unroll
-    for (int r = 0; r < kCvR; ++r) {
-      float pre[D + 1];
-      pre[0] = 1.0f;
-#pragma unroll
-      for (int i = 0; i < D; ++i) pre[i + 1] = pre[i] * C[i][r];
-      float suf = 1.0f;
-#pragma unroll
-      for (int i = D - 1; i >= 0; --i) {
-        Dg[((size_t)i * P + j) * kCvR + r] = e * pre[i] * suf;
-        suf *= C[i][r];
-      }
-    }
-  }
-  l2 = warp_sum_d(l2);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    loss_part[blockIdx.x] = s;
-  }
 }
 
 // grid (chunks, d); thread t owns outputs (r, k) = (t / 16, 2 (t % 16) + {0, 1}).
@@ -329,24 +101,23 @@ __global__ void cv_adam_kernel(const float* __restrict__ grad_part, int nchunk, 
   a[q] -= lr * mh / (sqrtf(vh) + eps);
 }
 
-template <int D>
-static void cv_launch_forward(int P, const float* B, const double* hv, const float* a, float* Dg, double* loss_part,
-                              cudaStream_t st) {
-  cv_forward_kernel<D><<<(P + 255) / 256, 256, 0, st>>>(B, hv, a, P, Dg, loss_part);
+static const void* cv_forward_for(int d) {
+  switch (d) {
+    case 1: return cv_forward_ptr<1>();
+    case 2: return cv_forward_ptr<2>();
+    case 3: return cv_forward_ptr<3>();
+    case 4: return cv_forward_ptr<4>();
+    case 5: return cv_forward_ptr<5>();
+    case 6: return cv_forward_ptr<6>();
+    case 7: return cv_forward_ptr<7>();
+    default: return cv_forward_ptr<8>();
+  }
 }
 
 static void cv_forward(int d, int P, const float* B, const double* hv, const float* a, float* Dg, double* lp,
                        cudaStream_t st) {
-  switch (d) {
-    case 1: cv_launch_forward<1>(P, B, hv, a, Dg, lp, st); break;
-    case 2: cv_launch_forward<2>(P, B, hv, a, Dg, lp, st); break;
-    case 3: cv_launch_forward<3>(P, B, hv, a, Dg, lp, st); break;
-    case 4: cv_launch_forward<4>(P, B, hv, a, Dg, lp, st); break;
-    case 5: cv_launch_forward<5>(P, B, hv, a, Dg, lp, st); break;
-    case 6: cv_launch_forward<6>(P, B, hv, a, Dg, lp, st); break;
-    case 7: cv_launch_forward<7>(P, B, hv, a, Dg, lp, st); break;
-    default: cv_launch_forward<8>(P, B, hv, a, Dg, lp, st); break;
-  }
+  void* args[6] = {(void*)&B, (void*)&hv, (void*)&a, (void*)&P, (void*)&Dg, (void*)&lp};
+  cudaLaunchKernel(cv_forward_for(d), dim3((P + 255) / 256), dim3(256), args, 0, st);
 }
 
 static float bf16_round(float v) {
@@ -470,8 +241,10 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
   for (int i = 0; i < d; ++i) sh2[i] = sh2[d + i] = shift_pilot[i];
   qmc_integrand f64 = *f;
   f64.precision = QMC_FP64;
+  qmc_transform tnone{QMC_TRANSFORM_NONE, 0};  // g approximates f itself on the cube
+  (void)t;
   Plan pilot;
-  rc = plan_build(&pilot, d, n_pilot, 2, g_pilot, sh2.data(), t, &f64, TuneChoice{});
+  rc = plan_build(&pilot, d, n_pilot, 2, g_pilot, sh2.data(), tnone, &f64, TuneChoice{});
   if (rc) return rc;
   const int P = (int)n_pilot;
   CvFit F;
@@ -573,14 +346,14 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
   const int tr = t.kind == QMC_TRANSFORM_KOROBOV ? TR_KOROBOV : (t.kind == QMC_TRANSFORM_BAKER ? TR_BAKER : TR_NONE);
   const void* func = nullptr;
   switch (d) {
-    case 1: func = cv_kernel_ptr<1>(tr, t.alpha); break;
-    case 2: func = cv_kernel_ptr<2>(tr, t.alpha); break;
-    case 3: func = cv_kernel_ptr<3>(tr, t.alpha); break;
-    case 4: func = cv_kernel_ptr<4>(tr, t.alpha); break;
-    case 5: func = cv_kernel_ptr<5>(tr, t.alpha); break;
-    case 6: func = cv_kernel_ptr<6>(tr, t.alpha); break;
-    case 7: func = cv_kernel_ptr<7>(tr, t.alpha); break;
-    case 8: func = cv_kernel_ptr<8>(tr, t.alpha); break;
+    case 1: func = cv_estimator_ptr<1>(tr, t.alpha); break;
+    case 2: func = cv_estimator_ptr<2>(tr, t.alpha); break;
+    case 3: func = cv_estimator_ptr<3>(tr, t.alpha); break;
+    case 4: func = cv_estimator_ptr<4>(tr, t.alpha); break;
+    case 5: func = cv_estimator_ptr<5>(tr, t.alpha); break;
+    case 6: func = cv_estimator_ptr<6>(tr, t.alpha); break;
+    case 7: func = cv_estimator_ptr<7>(tr, t.alpha); break;
+    case 8: func = cv_estimator_ptr<8>(tr, t.alpha); break;
   }
   if (!func) return fail(QMC_EUNSUPPORTED, "control variate: transform must be none, baker or Korobov 3");
   std::unique_ptr<CvParams> C(new CvParams());
@@ -627,6 +400,7 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
         uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
         C->base.shift64[kk][i] = s64;
         C->base.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
+        C->base.shiftf[kk][i] = (float)(2.0 * shifts[(size_t)src * d + i] - 2.0);
       }
     Launch ln;
     ln.func = func;

@@ -58,6 +58,7 @@ struct RuleParams {
   uint32_t gstep[QMC_DMAX];     // (kThreads * g_i) mod n
   uint64_t shift64[kMcMax][QMC_DMAX];
   uint32_t shift32[kMcMax][QMC_DMAX];
+  float shiftf[kMcMax][QMC_DMAX];   // 2 Delta - 2 (fast FP32 sector path)
   R kor[8];                // Korobov z(s) = s^(a+1) sum_k kor[k] s^k on s <= 1/2;
                            // kor[7] = (2a+1)!/(a!)^2 (general kernel weight)
   R cU[kPolyCoefMax];      // nested-Horner U (dense kernels)

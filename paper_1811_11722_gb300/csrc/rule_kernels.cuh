@@ -83,6 +83,18 @@ __device__ __forceinline__ typename FixT<R>::T shift_of(const RuleParams<R>& P, 
   else return P.shift64[k][i];
 }
 
+// Per-point base of the fast sector path: float frac for FP32, fixed point for FP64.
+template <typename R>
+struct SecBase;
+template <>
+struct SecBase<float> {
+  using T = float;
+};
+template <>
+struct SecBase<double> {
+  using T = uint64_t;
+};
+
 template <typename R, int TR, int ALPHA>
 __device__ __forceinline__ R coord(typename FixT<R>::T X, const R* kor, int alpha, R& w) {
   if constexpr (sizeof(R) == 4) return coord_f32<TR, ALPHA>(X, kor, alpha, w);
@@ -100,13 +112,17 @@ __device__ __forceinline__ double coord_used(typename FixT<R>::T X) {
 
 // f = U^-2 F^-1 with U, F dense of degrees KU, KF, times the transform weight
 // (other integer powers go to the general kernel, so this path has no
-// per-evaluation branch).
+// per-evaluation branch).  FP32: float-domain triangle coordinates from the
+// per-point bases b[i]; FP64: 64-bit fixed point.
 template <typename R, int D, int TR, int ALPHA, int KU, int KF>
-__device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename FixT<R>::T* base, int k) {
+__device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename SecBase<R>::T* base, int k) {
   R z[D];
   R w = R(1);
 #pragma unroll
-  for (int i = 0; i < D; ++i) z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
+  for (int i = 0; i < D; ++i) {
+    if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], P.shiftf[k][i], P.kor, w);
+    else z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
+  }
   const R U = poly_dense<D, KU>(P.cU, z);
   const R F = poly_dense<D, KF>(P.cF, z);
   R v = recip(U * U * F);
@@ -114,20 +130,32 @@ __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename
   return v;
 }
 
+template <typename R>
+__device__ __forceinline__ typename SecBase<R>::T sec_base(uint32_t idx, const Recip& rc) {
+  if constexpr (sizeof(R) == 4) return base_f32(frac64(idx, rc));
+  else return frac64(idx, rc);
+}
+
+template <typename R>
+__device__ __forceinline__ double sec_coord_used(const RuleParams<R>& P, typename SecBase<R>::T b, int k, int i) {
+  if constexpr (sizeof(R) == 4) return coord_tri_used(b, P.shiftf[k][i]);
+  else return coord_used<R>(b + shift_of(P, k, i));
+}
+
 template <typename R, int D, int TR, int ALPHA, int KU, int KF>
 __device__ void sector_sample(const RuleParams<R>& P, const SampleIO& sio) {
-  using FT = typename FixT<R>::T;
+  using BT = typename SecBase<R>::T;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= sio.count) return;
   uint64_t j = sio.j[s];
   int k = sio.k[s];
-  FT base[D];
+  BT base[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     uint32_t idx = lattice_index(j, P.g[i], P.n);
-    base[i] = fix_base<R>(idx, P.rc);
+    base[i] = sec_base<R>(idx, P.rc);
     if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
-    if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<R>(base[i] + shift_of(P, k, i));
+    if (sio.coord) sio.coord[(size_t)s * D + i] = sec_coord_used<R>(P, base[i], k, i);
   }
   R v = sector_value<R, D, TR, ALPHA, KU, KF>(P, base, k);
   sio.values[2 * (size_t)s] = (double)v * (double)P.value_scale;
@@ -187,9 +215,9 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
     for (int s = 0; s < steps; ++s) {
-      FT base[D];
+      typename SecBase<R>::T base[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) base[i] = fix_base<R>(idx[i], P.rc);
+      for (int i = 0; i < D; ++i) base[i] = sec_base<R>(idx[i], P.rc);
 #pragma unroll
       for (int kk = 0; kk < MC; ++kk) {
         R v = sector_value<R, D, TR, ALPHA, KU, KF>(P, base, kk);

@@ -70,6 +70,11 @@ class qmc_problem(ctypes.Structure):
                 ("shifts", ctypes.c_void_p), ("t", qmc_transform), ("f", ctypes.POINTER(qmc_integrand))]
 
 
+class qmc_cv_config(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int32), ("K", ctypes.c_int32), ("freq_step", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 RESULT_BYTES = ctypes.sizeof(qmc_result)
 
 _lib = None
@@ -102,12 +107,17 @@ def lib():
             L.qmc_batch_plan_launches.argtypes = [vp, ctypes.POINTER(i32)]
             L.qmc_batch_plan_tune.argtypes = [vp, vp, vp, ctypes.POINTER(u64)]
             L.qmc_sample_points.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, i32, vp, vp, vp, vp, vp, vp]
+            P_cfg = ctypes.POINTER(qmc_cv_config)
+            L.qmc_cv_train.argtypes = [i32, u64, vp, vp, qmc_transform, P_int, P_cfg, vp, vp, vp]
+            L.qmc_integrate_cv.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_cfg, vp, vp, vp, vp]
+            L.qmc_cv_loss_grad.argtypes = [i32, P_cfg, i32, vp, vp, vp, vp, vp, vp]
             L.qmc_last_error.restype = ctypes.c_char_p
             L.qmc_version.restype = i32
             for name in ("qmc_make_lattice", "qmc_integrate", "qmc_plan_create", "qmc_plan_execute",
                          "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_plan_tune", "qmc_integrate_batch", "qmc_batch_plan_create",
                          "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_batch_plan_launches",
-                         "qmc_batch_plan_tune", "qmc_sample_points"):
+                         "qmc_batch_plan_tune", "qmc_sample_points", "qmc_cv_train", "qmc_integrate_cv",
+                         "qmc_cv_loss_grad"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -364,3 +374,40 @@ def qmc_sample_points(d, n, m, g, shifts, t, f: Integrand, j, k, want_idx=True, 
     _check(lib().qmc_sample_points(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, cnt, _ptr(j), _ptr(k), _ptr(vals),
                                    _ptr(idx), _ptr(crd), ctypes.c_void_p(stream)))
     return vals, idx, crd
+
+
+# --------------------------------------------------------- control variate --
+
+def qmc_cv_train(d, n_pilot, g_pilot, shift_pilot, t, f: Integrand, cfg: qmc_cv_config, stream=0):
+    """Returns (a[R*d*K] float32 holding bfloat16 values, losses[2])."""
+    g = np.ascontiguousarray(np.asarray(g_pilot, dtype=np.uint64))
+    sh = np.ascontiguousarray(np.asarray(shift_pilot, dtype=np.float64))
+    a = np.zeros(cfg.R * d * cfg.K, dtype=np.float32)
+    losses = np.zeros(2)
+    _check(lib().qmc_cv_train(d, n_pilot, _ptr(g), _ptr(sh), t, f.ref, ctypes.byref(cfg), _ptr(a), _ptr(losses),
+                              ctypes.c_void_p(stream)))
+    return a, losses
+
+
+def qmc_integrate_cv(d, n, m, g, shifts, t, f: Integrand, cfg: qmc_cv_config, a, stream=0):
+    """Returns (qmc_result with [0] = control variate, [1] = plain; per_shift[m, 2])."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    res = qmc_result()
+    ps = np.zeros(2 * m)
+    rc = lib().qmc_integrate_cv(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(cfg), _ptr(a),
+                                ctypes.byref(res), _ptr(ps), ctypes.c_void_p(stream))
+    _check(rc, allow_warnings=True)
+    return res, ps.reshape(m, 2)
+
+
+def qmc_cv_loss_grad(d, cfg: qmc_cv_config, x, h, a, stream=0):
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    h = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    loss = ctypes.c_double(0.0)
+    grad = np.zeros(a.shape[0], dtype=np.float32)
+    _check(lib().qmc_cv_loss_grad(d, ctypes.byref(cfg), h.shape[0], _ptr(x), _ptr(h), _ptr(a), ctypes.byref(loss),
+                                  _ptr(grad), ctypes.c_void_p(stream)))
+    return float(loss.value), grad

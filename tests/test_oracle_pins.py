@@ -418,3 +418,47 @@ def test_cbc_fast_matches_plain(oracle_lib):
     gam = I.product_weights(8)
     for n in (31, 101, 1009, 4093, 10007):
         assert np.array_equal(cbc_fast(8 if n < 5000 else 4, n, gam), oracle_lib.cbc_plain(8 if n < 5000 else 4, n, gam))
+
+
+# --------------------------------------------------------- control variate --
+
+def test_cv_integral_closed_form(oracle_lib):
+    """int g = sum_r prod_i a_ri0 against tensor Gauss-Legendre of g itself
+    (g is a trigonometric polynomial of degree 31; 48 nodes per axis are exact
+    to double precision)."""
+    rng = np.random.default_rng(1)
+    d, R, K = 2, 3, 8
+    for F in (1, 2):
+        a = rng.normal(size=R * d * K).astype(np.float32)
+        x, w = np.polynomial.legendre.leggauss(48)
+        x, w = 0.5 * (x + 1), 0.5 * w
+        gl = sum(wi * wj * oracle_lib.cv_g(d, R, K, F, a, [xi, xj]) for xi, wi in zip(x, w) for xj, wj in zip(x, w))
+        assert abs(gl - oracle_lib.cv_integral(d, R, K, a)) < 1e-12 * max(1.0, abs(gl))
+
+
+def test_cv_gradient_finite_differences(oracle_lib):
+    """The analytic FP64 gradient of the fit loss against central differences."""
+    rng = np.random.default_rng(2)
+    d, R, K, P = 3, 2, 6, 40
+    a = (rng.normal(size=R * d * K) * 0.5).astype(np.float32)
+    x = rng.random((P, d))
+    h = rng.random(P)
+    _, grad = oracle_lib.cv_loss_grad(d, R, K, 1, x, h, a)
+    for q in rng.choice(R * d * K, 12, replace=False):
+        ap, am = a.copy(), a.copy()
+        ap[q] += np.float32(2.0 ** -8)
+        am[q] -= np.float32(2.0 ** -8)
+        lp, _ = oracle_lib.cv_loss_grad(d, R, K, 1, x, h, ap)
+        lm, _ = oracle_lib.cv_loss_grad(d, R, K, 1, x, h, am)
+        fd = (lp - lm) / (float(ap[q]) - float(am[q]))
+        assert abs(fd - grad[q]) < 1e-4 * max(1.0, abs(grad[q]))
+
+
+def test_cv_estimator_zero_surrogate_is_plain_rule(oracle_lib):
+    """With a = 0 the control-variate estimate is the plain rule."""
+    p = small_sector(3, 61, transform="korobov", alpha=3, n=2003, m=3)
+    g = I.random_generating_vector(I.SplitMix64(61), 3, p.n)
+    plain = oracle_lib.integrate(p, g)
+    p.cv = {"R": 2, "K": 4, "F": 1, "a": np.zeros(2 * 3 * 4, np.float32)}
+    cv = oracle_lib.integrate(p, g)
+    assert np.array_equal(plain["q"], cv["q"])
