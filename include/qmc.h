@@ -259,6 +259,26 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
 int qmc_cv_loss_grad(int32_t d, const qmc_cv_config* cfg, int32_t P, const double* x, const double* h,
                      const float* a, double* loss_out, float* grad_out, void* stream);
 
+/* The rule of qmc_integrate without any device allocation, for callers that
+ * cannot call cudaMalloc (code running where the CUDA allocator is locked,
+ * exhausted or owned by a host framework, or inside host callbacks).  The
+ * paper has no counterpart; this is an interface variant of qmc_integrate.
+ * Scratch (per-CTA result slots, counters, result staging) comes from one
+ * file-scope device array of 4 MiB per device, resident until the process
+ * exits.  Its address is looked up once per device, with that device
+ * current, by the first call on that device; make that first call before any
+ * stream capture.  Every call shares the array and leaves its contents
+ * behind (the counters are cleared at the start of each call), so calls
+ * whose GPU work overlaps (different streams or host threads) race on it:
+ * order them.  Supports SECTOR integrands U^-2 F^-1 with deg U <= 1,
+ * deg F <= 2, d <= 8 (FP64 or FP32EVAL; Korobov weight 3, baker or none).
+ * Returns QMC_EINVAL when m x (CTAs of one resident wave) slots exceed the
+ * fixed array, QMC_EUNSUPPORTED for other integrands.  Arguments, outputs and
+ * synchronisation as for qmc_integrate. */
+int qmc_integrate_noalloc(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                          qmc_transform t, const qmc_integrand* f, qmc_result* out, double* per_shift,
+                          void* stream);
+
 /* Single terms of Eq. (2), evaluated by the same device code the rule uses:
  * for each sample s, the weighted value f(z(x)) prod_i w(x_i) at point
  * j[s] (0-based, the paper's j-1) and shift k[s].

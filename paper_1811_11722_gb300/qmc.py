@@ -111,13 +111,14 @@ def lib():
             L.qmc_cv_train.argtypes = [i32, u64, vp, vp, qmc_transform, P_int, P_cfg, vp, vp, vp]
             L.qmc_integrate_cv.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_cfg, vp, vp, vp, vp]
             L.qmc_cv_loss_grad.argtypes = [i32, P_cfg, i32, vp, vp, vp, vp, vp, vp]
+            L.qmc_integrate_noalloc.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, vp, vp, vp]
             L.qmc_last_error.restype = ctypes.c_char_p
             L.qmc_version.restype = i32
             for name in ("qmc_make_lattice", "qmc_integrate", "qmc_plan_create", "qmc_plan_execute",
                          "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_plan_tune", "qmc_integrate_batch", "qmc_batch_plan_create",
                          "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_batch_plan_launches",
                          "qmc_batch_plan_tune", "qmc_sample_points", "qmc_cv_train", "qmc_integrate_cv",
-                         "qmc_cv_loss_grad"):
+                         "qmc_cv_loss_grad", "qmc_integrate_noalloc"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -411,3 +412,21 @@ def qmc_cv_loss_grad(d, cfg: qmc_cv_config, x, h, a, stream=0):
     _check(lib().qmc_cv_loss_grad(d, ctypes.byref(cfg), h.shape[0], _ptr(x), _ptr(h), _ptr(a), ctypes.byref(loss),
                                   _ptr(grad), ctypes.c_void_p(stream)))
     return float(loss.value), grad
+
+
+def qmc_integrate_noalloc(d, n, m, g, shifts, t: qmc_transform, f: Integrand, out=None, per_shift=None, stream=0):
+    """qmc_integrate without device allocation (fixed per-device scratch array).
+    Host result by default; with a device `out` address the call is asynchronous."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    if out is None:
+        res = qmc_result()
+        ps = np.zeros(2 * m) if per_shift is None else per_shift
+        rc = lib().qmc_integrate_noalloc(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(res), _addr(ps),
+                                         ctypes.c_void_p(stream))
+        _check(rc, allow_warnings=True)
+        return res, (ps.reshape(m, 2) if isinstance(ps, np.ndarray) else None)
+    rc = lib().qmc_integrate_noalloc(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, _addr(out), _addr(per_shift),
+                                     ctypes.c_void_p(stream))
+    _check(rc, allow_warnings=True)
+    return None, None
