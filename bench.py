@@ -291,6 +291,7 @@ def main():
     plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
     shifts_per_launch = 32 if args.no_tune else plan.tune(torch.cuda.current_stream().cuda_stream)  # untimed
     launches_per_step = plan.launches()
+    desc = plan.describe()
 
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
@@ -365,7 +366,10 @@ def main():
         "gpu_launches": launches_per_step * K,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": f"sector_kernel<float, D=6, MC={shifts_per_launch}, baker, U deg 1, F deg 2>",
+                     "kernel": (("qmc_jit_sector = sector_body specialised at run time for this U, F; "
+                                 if desc.get("specialised") == "1" else "sector_kernel ")
+                                + f"<float, D=6, MC={shifts_per_launch}, baker, U deg 1, F deg 2>"),
+                     "plan": desc,
                      "kernel_ms": 1e3 * rule_avg_s, "flops_per_eval": FLOPS_PER_EVAL,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (nominal max clock)",
                      "frac_at_observed_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)
@@ -374,6 +378,10 @@ def main():
         "result": {"mean": res["mean"][0], "err": res["err"][0]},
         "kernel_sha": sha,
     }
+    if dist:  # one exchange, after timing: every rank's per-shift values -> one Eq. (3) estimate
+        from paper_1811_11722_gb300.distributed import combine_across_ranks
+        comb = combine_across_ranks(per.view(-1, 2).cpu().numpy()).as_dict()
+        line["combined_estimate"] = {"shifts": p.m * world, "mean": comb["mean"][0], "err": comb["err"][0]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, g)
     if args.time_to_tol and rank == 0:

@@ -28,7 +28,9 @@
 #ifndef QMC_H
 #define QMC_H
 
+#ifndef __CUDACC_RTC__
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -127,7 +129,9 @@ typedef struct {
  * Host precompute: runs on the host cores (FFT-based cyclic convolution,
  * O(d n log n)); it touches no GPU.  Returns QMC_EINVAL for a composite or
  * out-of-range n. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_make_lattice(int32_t d, uint64_t n, const double* gamma, uint64_t* g_out);
+#endif
 
 /* The shifted rank-1 lattice rule, Eq. (2) and (3), on the GPU.
  *   d, n, m     dimension (1..QMC_DMAX), points (2 <= n < 2^31), shifts (2..1024)
@@ -142,34 +146,52 @@ int qmc_make_lattice(int32_t d, uint64_t n, const double* gamma, uint64_t* g_out
  * QMC_ECUDA if no GPU is usable, QMC_ENONFINITE / QMC_EDEFORM as warnings
  * (the estimate is still written) when `out` is host memory; with a device
  * `out` those two are reported in out->status only. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_integrate(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                   qmc_transform t, const qmc_integrand* f, qmc_result* out, double* per_shift,
                   void* stream);
+#endif
 
 /* A planned rule: the same arguments as qmc_integrate, validated and packed
  * once into launch descriptors and a device workspace owned by the plan, so
  * that qmc_plan_execute only launches kernels (no host staging, no
  * allocation). */
 typedef struct qmc_plan_s* qmc_plan;
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_plan_create(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                     qmc_transform t, const qmc_integrand* f, qmc_plan* plan_out);
+#endif
 /* out / per_shift as for qmc_integrate.  Device memory keeps execute fully
  * asynchronous. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_plan_execute(qmc_plan plan, qmc_result* out, double* per_shift, void* stream);
 int qmc_plan_destroy(qmc_plan plan);
+#endif
 /* Number of kernel launches one qmc_plan_execute issues. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_plan_launches(qmc_plan plan, int32_t* launches_out);
+#endif
 /* Autotuner: times the plan on `stream` with each specialised shift-chunk
  * size (shifts evaluated per point by one launch: 8, 16 or 32 for FP32EVAL
  * sector integrands; other plans have one choice) and keeps the fastest.
  * Reports the choice in *shifts_per_launch_out (may be NULL).  Synchronises
  * the device. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out);
+#endif
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+/* One-line description of the plan's launches (kernel family, dimension,
+ * shifts per launch, whether the kernel was specialised at run time for this
+ * integrand, grid and tile size), NUL-terminated into buf[len]. */
+int qmc_plan_describe(qmc_plan plan, char* buf, int32_t len);
+#endif
 /* Timing hook: when set (non-NULL cudaEvent_t handles passed as void*), every
  * later qmc_plan_execute records `before_rule` on its stream just before the
  * rule kernels and `after_rule` just after them (before the final pass), so a
  * caller can time the lattice kernels alone.  NULL, NULL clears the hook. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_plan_record_events(qmc_plan plan, void* before_rule, void* after_rule);
+#endif
 
 /* One problem of a batch: the arguments of qmc_integrate. */
 typedef struct {
@@ -192,24 +214,32 @@ typedef struct {
  *   out        [count] results (host or device); out[i].status per problem
  *   per_shift  optional; problem i writes 2*m_i doubles at offset 2*sum_{p<i} m_p
  * Returns the first non-OK per-problem status when `out` is host memory. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* out,
                         double* per_shift, void* stream);
+#endif
 
 /* Planned batch: validates and packs once and builds the CUDA graph; every
  * execute replays it (one cudaGraphLaunch). */
 typedef struct qmc_batch_plan_s* qmc_batch_plan;
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_batch_plan_create(int32_t count, const qmc_problem* problems, qmc_batch_plan* plan_out);
 int qmc_batch_plan_execute(qmc_batch_plan plan, qmc_result* out, double* per_shift, void* stream);
 int qmc_batch_plan_destroy(qmc_batch_plan plan);
+#endif
 /* Kernel launches in one replay (rule kernels + the final pass). */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_batch_plan_launches(qmc_batch_plan plan, int32_t* launches_out);
+#endif
 /* Autotuner: times the graph on `stream` for evaluations-per-CTA budgets
  * 2^18..2^24 (the per-problem grid is ceil(n m / budget) CTAs), rebuilds the
  * plan with the fastest and reports it in *work_per_cta_out (may be NULL).
  * `problems` must describe the same batch the plan was created from.
  * Synchronises `stream`. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* stream,
                         uint64_t* work_per_cta_out);
+#endif
 
 /* Learned control variate (a separable rank-R cosine surrogate):
  *   g(z) = sum_{r<R} prod_{i<d} sum_{k<K} a[(r*d + i)*K + k] cos(F pi k z_i),
@@ -237,9 +267,11 @@ typedef struct {
  *   a_out     [R*d*K] host, the parameters rounded to bfloat16 (stored as float)
  *   loss_out  optional [2] host: loss before the first and after the last step
  * Synchronises `stream`. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const double* shift_pilot,
                  qmc_transform t, const qmc_integrand* f, const qmc_cv_config* cfg, float* a_out,
                  double* loss_out, void* stream);
+#endif
 
 /* The rule with the control variate: one pass evaluates f and g at every
  * transformed point z(x) and sums both times the transform weight.
@@ -249,15 +281,19 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
  * per_shift (optional, [m*2]) gets the two per-shift values.  Supports
  * FP32EVAL sector integrands U^-2 F^-1 with deg U <= 1, deg F <= 2, d <= 8,
  * transform none, baker or Korobov 3. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                      qmc_transform t, const qmc_integrand* f, const qmc_cv_config* cfg, const float* a,
                      qmc_result* out, double* per_shift, void* stream);
+#endif
 
 /* The training kernels' loss and gradient at given parameters on given
  * points (x [P*d] in [0,1), targets h [P], host), for checking them against
  * an independent computation.  grad_out [R*d*K] host. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_cv_loss_grad(int32_t d, const qmc_cv_config* cfg, int32_t P, const double* x, const double* h,
                      const float* a, double* loss_out, float* grad_out, void* stream);
+#endif
 
 /* The rule of qmc_integrate without any device allocation, for callers that
  * cannot call cudaMalloc (code running where the CUDA allocator is locked,
@@ -275,9 +311,11 @@ int qmc_cv_loss_grad(int32_t d, const qmc_cv_config* cfg, int32_t P, const doubl
  * Returns QMC_EINVAL when m x (CTAs of one resident wave) slots exceed the
  * fixed array, QMC_EUNSUPPORTED for other integrands.  Arguments, outputs and
  * synchronisation as for qmc_integrate. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_integrate_noalloc(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                           qmc_transform t, const qmc_integrand* f, qmc_result* out, double* per_shift,
                           void* stream);
+#endif
 
 /* Single terms of Eq. (2), evaluated by the same device code the rule uses:
  * for each sample s, the weighted value f(z(x)) prod_i w(x_i) at point
@@ -286,15 +324,30 @@ int qmc_integrate_noalloc(int32_t d, uint64_t n, int32_t m, const uint64_t* g, c
  *   idx     optional [count * d] lattice indices (j g_i) mod n, host
  *   coord   optional [count * d] the coordinate x the kernel used, as double, host
  * Synchronises `stream`. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                       qmc_transform t, const qmc_integrand* f, int32_t count, const uint64_t* j,
                       const int32_t* k, double* values, uint64_t* idx, double* coord, void* stream);
+#endif
+
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+/* Eq. (2)/(3) from per-shift values alone: Qbar and sigma^2 (two-pass,
+ * compensated) over m values Q^(k) given as per_shift [m][2] (re, im), host
+ * memory; host only, no GPU.  Combines independent shift sets (from several
+ * GPUs, or earlier and later calls that append shifts) into one estimate.
+ * Returns QMC_EINVAL for m < 2. */
+int qmc_combine_shifts(int32_t m, const double* per_shift, qmc_result* out);
+#endif
 
 /* Text of the last error raised on the calling thread ("" if none). */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 const char* qmc_last_error(void);
+#endif
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int32_t qmc_version(void);
+#endif
 
 #ifdef __cplusplus
 }

@@ -59,37 +59,51 @@ class _Problem(ctypes.Structure):
     ]
 
 
+def _configure(L):
+    P = ctypes.POINTER(_Problem)
+    vp, u64, i32, dbl = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    L.orc_rule_sums.argtypes = [P, u64, vp, i32, vp, u64, u64, i32, vp, vp, vp]
+    L.orc_estimate.argtypes = [i32, u64, vp, vp, vp, vp]
+    L.orc_point.argtypes = [P, u64, vp, vp, u64, vp, vp, vp, vp, vp]
+    L.orc_transform.argtypes = [i32, i32, dbl, vp]
+    L.orc_transform.restype = dbl
+    L.orc_integrand.argtypes = [P, vp, vp, vp]
+    L.orc_gauss_legendre.argtypes = [P, i32, vp, vp, i32, vp]
+    L.orc_det_lu_out.argtypes = [i32, vp, vp]
+    L.orc_index.argtypes = [u64, u64, u64]
+    L.orc_index.restype = u64
+    L.orc_cbc_error.argtypes = [i32, u64, vp, vp]
+    L.orc_cbc_error.restype = dbl
+    L.orc_cbc_plain.argtypes = [i32, u64, vp, vp]
+    L.orc_cbc_candidate.argtypes = [u64, vp, u64]
+    L.orc_cbc_candidate.restype = dbl
+    L.orc_cv_g.argtypes = [i32, i32, i32, i32, vp, vp]
+    L.orc_cv_g.restype = dbl
+    L.orc_cv_integral.argtypes = [i32, i32, i32, vp]
+    L.orc_cv_integral.restype = dbl
+    L.orc_cv_loss_grad.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp]
+    L.orc_cv_loss_grad.restype = dbl
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB_PATH)
-            P = ctypes.POINTER(_Problem)
-            vp, u64, i32, dbl = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
-            L.orc_rule_sums.argtypes = [P, u64, vp, i32, vp, u64, u64, i32, vp, vp, vp]
-            L.orc_estimate.argtypes = [i32, u64, vp, vp, vp, vp]
-            L.orc_point.argtypes = [P, u64, vp, vp, u64, vp, vp, vp, vp, vp]
-            L.orc_transform.argtypes = [i32, i32, dbl, vp]
-            L.orc_transform.restype = dbl
-            L.orc_integrand.argtypes = [P, vp, vp, vp]
-            L.orc_gauss_legendre.argtypes = [P, i32, vp, vp, i32, vp]
-            L.orc_det_lu_out.argtypes = [i32, vp, vp]
-            L.orc_index.argtypes = [u64, u64, u64]
-            L.orc_index.restype = u64
-            L.orc_cbc_error.argtypes = [i32, u64, vp, vp]
-            L.orc_cbc_error.restype = dbl
-            L.orc_cbc_plain.argtypes = [i32, u64, vp, vp]
-            L.orc_cbc_candidate.argtypes = [u64, vp, u64]
-            L.orc_cv_g.argtypes = [i32, i32, i32, i32, vp, vp]
-            L.orc_cv_g.restype = dbl
-            L.orc_cv_integral.argtypes = [i32, i32, i32, vp]
-            L.orc_cv_integral.restype = dbl
-            L.orc_cv_loss_grad.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp]
-            L.orc_cv_loss_grad.restype = dbl
-            L.orc_cbc_candidate.restype = dbl
-            _lib = L
+            _lib = _configure(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+def use_library(path):
+    """Point every wrapper at another build of oracle.c (tests that plant a
+    mistake in a copy of the source use this); returns the previous handle.
+    use_library(None) restores the default build."""
+    global _lib
+    with _lock:
+        prev = _lib
+        _lib = None if path is None else _configure(ctypes.CDLL(path))
+    return prev
 
 
 def _ptr(a):

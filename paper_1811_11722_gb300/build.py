@@ -43,7 +43,7 @@ def _units():
         units.append((f"misc_{real}.o", "kernels_misc.cu", [f"-DQMC_REAL={real}"]))
     for d in SECTOR_DIMS:
         units.append((f"cv_{d}.o", "cv_inst.cu", [f"-DQMC_D={d}"]))
-    for src in ("finalize.cu", "api.cu", "deformed.cu", "batch.cu", "cbc.cpp", "cv.cu", "noalloc.cu"):
+    for src in ("finalize.cu", "api.cu", "deformed.cu", "batch.cu", "cbc.cpp", "cv.cu", "noalloc.cu", "jit.cu"):
         if os.path.exists(os.path.join(CSRC, src)):
             units.append((os.path.splitext(src)[0] + ".o", src, []))
     return units
@@ -81,7 +81,7 @@ def build_library(jobs: int | None = None, force: bool = False, verbose: bool = 
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda u: _compile(nvcc, u[0], u[1], u[2], verbose), units))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lnvrtc", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -338,6 +339,8 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
   RuleParams<R> base;
   fill_common(base, d, n, g, t, f);
   const void* func = nullptr;
+  void* jit_fn = nullptr;
+  int jit_occ = 0;
   size_t pbytes = sizeof(RuleParams<R>);
   std::vector<uint8_t> blob;
   int mc = tune.mc > 0 ? tune.mc : pick_mc(m, fp32);
@@ -373,6 +376,15 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
       for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
       for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
       if (base.tr == TR_KOROBOV) base.value_scale = std::pow((double)base.kor[7], (double)d);
+      if (fp32 && KU == 1 && KF == 2 && !tune.no_jit && jit_enabled()) {
+        void* fn = nullptr;
+        int occ = 0;
+        if (jit_sector_f32(d, mc, base.tr, base.tr == TR_KOROBOV ? 3 : 0, base.check_finite != 0, cu, cf, &fn,
+                           &occ) == QMC_OK) {
+          jit_fn = fn;
+          jit_occ = occ;
+        }
+      }
     } else {
       general = true;
     }
@@ -404,7 +416,8 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
 
   int nblk = 0, L = 0;
   uint64_t tiles = 0;
-  int rc = choose_grid(func, 0, n, nblk, L, tiles, tune.occupancy);
+  int rc = choose_grid(func, 0, n, nblk, L, tiles, jit_fn ? (tune.occupancy > 0 ? std::min(tune.occupancy, jit_occ) : jit_occ)
+                                                          : tune.occupancy);
   if (rc) return rc;
   if (tune.max_ctas > 0 && nblk > tune.max_ctas) {
     nblk = tune.max_ctas;
@@ -442,6 +455,7 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
       }
     Launch ln;
     ln.func = func;
+    ln.cufunc = jit_fn;
     ln.grid = dim3(nblk);
     ln.params.resize(pbytes);
     if (general) {
@@ -549,7 +563,8 @@ int launch_rule(const Plan* pl, const Workspace& ws, cudaStream_t stream, const 
     args[1] = &partial;
     args[2] = &counters;
     args[3] = (void*)&sio;
-    QMC_CUDA(cudaLaunchKernel(ln.func, ln.grid, dim3(kThreads), args, 0, stream));
+    int rc = launch_any(ln, ln.grid, args, stream);
+    if (rc) return rc;
   }
   return QMC_OK;
 }
@@ -715,6 +730,48 @@ int qmc_plan_launches(qmc_plan plan, int32_t* launches_out) {
   return QMC_OK;
 }
 
+int qmc_combine_shifts(int32_t m, const double* per_shift, qmc_result* out) {
+  if (m < 2 || !per_shift || !out) return fail(QMC_EINVAL, "combine needs m >= 2 values and an output");
+  std::memset(out, 0, sizeof(*out));
+  for (int part = 0; part < 2; ++part) {
+    // Neumaier-compensated two-pass mean and variance
+    double s = 0.0, c = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double v = per_shift[2 * k + part], t = s + v;
+      c += std::fabs(s) >= std::fabs(v) ? (s - t) + v : (v - t) + s;
+      s = t;
+    }
+    const double mean = (s + c) / (double)m;
+    double vs = 0.0, vc = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double dlt = per_shift[2 * k + part] - mean, v = dlt * dlt, t = vs + v;
+      vc += std::fabs(vs) >= std::fabs(v) ? (vs - t) + v : (v - t) + vs;
+      vs = t;
+    }
+    out->mean[part] = mean;
+    out->var[part] = (vs + vc) / ((double)m * (double)(m - 1));
+    out->err[part] = std::sqrt(out->var[part]);
+  }
+  out->status = QMC_OK;
+  return QMC_OK;
+}
+
+int qmc_plan_describe(qmc_plan plan, char* buf, int32_t len) {
+  if (!plan || !buf || len < 1) return fail(QMC_EINVAL, "null plan or buffer");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  const Launch* ln = pl->launches.empty() ? nullptr : &pl->launches[0];
+  int L = 0;
+  if (ln && ln->params.size() >= sizeof(RuleParams<float>)) {
+    int32_t v;
+    std::memcpy(&v, ln->params.data() + offsetof(RuleParams<float>, L), sizeof(v));
+    L = v;
+  }
+  snprintf(buf, (size_t)len, "d=%d n=%llu m=%d complex=%d shifts_per_launch=%d launches=%zu specialised=%d ctas=%d L=%d",
+           pl->d, (unsigned long long)pl->n, pl->m, pl->is_complex, pl->mc, pl->launches.size() + 1,
+           (ln && ln->cufunc) ? 1 : 0, pl->nblk, L);
+  return QMC_OK;
+}
+
 int qmc_plan_record_events(qmc_plan plan, void* before_rule, void* after_rule) {
   if (!plan) return fail(QMC_EINVAL, "null plan");
   Plan* pl = reinterpret_cast<Plan*>(plan);
@@ -794,7 +851,8 @@ int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const
     args[1] = &partial;
     args[2] = &counters;
     args[3] = &sio;
-    QMC_CUDA(cudaLaunchKernel(ln.func, dim3((cnt + 255) / 256), dim3(kThreads), args, 0, st));
+    rc = launch_any(ln, dim3((cnt + 255) / 256), args, st);
+    if (rc) return rc;
     off += cnt;
   }
   std::vector<double> hv(2 * (size_t)count), hc((size_t)count * dd);

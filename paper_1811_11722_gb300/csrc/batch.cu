@@ -151,16 +151,9 @@ static int batch_graph(BatchPlan* bp) {
       double* partial = pl->ws.partial;
       unsigned long long* counters = pl->ws.counters;
       void* args[4] = {(void*)ln.params.data(), &partial, &counters, &none};
-      cudaKernelNodeParams kp;
-      std::memset(&kp, 0, sizeof(kp));
-      kp.func = (void*)ln.func;
-      kp.gridDim = ln.grid;
-      kp.blockDim = dim3(kThreads);
-      kp.sharedMemBytes = 0;
-      kp.kernelParams = args;
       cudaGraphNode_t node;
-      e = cudaGraphAddKernelNode(&node, bp->graph, nullptr, 0, &kp);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddKernelNode");
+      int rc = graph_add_launch(bp->graph, ln, args, &node);
+      if (rc) return rc;
       nodes.push_back(node);
     }
   }

@@ -9,9 +9,11 @@
 // turned into a float in [1, 2) by placing its top 23 bits in the mantissa.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#endif
 
 #include "qmc_internal.h"
 
@@ -71,8 +73,8 @@ __device__ __forceinline__ R ipow(R x, int a) {
   return a < 0 ? recip(p) : p;
 }
 
-__device__ __forceinline__ bool finite_(float v) { return fabsf(v) < INFINITY; }
-__device__ __forceinline__ bool finite_(double v) { return fabs(v) < (double)INFINITY; }
+__device__ __forceinline__ bool finite_(float v) { return fabsf(v) < __int_as_float(0x7f800000); }
+__device__ __forceinline__ bool finite_(double v) { return fabs(v) < __longlong_as_double(0x7ff0000000000000ll); }
 
 // ------------------------------------------------------------ transforms --
 

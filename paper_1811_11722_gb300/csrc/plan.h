@@ -16,6 +16,7 @@ struct SampleIO;
 
 struct Launch {
   const void* func = nullptr;
+  void* cufunc = nullptr;  // run-time specialised kernel (CUfunction), if any
   dim3 grid;
   size_t smem = 0;
   std::vector<uint8_t> params;  // kernel parameter struct, passed as args[0]
@@ -26,6 +27,7 @@ struct TuneChoice {
   int mc = 0;          // shifts per launch chunk (8, 16, 32)
   int L = 0;           // points per thread per tile
   int occupancy = 0;   // cap on CTAs per SM
+  bool no_jit = false; // keep the template kernel (no run-time specialisation)
   int max_ctas = 0;    // cap on CTAs of each launch (batched sectors run side by side)
   bool force_general = false;
 };
@@ -95,5 +97,11 @@ int launch_rule(const Plan* pl, const Workspace& ws, cudaStream_t stream, const 
 int launch_finalize(const Plan* pl, const Workspace& ws, qmc_result* res_dev, double* per_shift_dev,
                     cudaStream_t stream);
 int plan_execute(Plan* pl, qmc_result* out, double* per_shift, cudaStream_t stream);
+
+bool jit_enabled();
+int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
+                   const std::vector<double>& cf, void** fn_out, int* occ_out);
+int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream);
+int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraphNode_t* node);
 
 }  // namespace qmc

@@ -5,7 +5,15 @@
 // global loads on the hot path).
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// run-time compilation (NVRTC): no host headers
+typedef unsigned long long uint64_t;
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned char uint8_t;
+#else
 #include <cstdint>
+#endif
 
 #include "../../include/qmc.h"
 

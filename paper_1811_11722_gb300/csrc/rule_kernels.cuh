@@ -114,7 +114,18 @@ __device__ __forceinline__ double coord_used(typename FixT<R>::T X) {
 // (other integer powers go to the general kernel, so this path has no
 // per-evaluation branch).  FP32: float-domain triangle coordinates from the
 // per-point bases b[i]; FP64: 64-bit fixed point.
-template <typename R, int D, int TR, int ALPHA, int KU, int KF>
+// Polynomial policies: U and F from the nested-Horner coefficients in the
+// kernel parameters (DensePolys), or as straight-line code generated for one
+// plan (a policy struct written by the run-time specialiser, see jit.cu).
+struct DensePolys {
+  template <int D, int KU, int KF, typename R>
+  __device__ static __forceinline__ void eval(const RuleParams<R>& P, const R* z, R& U, R& F) {
+    U = poly_dense<D, KU>(P.cU, z);
+    F = poly_dense<D, KF>(P.cF, z);
+  }
+};
+
+template <typename R, int D, int TR, int ALPHA, int KU, int KF, class POLY = DensePolys>
 __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename SecBase<R>::T* base, int k) {
   R z[D];
   R w = R(1);
@@ -123,8 +134,8 @@ __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename
     if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], P.shiftf[k][i], P.kor, w);
     else z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
   }
-  const R U = poly_dense<D, KU>(P.cU, z);
-  const R F = poly_dense<D, KF>(P.cF, z);
+  R U, F;
+  POLY::template eval<D, KU, KF, R>(P, z, U, F);
   R v = recip(U * U * F);
   if constexpr (TR == TR_KOROBOV) v *= w;
   return v;
@@ -142,7 +153,7 @@ __device__ __forceinline__ double sec_coord_used(const RuleParams<R>& P, typenam
   else return coord_used<R>(b + shift_of(P, k, i));
 }
 
-template <typename R, int D, int TR, int ALPHA, int KU, int KF>
+template <typename R, int D, int TR, int ALPHA, int KU, int KF, class POLY>
 __device__ void sector_sample(const RuleParams<R>& P, const SampleIO& sio) {
   using BT = typename SecBase<R>::T;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,7 +168,7 @@ __device__ void sector_sample(const RuleParams<R>& P, const SampleIO& sio) {
     if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
     if (sio.coord) sio.coord[(size_t)s * D + i] = sec_coord_used<R>(P, base[i], k, i);
   }
-  R v = sector_value<R, D, TR, ALPHA, KU, KF>(P, base, k);
+  R v = sector_value<R, D, TR, ALPHA, KU, KF, POLY>(P, base, k);
   sio.values[2 * (size_t)s] = (double)v * (double)P.value_scale;
   sio.values[2 * (size_t)s + 1] = 0.0;
 }
@@ -191,13 +202,12 @@ __device__ __forceinline__ void block_epilogue(Acc<R>* acc, int mk, unsigned nba
 // copies of row 0, so the unrolled shift loop carries no predicate; only the
 // epilogue drops them.  CHECK: count and leave out NaN/Inf values (off when
 // the host has shown U and F positive on the cube).
-template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF, bool CHECK>
-__global__ void __launch_bounds__(kThreads)
-    sector_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
-                  unsigned long long* __restrict__ counters, const SampleIO sio) {
+template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF, bool CHECK, class POLY>
+__device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __restrict__ partial,
+                                            unsigned long long* __restrict__ counters, const SampleIO& sio) {
   using FT = typename FixT<R>::T;
   if (sio.count > 0) {
-    sector_sample<R, D, TR, ALPHA, KU, KF>(P, sio);
+    sector_sample<R, D, TR, ALPHA, KU, KF, POLY>(P, sio);
     return;
   }
   const uint32_t n = (uint32_t)P.n;
@@ -220,7 +230,7 @@ __global__ void __launch_bounds__(kThreads)
       for (int i = 0; i < D; ++i) base[i] = sec_base<R>(idx[i], P.rc);
 #pragma unroll
       for (int kk = 0; kk < MC; ++kk) {
-        R v = sector_value<R, D, TR, ALPHA, KU, KF>(P, base, kk);
+        R v = sector_value<R, D, TR, ALPHA, KU, KF, POLY>(P, base, kk);
         if constexpr (CHECK) {
           const bool ok = finite_(v);
           nbad += (ok || kk >= P.m_launch) ? 0u : 1u;  // padded rows are not counted
@@ -240,6 +250,13 @@ __global__ void __launch_bounds__(kThreads)
   }
   if constexpr (!CHECK) nbad = 0;
   block_epilogue<R, MC>(acc, P.m_launch, nbad, P, partial, counters);
+}
+
+template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF, bool CHECK>
+__global__ void __launch_bounds__(kThreads)
+    sector_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
+                  unsigned long long* __restrict__ counters, const SampleIO sio) {
+  sector_body<R, D, MC, TR, ALPHA, KU, KF, CHECK, DensePolys>(P, partial, counters, sio);
 }
 
 // ------------------------------------------------ separable integrands --

@@ -100,6 +100,8 @@ def lib():
             L.qmc_plan_launches.argtypes = [vp, ctypes.POINTER(i32)]
             L.qmc_plan_record_events.argtypes = [vp, vp, vp]
             L.qmc_plan_tune.argtypes = [vp, vp, ctypes.POINTER(i32)]
+            L.qmc_plan_describe.argtypes = [vp, ctypes.c_char_p, i32]
+            L.qmc_combine_shifts.argtypes = [i32, vp, vp]
             L.qmc_integrate_batch.argtypes = [i32, vp, vp, vp, vp]
             L.qmc_batch_plan_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
             L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
@@ -115,10 +117,10 @@ def lib():
             L.qmc_last_error.restype = ctypes.c_char_p
             L.qmc_version.restype = i32
             for name in ("qmc_make_lattice", "qmc_integrate", "qmc_plan_create", "qmc_plan_execute",
-                         "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_plan_tune", "qmc_integrate_batch", "qmc_batch_plan_create",
+                         "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_plan_tune", "qmc_plan_describe", "qmc_integrate_batch", "qmc_batch_plan_create",
                          "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_batch_plan_launches",
                          "qmc_batch_plan_tune", "qmc_sample_points", "qmc_cv_train", "qmc_integrate_cv",
-                         "qmc_cv_loss_grad", "qmc_integrate_noalloc"):
+                         "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -267,6 +269,11 @@ class Plan:
         v = ctypes.c_int32(0)
         _check(lib().qmc_plan_launches(self.h, ctypes.byref(v)))
         return int(v.value)
+
+    def describe(self) -> dict:
+        buf = ctypes.create_string_buffer(256)
+        _check(lib().qmc_plan_describe(self.h, buf, 256))
+        return dict(kv.split("=") for kv in buf.value.decode().split())
 
     def destroy(self):
         if self.h:
@@ -430,3 +437,11 @@ def qmc_integrate_noalloc(d, n, m, g, shifts, t: qmc_transform, f: Integrand, ou
                                      ctypes.c_void_p(stream))
     _check(rc, allow_warnings=True)
     return None, None
+
+
+def qmc_combine_shifts(per_shift) -> qmc_result:
+    """Eq. (3) over the rows (Q^(k) re, im) of per_shift[m, 2] (host computation)."""
+    ps = np.ascontiguousarray(np.asarray(per_shift, dtype=np.float64).reshape(-1, 2))
+    res = qmc_result()
+    _check(lib().qmc_combine_shifts(ps.shape[0], _ptr(ps), ctypes.byref(res)))
+    return res

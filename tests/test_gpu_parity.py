@@ -516,3 +516,24 @@ def test_cv_gain_reported(Q):
               f"plain {r['err'][1]:.3e} ratio {r['err'][1] / r['err'][0]:.2f}")
         assert np.isfinite(r["err"][0]) and np.isfinite(r["err"][1])
         assert abs(r["mean"][0] - r["mean"][1]) <= 6 * (r["err"][0] + r["err"][1])
+
+
+# ------------------------------------------------ run-time specialisation --
+
+def test_specialised_kernel_bit_identical(Q, monkeypatch):
+    """The kernel specialised at run time for the plan's U and F (nonzero
+    monomials only) gives bit-identical results to the template kernel."""
+    p = I.config2(n=1000003, m=32)
+    g = I.random_generating_vector(I.SplitMix64(4), 6, p.n)
+    f = Q.integrand_from_problem(p, "fp32")
+    t = Q.transform("baker")
+    plan = Q.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
+    assert plan.describe()["specialised"] == "1", Q.qmc_last_error()
+    a = plan.execute().as_dict()
+    plan.destroy()
+    monkeypatch.setenv("QMC_JIT", "0")
+    plan = Q.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
+    assert plan.describe()["specialised"] == "0"
+    b = plan.execute().as_dict()
+    plan.destroy()
+    assert a["mean"][0] == b["mean"][0] and a["var"][0] == b["var"][0]
