@@ -186,6 +186,66 @@ def run_reference(args, rank, world):
     return 0
 
 
+def device_time(fn, stream, reps=5):
+    """Best device time (s) of fn() bracketed by CUDA events on `stream`."""
+    import torch
+    best = 1e30
+    fn()
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b) / 1e3)
+    return best
+
+
+def extras(qmc, I, torch):
+    """Measured peaks and the other configurations' throughput (one GPU)."""
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    out = {"peaks_measured": qmc.qmc_measure_peaks(sh)}
+    dev_res = torch.zeros(qmc.RESULT_BYTES * 256, dtype=torch.uint8, device="cuda")
+    # configuration 1 at the throughput size (FP64, separable exp, Korobov 3)
+    p = I.config1(n=I.N_C1_THROUGHPUT)
+    g = I.random_generating_vector(I.SplitMix64(1), p.d, p.n)
+    plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, qmc.transform(p.transform, p.alpha), qmc.integrand_from_problem(p))
+    t = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream)
+    out["c1_fp64_separable_d3_n16777213_m10"] = {"evals_per_s": p.n * p.m / t, "ms": 1e3 * t}
+    plan.destroy()
+    # configuration 4 (complex deformed, d=5, Korobov 3, n=4194301, m=20), FP64 and FP32
+    p = I.config4()
+    g = I.random_generating_vector(I.SplitMix64(4), p.d, p.n)
+    for prec in ("fp64", "fp32"):
+        plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, qmc.transform(p.transform, p.alpha),
+                        qmc.integrand_from_problem(p, prec))
+        t = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream, reps=3)
+        out[f"c4_deformed_d5_{prec}"] = {"evals_per_s": p.n * p.m / t, "ms": 1e3 * t}
+        plan.destroy()
+    # configuration 3: 256 sectors in one graph replay vs the same plans one after another
+    sect = I.config3()
+    gs = [I.random_generating_vector(I.SplitMix64(900 + i), q.d, q.n) for i, q in enumerate(sect)]
+    tuples = [(q.d, q.n, q.m, gg, q.shifts, qmc.transform(q.transform, q.alpha), qmc.integrand_from_problem(q))
+              for q, gg in zip(sect, gs)]
+    evals = sum(q.n * q.m for q in sect)
+    t0 = time.perf_counter()
+    bp = qmc.BatchPlan(tuples)
+    build_s = time.perf_counter() - t0
+    w = bp.tune(sh)
+    t = device_time(lambda: bp.execute(out=dev_res, stream=sh), stream, reps=3)
+    plans = [qmc.Plan(*tt) for tt in tuples]
+    t1 = device_time(lambda: [pl.execute(out=dev_res, stream=sh) for pl in plans], stream, reps=2)
+    out["c3_batch_256_sectors"] = {"evals": evals, "evals_per_s_graph": evals / t, "ms_graph": 1e3 * t,
+                                   "ms_one_by_one": 1e3 * t1, "speedup_vs_one_by_one": t1 / t,
+                                   "work_per_cta": w, "plan_build_s": build_s, "launches": bp.launches(),
+                                   "note": "generating vectors drawn at random (any valid g; throughput only)"}
+    for pl in plans:
+        pl.destroy()
+    bp.destroy()
+    return out
+
+
 def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
     """Wall time until err/|Qbar| <= tol walking the lattice ladder (largest prime
     <= 2^(e/2)), each level a fresh rule with its CBC vector; lattice
@@ -261,6 +321,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner (profiler captures)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other configurations' throughput")
     ap.add_argument("--time-to-tol", action="store_true",
                     help="also measure wall time to 1e-8 relative error (plain vs control variate)")
     ap.add_argument("--n", type=int, default=None,
@@ -384,6 +445,12 @@ def main():
         line["combined_estimate"] = {"shifts": p.m * world, "mean": comb["mean"][0], "err": comb["err"][0]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, g)
+    if rank == 0 and world == 1 and not args.no_extras and args.n is None:
+        from paper_1811_11722_gb300 import inputs as I
+        line["extras"] = extras(qmc, I, torch)
+        pk = line["extras"]["peaks_measured"]["fp32_tflops"]
+        line["roofline"]["peak_measured_probe"] = pk
+        line["roofline"]["frac_of_measured_probe"] = achieved / pk
     if args.time_to_tol and rank == 0:
         from paper_1811_11722_gb300 import inputs as I
         line["time_to_1e-8"] = time_to_tolerance(qmc, I, torch)

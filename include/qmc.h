@@ -339,6 +339,14 @@ int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const
 int qmc_combine_shifts(int32_t m, const double* per_shift, qmc_result* out);
 #endif
 
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+/* Measured arithmetic peaks of the current GPU: out[0] FP32 FMA TFLOP/s,
+ * out[1] FP64 FMA TFLOP/s (independent dependency chains on a full grid,
+ * best of 5, CUDA events on `stream`).
+ * A measurement utility beside the rule; synchronises `stream`. */
+int qmc_measure_peaks(void* stream, double* out);
+#endif
+
 /* Text of the last error raised on the calling thread ("" if none). */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 const char* qmc_last_error(void);

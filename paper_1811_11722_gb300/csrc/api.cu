@@ -341,6 +341,7 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
   const void* func = nullptr;
   void* jit_fn = nullptr;
   int jit_occ = 0;
+  size_t jit_smem = 0;
   size_t pbytes = sizeof(RuleParams<R>);
   std::vector<uint8_t> blob;
   int mc = tune.mc > 0 ? tune.mc : pick_mc(m, fp32);
@@ -379,10 +380,12 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
       if (fp32 && KU == 1 && KF == 2 && !tune.no_jit && jit_enabled()) {
         void* fn = nullptr;
         int occ = 0;
+        size_t sm = 0;
         if (jit_sector_f32(d, mc, base.tr, base.tr == TR_KOROBOV ? 3 : 0, base.check_finite != 0, cu, cf, &fn,
-                           &occ) == QMC_OK) {
+                           &occ, &sm) == QMC_OK) {
           jit_fn = fn;
           jit_occ = occ;
+          jit_smem = sm;
         }
       }
     } else {
@@ -456,6 +459,7 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
     Launch ln;
     ln.func = func;
     ln.cufunc = jit_fn;
+    ln.smem = jit_fn ? jit_smem : 0;
     ln.grid = dim3(nblk);
     ln.params.resize(pbytes);
     if (general) {

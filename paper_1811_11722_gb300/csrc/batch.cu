@@ -15,6 +15,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <string>
+#include <thread>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -66,19 +69,40 @@ static int batch_build(BatchPlan* bp, int32_t count, const qmc_problem* problems
     cudaGetLastError();
     return fail(QMC_ECUDA, "no CUDA device");
   }
+  // pack every problem (and compile its specialised kernel) on the host
+  // cores; problems are independent, the results keep the input order
+  std::vector<std::unique_ptr<Plan>> plans(count);
+  std::vector<int> rcs(count, QMC_OK);
+  std::vector<std::string> errs(count);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    int dev_here = 0;
+    cudaSetDevice(dev);
+    (void)dev_here;
+    for (int i = next++; i < count; i = next++) {
+      const qmc_problem& q = problems[i];
+      std::unique_ptr<Plan> pl(new Plan());
+      TuneChoice tc;
+      const uint64_t evals = q.n * (uint64_t)std::max(q.m, 1);
+      tc.max_ctas = (int)std::max<uint64_t>(1, std::min<uint64_t>((evals + work_per_cta - 1) / work_per_cta, 4ull * sms));
+      rcs[i] = plan_build(pl.get(), q.d, q.n, q.m, q.g, q.shifts, q.t, q.f, tc);
+      if (rcs[i]) errs[i] = qmc_last_error();
+      plans[i] = std::move(pl);
+    }
+  };
+  const unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)std::min(count, 32)));
+  std::vector<std::thread> th;
+  for (unsigned t = 1; t < nt; ++t) th.emplace_back(work);
+  work();
+  for (auto& x : th) x.join();
   for (int i = 0; i < count; ++i) {
-    const qmc_problem& q = problems[i];
-    std::unique_ptr<Plan> pl(new Plan());
-    TuneChoice tc;
-    const uint64_t evals = q.n * (uint64_t)std::max(q.m, 1);
-    tc.max_ctas = (int)std::max<uint64_t>(1, std::min<uint64_t>((evals + work_per_cta - 1) / work_per_cta, 4ull * sms));
-    int rc = plan_build(pl.get(), q.d, q.n, q.m, q.g, q.shifts, q.t, q.f, tc);
-    if (rc) return fail(rc, "problem %d: %s", i, qmc_last_error());
+    if (rcs[i]) return fail(rcs[i], "problem %d: %s", i, errs[i].c_str());
+    const Plan* pl = plans[i].get();
     bp->ps_off.push_back((size_t)bp->total_m * 2);
-    bp->total_m += q.m;
-    bp->max_m = std::max(bp->max_m, q.m);
+    bp->total_m += pl->m;
+    bp->max_m = std::max(bp->max_m, pl->m);
     bp->launches += (int)pl->launches.size();
-    bp->probs.push_back(std::move(pl));
+    bp->probs.push_back(std::move(plans[i]));
   }
   return QMC_OK;
 }

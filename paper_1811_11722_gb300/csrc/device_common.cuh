@@ -182,18 +182,20 @@ __device__ __forceinline__ double coord_f64(uint64_t X, const double* kor, int a
 }
 
 // Float-domain coordinates of the fast FP32 sector path.  With the point's
-// base b = frac(idx/n) (one correctly rounded conversion per point and
-// dimension) and the shift constant c = 2 Delta - 2, one FMA gives
-// t = 2 (b + Delta) - 2 in [-2, 2), i.e. y = b + Delta in [0, 2) before the
-// wrap.  Then v = |t| - 1 = +-(2 {y} - 1), so the baker map is
+// doubled base b2 = 2 frac(idx/n) (one correctly rounded conversion per point
+// and dimension; doubling is exact) and the shift constant c = 2 Delta - 2,
+// one add gives t = 2 (b + Delta) - 2 in [-2, 2), i.e. y = b + Delta in [0, 2)
+// before the wrap.  (An add with one constant operand encodes directly; an
+// FMA with an immediate 2 and a constant would first load the constant.)
+// Then v = |t| - 1 = +-(2 {y} - 1), so the baker map is
 // z = 1 - |2 {y} - 1| = 1 - |v| with no wrap test at all, and
 // s = min({y}, 1 - {y}) = (1 - |v|) / 2; {y} > 1/2 exactly when t and v have
 // the same sign.
-__device__ __forceinline__ float base_f32(uint64_t p64) { return __ull2float_rn(p64) * 0x1p-64f; }
+__device__ __forceinline__ float base2_f32(uint64_t p64) { return __ull2float_rn(p64) * 0x1p-63f; }
 
 template <int TR, int ALPHA>
-__device__ __forceinline__ float coord_tri(float b, float c, const float* kor, float& w) {
-  const float t = __fmaf_rn(2.0f, b, c);
+__device__ __forceinline__ float coord_tri(float b2, float c, const float* kor, float& w) {
+  const float t = b2 + c;
   if constexpr (TR == TR_NONE) {
     return __fmaf_rn(0.5f, t, t < 0.0f ? 1.0f : 0.0f);
   } else {
@@ -209,8 +211,8 @@ __device__ __forceinline__ float coord_tri(float b, float c, const float* kor, f
 }
 
 // The coordinate {y} the triangle form stands for, as a double (sampling output).
-__device__ __forceinline__ double coord_tri_used(float b, float c) {
-  const double t = (double)__fmaf_rn(2.0f, b, c);
+__device__ __forceinline__ double coord_tri_used(float b2, float c) {
+  const double t = (double)(b2 + c);
   return 0.5 * t + (t < 0.0 ? 1.0 : 0.0);
 }
 

@@ -45,6 +45,7 @@ struct DriverApi {
   CUresult (*graphAddKernelNode)(CUgraphNode*, CUgraph, const CUgraphNode*, size_t,
                                  const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
   CUresult (*getErrorString)(CUresult, const char**) = nullptr;
+  CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
   bool ok = false;
 };
 
@@ -63,7 +64,8 @@ const DriverApi& driver() {
              get("cuLaunchKernel", (void**)&api.launchKernel) &&
              get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&api.occupancy) &&
              get("cuGraphAddKernelNode", (void**)&api.graphAddKernelNode) &&
-             get("cuGetErrorString", (void**)&api.getErrorString);
+             get("cuGetErrorString", (void**)&api.getErrorString) &&
+             get("cuFuncSetAttribute", (void**)&api.funcSetAttribute);
     if (!api.ok) cudaGetLastError();
   });
   return api;
@@ -131,10 +133,19 @@ bool jit_enabled() {
   return !(e && e[0] == '0');
 }
 
+// Accumulator pairs in shared memory for the specialised kernel (QMC_JIT_SMACC=1; registers otherwise).
+bool jit_smacc() {
+  const char* e = std::getenv("QMC_JIT_SMACC");
+  return e && e[0] == '1';
+}
+
 // Compile (or fetch) the specialised FP32 sector kernel.  Returns QMC_OK and
 // the CUfunction / occupancy, or an error code (the caller falls back).
 int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
-                   const std::vector<double>& cf, void** fn_out, int* occ_out) {
+                   const std::vector<double>& cf, void** fn_out, int* occ_out, size_t* smem_out) {
+  const bool smacc = jit_smacc();
+  const size_t smem = smacc ? (size_t)MC * kThreads * 8 : 0;
+  *smem_out = smem;
   std::string src;
   src += "#include \"rule_kernels.cuh\"\n";
   src += "namespace qmc {\nstruct GenPolys {\n";
@@ -147,24 +158,28 @@ int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vect
   src += "    unsigned long long* __restrict__ counters, const qmc::SampleIO sio) {\n";
   src += "  qmc::sector_body<float, " + std::to_string(D) + ", " + std::to_string(MC) + ", " + std::to_string(TR) +
          ", " + std::to_string(ALPHA) + ", 1, 2, " + (check ? "true" : "false") +
-         ", qmc::GenPolys>(P, partial, counters, sio);\n}\n";
+         ", qmc::GenPolys, " + (smacc ? "true" : "false") + ">(P, partial, counters, sio);\n}\n";
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return QMC_ECUDA;
   }
   const std::string key = std::to_string(dev) + "\n" + src;
-  std::lock_guard<std::mutex> lk(g_jit_mu);
-  auto it = g_jit_cache.find(key);
-  if (it != g_jit_cache.end()) {
-    *fn_out = (void*)it->second.fn;
-    *occ_out = it->second.occupancy;
-    return QMC_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    auto it = g_jit_cache.find(key);
+    if (it != g_jit_cache.end()) {
+      *fn_out = (void*)it->second.fn;
+      *occ_out = it->second.occupancy;
+      return QMC_OK;
+    }
   }
   int major = 0, minor = 0;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (major != 10 || minor != 3) return QMC_EUNSUPPORTED;  // the build targets sm_103a only
+  // compile outside the lock (NVRTC programs are independent, so plans can be
+  // built on several host threads at once)
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "qmc_jit_sector.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
     return QMC_EUNSUPPORTED;
@@ -188,13 +203,25 @@ int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vect
   cudaFree(nullptr);  // make sure the runtime's primary context is current for the driver API
   const DriverApi& drv = driver();
   if (!drv.ok) return QMC_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  auto it = g_jit_cache.find(key);  // another thread may have finished the same source
+  if (it != g_jit_cache.end()) {
+    *fn_out = (void*)it->second.fn;
+    *occ_out = it->second.occupancy;
+    return QMC_OK;
+  }
   JitEntry e;
   if (drv.moduleLoadData(&e.mod, cubin.data()) != CUDA_SUCCESS) return QMC_EUNSUPPORTED;
   if (drv.moduleGetFunction(&e.fn, e.mod, "qmc_jit_sector") != CUDA_SUCCESS) {
     drv.moduleUnload(e.mod);
     return QMC_EUNSUPPORTED;
   }
-  if (drv.occupancy(&e.occupancy, e.fn, kThreads, 0) != CUDA_SUCCESS || e.occupancy < 1) e.occupancy = 1;
+  if (smem > 48 * 1024 &&
+      drv.funcSetAttribute(e.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS) {
+    drv.moduleUnload(e.mod);
+    return QMC_EUNSUPPORTED;
+  }
+  if (drv.occupancy(&e.occupancy, e.fn, kThreads, smem) != CUDA_SUCCESS || e.occupancy < 1) e.occupancy = 1;
   g_jit_cache[key] = e;
   *fn_out = (void*)e.fn;
   *occ_out = e.occupancy;
@@ -205,8 +232,8 @@ int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vect
 int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream) {
   if (ln.cufunc) {
     const DriverApi& drv = driver();
-    CUresult r = drv.launchKernel((CUfunction)ln.cufunc, grid.x, grid.y, grid.z, kThreads, 1, 1, 0, (CUstream)stream,
-                                  args, nullptr);
+    CUresult r = drv.launchKernel((CUfunction)ln.cufunc, grid.x, grid.y, grid.z, kThreads, 1, 1, (unsigned)ln.smem,
+                                  (CUstream)stream, args, nullptr);
     if (r != CUDA_SUCCESS) {
       const char* msg = nullptr;
       drv.getErrorString(r, &msg);
@@ -231,6 +258,7 @@ int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraph
     kp.blockDimX = kThreads;
     kp.blockDimY = 1;
     kp.blockDimZ = 1;
+    kp.sharedMemBytes = (unsigned)ln.smem;
     kp.kernelParams = args;
     CUgraphNode n;
     if (driver().graphAddKernelNode(&n, (CUgraph)graph, nullptr, 0, &kp) != CUDA_SUCCESS)

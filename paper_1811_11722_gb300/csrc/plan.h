@@ -99,8 +99,9 @@ int launch_finalize(const Plan* pl, const Workspace& ws, qmc_result* res_dev, do
 int plan_execute(Plan* pl, qmc_result* out, double* per_shift, cudaStream_t stream);
 
 bool jit_enabled();
+bool jit_smacc();
 int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
-                   const std::vector<double>& cf, void** fn_out, int* occ_out);
+                   const std::vector<double>& cf, void** fn_out, int* occ_out, size_t* smem_out);
 int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream);
 int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraphNode_t* node);
 

@@ -143,7 +143,7 @@ __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename
 
 template <typename R>
 __device__ __forceinline__ typename SecBase<R>::T sec_base(uint32_t idx, const Recip& rc) {
-  if constexpr (sizeof(R) == 4) return base_f32(frac64(idx, rc));
+  if constexpr (sizeof(R) == 4) return base2_f32(frac64(idx, rc));
   else return frac64(idx, rc);
 }
 
@@ -202,7 +202,11 @@ __device__ __forceinline__ void block_epilogue(Acc<R>* acc, int mk, unsigned nba
 // copies of row 0, so the unrolled shift loop carries no predicate; only the
 // epilogue drops them.  CHECK: count and leave out NaN/Inf values (off when
 // the host has shown U and F positive on the cube).
-template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF, bool CHECK, class POLY>
+// SMACC (FP32 only): the per-shift Fast2Sum pairs (hi, lo) live in dynamic
+// shared memory (MC * kThreads float2) and only the short float runs stay in
+// registers, which frees two thirds of the accumulator registers for higher
+// occupancy.
+template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF, bool CHECK, class POLY, bool SMACC = false>
 __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __restrict__ partial,
                                             unsigned long long* __restrict__ counters, const SampleIO& sio) {
   using FT = typename FixT<R>::T;
@@ -214,6 +218,12 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
   Acc<R> acc[MC];
 #pragma unroll
   for (int kk = 0; kk < MC; ++kk) acc[kk].init();
+  constexpr bool kSm = SMACC && sizeof(R) == 4;
+  extern __shared__ float2 accsm[];  // [MC][kThreads] (hi, lo), used when kSm
+  if constexpr (kSm) {
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) accsm[kk * kThreads + threadIdx.x] = make_float2(0.0f, 0.0f);
+  }
   unsigned nbad = 0;
   const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
   for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
@@ -243,9 +253,26 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
       if constexpr (sizeof(R) == 4) {
         if ((s & (kFoldG - 1)) == kFoldG - 1) {
 #pragma unroll
-          for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
+          for (int kk = 0; kk < MC; ++kk) {
+            if constexpr (kSm) {
+              float2 a = accsm[kk * kThreads + threadIdx.x];
+              fast2sum_add(a.x, a.y, acc[kk].run);
+              accsm[kk * kThreads + threadIdx.x] = a;
+              acc[kk].run = 0.0f;
+            } else {
+              acc[kk].fold();
+            }
+          }
         }
       }
+    }
+  }
+  if constexpr (kSm) {
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) {
+      const float2 a = accsm[kk * kThreads + threadIdx.x];
+      acc[kk].hi = a.x;
+      acc[kk].lo = a.y;
     }
   }
   if constexpr (!CHECK) nbad = 0;

@@ -102,6 +102,7 @@ def lib():
             L.qmc_plan_tune.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.qmc_plan_describe.argtypes = [vp, ctypes.c_char_p, i32]
             L.qmc_combine_shifts.argtypes = [i32, vp, vp]
+            L.qmc_measure_peaks.argtypes = [vp, vp]
             L.qmc_integrate_batch.argtypes = [i32, vp, vp, vp, vp]
             L.qmc_batch_plan_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
             L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
@@ -120,7 +121,7 @@ def lib():
                          "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_plan_tune", "qmc_plan_describe", "qmc_integrate_batch", "qmc_batch_plan_create",
                          "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_batch_plan_launches",
                          "qmc_batch_plan_tune", "qmc_sample_points", "qmc_cv_train", "qmc_integrate_cv",
-                         "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts"):
+                         "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts", "qmc_measure_peaks"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -445,3 +446,10 @@ def qmc_combine_shifts(per_shift) -> qmc_result:
     res = qmc_result()
     _check(lib().qmc_combine_shifts(ps.shape[0], _ptr(ps), ctypes.byref(res)))
     return res
+
+
+def qmc_measure_peaks(stream=0) -> dict:
+    """Measured FP32 / FP64 FMA TFLOP/s of the current GPU."""
+    out = np.zeros(2)
+    _check(lib().qmc_measure_peaks(ctypes.c_void_p(stream), _ptr(out)))
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1])}
