@@ -331,6 +331,23 @@ int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const
 #endif
 
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
+/* Automatic choice of n: applies the rule (Eq. 2, 3) on the lattices
+ * (n[l], g[l * d ...]) for l = 0, 1, ... in turn and stops at the first whose
+ * error estimate satisfies err / |Qbar| <= rel_tol (real part, or modulus for
+ * complex integrands), or after the last.
+ *   levels       number of lattices (1..64), increasing n
+ *   n            [levels] lattice sizes;  g  [levels * d] generating vectors (host)
+ *   level_out    index of the lattice that produced *out
+ * The shifts, transform and integrand are those of qmc_integrate; `out`
+ * must be host memory.  Returns QMC_OK if the tolerance was met, else the
+ * last level's estimate with status QMC_ETIMEOUT in out->status and as the
+ * return value. */
+int qmc_integrate_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, const uint64_t* g, int32_t m,
+                               const double* shifts, qmc_transform t, const qmc_integrand* f, double rel_tol,
+                               qmc_result* out, int32_t* level_out, void* stream);
+#endif
+
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 /* Eq. (2)/(3) from per-shift values alone: Qbar and sigma^2 (two-pass,
  * compensated) over m values Q^(k) given as per_shift [m][2] (re, im), host
  * memory; host only, no GPU.  Combines independent shift sets (from several

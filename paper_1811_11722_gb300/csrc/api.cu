@@ -734,6 +734,24 @@ int qmc_plan_launches(qmc_plan plan, int32_t* launches_out) {
   return QMC_OK;
 }
 
+int qmc_integrate_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, const uint64_t* g, int32_t m,
+                               const double* shifts, qmc_transform t, const qmc_integrand* f, double rel_tol,
+                               qmc_result* out, int32_t* level_out, void* stream) {
+  if (levels < 1 || levels > 64 || !n || !g || !out || !(rel_tol > 0.0)) return fail(QMC_EINVAL, "bad ladder arguments");
+  if (is_device_pointer(out)) return fail(QMC_EINVAL, "the result must be host memory");
+  int rc = QMC_OK;
+  for (int l = 0; l < levels; ++l) {
+    rc = qmc_integrate(d, n[l], m, g + (size_t)l * d, shifts, t, f, out, nullptr, stream);
+    if (rc != QMC_OK && rc != QMC_ENONFINITE && rc != QMC_EDEFORM) return rc;
+    if (level_out) *level_out = l;
+    const double mag = std::hypot(out->mean[0], out->mean[1]);
+    const double err = std::hypot(out->err[0], out->err[1]);
+    if (mag > 0.0 && err <= rel_tol * mag) return rc;
+  }
+  out->status = QMC_ETIMEOUT;
+  return fail(QMC_ETIMEOUT, "relative error %.3g not reached after %d lattices", rel_tol, levels);
+}
+
 int qmc_combine_shifts(int32_t m, const double* per_shift, qmc_result* out) {
   if (m < 2 || !per_shift || !out) return fail(QMC_EINVAL, "combine needs m >= 2 values and an output");
   std::memset(out, 0, sizeof(*out));

@@ -1,4 +1,5 @@
 // Plan builder for contour-deformed (complex) sector integrands.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -8,17 +9,39 @@ namespace qmc {
 
 constexpr int kMcDef = 8;  // shifts per launch (matches the kernel's shared accumulators)
 
+// Offset of q_ij (i <= j) in the nested degree-2 layout (host copy of q_off).
+static int q_off_host(int D, int i, int j) {
+  int off = 1;
+  for (int a = 0; a < i; ++a) off += 1 + (D - a);
+  return off + 1 + (j - i);
+}
+
 template <typename R>
 static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                      const qmc_transform& t, const qmc_integrand* f, const TuneChoice& tune) {
   if (d > kDFast) return fail(QMC_EUNSUPPORTED, "deformed sector integrands need d <= %d", kDFast);
   RuleParams<R> base;
   fill_common(base, d, n, g, t, f);
+  auto cf = pack_dense(f->F, d, 2);
+  // J = I + i M with M_kl = -lam (y_k (1 - y_k) S_kl + delta_kl (1 - 2 y_k) dF_k), S = Hessian of F.
+  // |J_kk| >= 1 and sum_{l != k} |M_kl| <= lam / 4 * sum_{l != k} |S_kl|: below 1 for every row,
+  // J is strictly row diagonally dominant on the whole cube and LU needs no pivoting.
+  double worst = 0.0;
+  for (int k = 0; k < d; ++k) {
+    double row = 0.0;
+    for (int l = 0; l < d; ++l) {
+      if (l == k) continue;
+      const int a = k < l ? k : l, b = k < l ? l : k;
+      row += std::fabs(cf[q_off_host(d, a, b)]);
+    }
+    worst = std::max(worst, 0.25 * f->lambda * row);
+  }
+  const bool fast = worst < 1.0 && t.kind == QMC_TRANSFORM_KOROBOV && t.alpha == 3 && !tune.force_general;
   const void* func = nullptr;
   switch (d) {
 #define QMC_D_CASE(DD) \
   case DD:             \
-    func = deformed_ptr<R, DD>(); \
+    func = deformed_ptr<R, DD>(fast); \
     break;
     QMC_D_CASE(1) QMC_D_CASE(2) QMC_D_CASE(3) QMC_D_CASE(4) QMC_D_CASE(5) QMC_D_CASE(6) QMC_D_CASE(7)
     QMC_D_CASE(8)
@@ -27,7 +50,6 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
   }
   if (!func) return fail(QMC_EUNSUPPORTED, "no deformed kernel for d=%d", d);
   auto cu = pack_dense(f->U, d, 2);
-  auto cf = pack_dense(f->F, d, 2);
   for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
   for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
   base.value_scale = 1.0;  // transform weights normalised per factor in this kernel

@@ -83,8 +83,10 @@ __device__ __forceinline__ R cmag1(R re, R im) {
   return fabs(re) + fabs(im);
 }
 
-// det(J) for J = I + i M (M real, D x D) by LU with partial pivoting.
-template <int D, typename R>
+// det(J) for J = I + i M (M real, D x D) by LU; with PIVOT by partial
+// pivoting, without it when the host has shown J strictly row diagonally
+// dominant on the whole cube (then no pivoting is needed for stability).
+template <int D, typename R, bool PIVOT = true>
 __device__ __forceinline__ Cx<R> det_ipm(R (&M)[D][D]) {
   R ar[D][D], ai[D][D];
 #pragma unroll
@@ -99,7 +101,7 @@ __device__ __forceinline__ Cx<R> det_ipm(R (&M)[D][D]) {
 #pragma unroll
   for (int c = 0; c < D; ++c) {
 #pragma unroll
-    for (int r = c + 1; r < D; ++r) {
+    for (int r = c + 1; r < (PIVOT ? D : 0); ++r) {
       const bool sw = cmag1(ar[r][c], ai[r][c]) > cmag1(ar[c][c], ai[c][c]);
       neg ^= sw;
 #pragma unroll
@@ -133,13 +135,18 @@ __device__ __forceinline__ Cx<R> det_ipm(R (&M)[D][D]) {
 }
 
 // Weighted complex value at one point and shift; *bad set when Im F(w) > 0.
-template <typename R, int D>
+// FAST: compile-time Korobov weight 3 and no pivoting (host-checked);
+// otherwise the runtime transform and pivoted LU.
+template <typename R, int D, bool FAST = false>
 __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const typename FixT<R>::T* base, int k,
                                                 bool& bad) {
   R y[D];
   R wt = R(1);
 #pragma unroll
-  for (int i = 0; i < D; ++i) y[i] = coord_general<R>(P, base[i] + shift_of(P, k, i), wt);
+  for (int i = 0; i < D; ++i) {
+    if constexpr (FAST) y[i] = coord<R, TR_KOROBOV, 0>(base[i] + shift_of(P, k, i), P.kor, 3, wt);
+    else y[i] = coord_general<R>(P, base[i] + shift_of(P, k, i), wt);
+  }
   const R* cF = P.cF;
   // gradient of F (linear form) and the contour
   R gr[D];
@@ -171,7 +178,7 @@ __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const ty
       M[kk][l] = -lam * v;
     }
   }
-  const Cx<R> dJ = det_ipm<D, R>(M);
+  const Cx<R> dJ = det_ipm<D, R, !FAST>(M);
   const Cx<R> U = poly2_complex<D, R>(P.cU, z);
   const Cx<R> F = poly2_complex<D, R>(cF, z);
   bad = F.im > R(0);
@@ -185,7 +192,7 @@ __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const ty
 
 constexpr int kMcDeformed = 8;
 
-template <typename R, int D>
+template <typename R, int D, bool FAST = false>
 __global__ void __launch_bounds__(kThreads)
     deformed_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
                     unsigned long long* __restrict__ counters, const SampleIO sio) {
@@ -204,7 +211,7 @@ __global__ void __launch_bounds__(kThreads)
       if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<R>(base[i] + shift_of(P, k, i));
     }
     bool bad;
-    Cx<R> v = deformed_value<R, D>(P, base, k, bad);
+    Cx<R> v = deformed_value<R, D, FAST>(P, base, k, bad);
     sio.values[2 * (size_t)s] = (double)v.re * P.value_scale;
     sio.values[2 * (size_t)s + 1] = (double)v.im * P.value_scale;
     return;
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int i = 0; i < D; ++i) base[i] = fix_base<R>(idx[i], P.rc);
         bool bad;
-        Cx<R> v = deformed_value<R, D>(P, base, kk, bad);
+        Cx<R> v = deformed_value<R, D, FAST>(P, base, kk, bad);
         ndef += bad ? 1u : 0u;
         if (P.check_finite) {
           const bool ok = finite_(v.re) && finite_(v.im);

@@ -182,8 +182,9 @@ __device__ __forceinline__ double coord_f64(uint64_t X, const double* kor, int a
 }
 
 // Float-domain coordinates of the fast FP32 sector path.  With the point's
-// doubled base b2 = 2 frac(idx/n) (one correctly rounded conversion per point
-// and dimension; doubling is exact) and the shift constant c = 2 Delta - 2,
+// doubled base b2 = 2 frac(idx/n) (the 32-bit fraction rounded to 23 bits and
+// placed in a float mantissa, integer and FMA pipes only; doubling is exact)
+// and the shift constant c = 2 Delta - 2,
 // one add gives t = 2 (b + Delta) - 2 in [-2, 2), i.e. y = b + Delta in [0, 2)
 // before the wrap.  (An add with one constant operand encodes directly; an
 // FMA with an immediate 2 and a constant would first load the constant.)
@@ -191,7 +192,10 @@ __device__ __forceinline__ double coord_f64(uint64_t X, const double* kor, int a
 // z = 1 - |2 {y} - 1| = 1 - |v| with no wrap test at all, and
 // s = min({y}, 1 - {y}) = (1 - |v|) / 2; {y} > 1/2 exactly when t and v have
 // the same sign.
-__device__ __forceinline__ float base2_f32(uint64_t p64) { return __ull2float_rn(p64) * 0x1p-63f; }
+__device__ __forceinline__ float base2_f32(uint64_t p64) {
+  const uint32_t X = frac32(p64) + 0x100u;         // round to 23 bits (wraps to 0 near 1: periodic)
+  return __fmaf_rn(2.0f, unit_f32(X), -2.0f);      // 2 (x + 1) - 2 = 2x, exact
+}
 
 template <int TR, int ALPHA>
 __device__ __forceinline__ float coord_tri(float b2, float c, const float* kor, float& w) {

@@ -21,10 +21,12 @@ QMC_DECL_SECTOR(double, 1) QMC_DECL_SECTOR(double, 2) QMC_DECL_SECTOR(double, 3)
 QMC_DECL_SECTOR(double, 5) QMC_DECL_SECTOR(double, 6) QMC_DECL_SECTOR(double, 7) QMC_DECL_SECTOR(double, 8)
 #undef QMC_DECL_SECTOR
 
-// Contour-deformed complex sector kernel, d = D <= kDFast (runtime transform).
+// Contour-deformed complex sector kernel, d = D <= kDFast: fast = Korobov 3
+// and unpivoted LU (host-checked dominance); otherwise runtime transform and
+// pivoted LU.
 template <typename R, int D>
-const void* deformed_ptr();
-#define QMC_DECL_DEF(R, D) template <> const void* deformed_ptr<R, D>();
+const void* deformed_ptr(bool fast);
+#define QMC_DECL_DEF(R, D) template <> const void* deformed_ptr<R, D>(bool);
 QMC_DECL_DEF(float, 1) QMC_DECL_DEF(float, 2) QMC_DECL_DEF(float, 3) QMC_DECL_DEF(float, 4)
 QMC_DECL_DEF(float, 5) QMC_DECL_DEF(float, 6) QMC_DECL_DEF(float, 7) QMC_DECL_DEF(float, 8)
 QMC_DECL_DEF(double, 1) QMC_DECL_DEF(double, 2) QMC_DECL_DEF(double, 3) QMC_DECL_DEF(double, 4)

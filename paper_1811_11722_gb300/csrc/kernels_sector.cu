@@ -47,8 +47,8 @@ const void* sector_ptr<QMC_REAL, QMC_D>(int mc, int tr, int alpha, int ku, int k
 }
 
 template <>
-const void* deformed_ptr<QMC_REAL, QMC_D>() {
-  return (const void*)&deformed_kernel<QMC_REAL, QMC_D>;
+const void* deformed_ptr<QMC_REAL, QMC_D>(bool fast) {
+  return fast ? (const void*)&deformed_kernel<QMC_REAL, QMC_D, true> : (const void*)&deformed_kernel<QMC_REAL, QMC_D, false>;
 }
 
 }  // namespace qmc

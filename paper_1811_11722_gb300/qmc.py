@@ -103,6 +103,8 @@ def lib():
             L.qmc_plan_describe.argtypes = [vp, ctypes.c_char_p, i32]
             L.qmc_combine_shifts.argtypes = [i32, vp, vp]
             L.qmc_measure_peaks.argtypes = [vp, vp]
+            L.qmc_integrate_to_tolerance.argtypes = [i32, i32, vp, vp, i32, vp, qmc_transform, P_int,
+                                                     ctypes.c_double, vp, ctypes.POINTER(i32), vp]
             L.qmc_integrate_batch.argtypes = [i32, vp, vp, vp, vp]
             L.qmc_batch_plan_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
             L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
@@ -121,7 +123,8 @@ def lib():
                          "qmc_plan_destroy", "qmc_plan_launches", "qmc_plan_record_events", "qmc_plan_tune", "qmc_plan_describe", "qmc_integrate_batch", "qmc_batch_plan_create",
                          "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_batch_plan_launches",
                          "qmc_batch_plan_tune", "qmc_sample_points", "qmc_cv_train", "qmc_integrate_cv",
-                         "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts", "qmc_measure_peaks"):
+                         "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts", "qmc_measure_peaks",
+                         "qmc_integrate_to_tolerance"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -453,3 +456,18 @@ def qmc_measure_peaks(stream=0) -> dict:
     out = np.zeros(2)
     _check(lib().qmc_measure_peaks(ctypes.c_void_p(stream), _ptr(out)))
     return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1])}
+
+
+def qmc_integrate_to_tolerance(d, ns, gs, m, shifts, t, f: Integrand, rel_tol, stream=0):
+    """Walk the lattices (ns[l], gs[l]) until err/|Qbar| <= rel_tol.
+    Returns (qmc_result, level index, reached: bool)."""
+    ns = np.ascontiguousarray(np.asarray(ns, dtype=np.uint64))
+    gs = np.ascontiguousarray(np.asarray(gs, dtype=np.uint64).reshape(len(ns), d))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    res = qmc_result()
+    lvl = ctypes.c_int32(-1)
+    rc = lib().qmc_integrate_to_tolerance(d, len(ns), _ptr(ns), _ptr(gs), m, _ptr(shifts), t, f.ref, rel_tol,
+                                          ctypes.byref(res), ctypes.byref(lvl), ctypes.c_void_p(stream))
+    if rc not in (QMC_OK, QMC_ETIMEOUT) and rc not in WARNINGS:
+        _check(rc)
+    return res, int(lvl.value), rc != QMC_ETIMEOUT

@@ -537,3 +537,73 @@ def test_specialised_kernel_bit_identical(Q, monkeypatch):
     b = plan.execute().as_dict()
     plan.destroy()
     assert a["mean"][0] == b["mean"][0] and a["var"][0] == b["var"][0]
+
+
+# ------------------------------------------------------------- utilities --
+
+def test_measure_peaks_sane(Q):
+    pk = Q.qmc_measure_peaks()
+    assert 10.0 < pk["fp32_tflops"] < 100.0
+    assert 0.1 < pk["fp64_tflops"] < pk["fp32_tflops"]
+
+
+def test_combine_shifts_equals_one_call(Q):
+    """Two calls with disjoint shift sets, combined on the host, equal one call
+    with all shifts (appending shifts to an estimate, or merging GPUs)."""
+    p = I.config2(n=200003, m=16, precision="fp64")
+    g = I.random_generating_vector(I.SplitMix64(9), 6, p.n)
+    f = Q.integrand_from_problem(p)
+    t = Q.transform("baker")
+    _, ps_all = Q.qmc_integrate(p.d, p.n, 16, g, p.shifts, t, f, want_per_shift=True)
+    _, ps_a = Q.qmc_integrate(p.d, p.n, 6, g, p.shifts[:6], t, f, want_per_shift=True)
+    _, ps_b = Q.qmc_integrate(p.d, p.n, 10, g, p.shifts[6:], t, f, want_per_shift=True)
+    one = Q.qmc_combine_shifts(ps_all).as_dict()
+    two = Q.qmc_combine_shifts(np.concatenate([ps_a, ps_b])).as_dict()
+    assert abs(one["mean"][0] - two["mean"][0]) <= 1e-14 * abs(one["mean"][0])
+    assert abs(one["err"][0] - two["err"][0]) <= 1e-12 * abs(one["mean"][0])
+
+
+# ------------------------------------------------- Fig. 3 and automatic n --
+
+@pytest.mark.parametrize("d", [6, 9, 10])
+def test_fig3_constant_integrand_korobov(Q, d):
+    """Sec. 2 / Fig. 3: the constant 1 under Korobov weights 3 and 6: the error
+    against the exact value 1 shrinks from n ~ 1e3 to n ~ 1e6 and the Eq. (3)
+    estimate brackets it; the baker transform is exact (Q^(k) = 1, sigma = 0)."""
+    rng = I.SplitMix64(300 + d)
+    sh = I.make_shifts(rng, 8, d)
+    gam = I.product_weights(d)
+    for alpha in (3, 6):
+        errs = []
+        for n in (1021, 32749, 1048573):
+            g = Q.qmc_make_lattice(d, n, gam)
+            p = I.Problem("c", d, n, 8, sh, "korobov", alpha=alpha, kind="const")
+            r, _ = Q.qmc_integrate(d, n, 8, g, sh, Q.transform("korobov", alpha), Q.integrand_from_problem(p, "fp64"))
+            e = abs(r.mean[0] - 1.0)
+            errs.append(e)
+            assert e <= 8 * r.err[0] + 1e-14
+        assert errs[-1] < errs[0] / 10, (alpha, errs)
+    p = I.Problem("c", d, 1021, 8, sh, "baker", kind="const")
+    r, ps = Q.qmc_integrate(d, 1021, 8, Q.qmc_make_lattice(d, 1021, gam), sh, Q.transform("baker"),
+                            Q.integrand_from_problem(p, "fp64"), want_per_shift=True)
+    assert np.all(ps[:, 0] == 1.0) and r.var[0] == 0.0
+
+
+def test_integrate_to_tolerance(Q):
+    """Automatic n: the ladder stops at the first lattice whose relative error
+    estimate meets the target, and that estimate equals a direct call's."""
+    p = I.config2(m=16)
+    ladder = [n for n in I.ladder_primes() if 100000 < n < 20000000]
+    gs = [Q.qmc_make_lattice(6, n, p.gamma) for n in ladder]
+    f = Q.integrand_from_problem(p, "fp32")
+    t = Q.transform("baker")
+    res, lvl, ok = Q.qmc_integrate_to_tolerance(6, ladder, gs, 16, p.shifts, t, f, 1e-7)
+    assert ok and 0 <= lvl < len(ladder)
+    assert res.err[0] <= 1e-7 * abs(res.mean[0])
+    if lvl > 0:
+        prev, _ = Q.qmc_integrate(6, ladder[lvl - 1], 16, gs[lvl - 1], p.shifts, t, f)
+        assert prev.err[0] > 1e-7 * abs(prev.mean[0])
+    direct, _ = Q.qmc_integrate(6, ladder[lvl], 16, gs[lvl], p.shifts, t, f)
+    assert direct.mean[0] == res.mean[0]
+    res, lvl, ok = Q.qmc_integrate_to_tolerance(6, ladder[:2], gs[:2], 16, p.shifts, t, f, 1e-16)
+    assert not ok and lvl == 1 and res.status == Q.QMC_ETIMEOUT
