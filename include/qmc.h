@@ -364,6 +364,45 @@ int qmc_combine_shifts(int32_t m, const double* per_shift, qmc_result* out);
 int qmc_measure_peaks(void* stream, double* out);
 #endif
 
+/* Epsilon expansion of the sector integrand (Eq. 7 with regulated powers,
+ * Sec. 2): for U^(aU + bU eps) F^(aF + bF eps) = sum_k eps^k f_k,
+ *   f_k = U^aU F^aF L^k / k!,  L = bU log U + bF log F,
+ * one pass over the lattice estimates f_0 .. f_{orders-1} together: the
+ * point, transform, U and F are computed once per (point, shift) and shared
+ * by all orders.  f_0 is the SECTOR integrand itself (eps = 0).
+ *   orders  1..QMC_EPS_MAX coefficient integrands
+ *   bU, bF  finite slopes of the powers in eps (U^(-2+eps) F^(-1-eps): 1, -1)
+ * Values where U <= 0 or F <= 0 make L NaN; each order counts and leaves out
+ * its own non-finite values (out[o].nonfinite, status QMC_ENONFINITE). */
+#define QMC_EPS_MAX 6
+typedef struct {
+  int32_t orders;
+  int32_t reserved;
+  double bU;
+  double bF;
+} qmc_eps;
+
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+/* Eq. (2)/(3) for every order.  Arguments as qmc_integrate, f->kind must be
+ * QMC_F_SECTOR (else QMC_EINVAL), and
+ *   out        [orders] results, order o in out[o] (host or device)
+ *   per_shift  optional [orders][m][2] Q^(k) per order
+ * Returns the first non-OK status of the orders when `out` is host memory. */
+int qmc_integrate_eps(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                      qmc_transform t, const qmc_integrand* f, const qmc_eps* eps, qmc_result* out,
+                      double* per_shift, void* stream);
+/* A plan of the same (see qmc_plan_create); qmc_plan_execute on it writes
+ * out[orders] and per_shift [orders][m][2]. */
+int qmc_eps_plan_create(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                        qmc_transform t, const qmc_integrand* f, const qmc_eps* eps, qmc_plan* plan_out);
+/* Single terms: values [count][orders] (host), order o of the weighted value
+ * at point j[s], shift k[s], by the device code of qmc_integrate_eps.
+ * Synchronises `stream`. */
+int qmc_sample_points_eps(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                          qmc_transform t, const qmc_integrand* f, const qmc_eps* eps, int32_t count,
+                          const uint64_t* j, const int32_t* k, double* values, void* stream);
+#endif
+
 /* Text of the last error raised on the calling thread ("" if none). */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 const char* qmc_last_error(void);

@@ -56,6 +56,7 @@ class _Problem(ctypes.Structure):
         ("aU", ctypes.c_int), ("aF", ctypes.c_int), ("lam", ctypes.c_double),
         ("c", ctypes.c_void_p), ("b", ctypes.c_void_p), ("h", ctypes.c_void_p),
         ("cvR", ctypes.c_int), ("cvK", ctypes.c_int), ("cvF", ctypes.c_int), ("cva", ctypes.c_void_p),
+        ("eps_order", ctypes.c_int), ("eps_bU", ctypes.c_double), ("eps_bF", ctypes.c_double),
     ]
 
 
@@ -139,6 +140,9 @@ class _Marshalled:
         s.c = _ptr(arr(p.c, np.float64))
         s.b = _ptr(arr(p.b, np.float64))
         s.h = _ptr(arr(p.h, np.int32))
+        eps = getattr(p, "eps", None)
+        if eps is not None:
+            s.eps_order, s.eps_bU, s.eps_bF = int(eps["order"]), float(eps["bU"]), float(eps["bF"])
         cv = getattr(p, "cv", None)
         if cv is not None:
             s.cvR, s.cvK, s.cvF = int(cv["R"]), int(cv["K"]), int(cv["F"])

@@ -63,6 +63,11 @@ typedef struct {
    * transformed point z (so the value becomes (f - g)(z) prod_i w_i) */
   int cvR, cvK, cvF;
   const float* cva;
+  /* epsilon expansion of Eq. (7): U^(aU + bU eps) F^(aF + bF eps) =
+   * sum_k eps^k U^aU F^aF (bU log U + bF log F)^k / k!; eps_order = k selects
+   * the coefficient integrand (0 = the plain U^aU F^aF) */
+  int eps_order;
+  double eps_bU, eps_bF;
 } orc_problem;
 
 /* ---------------------------------------------------------------- sums --- */
@@ -270,6 +275,12 @@ int orc_integrand(const orc_problem* p, const double* y, double* out, int* bad) 
       double U = poly_eval_real(p->nU, p->cU, p->eU, d, y);
       double F = poly_eval_real(p->nF, p->cF, p->eF, d, y);
       out[0] = pow_int(U, p->aU) * pow_int(F, p->aF);
+      if (p->eps_order > 0) {
+        double L = p->eps_bU * log(U) + p->eps_bF * log(F);
+        double c = 1.0;
+        for (int k = 1; k <= p->eps_order; ++k) c *= L / (double)k;
+        out[0] *= c;
+      }
       return 0;
     }
     case ORC_SECTOR_DEFORMED: {

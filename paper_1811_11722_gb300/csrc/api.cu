@@ -334,7 +334,8 @@ static int pick_mc(int m, bool fp32) {
 
 template <typename R>
 static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
-                           const qmc_transform& t, const qmc_integrand* f, const TuneChoice& tune) {
+                           const qmc_transform& t, const qmc_integrand* f, const TuneChoice& tune,
+                           const qmc_eps* eps) {
   const bool fp32 = sizeof(R) == 4;
   RuleParams<R> base;
   fill_common(base, d, n, g, t, f);
@@ -347,7 +348,39 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
   int mc = tune.mc > 0 ? tune.mc : pick_mc(m, fp32);
   bool general = false;
 
-  if (f->kind == QMC_F_SECTOR) {
+  if (eps) {
+    // Eq. (7) expansion: 3 or kEpsMax orders per pass, kEpsAcc sums per thread
+    base.eps_orders = eps->orders;
+    base.m_total = m;
+    base.eps_b[0] = (R)eps->bU;
+    base.eps_b[1] = (R)eps->bF;
+    for (int k = 0; k < kEpsMax; ++k) base.eps_inv[k] = (R)(1.0 / (double)(k + 1));
+    const int ne = eps->orders <= 3 ? 3 : kEpsMax;
+    const int ku = poly_degree(f->U, d), kf = poly_degree(f->F, d);
+    const bool fast_tr = base.tr == TR_BAKER || (base.tr == TR_KOROBOV && base.alpha == 3);
+    if (ku <= 1 && kf <= 2 && f->aU == -2 && f->aF == -1 && d <= kDFast && fast_tr && !tune.force_general) {
+      switch (d) {
+#define QMC_D_CASE(DD) \
+  case DD:             \
+    func = eps_ptr<R, DD>(ne, base.tr); \
+    break;
+        QMC_D_CASE(1) QMC_D_CASE(2) QMC_D_CASE(3) QMC_D_CASE(4) QMC_D_CASE(5) QMC_D_CASE(6)
+        QMC_D_CASE(7) QMC_D_CASE(8)
+#undef QMC_D_CASE
+        default: break;
+      }
+    }
+    if (func) {
+      mc = kEpsAcc / ne;
+      auto cu = pack_dense(f->U, d, 1);
+      auto cf = pack_dense(f->F, d, 2);
+      for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
+      for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
+      if (base.tr == TR_KOROBOV) base.value_scale = std::pow((double)base.kor[7], (double)d);
+    } else {
+      general = true;
+    }
+  } else if (f->kind == QMC_F_SECTOR) {
     int ku = poly_degree(f->U, d), kf = poly_degree(f->F, d);
     int KU = -1, KF = -1;
     if (ku <= 1 && kf <= 2) {
@@ -402,9 +435,9 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
 
   GeneralParams<R> gp;
   if (general) {
-    mc = 8;
+    mc = eps ? kEpsAcc / kEpsMax : 8;
     std::memset(&gp, 0, sizeof(gp));
-    func = general_ptr(fp32);
+    func = eps ? general_eps_ptr(fp32) : general_ptr(fp32);
     pbytes = sizeof(GeneralParams<R>);
     auto fill_sparse = [&](SparsePoly<R>& S, const qmc_poly& p) {
       S.nterms = p.nterms;
@@ -507,9 +540,16 @@ void SavedProblem::save(int32_t d_, uint64_t n_, int32_t m_, const uint64_t* g_,
 }
 
 int plan_build(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
-               qmc_transform t, const qmc_integrand* f, const TuneChoice& tune) {
+               qmc_transform t, const qmc_integrand* f, const TuneChoice& tune, const qmc_eps* eps) {
   int rc = validate_problem(d, n, m, g, shifts, t, f);
   if (rc) return rc;
+  if (eps) {
+    if (eps->orders < 1 || eps->orders > kEpsMax)
+      return fail(QMC_EINVAL, "epsilon orders %d outside [1, %d]", eps->orders, kEpsMax);
+    if (!std::isfinite(eps->bU) || !std::isfinite(eps->bF)) return fail(QMC_EINVAL, "non-finite epsilon slopes");
+    if (f->kind != QMC_F_SECTOR) return fail(QMC_EINVAL, "the epsilon expansion applies to SECTOR integrands");
+  }
+  pl->orders = eps ? eps->orders : 1;
   pl->tune = tune;
   pl->d = d;
   pl->n = n;
@@ -518,16 +558,17 @@ int plan_build(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, co
   if (f->kind == QMC_F_SECTOR_DEFORMED) {
     rc = build_deformed_plan(pl, d, n, m, g, shifts, t, f, tune);
   } else if (f->precision == QMC_FP32EVAL) {
-    rc = build_rule_plan<float>(pl, d, n, m, g, shifts, t, f, tune);
+    rc = build_rule_plan<float>(pl, d, n, m, g, shifts, t, f, tune, eps);
   } else {
-    rc = build_rule_plan<double>(pl, d, n, m, g, shifts, t, f, tune);
+    rc = build_rule_plan<double>(pl, d, n, m, g, shifts, t, f, tune, eps);
   }
   return rc;
 }
 
 int plan_alloc(Plan* pl, cudaStream_t stream, bool async) {
-  size_t partial_bytes = (size_t)pl->m * pl->nblk * 2 * sizeof(double);
-  size_t total = partial_bytes + 2 * sizeof(unsigned long long) + sizeof(qmc_result) + (size_t)pl->m * 2 * sizeof(double) + 256;
+  const size_t G = (size_t)pl->orders;
+  size_t partial_bytes = G * pl->m * pl->nblk * 2 * sizeof(double);
+  size_t total = partial_bytes + G * (2 * sizeof(unsigned long long) + sizeof(qmc_result) + (size_t)pl->m * 2 * sizeof(double)) + 256;
   void* p = nullptr;
   cudaError_t e = async ? cudaMallocAsync(&p, total, stream) : cudaMalloc(&p, total);
   if (e != cudaSuccess) {
@@ -540,13 +581,13 @@ int plan_alloc(Plan* pl, cudaStream_t stream, bool async) {
   pl->ws.partial = (double*)c;
   c += partial_bytes;
   pl->ws.counters = (unsigned long long*)c;
-  c += 2 * sizeof(unsigned long long);
+  c += G * 2 * sizeof(unsigned long long);
   pl->ws.result = (qmc_result*)c;
-  c += sizeof(qmc_result);
+  c += G * sizeof(qmc_result);
   c = (char*)(((uintptr_t)c + 15) & ~(uintptr_t)15);
   pl->ws.per_shift = (double*)c;
-  e = async ? cudaMemsetAsync(pl->ws.counters, 0, 2 * sizeof(unsigned long long), stream)
-            : cudaMemset(pl->ws.counters, 0, 2 * sizeof(unsigned long long));
+  e = async ? cudaMemsetAsync(pl->ws.counters, 0, G * 2 * sizeof(unsigned long long), stream)
+            : cudaMemset(pl->ws.counters, 0, G * 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_fail(e, "clear counters");
   return QMC_OK;
 }
@@ -580,7 +621,7 @@ int launch_finalize(const Plan* pl, const Workspace& ws, qmc_result* res_dev, do
   A.nblk = pl->nblk;
   A.m = pl->m;
   A.is_complex = pl->is_complex;
-  A.pad = 0;
+  A.groups = pl->orders;
   A.dn = (double)pl->n;
   A.value_scale = pl->final_scale;
   A.offset[0] = pl->offset[0];
@@ -590,7 +631,7 @@ int launch_finalize(const Plan* pl, const Workspace& ws, qmc_result* res_dev, do
   A.per_shift = per_shift_dev;
   void* args[1] = {&A};
   size_t smem = (size_t)pl->m * 2 * sizeof(double);
-  QMC_CUDA(cudaLaunchKernel(finalize_ptr(), dim3(1), dim3(256), args, smem, stream));
+  QMC_CUDA(cudaLaunchKernel(finalize_ptr(), dim3(pl->orders), dim3(256), args, smem, stream));
   return QMC_OK;
 }
 
@@ -607,13 +648,19 @@ int plan_execute(Plan* pl, qmc_result* out, double* per_shift, cudaStream_t stre
   rc = launch_finalize(pl, pl->ws, out_dev ? out : pl->ws.result,
                        (per_shift && ps_dev) ? per_shift : (per_shift ? pl->ws.per_shift : nullptr), stream);
   if (rc) return rc;
-  if (!out_dev) QMC_CUDA(cudaMemcpyAsync(out, pl->ws.result, sizeof(qmc_result), cudaMemcpyDeviceToHost, stream));
+  const size_t G = (size_t)pl->orders;
+  if (!out_dev) QMC_CUDA(cudaMemcpyAsync(out, pl->ws.result, G * sizeof(qmc_result), cudaMemcpyDeviceToHost, stream));
   if (per_shift && !ps_dev)
-    QMC_CUDA(cudaMemcpyAsync(per_shift, pl->ws.per_shift, (size_t)pl->m * 2 * sizeof(double),
+    QMC_CUDA(cudaMemcpyAsync(per_shift, pl->ws.per_shift, G * pl->m * 2 * sizeof(double),
                              cudaMemcpyDeviceToHost, stream));
   if (!out_dev || (per_shift && !ps_dev)) {
     QMC_CUDA(cudaStreamSynchronize(stream));
-    if (!out_dev) return out->status;
+    if (!out_dev) {
+      // the first failing order's status (NaN/Inf values are counted per order)
+      for (size_t o = 0; o < G; ++o)
+        if (out[o].status != QMC_OK) return out[o].status;
+      return QMC_OK;
+    }
   }
   return QMC_OK;
 }
@@ -650,7 +697,7 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
   cudaStream_t st = (cudaStream_t)stream;
   const SavedProblem& sp = pl->saved;
   std::vector<int> cands;
-  if (sp.f.precision == QMC_FP32EVAL && sp.f.kind == QMC_F_SECTOR) cands = {8, 16, 32};
+  if (sp.f.precision == QMC_FP32EVAL && sp.f.kind == QMC_F_SECTOR && sp.eps.orders == 0) cands = {8, 16, 32};
   if (cands.empty()) {
     if (shifts_per_launch_out) *shifts_per_launch_out = pl->mc;
     return QMC_OK;
@@ -788,8 +835,9 @@ int qmc_plan_describe(qmc_plan plan, char* buf, int32_t len) {
     std::memcpy(&v, ln->params.data() + offsetof(RuleParams<float>, L), sizeof(v));
     L = v;
   }
-  snprintf(buf, (size_t)len, "d=%d n=%llu m=%d complex=%d shifts_per_launch=%d launches=%zu specialised=%d ctas=%d L=%d",
-           pl->d, (unsigned long long)pl->n, pl->m, pl->is_complex, pl->mc, pl->launches.size() + 1,
+  snprintf(buf, (size_t)len,
+           "d=%d n=%llu m=%d complex=%d orders=%d shifts_per_launch=%d launches=%zu specialised=%d ctas=%d L=%d",
+           pl->d, (unsigned long long)pl->n, pl->m, pl->is_complex, pl->orders, pl->mc, pl->launches.size() + 1,
            (ln && ln->cufunc) ? 1 : 0, pl->nblk, L);
   return QMC_OK;
 }
@@ -815,32 +863,21 @@ int qmc_integrate(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const dou
   return rc;
 }
 
-int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts, qmc_transform t,
-                      const qmc_integrand* f, int32_t count, const uint64_t* j, const int32_t* k, double* values,
-                      uint64_t* idx, double* coord, void* stream) {
-  if (count < 0 || (count > 0 && (!j || !k || !values))) return fail(QMC_EINVAL, "bad sample arrays");
-  if (count == 0) return QMC_OK;
-  for (int s = 0; s < count; ++s) {
-    if (j[s] >= n) return fail(QMC_EINVAL, "sample %d: j=%llu >= n", s, (unsigned long long)j[s]);
-    if (k[s] < 0 || k[s] >= m) return fail(QMC_EINVAL, "sample %d: k=%d outside [0, m)", s, k[s]);
-  }
-  Plan pl;
-  cudaStream_t st = (cudaStream_t)stream;
-  int rc = plan_build(&pl, d, n, m, g, shifts, t, f, TuneChoice{});
-  if (rc) return rc;
+// Evaluates listed (j, k) terms with the kernels of a built plan; each sample
+// gets `vstride` values (2: real and imaginary part; epsilon plans: one per order).
+static int sample_with_plan(Plan& pl, int32_t d, int32_t count, const uint64_t* j, const int32_t* k, double* values,
+                            int vstride, uint64_t* idx, double* coord, cudaStream_t st) {
   const int dd = d;
-  const int comps = pl.is_complex ? 2 : 1;
-  (void)comps;
   // group samples by shift chunk (each launch holds mc shifts)
   std::vector<std::vector<int>> by_chunk(pl.launches.size());
   for (int s = 0; s < count; ++s) by_chunk[k[s] / pl.mc].push_back(s);
-  size_t bytes = (size_t)count * (8 + 4 + 16 + 8 * dd + 8 * dd) + 64;
+  size_t bytes = (size_t)count * (8 + 4 + 8 * vstride + 8 * dd + 8 * dd) + 64;
   char* dbuf = nullptr;
   QMC_CUDA(cudaMallocAsync((void**)&dbuf, bytes, st));
   uint64_t* dj = (uint64_t*)dbuf;
   int32_t* dk = (int32_t*)(dj + count);
   double* dv = (double*)(((uintptr_t)(dk + count) + 15) & ~(uintptr_t)15);
-  uint64_t* di = (uint64_t*)(dv + 2 * (size_t)count);
+  uint64_t* di = (uint64_t*)(dv + (size_t)vstride * count);
   double* dc = (double*)(di + (size_t)count * dd);
   std::vector<uint64_t> hj(count);
   std::vector<int32_t> hk(count);
@@ -859,10 +896,10 @@ int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const
     if (!cnt) continue;
     SampleIO sio;
     sio.count = cnt;
-    sio.pad = 0;
+    sio.stride = vstride;
     sio.j = dj + off;
     sio.k = dk + off;
-    sio.values = dv + 2 * (size_t)off;
+    sio.values = dv + (size_t)vstride * off;
     sio.idx = di + (size_t)off * dd;
     sio.coord = dc + (size_t)off * dd;
     const Launch& ln = pl.launches[c];
@@ -873,27 +910,88 @@ int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const
     args[1] = &partial;
     args[2] = &counters;
     args[3] = &sio;
-    rc = launch_any(ln, dim3((cnt + 255) / 256), args, st);
+    int rc = launch_any(ln, dim3((cnt + 255) / 256), args, st);
     if (rc) return rc;
     off += cnt;
   }
-  std::vector<double> hv(2 * (size_t)count), hc((size_t)count * dd);
+  std::vector<double> hv((size_t)vstride * count), hc((size_t)count * dd);
   std::vector<uint64_t> hi((size_t)count * dd);
-  QMC_CUDA(cudaMemcpyAsync(hv.data(), dv, 16 * (size_t)count, cudaMemcpyDeviceToHost, st));
+  QMC_CUDA(cudaMemcpyAsync(hv.data(), dv, 8 * (size_t)vstride * count, cudaMemcpyDeviceToHost, st));
   QMC_CUDA(cudaMemcpyAsync(hi.data(), di, 8 * (size_t)count * dd, cudaMemcpyDeviceToHost, st));
   QMC_CUDA(cudaMemcpyAsync(hc.data(), dc, 8 * (size_t)count * dd, cudaMemcpyDeviceToHost, st));
   QMC_CUDA(cudaFreeAsync(dbuf, st));
   QMC_CUDA(cudaStreamSynchronize(st));
   for (int q = 0; q < count; ++q) {
     int s = order[q];
-    values[2 * (size_t)s] = hv[2 * (size_t)q];
-    values[2 * (size_t)s + 1] = hv[2 * (size_t)q + 1];
+    for (int v = 0; v < vstride; ++v) values[(size_t)vstride * s + v] = hv[(size_t)vstride * q + v];
     for (int i = 0; i < dd; ++i) {
       if (idx) idx[(size_t)s * dd + i] = hi[(size_t)q * dd + i];
       if (coord) coord[(size_t)s * dd + i] = hc[(size_t)q * dd + i];
     }
   }
   return QMC_OK;
+}
+
+static int check_samples(uint64_t n, int32_t m, int32_t count, const uint64_t* j, const int32_t* k,
+                         const double* values) {
+  if (count < 0 || (count > 0 && (!j || !k || !values))) return fail(QMC_EINVAL, "bad sample arrays");
+  for (int s = 0; s < count; ++s) {
+    if (j[s] >= n) return fail(QMC_EINVAL, "sample %d: j=%llu >= n", s, (unsigned long long)j[s]);
+    if (k[s] < 0 || k[s] >= m) return fail(QMC_EINVAL, "sample %d: k=%d outside [0, m)", s, k[s]);
+  }
+  return QMC_OK;
+}
+
+int qmc_sample_points(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts, qmc_transform t,
+                      const qmc_integrand* f, int32_t count, const uint64_t* j, const int32_t* k, double* values,
+                      uint64_t* idx, double* coord, void* stream) {
+  int rc = check_samples(n, m, count, j, k, values);
+  if (rc || count == 0) return rc;
+  Plan pl;
+  rc = plan_build(&pl, d, n, m, g, shifts, t, f, TuneChoice{});
+  if (rc) return rc;
+  return sample_with_plan(pl, d, count, j, k, values, 2, idx, coord, (cudaStream_t)stream);
+}
+
+int qmc_eps_plan_create(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts, qmc_transform t,
+                        const qmc_integrand* f, const qmc_eps* eps, qmc_plan* plan_out) {
+  if (!plan_out || !eps) return fail(QMC_EINVAL, "null plan_out or epsilon descriptor");
+  *plan_out = nullptr;
+  std::unique_ptr<Plan> pl(new Plan());
+  int rc = plan_build(pl.get(), d, n, m, g, shifts, t, f, TuneChoice{}, eps);
+  if (rc) return rc;
+  rc = plan_alloc(pl.get(), nullptr, false);
+  if (rc) return rc;
+  pl->saved.save(d, n, m, g, shifts, t, f);
+  pl->saved.eps = *eps;
+  *plan_out = reinterpret_cast<qmc_plan>(pl.release());
+  return QMC_OK;
+}
+
+int qmc_integrate_eps(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts, qmc_transform t,
+                      const qmc_integrand* f, const qmc_eps* eps, qmc_result* out, double* per_shift, void* stream) {
+  if (!eps) return fail(QMC_EINVAL, "null epsilon descriptor");
+  Plan pl;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = plan_build(&pl, d, n, m, g, shifts, t, f, TuneChoice{}, eps);
+  if (rc) return rc;
+  rc = plan_alloc(&pl, s, true);
+  if (rc) return rc;
+  rc = plan_execute(&pl, out, per_shift, s);
+  plan_free(&pl, s);
+  return rc;
+}
+
+int qmc_sample_points_eps(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                          qmc_transform t, const qmc_integrand* f, const qmc_eps* eps, int32_t count,
+                          const uint64_t* j, const int32_t* k, double* values, void* stream) {
+  if (!eps) return fail(QMC_EINVAL, "null epsilon descriptor");
+  int rc = check_samples(n, m, count, j, k, values);
+  if (rc || count == 0) return rc;
+  Plan pl;
+  rc = plan_build(&pl, d, n, m, g, shifts, t, f, TuneChoice{}, eps);
+  if (rc) return rc;
+  return sample_with_plan(pl, d, count, j, k, values, eps->orders, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -7,10 +7,15 @@ namespace qmc {
 
 constexpr int kFinThreads = 256;
 
-// One CTA per problem.  Warp w adds the CTA slots of (shift, part) tasks
-// w, w+8, ... in a fixed order; warp 0 then forms Qbar and the two-pass
-// sigma^2 per part.
-__device__ void finalize_one(const FinalizeArgs& A, double* q /* shared [m][2] */) {
+// One CTA per problem (per group of a problem: the epsilon orders of one
+// pass have their slots, counters and results one after another).  Warp w
+// adds the CTA slots of (shift, part) tasks w, w+8, ... in a fixed order;
+// warp 0 then forms Qbar and the two-pass sigma^2 per part.
+__device__ void finalize_one(FinalizeArgs A, int grp, double* q /* shared [m][2] */) {
+  A.partial += (size_t)grp * A.m * A.nblk * 2;
+  A.counters += 2 * grp;
+  A.result += grp;
+  if (A.per_shift) A.per_shift += (size_t)grp * A.m * 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int parts = A.is_complex ? 2 : 1;
   const int tasks = A.m * parts;
@@ -60,14 +65,13 @@ __device__ void finalize_one(const FinalizeArgs& A, double* q /* shared [m][2] *
 
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArgs A) {
   extern __shared__ double q[];
-  finalize_one(A, q);
+  finalize_one(A, blockIdx.x, q);
 }
 
 // Batched final pass: CTA b finalises problem b.
 __global__ void __launch_bounds__(kFinThreads) finalize_batch_kernel(const FinalizeArgs* __restrict__ args) {
   extern __shared__ double q[];
-  const FinalizeArgs A = args[blockIdx.x];
-  finalize_one(A, q);
+  finalize_one(args[blockIdx.x], 0, q);
 }
 
 const void* finalize_ptr() { return (const void*)&finalize_kernel; }

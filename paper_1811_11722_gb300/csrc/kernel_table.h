@@ -21,6 +21,18 @@ QMC_DECL_SECTOR(double, 1) QMC_DECL_SECTOR(double, 2) QMC_DECL_SECTOR(double, 3)
 QMC_DECL_SECTOR(double, 5) QMC_DECL_SECTOR(double, 6) QMC_DECL_SECTOR(double, 7) QMC_DECL_SECTOR(double, 8)
 #undef QMC_DECL_SECTOR
 
+// Epsilon-order kernel (Eq. 7 expansion): dense U of degree 1, F of degree 2,
+// U^-2 F^-1 at eps = 0, d = D, baker or Korobov-3; ne = 3 or kEpsMax orders
+// accumulated (kEpsAcc / ne shifts per launch).
+template <typename R, int D>
+const void* eps_ptr(int ne, int tr);
+#define QMC_DECL_EPS(R, D) template <> const void* eps_ptr<R, D>(int, int);
+QMC_DECL_EPS(float, 1) QMC_DECL_EPS(float, 2) QMC_DECL_EPS(float, 3) QMC_DECL_EPS(float, 4)
+QMC_DECL_EPS(float, 5) QMC_DECL_EPS(float, 6) QMC_DECL_EPS(float, 7) QMC_DECL_EPS(float, 8)
+QMC_DECL_EPS(double, 1) QMC_DECL_EPS(double, 2) QMC_DECL_EPS(double, 3) QMC_DECL_EPS(double, 4)
+QMC_DECL_EPS(double, 5) QMC_DECL_EPS(double, 6) QMC_DECL_EPS(double, 7) QMC_DECL_EPS(double, 8)
+#undef QMC_DECL_EPS
+
 // Contour-deformed complex sector kernel, d = D <= kDFast: fast = Korobov 3
 // and unpivoted LU (host-checked dominance); otherwise runtime transform and
 // pivoted LU.
@@ -50,6 +62,15 @@ template <> const void* general_ptr_t<float>();
 template <> const void* general_ptr_t<double>();
 inline const void* general_ptr(bool fp32) { return fp32 ? general_ptr_t<float>() : general_ptr_t<double>(); }
 
+// General sparse kernel with kEpsMax epsilon orders (kEpsAcc / kEpsMax shifts per launch).
+template <typename R>
+const void* general_eps_ptr_t();
+template <> const void* general_eps_ptr_t<float>();
+template <> const void* general_eps_ptr_t<double>();
+inline const void* general_eps_ptr(bool fp32) {
+  return fp32 ? general_eps_ptr_t<float>() : general_eps_ptr_t<double>();
+}
+
 // Final deterministic pass: per-shift sums -> Q^(k), Qbar, sigma^2; the
 // batched form takes a device array of FinalizeArgs, one CTA per problem.
 const void* finalize_ptr();
@@ -57,17 +78,17 @@ const void* finalize_batch_ptr();
 
 // Arguments of the final pass.
 struct FinalizeArgs {
-  const double* partial;   // [m][nblk][2]
+  const double* partial;   // [groups][m][nblk][2]
   int32_t nblk;
   int32_t m;
   int32_t is_complex;
-  int32_t pad;
+  int32_t groups;          // finalize_kernel: CTA b finalises group b (epsilon order b)
   double dn;      // n as a double
   double value_scale;
   double offset[2];  // added to Q^(k) of each part (control-variate integral)
-  unsigned long long* counters;  // [2], reset to zero after reading
-  qmc_result* result;            // device
-  double* per_shift;             // device [m][2] or null
+  unsigned long long* counters;  // [groups][2], reset to zero after reading
+  qmc_result* result;            // device [groups]
+  double* per_shift;             // device [groups][m][2] or null
 };
 
 }  // namespace qmc

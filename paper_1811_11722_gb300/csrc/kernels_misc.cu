@@ -29,4 +29,9 @@ const void* general_ptr_t<QMC_REAL>() {
   return (const void*)&general_kernel<QMC_REAL, 8>;
 }
 
+template <>
+const void* general_eps_ptr_t<QMC_REAL>() {
+  return (const void*)&general_eps_kernel<QMC_REAL>;
+}
+
 }  // namespace qmc

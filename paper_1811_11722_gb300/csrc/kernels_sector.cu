@@ -1,4 +1,4 @@
-// Instantiations of the specialised sector and deformed kernels for one
+// Instantiations of the specialised sector, epsilon-order and deformed kernels for one
 // (precision, d).
 // Compiled once per pair with -DQMC_REAL=float|double -DQMC_D=1..8 so the
 // build spreads the template work over parallel nvcc processes.
@@ -42,6 +42,20 @@ const void* sector_ptr<QMC_REAL, QMC_D>(int mc, int tr, int alpha, int ku, int k
   }
   if constexpr (kF32) {
     if (ku == 2 && kf == 3 && mc == 16) QMC_SECTOR_TR(QMC_REAL, 16, 2, 3);
+  }
+  return nullptr;
+}
+
+template <>
+const void* eps_ptr<QMC_REAL, QMC_D>(int ne, int tr) {
+  // orders x shifts per launch = kEpsAcc accumulators
+  if (ne == 3) {
+    if (tr == TR_BAKER) return (const void*)&eps_kernel<QMC_REAL, QMC_D, kEpsAcc / 3, 3, TR_BAKER, 0>;
+    if (tr == TR_KOROBOV) return (const void*)&eps_kernel<QMC_REAL, QMC_D, kEpsAcc / 3, 3, TR_KOROBOV, 3>;
+  }
+  if (ne == kEpsMax) {
+    if (tr == TR_BAKER) return (const void*)&eps_kernel<QMC_REAL, QMC_D, kEpsAcc / kEpsMax, kEpsMax, TR_BAKER, 0>;
+    if (tr == TR_KOROBOV) return (const void*)&eps_kernel<QMC_REAL, QMC_D, kEpsAcc / kEpsMax, kEpsMax, TR_KOROBOV, 3>;
   }
   return nullptr;
 }

@@ -43,6 +43,7 @@ struct SavedProblem {
   std::vector<uint8_t> eu, ef;
   std::vector<int32_t> h;
   qmc_integrand f{};
+  qmc_eps eps{};  // orders == 0: no epsilon expansion
   void save(int32_t d_, uint64_t n_, int32_t m_, const uint64_t* g_, const double* shifts_, qmc_transform t_,
             const qmc_integrand* f_);
 };
@@ -52,6 +53,7 @@ struct Plan {
   uint64_t n = 0;
   int m = 0;
   int is_complex = 0;
+  int orders = 1;  // result groups: epsilon orders f_0..f_{orders-1} (1 = the plain rule)
   int nblk = 0;
   int mc = 0;
   const void* func = nullptr;
@@ -88,7 +90,7 @@ void fill_common(RuleParams<R>& P, int32_t d, uint64_t n, const uint64_t* g, con
                  const qmc_integrand* f);
 
 int plan_build(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
-               qmc_transform t, const qmc_integrand* f, const TuneChoice& tune);
+               qmc_transform t, const qmc_integrand* f, const TuneChoice& tune, const qmc_eps* eps = nullptr);
 int build_deformed_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                         const qmc_transform& t, const qmc_integrand* f, const TuneChoice& tune);
 int plan_alloc(Plan* pl, cudaStream_t stream, bool async);

@@ -24,6 +24,8 @@ constexpr int kDFast = 8;       // largest d with a specialised sector kernel
 constexpr int kPolyCoefMax = 168;  // nested-Horner slots: d=8 degree 3 needs 165
 constexpr int kTermsMax = 64;   // sparse monomials per polynomial (general kernel)
 constexpr int kThreads = 256;   // threads per CTA of the rule kernels
+constexpr int kEpsMax = QMC_EPS_MAX;  // epsilon orders of one pass (Eq. 7 expansion)
+constexpr int kEpsAcc = 24;     // shifts x orders accumulated by one epsilon launch
 
 enum TransformCode { TR_NONE = 0, TR_BAKER = 1, TR_KOROBOV = 2 };
 
@@ -73,6 +75,13 @@ struct RuleParams {
   R cF[kPolyCoefMax];      // nested-Horner F
   R sep_c[QMC_DMAX];       // separable: (1 + c z) exp(b z), trig: h as R
   R sep_b[QMC_DMAX];
+  // epsilon expansion of Eq. (7): orders f_0..f_{eps_orders-1} of
+  // U^(aU + bU eps) F^(aF + bF eps); their CTA slots follow one another
+  // ([order][m_total][nblk][2]) and counters[2 o] counts order o's non-finite values
+  int32_t eps_orders;
+  int32_t m_total;
+  R eps_b[2];              // (bU, bF)
+  R eps_inv[kEpsMax];      // 1 / k for k = 1..kEpsMax
 };
 
 // Sparse monomial table for the general kernel (any degree, d <= QMC_DMAX).
@@ -94,10 +103,10 @@ struct GeneralParams {
 // Sampling mode: the rule kernels evaluate listed (j, k) terms instead of the rule.
 struct SampleIO {
   int32_t count;
-  int32_t pad;
+  int32_t stride;      // epsilon kernels: values per sample (one per order)
   const uint64_t* j;
   const int32_t* k;    // chunk-local shift index
-  double* values;      // [count][2]
+  double* values;      // [count][2] ([count][stride] for the epsilon kernels)
   uint64_t* idx;       // [count][d] or null
   double* coord;       // [count][d] or null
 };

@@ -141,6 +141,23 @@ __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename
   return v;
 }
 
+// U^-2 F^-1 times the weight at one (point, shift) of the dense degree-(1, 2)
+// sector path, with U and F handed back (epsilon orders need their logs).
+template <typename R, int D, int TR, int ALPHA>
+__device__ __forceinline__ R eps_point(const RuleParams<R>& P, const typename SecBase<R>::T* base, int k, R& U, R& F) {
+  R z[D];
+  R w = R(1);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], P.shiftf[k][i], P.kor, w);
+    else z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
+  }
+  DensePolys::template eval<D, 1, 2, R>(P, z, U, F);
+  R v = recip(U * U * F);
+  if constexpr (TR == TR_KOROBOV) v *= w;
+  return v;
+}
+
 template <typename R>
 __device__ __forceinline__ typename SecBase<R>::T sec_base(uint32_t idx, const Recip& rc) {
   if constexpr (sizeof(R) == 4) return base2_f32(frac64(idx, rc));
@@ -433,8 +450,8 @@ __device__ __forceinline__ R sparse_eval(const SparsePoly<R>& Q, const R* z, int
 // U^aU F^aF for any degree and d <= QMC_DMAX, everything at run time; the
 // per-thread coordinates and per-shift accumulators live in shared memory.
 template <typename R>
-__device__ __forceinline__ R general_value(const GeneralParams<R>& G, uint64_t j, int k, R* zsh,
-                                           uint64_t* idx_out, double* coord_out) {
+__device__ __forceinline__ R general_eval(const GeneralParams<R>& G, uint64_t j, int k, R* zsh,
+                                          uint64_t* idx_out, double* coord_out, R& U, R& F) {
   const RuleParams<R>& P = G.base;
   R w = R(1);
 #pragma unroll 1
@@ -445,9 +462,16 @@ __device__ __forceinline__ R general_value(const GeneralParams<R>& G, uint64_t j
     if (coord_out) coord_out[i] = coord_used<R>(X);
     zsh[i * kThreads + threadIdx.x] = coord_general<R>(P, X, w);
   }
-  R U = sparse_eval(G.U, zsh, P.d);
-  R F = sparse_eval(G.F, zsh, P.d);
+  U = sparse_eval(G.U, zsh, P.d);
+  F = sparse_eval(G.F, zsh, P.d);
   return ipow(U, P.aU) * ipow(F, P.aF) * w;
+}
+
+template <typename R>
+__device__ __forceinline__ R general_value(const GeneralParams<R>& G, uint64_t j, int k, R* zsh,
+                                           uint64_t* idx_out, double* coord_out) {
+  R U, F;
+  return general_eval<R>(G, j, k, zsh, idx_out, coord_out, U, F);
 }
 
 template <typename R, int MC>
@@ -499,6 +523,197 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   block_epilogue<R, MC>(acc, mk, nbad, P, partial, counters);
+}
+
+
+// ------------------------------------------- epsilon expansion of Eq. (7) --
+//
+// With regulated powers U^(aU + bU eps) F^(aF + bF eps) the integrand is
+// sum_k eps^k f_k, f_k = U^aU F^aF L^k / k!, L = bU log U + bF log F.  One
+// pass computes the point, the transform, U and F once and accumulates the
+// NE coefficient integrands f_0..f_{NE-1} for MC shifts (NE * MC sums);
+// f_k = f_{k-1} L / k.  Orders beyond P.eps_orders are evaluated but never
+// written back.  Every order counts and leaves out its own NaN/Inf values (L
+// is NaN where U or F is negative).
+
+template <typename R>
+__device__ __forceinline__ R log_(R x) {
+  if constexpr (sizeof(R) == 4) return logf(x);
+  else return log(x);
+}
+
+// Per-(order, shift) warp totals -> fixed CTA slots; per-order bad counts.
+template <typename R, int MC, int NE>
+__device__ __forceinline__ void eps_epilogue(Acc<R> (&acc)[NE][MC], const unsigned (&nbad)[NE],
+                                             const RuleParams<R>& P, double* __restrict__ partial,
+                                             unsigned long long* __restrict__ counters) {
+  __shared__ double red[kThreads / 32][NE * MC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 0; o < NE; ++o) {
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) {
+      double t = acc[o][kk].warp_total();
+      if (lane == 0) red[warp][o * MC + kk] = t;
+    }
+    unsigned long long bad = warp_sum_u64((unsigned long long)nbad[o]);
+    if (lane == 0 && bad && o < P.eps_orders) atomicAdd(&counters[2 * o], bad);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NE * MC; t += kThreads) {
+    const int o = t / MC, kk = t % MC;
+    if (o >= P.eps_orders || kk >= P.m_launch) continue;
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][t];
+    size_t slot = (((size_t)o * P.m_total + P.k_base + kk) * P.nblk + blockIdx.x) * 2;
+    partial[slot] = s;
+    partial[slot + 1] = 0.0;
+  }
+}
+
+// Adds order values f_0..f_{NE-1} at one (point, shift) to the sums.
+template <typename R, int MC, int NE>
+__device__ __forceinline__ void eps_add(Acc<R> (&acc)[NE][MC], unsigned (&nbad)[NE], int kk, R v, R L,
+                                        const RuleParams<R>& P, bool counted) {
+#pragma unroll
+  for (int o = 0; o < NE; ++o) {
+    const bool ok = finite_(v);
+    nbad[o] += (ok || !counted) ? 0u : 1u;
+    acc[o][kk].add(ok ? v : R(0));
+    if (o + 1 < NE) v = v * L * P.eps_inv[o];
+  }
+}
+
+template <typename R, int MC, int NE>
+__device__ __forceinline__ void eps_fold(Acc<R> (&acc)[NE][MC]) {
+#pragma unroll
+  for (int o = 0; o < NE; ++o)
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) acc[o][kk].fold();
+}
+
+// Dense U (degree 1), F (degree 2), U^-2 F^-1 at eps = 0, d = D, baker or
+// Korobov-3: the coordinates of the fast sector path.
+template <typename R, int D, int MC, int NE, int TR, int ALPHA>
+__global__ void __launch_bounds__(kThreads)
+    eps_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
+               unsigned long long* __restrict__ counters, const SampleIO sio) {
+  using BT = typename SecBase<R>::T;
+  if (sio.count > 0) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sio.count) return;
+    const uint64_t j = sio.j[s];
+    const int k = sio.k[s];
+    BT base[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      uint32_t idx = lattice_index(j, P.g[i], P.n);
+      base[i] = sec_base<R>(idx, P.rc);
+      if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
+      if (sio.coord) sio.coord[(size_t)s * D + i] = sec_coord_used<R>(P, base[i], k, i);
+    }
+    R U, F;
+    R v = eps_point<R, D, TR, ALPHA>(P, base, k, U, F);
+    const R L = P.eps_b[0] * log_(U) + P.eps_b[1] * log_(F);
+    for (int o = 0; o < P.eps_orders; ++o) {
+      sio.values[(size_t)s * sio.stride + o] = (double)v * P.value_scale;
+      v = v * L * P.eps_inv[o];
+    }
+    return;
+  }
+  const uint32_t n = (uint32_t)P.n;
+  Acc<R> acc[NE][MC];
+#pragma unroll
+  for (int o = 0; o < NE; ++o)
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) acc[o][kk].init();
+  unsigned nbad[NE];
+#pragma unroll
+  for (int o = 0; o < NE; ++o) nbad[o] = 0;
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+    uint32_t idx[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
+    for (int s = 0; s < steps; ++s) {
+      BT base[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) base[i] = sec_base<R>(idx[i], P.rc);
+#pragma unroll
+      for (int kk = 0; kk < MC; ++kk) {
+        R U, F;
+        const R v = eps_point<R, D, TR, ALPHA>(P, base, kk, U, F);
+        const R L = P.eps_b[0] * log_(U) + P.eps_b[1] * log_(F);
+        eps_add<R, MC, NE>(acc, nbad, kk, v, L, P, kk < P.m_launch);
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
+      if constexpr (sizeof(R) == 4) {
+        if ((s & (kFoldG - 1)) == kFoldG - 1) eps_fold<R, MC, NE>(acc);
+      }
+    }
+  }
+  eps_epilogue<R, MC, NE>(acc, nbad, P, partial, counters);
+}
+
+// Any integer powers, sparse U and F, runtime d and transform: the general
+// kernel's evaluation with the orders added (NE = kEpsMax, MC = kEpsAcc / NE).
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    general_eps_kernel(const __grid_constant__ GeneralParams<R> G, double* __restrict__ partial,
+                       unsigned long long* __restrict__ counters, const SampleIO sio) {
+  constexpr int NE = kEpsMax, MC = kEpsAcc / kEpsMax;
+  __shared__ R zsh[QMC_DMAX * kThreads];
+  const RuleParams<R>& P = G.base;
+  if (sio.count > 0) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sio.count) return;
+    R U, F;
+    R v = general_eval<R>(G, sio.j[s], sio.k[s], zsh, sio.idx ? sio.idx + (size_t)s * P.d : nullptr,
+                          sio.coord ? sio.coord + (size_t)s * P.d : nullptr, U, F);
+    const R L = P.eps_b[0] * log_(U) + P.eps_b[1] * log_(F);
+    for (int o = 0; o < P.eps_orders; ++o) {
+      sio.values[(size_t)s * sio.stride + o] = (double)v * P.value_scale;
+      v = v * L * P.eps_inv[o];
+    }
+    return;
+  }
+  Acc<R> acc[NE][MC];
+#pragma unroll
+  for (int o = 0; o < NE; ++o)
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) acc[o][kk].init();
+  unsigned nbad[NE];
+#pragma unroll
+  for (int o = 0; o < NE; ++o) nbad[o] = 0;
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+    for (int s = 0; s < steps; ++s) {
+      const uint64_t j = j0 + (uint64_t)s * kThreads;
+#pragma unroll
+      for (int kk = 0; kk < MC; ++kk) {
+        if (kk < P.m_launch) {
+          R U, F;
+          const R v = general_eval<R>(G, j, kk, zsh, nullptr, nullptr, U, F);
+          const R L = P.eps_b[0] * log_(U) + P.eps_b[1] * log_(F);
+          eps_add<R, MC, NE>(acc, nbad, kk, v, L, P, true);
+        }
+      }
+      if constexpr (sizeof(R) == 4) {
+        if ((s & (kFoldG - 1)) == kFoldG - 1) eps_fold<R, MC, NE>(acc);
+      }
+    }
+  }
+  eps_epilogue<R, MC, NE>(acc, nbad, P, partial, counters);
 }
 
 }  // namespace qmc

@@ -70,6 +70,11 @@ class qmc_problem(ctypes.Structure):
                 ("shifts", ctypes.c_void_p), ("t", qmc_transform), ("f", ctypes.POINTER(qmc_integrand))]
 
 
+class qmc_eps(ctypes.Structure):
+    _fields_ = [("orders", ctypes.c_int32), ("reserved", ctypes.c_int32), ("bU", ctypes.c_double),
+                ("bF", ctypes.c_double)]
+
+
 class qmc_cv_config(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("K", ctypes.c_int32), ("freq_step", ctypes.c_int32), ("steps", ctypes.c_int32),
                 ("lr", ctypes.c_float), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
@@ -117,6 +122,12 @@ def lib():
             L.qmc_integrate_cv.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_cfg, vp, vp, vp, vp]
             L.qmc_cv_loss_grad.argtypes = [i32, P_cfg, i32, vp, vp, vp, vp, vp, vp]
             L.qmc_integrate_noalloc.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, vp, vp, vp]
+            P_eps = ctypes.POINTER(qmc_eps)
+            L.qmc_integrate_eps.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_eps, vp, vp, vp]
+            L.qmc_eps_plan_create.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_eps,
+                                              ctypes.POINTER(vp)]
+            L.qmc_sample_points_eps.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_eps, i32, vp, vp,
+                                                vp, vp]
             L.qmc_last_error.restype = ctypes.c_char_p
             L.qmc_version.restype = i32
             for name in ("qmc_make_lattice", "qmc_integrate", "qmc_plan_create", "qmc_plan_execute",
@@ -124,7 +135,8 @@ def lib():
                          "qmc_batch_plan_execute", "qmc_batch_plan_destroy", "qmc_batch_plan_launches",
                          "qmc_batch_plan_tune", "qmc_sample_points", "qmc_cv_train", "qmc_integrate_cv",
                          "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts", "qmc_measure_peaks",
-                         "qmc_integrate_to_tolerance"):
+                         "qmc_integrate_to_tolerance", "qmc_integrate_eps", "qmc_eps_plan_create",
+                         "qmc_sample_points_eps"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -237,23 +249,30 @@ def qmc_integrate(d, n, m, g, shifts, t: qmc_transform, f: Integrand, out=None, 
 
 
 class Plan:
-    """qmc_plan_create / qmc_plan_execute / qmc_plan_destroy."""
+    """qmc_plan_create / qmc_plan_execute / qmc_plan_destroy.  With `eps`
+    (a qmc_eps) the plan comes from qmc_eps_plan_create and execute() returns
+    one result per epsilon order."""
 
-    def __init__(self, d, n, m, g, shifts, t: qmc_transform, f: Integrand):
+    def __init__(self, d, n, m, g, shifts, t: qmc_transform, f: Integrand, eps: qmc_eps | None = None):
         self.m = m
         self._f = f
+        self.orders = 1 if eps is None else int(eps.orders)
         g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
         shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
         h = ctypes.c_void_p()
-        _check(lib().qmc_plan_create(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(h)))
+        if eps is None:
+            _check(lib().qmc_plan_create(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(h)))
+        else:
+            _check(lib().qmc_eps_plan_create(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(eps),
+                                             ctypes.byref(h)))
         self.h = h
 
     def execute(self, out=None, per_shift=None, stream=0):
         if out is None:
-            res = qmc_result()
-            rc = lib().qmc_plan_execute(self.h, ctypes.byref(res), _addr(per_shift), ctypes.c_void_p(stream))
+            res = (qmc_result * self.orders)()
+            rc = lib().qmc_plan_execute(self.h, res, _addr(per_shift), ctypes.c_void_p(stream))
             _check(rc, allow_warnings=True)
-            return res
+            return res[0] if self.orders == 1 else list(res)
         _check(lib().qmc_plan_execute(self.h, _addr(out), _addr(per_shift), ctypes.c_void_p(stream)),
                allow_warnings=True)
         return None
@@ -386,6 +405,41 @@ def qmc_sample_points(d, n, m, g, shifts, t, f: Integrand, j, k, want_idx=True, 
     _check(lib().qmc_sample_points(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, cnt, _ptr(j), _ptr(k), _ptr(vals),
                                    _ptr(idx), _ptr(crd), ctypes.c_void_p(stream)))
     return vals, idx, crd
+
+
+# ------------------------------------------------------- epsilon expansion --
+
+def eps_spec(orders: int, bU: float = 1.0, bF: float = -1.0) -> qmc_eps:
+    """Orders f_0..f_{orders-1} of U^(aU + bU eps) F^(aF + bF eps) (Eq. 7)."""
+    return qmc_eps(int(orders), 0, float(bU), float(bF))
+
+
+def qmc_integrate_eps(d, n, m, g, shifts, t, f: Integrand, eps: qmc_eps, want_per_shift=False, stream=0):
+    """Returns (list of qmc_result, one per order; per_shift[orders, m, 2] or None)."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    res = (qmc_result * eps.orders)()
+    ps = np.zeros((eps.orders, m, 2)) if want_per_shift else None
+    rc = lib().qmc_integrate_eps(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(eps), res, _ptr(ps),
+                                 ctypes.c_void_p(stream))
+    _check(rc, allow_warnings=True)
+    return list(res), ps
+
+
+def qmc_eps_plan_create(d, n, m, g, shifts, t, f: Integrand, eps: qmc_eps) -> Plan:
+    return Plan(d, n, m, g, shifts, t, f, eps)
+
+
+def qmc_sample_points_eps(d, n, m, g, shifts, t, f: Integrand, eps: qmc_eps, j, k, stream=0):
+    """values[count, orders]: order o of the weighted value at (j[s], k[s])."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    j = np.ascontiguousarray(np.asarray(j, dtype=np.uint64))
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.int32))
+    vals = np.zeros((j.shape[0], eps.orders))
+    _check(lib().qmc_sample_points_eps(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(eps), j.shape[0],
+                                       _ptr(j), _ptr(k), _ptr(vals), ctypes.c_void_p(stream)))
+    return vals
 
 
 # --------------------------------------------------------- control variate --

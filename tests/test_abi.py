@@ -51,7 +51,10 @@ def test_struct_layouts(Q):
     assert ctypes.sizeof(Q.qmc_poly) == 24
     assert ctypes.sizeof(Q.qmc_result) == 72
     assert ctypes.sizeof(Q.qmc_integrand) == 4 * 3 + 4 + 2 * 24 + 8 + 8 + 3 * 8
+    assert ctypes.sizeof(Q.qmc_eps) == 24
     assert Q.qmc_version() >= 100
+    hdr = open(HEADER).read()
+    assert int(re.search(r"#define QMC_EPS_MAX (\d+)", hdr).group(1)) == 6
 
 
 def _sector(Q, d=3, n=101, m=4):
@@ -99,6 +102,33 @@ def test_validation_rejects_bad_arguments(Q, case):
         Q.qmc_integrate(d, n, m, g, shifts, t, f)
     assert ei.value.status == Q.QMC_EINVAL
     assert Q.qmc_last_error() != ""
+
+
+@pytest.mark.parametrize("case", ["orders0", "orders7", "nan_slope", "not_sector"])
+def test_eps_validation_rejects_bad_arguments(Q, case):
+    """The epsilon entry points check their descriptor on the host."""
+    d, n, m = 3, 101, 4
+    g = np.array([1, 5, 7], dtype=np.uint64)
+    shifts = np.full((m, d), 0.25)
+    t = Q.transform("baker")
+    coef = np.array([1.0, 0.5])
+    expo = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.uint8)
+    f = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP64, (coef, expo), (coef, expo))
+    eps = Q.eps_spec(3)
+    if case == "orders0":
+        eps = Q.eps_spec(0)
+    elif case == "orders7":
+        eps = Q.eps_spec(7)
+    elif case == "nan_slope":
+        eps = Q.eps_spec(2, float("nan"), -1.0)
+    elif case == "not_sector":
+        f = Q.Integrand(Q.QMC_F_CONST, d)
+    with pytest.raises(Q.QmcError) as ei:
+        Q.qmc_integrate_eps(d, n, m, g, shifts, t, f, eps)
+    assert ei.value.status == Q.QMC_EINVAL
+    with pytest.raises(Q.QmcError) as ei:
+        Q.qmc_sample_points_eps(d, n, m, g, shifts, t, f, eps, [0], [0])
+    assert ei.value.status == Q.QMC_EINVAL
 
 
 def test_make_lattice_rejects_composite(Q):

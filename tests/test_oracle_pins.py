@@ -462,3 +462,31 @@ def test_cv_estimator_zero_surrogate_is_plain_rule(oracle_lib):
     p.cv = {"R": 2, "K": 4, "F": 1, "a": np.zeros(2 * 3 * 4, np.float32)}
     cv = oracle_lib.integrate(p, g)
     assert np.array_equal(plain["q"], cv["q"])
+
+
+# -------------------------------------------------------- epsilon expansion --
+
+def test_eps_expansion_d1_against_quad(oracle_lib):
+    """Eq. (7) with regulated powers: sum_k eps^k I_k of the coefficient
+    integrands U^-2 F^-1 (bU log U + bF log F)^k / k! reproduces the integral
+    of U^(-2 + bU eps) F^(-1 + bF eps) at small eps (scipy quad), and each I_k
+    matches quad of its own coefficient integrand."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    a, b, c, e = 0.7, 1.3, 0.4, 1.9
+    bU, bF, eps = 1.0, -1.0, 0.05
+    U = I.Poly(np.array([a, b]), np.array([[0], [1]], dtype=np.uint8))
+    F = I.Poly(np.array([c, e]), np.array([[0], [2]], dtype=np.uint8))
+    rng = I.SplitMix64(8)
+    p = I.Problem("eps", 1, 65521, 6, I.make_shifts(rng, 6, 1), "korobov", alpha=3, kind="sector", U=U, F=F)
+    total = 0.0
+    for k in range(5):
+        p.eps = {"order": k, "bU": bU, "bF": bF}
+        r = oracle_lib.integrate(p, [1])
+        ref_k, _ = quad(lambda x: (a + b * x) ** -2 * (c + e * x * x) ** -1
+                        * (bU * math.log(a + b * x) + bF * math.log(c + e * x * x)) ** k / math.factorial(k),
+                        0, 1, epsabs=1e-15, epsrel=1e-13)
+        assert abs(r["mean"][0] - ref_k) < 1e-10 * max(1.0, abs(ref_k))
+        total += eps ** k * r["mean"][0]
+    full, _ = quad(lambda x: (a + b * x) ** (-2 + bU * eps) * (c + e * x * x) ** (-1 + bF * eps), 0, 1,
+                   epsabs=1e-15, epsrel=1e-13)
+    assert abs(total - full) < 2 * eps ** 5 * 10 + 1e-10
