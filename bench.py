@@ -223,6 +223,19 @@ def extras(qmc, I, torch):
         t = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream, reps=3)
         out[f"c4_deformed_d5_{prec}"] = {"evals_per_s": p.n * p.m / t, "ms": 1e3 * t}
         plan.destroy()
+    # epsilon expansion of the configuration-2 integrand, U^(-2+eps) F^(-1-eps):
+    # orders 0..2 and 0..5 from one pass (FP32 eval), against the plain rule
+    p = I.config2()
+    g = I.random_generating_vector(I.SplitMix64(2), p.d, p.n)
+    t_ = qmc.transform(p.transform, p.alpha)
+    f_ = qmc.integrand_from_problem(p, "fp32")
+    for orders in (3, 6):
+        plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, t_, f_, qmc.eps_spec(orders, 1.0, -1.0))
+        t = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream, reps=3)
+        out[f"c2_eps_orders{orders}_fp32"] = {"evals_per_s": p.n * p.m / t, "ms": 1e3 * t,
+                                              "order_evals_per_s": orders * p.n * p.m / t,
+                                              "plan": plan.describe()}
+        plan.destroy()
     # configuration 3: 256 sectors in one graph replay vs the same plans one after another
     sect = I.config3()
     gs = [I.random_generating_vector(I.SplitMix64(900 + i), q.d, q.n) for i, q in enumerate(sect)]
