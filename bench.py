@@ -236,6 +236,28 @@ def extras(qmc, I, torch):
                                               "order_evals_per_s": orders * p.n * p.m / t,
                                               "plan": plan.describe()}
         plan.destroy()
+    # shared-lattice variant of configuration 3: 32 sectors of d = 6 on the
+    # configuration-2 lattice, one fused sweep vs one tuned plan per sector
+    probs = I.config3_shared()
+    g = I.random_generating_vector(I.SplitMix64(2), 6, probs[0].n)
+    fs = [qmc.integrand_from_problem(q) for q in probs]
+    tb = qmc.transform("baker")
+    t0 = time.perf_counter()
+    mp = qmc.MultiPlan(6, probs[0].n, probs[0].m, g, probs[0].shifts, tb, fs)
+    build_s = time.perf_counter() - t0
+    t = device_time(lambda: mp.execute(out=dev_res, stream=sh), stream, reps=3)
+    singles = [qmc.Plan(6, q.n, q.m, g, q.shifts, tb, f) for q, f in zip(probs, fs)]
+    for pl in singles:
+        pl.tune(sh)
+    t1 = device_time(lambda: [pl.execute(out=dev_res, stream=sh) for pl in singles], stream, reps=2)
+    evals = sum(q.n * q.m for q in probs)
+    out["c3_shared_lattice_32_sectors_d6"] = {
+        "evals": evals, "evals_per_s_fused": evals / t, "ms_fused": 1e3 * t, "ms_one_plan_per_sector": 1e3 * t1,
+        "speedup_vs_one_plan_per_sector": t1 / t, "plan_build_s": build_s, "launches": mp.launches(),
+        "workload": "32 sectors, d=6, T_U~U{4..10}, T_F~U{6..20}, baker, n=16777213, m=16, FP32 eval"}
+    mp.destroy()
+    for pl in singles:
+        pl.destroy()
     # configuration 3: 256 sectors in one graph replay vs the same plans one after another
     sect = I.config3()
     gs = [I.random_generating_vector(I.SplitMix64(900 + i), q.d, q.n) for i, q in enumerate(sect)]

@@ -403,6 +403,33 @@ int qmc_sample_points_eps(int32_t d, uint64_t n, int32_t m, const uint64_t* g, c
                           const uint64_t* j, const int32_t* k, double* values, void* stream);
 #endif
 
+/* Several integrands on one lattice.  The sectors of one dimension that share
+ * (n, g, shifts, transform) are evaluated in one sweep (Eq. 2 for each): the
+ * lattice index, fixed-point base and transformed coordinates of every
+ * (point, shift) are computed once and shared by all of them.  The sum of
+ * the integrands is reported too: its per-shift values are the sums of the
+ * integrands' per-shift values, and Eq. (3) is applied to those.
+ *   count      1..QMC_MULTI_MAX integrands fs[0..count-1], each QMC_F_SECTOR
+ *              of dimension d (<= 8), precision QMC_FP32EVAL, U of degree <= 1,
+ *              F of degree <= 2, powers aU = -2, aF = -1
+ *   transform  baker, Korobov 3 or none
+ *   out        [count + 1] results: out[s] for fs[s], out[count] for the sum
+ *              (host or device)
+ *   per_shift  optional [(count + 1)][m][2]
+ * The fused kernel is specialised at run time for the integrands' monomials
+ * (NVRTC); without run-time compilation the call returns QMC_EUNSUPPORTED.
+ * Other requests return QMC_EINVAL (bad arguments) or QMC_EUNSUPPORTED. */
+#define QMC_MULTI_MAX 256
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+int qmc_integrate_multi(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                        qmc_transform t, int32_t count, const qmc_integrand* fs, qmc_result* out,
+                        double* per_shift, void* stream);
+/* A plan of the same; qmc_plan_execute on it writes out[count + 1] and
+ * per_shift [(count + 1)][m][2]. */
+int qmc_multi_plan_create(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
+                          qmc_transform t, int32_t count, const qmc_integrand* fs, qmc_plan* plan_out);
+#endif
+
 /* Text of the last error raised on the calling thread ("" if none). */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 const char* qmc_last_error(void);

@@ -14,7 +14,9 @@
  *   Eq. (5)  Korobov transform of weight alpha: z = int_0^x w, w(u) =
  *            u^a (1-u)^a / B(a+1, a+1); the rule integrates f(z(x)) prod_i w(x_i)
  *   Eq. (6)  baker's transform z = 1 - |2x - 1| (weight 1)
- *   Eq. (7)  integrand class prod_j P_j^{a_j}: here U^{aU} F^{aF} at eps = 0
+ *   Eq. (7)  integrand class prod_j P_j^{a_j + b_j eps}: here U^{aU} F^{aF} at
+ *            eps = 0, and the coefficient integrands of its eps expansion,
+ *            U^{aU} F^{aF} (bU log U + bF log F)^k / k!
  *   Sec. 3   contour deformation z_k = y_k - i lambda y_k (1 - y_k) dF/dy_k,
  *            which vanishes at the endpoints y_k in {0, 1}
  * Per-shift sums use Neumaier's compensated summation.  Threads, when asked

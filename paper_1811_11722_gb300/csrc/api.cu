@@ -305,6 +305,8 @@ static int device_sm_count() {
   return sms;
 }
 
+int device_sms() { return device_sm_count(); }
+
 // Grid: one resident wave (SMs x CTAs per SM), each CTA one tile of
 // kThreads * L points, L from the point count.
 int choose_grid(const void* func, size_t smem, uint64_t n, int& nblk, int& L, uint64_t& tiles,
@@ -409,6 +411,7 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
       auto cf = pack_dense(f->F, d, KF);
       for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
       for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
+      if (fp32 && KU == 1 && KF == 2) fill_pairs(base, d);
       if (base.tr == TR_KOROBOV) base.value_scale = std::pow((double)base.kor[7], (double)d);
       if (fp32 && KU == 1 && KF == 2 && !tune.no_jit && jit_enabled()) {
         void* fn = nullptr;
@@ -487,7 +490,7 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
         uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
         P.shift64[kk][i] = s64;
         P.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
-        P.shiftf[kk][i] = (float)(2.0 * shifts[(size_t)src * d + i] - 2.0);
+        set_shift_tri(P, kk, i, (float)(2.0 * shifts[(size_t)src * d + i] - 2.0));
       }
     Launch ln;
     ln.func = func;
@@ -622,6 +625,8 @@ int launch_finalize(const Plan* pl, const Workspace& ws, qmc_result* res_dev, do
   A.m = pl->m;
   A.is_complex = pl->is_complex;
   A.groups = pl->orders;
+  A.sum_last = pl->sum_last ? 1 : 0;
+  A.pad = 0;
   A.dn = (double)pl->n;
   A.value_scale = pl->final_scale;
   A.offset[0] = pl->offset[0];

@@ -400,7 +400,7 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
         uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
         C->base.shift64[kk][i] = s64;
         C->base.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
-        C->base.shiftf[kk][i] = (float)(2.0 * shifts[(size_t)src * d + i] - 2.0);
+        set_shift_tri(C->base, kk, i, (float)(2.0 * shifts[(size_t)src * d + i] - 2.0));
       }
     Launch ln;
     ln.func = func;

@@ -65,6 +65,27 @@ __device__ __forceinline__ double recip(double x) {
   return __fma_rn(r, e, r);
 }
 
+// ------------------------------------------------ packed FP32 (f32x2) --
+//
+// sm_100-class SMs execute the same FP32 operation on both halves of a
+// register pair in one instruction; each half rounds exactly as the scalar
+// operation would.  The packed sector path evaluates two shifts per
+// instruction where the work is a plain add, multiply or FMA.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// 1 / x for both halves, given y = -x: q = rcp.approx(y) ~ -1/x, one Newton
+// step in the form q (y q - 2) = (1/x)(1 - e^2) for q = (1 + e)/y.  Taking
+// -x as input (the host negates F's coefficients) leaves no negation on the
+// packed path.
+__device__ __forceinline__ float2 recip_neg2(float2 y) {
+  float2 q;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q.x) : "f"(y.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q.y) : "f"(y.y));
+  return mul2(q, fma2(y, q, make_float2(-2.0f, -2.0f)));
+}
+
 template <typename R>
 __device__ __forceinline__ R ipow(R x, int a) {
   R p = R(1);
@@ -197,9 +218,9 @@ __device__ __forceinline__ float base2_f32(uint64_t p64) {
   return __fmaf_rn(2.0f, unit_f32(X), -2.0f);      // 2 (x + 1) - 2 = 2x, exact
 }
 
+// The triangle coordinate from t = b2 + c.
 template <int TR, int ALPHA>
-__device__ __forceinline__ float coord_tri(float b2, float c, const float* kor, float& w) {
-  const float t = b2 + c;
+__device__ __forceinline__ float coord_tri_t(float t, const float* kor, float& w) {
   if constexpr (TR == TR_NONE) {
     return __fmaf_rn(0.5f, t, t < 0.0f ? 1.0f : 0.0f);
   } else {
@@ -212,6 +233,11 @@ __device__ __forceinline__ float coord_tri(float b2, float c, const float* kor, 
       return korobov_apply<ALPHA>(s, upper, kor, 0, w);
     }
   }
+}
+
+template <int TR, int ALPHA>
+__device__ __forceinline__ float coord_tri(float b2, float c, const float* kor, float& w) {
+  return coord_tri_t<TR, ALPHA>(b2 + c, kor, w);
 }
 
 // The coordinate {y} the triangle form stands for, as a double (sampling output).
@@ -260,6 +286,29 @@ __device__ __forceinline__ R poly_dense(const R* c, const R* z) {
         r = fma_(z[j], r2, r);
       }
       acc = fma_(z[i], r, acc);
+    }
+  }
+  return acc;
+}
+
+// poly_dense of degree 1 or 2 on coordinate pairs, with (c, c) coefficient
+// pairs: the same operations in the same order, two shifts per instruction.
+template <int D, int K>
+__device__ __forceinline__ float2 poly_dense2(const float2* c, const float2* z) {
+  static_assert(K == 1 || K == 2, "packed polynomials: degree 1 or 2");
+  float2 acc = c[0];
+  if constexpr (K == 1) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) acc = fma2(c[1 + i], z[i], acc);
+  } else {
+    int off = 1;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float2 r = c[off];
+#pragma unroll
+      for (int j = i; j < D; ++j) r = fma2(c[off + 1 + (j - i)], z[j], r);
+      acc = fma2(z[i], r, acc);
+      off += 1 + (D - i);
     }
   }
   return acc;

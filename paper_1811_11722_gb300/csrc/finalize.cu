@@ -12,6 +12,8 @@ constexpr int kFinThreads = 256;
 // adds the CTA slots of (shift, part) tasks w, w+8, ... in a fixed order;
 // warp 0 then forms Qbar and the two-pass sigma^2 per part.
 __device__ void finalize_one(FinalizeArgs A, int grp, double* q /* shared [m][2] */) {
+  const double* all = A.partial;
+  const bool sum_group = A.sum_last && grp == A.groups - 1;
   A.partial += (size_t)grp * A.m * A.nblk * 2;
   A.counters += 2 * grp;
   A.result += grp;
@@ -23,7 +25,13 @@ __device__ void finalize_one(FinalizeArgs A, int grp, double* q /* shared [m][2]
   for (int t = warp; t < tasks; t += kFinThreads / 32) {
     const int k = t / parts, part = t % parts;
     double s = 0.0;
-    for (int b = lane; b < A.nblk; b += 32) s += A.partial[((size_t)k * A.nblk + b) * 2 + part];
+    if (sum_group) {
+      // the sum of the integrands: their slots, group by group in a fixed order
+      for (int gg = 0; gg < A.groups - 1; ++gg)
+        for (int b = lane; b < A.nblk; b += 32) s += all[(((size_t)gg * A.m + k) * A.nblk + b) * 2 + part];
+    } else {
+      for (int b = lane; b < A.nblk; b += 32) s += A.partial[((size_t)k * A.nblk + b) * 2 + part];
+    }
     s = warp_sum_d(s);
     if (lane == 0) q[2 * k + part] = (s * A.value_scale) / dn + A.offset[part];
   }

@@ -9,7 +9,8 @@
 // coefficient an exact hexadecimal float literal, and compiles the kernel
 // template around it with NVRTC for sm_103a.  Dropped terms are exact zeros
 // (fma(0, z, r) == r), so the specialised kernel returns bit-identical
-// results; it only executes fewer instructions.  Any failure (no NVRTC, an
+// results; it only executes fewer instructions.  Both the scalar form (point
+// sampling) and the packed two-shift form (the rule) are generated.  Any failure (no NVRTC, an
 // architecture it does not know, a compile error) leaves the plan on the
 // template kernel.  Compiled modules are cached per process by source text
 // and device.
@@ -126,6 +127,37 @@ std::string poly_code(int D, const std::vector<double>& cu, const std::vector<do
   return s;
 }
 
+// The packed counterpart (U and -F on coordinate pairs, DensePolys::eval2):
+// the same chains over the (c, c) pairs of the kernel parameters, skipping the
+// slots whose coefficient is zero.
+std::string poly_code2(int D, const std::vector<double>& cu, const std::vector<double>& cf,
+                       const std::string& arr = "P.cp") {
+  auto pc = [&arr](int slot) { return arr + "[" + std::to_string(slot) + "]"; };
+  const int nu = 1 + D;
+  std::string s;
+  s += "    float2 u = " + pc(0) + ";\n";
+  for (int i = 0; i < D; ++i)
+    if ((float)cu[1 + i] != 0.0f) s += "    u = fma2(" + pc(1 + i) + ", z[" + std::to_string(i) + "], u);\n";
+  s += "    float2 f = " + pc(nu) + ";\n";
+  int off = 1;
+  for (int i = 0; i < D; ++i) {
+    std::string r;
+    bool any = (float)cf[off] != 0.0f;
+    if (any) r = pc(nu + off);
+    for (int j = i; j < D; ++j) {
+      const int slot = off + 1 + (j - i);
+      if ((float)cf[slot] == 0.0f) continue;
+      const std::string zj = "z[" + std::to_string(j) + "]";
+      r = any ? "fma2(" + pc(nu + slot) + ", " + zj + ", " + r + ")" : "mul2(" + pc(nu + slot) + ", " + zj + ")";
+      any = true;
+    }
+    if (any) s += "    f = fma2(z[" + std::to_string(i) + "], " + r + ", f);\n";
+    off += 1 + (D - i);
+  }
+  s += "    U = u;\n    Fn = f;\n";
+  return s;
+}
+
 }  // namespace
 
 bool jit_enabled() {
@@ -139,26 +171,11 @@ bool jit_smacc() {
   return e && e[0] == '1';
 }
 
-// Compile (or fetch) the specialised FP32 sector kernel.  Returns QMC_OK and
-// the CUfunction / occupancy, or an error code (the caller falls back).
-int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
-                   const std::vector<double>& cf, void** fn_out, int* occ_out, size_t* smem_out) {
-  const bool smacc = jit_smacc();
-  const size_t smem = smacc ? (size_t)MC * kThreads * 8 : 0;
-  *smem_out = smem;
-  std::string src;
-  src += "#include \"rule_kernels.cuh\"\n";
-  src += "namespace qmc {\nstruct GenPolys {\n";
-  src += "  template <int D_, int KU, int KF, typename R>\n";
-  src += "  __device__ static __forceinline__ void eval(const RuleParams<R>&, const R* z, R& U, R& F) {\n";
-  src += poly_code(D, cu, cf);
-  src += "  }\n};\n}  // namespace qmc\n";
-  src += "extern \"C\" __global__ void __launch_bounds__(256) qmc_jit_sector(\n";
-  src += "    const __grid_constant__ qmc::RuleParams<float> P, double* __restrict__ partial,\n";
-  src += "    unsigned long long* __restrict__ counters, const qmc::SampleIO sio) {\n";
-  src += "  qmc::sector_body<float, " + std::to_string(D) + ", " + std::to_string(MC) + ", " + std::to_string(TR) +
-         ", " + std::to_string(ALPHA) + ", 1, 2, " + (check ? "true" : "false") +
-         ", qmc::GenPolys, " + (smacc ? "true" : "false") + ">(P, partial, counters, sio);\n}\n";
+// NVRTC-compile `src` for this device (or fetch it from the cache) and
+// return kernel `name` with its occupancy at kThreads threads and `smem`
+// bytes of dynamic shared memory.  QMC_OK, or an error code (callers fall
+// back or report it).
+static int jit_compile(const std::string& src, const char* name, size_t smem, void** fn_out, int* occ_out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -181,7 +198,7 @@ int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vect
   // compile outside the lock (NVRTC programs are independent, so plans can be
   // built on several host threads at once)
   nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "qmc_jit_sector.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+  if (nvrtcCreateProgram(&prog, src.c_str(), "qmc_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
     return QMC_EUNSUPPORTED;
   const std::string inc = "-I" + csrc_dir();
   const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", inc.c_str(), "-lineinfo"};
@@ -212,7 +229,7 @@ int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vect
   }
   JitEntry e;
   if (drv.moduleLoadData(&e.mod, cubin.data()) != CUDA_SUCCESS) return QMC_EUNSUPPORTED;
-  if (drv.moduleGetFunction(&e.fn, e.mod, "qmc_jit_sector") != CUDA_SUCCESS) {
+  if (drv.moduleGetFunction(&e.fn, e.mod, name) != CUDA_SUCCESS) {
     drv.moduleUnload(e.mod);
     return QMC_EUNSUPPORTED;
   }
@@ -226,6 +243,62 @@ int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vect
   *fn_out = (void*)e.fn;
   *occ_out = e.occupancy;
   return QMC_OK;
+}
+
+// Compile (or fetch) the specialised FP32 sector kernel.  Returns QMC_OK and
+// the CUfunction / occupancy, or an error code (the caller falls back).
+int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
+                   const std::vector<double>& cf, void** fn_out, int* occ_out, size_t* smem_out) {
+  const bool smacc = jit_smacc();
+  const size_t smem = smacc ? (size_t)MC * kThreads * 8 : 0;
+  *smem_out = smem;
+  std::string src;
+  src += "#include \"rule_kernels.cuh\"\n";
+  src += "namespace qmc {\nstruct GenPolys {\n";
+  src += "  template <int D_, int KU, int KF, typename R>\n";
+  src += "  __device__ static __forceinline__ void eval(const RuleParams<R>&, const R* z, R& U, R& F) {\n";
+  src += poly_code(D, cu, cf);
+  src += "  }\n";
+  src += "  template <int D_, int KU, int KF>\n";
+  src += "  __device__ static __forceinline__ void eval2(const RuleParams<float>& P, const float2* z, float2& U,\n";
+  src += "                                               float2& Fn) {\n";
+  src += poly_code2(D, cu, cf);
+  src += "  }\n};\n}  // namespace qmc\n";
+  src += "extern \"C\" __global__ void __launch_bounds__(256) qmc_jit_sector(\n";
+  src += "    const __grid_constant__ qmc::RuleParams<float> P, double* __restrict__ partial,\n";
+  src += "    unsigned long long* __restrict__ counters, const qmc::SampleIO sio) {\n";
+  src += "  qmc::sector_body<float, " + std::to_string(D) + ", " + std::to_string(MC) + ", " + std::to_string(TR) +
+         ", " + std::to_string(ALPHA) + ", 1, 2, " + (check ? "true" : "false") +
+         ", qmc::GenPolys, " + (smacc ? "true" : "false") + ">(P, partial, counters, sio);\n}\n";
+  return jit_compile(src, "qmc_jit_sector", smem, fn_out, occ_out);
+}
+
+// Compile (or fetch) the shared-lattice kernel for one chunk of integrands:
+// polys[s] = (U slots, F slots) of integrand s of the chunk.  Their
+// coefficients are read from MultiParams::cps, so chunks whose integrands
+// have the same monomials share one compiled kernel.
+int jit_multi_f32(int D, int MC, int TR, int ALPHA, bool check,
+                  const std::vector<std::pair<std::vector<double>, std::vector<double>>>& polys, void** fn_out,
+                  int* occ_out) {
+  const int SC = (int)polys.size();
+  if (SC < 1 || SC > kMultiChunk) return QMC_EINVAL;
+  std::string src;
+  src += "#include \"rule_kernels.cuh\"\n";
+  src += "namespace qmc {\nstruct GenMulti {\n";
+  src += "  __device__ static __forceinline__ void eval2(const MultiParams& M, int s, const float2* z, float2& U,\n";
+  src += "                                               float2& Fn) {\n";
+  for (int s = 0; s < SC; ++s) {
+    src += std::string(s ? "    } else if" : "    if") + " (s == " + std::to_string(s) + ") {\n";
+    src += poly_code2(D, polys[s].first, polys[s].second, "M.cps[" + std::to_string(s) + "]");
+  }
+  src += "    }\n  }\n};\n}  // namespace qmc\n";
+  src += "extern \"C\" __global__ void __launch_bounds__(256) qmc_jit_multi(\n";
+  src += "    const __grid_constant__ qmc::MultiParams M, double* __restrict__ partial,\n";
+  src += "    unsigned long long* __restrict__ counters, const qmc::SampleIO sio) {\n";
+  src += "  qmc::multi_body<" + std::to_string(D) + ", " + std::to_string(MC) + ", " + std::to_string(SC) + ", " +
+         std::to_string(TR) + ", " + std::to_string(ALPHA) + ", " + (check ? "true" : "false") +
+         ", qmc::GenMulti>(M, partial, counters);\n}\n";
+  return jit_compile(src, "qmc_jit_multi", 0, fn_out, occ_out);
 }
 
 // Launch either a runtime kernel (ln.func) or a specialised one (ln.cufunc).

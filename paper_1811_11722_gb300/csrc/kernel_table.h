@@ -82,7 +82,9 @@ struct FinalizeArgs {
   int32_t nblk;
   int32_t m;
   int32_t is_complex;
-  int32_t groups;          // finalize_kernel: CTA b finalises group b (epsilon order b)
+  int32_t groups;          // finalize_kernel: CTA b finalises group b (epsilon order b, integrand b)
+  int32_t sum_last;        // 1: the last group is the sum of the others (shared-lattice plans)
+  int32_t pad;
   double dn;      // n as a double
   double value_scale;
   double offset[2];  // added to Q^(k) of each part (control-variate integral)

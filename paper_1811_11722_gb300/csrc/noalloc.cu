@@ -117,6 +117,7 @@ static int noalloc_run(int32_t d, uint64_t n, int32_t m, const uint64_t* g, cons
   if (rc) return rc;
   rc = pack_dense_into<R>(f->F, d, 2, P.cF);
   if (rc) return rc;
+  if (fp32) fill_pairs(P, d);
   if (P.tr == TR_KOROBOV) {
     double s = 1.0;
     for (int i = 0; i < d; ++i) s *= (double)P.kor[7];
@@ -161,7 +162,7 @@ static int noalloc_run(int32_t d, uint64_t n, int32_t m, const uint64_t* g, cons
         const uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
         P.shift64[kk][i] = s64;
         P.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
-        P.shiftf[kk][i] = (float)(2.0 * shifts[(size_t)src * d + i] - 2.0);
+        set_shift_tri(P, kk, i, (float)(2.0 * shifts[(size_t)src * d + i] - 2.0));
       }
     void* args[4] = {&P, &partial, &counters, &none};
     e = cudaLaunchKernel(func, dim3(nblk), dim3(kThreads), args, 0, st);

@@ -53,7 +53,8 @@ struct Plan {
   uint64_t n = 0;
   int m = 0;
   int is_complex = 0;
-  int orders = 1;  // result groups: epsilon orders f_0..f_{orders-1} (1 = the plain rule)
+  int orders = 1;  // result groups: epsilon orders f_0..f_{orders-1}, or integrands + their sum
+  bool sum_last = false;  // the last group is the sum of the others (shared-lattice plans)
   int nblk = 0;
   int mc = 0;
   const void* func = nullptr;
@@ -104,6 +105,10 @@ bool jit_enabled();
 bool jit_smacc();
 int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
                    const std::vector<double>& cf, void** fn_out, int* occ_out, size_t* smem_out);
+int jit_multi_f32(int D, int MC, int TR, int ALPHA, bool check,
+                  const std::vector<std::pair<std::vector<double>, std::vector<double>>>& polys, void** fn_out,
+                  int* occ_out);
+int device_sms();
 int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream);
 int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraphNode_t* node);
 

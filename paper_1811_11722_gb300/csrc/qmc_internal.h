@@ -24,6 +24,7 @@ constexpr int kDFast = 8;       // largest d with a specialised sector kernel
 constexpr int kPolyCoefMax = 168;  // nested-Horner slots: d=8 degree 3 needs 165
 constexpr int kTermsMax = 64;   // sparse monomials per polynomial (general kernel)
 constexpr int kThreads = 256;   // threads per CTA of the rule kernels
+constexpr int kPairCoefMax = 56;  // packed FP32 path: U (deg 1) + F (deg 2) slots at d = 8 is 54
 constexpr int kEpsMax = QMC_EPS_MAX;  // epsilon orders of one pass (Eq. 7 expansion)
 constexpr int kEpsAcc = 24;     // shifts x orders accumulated by one epsilon launch
 
@@ -68,11 +69,13 @@ struct RuleParams {
   uint32_t gstep[QMC_DMAX];     // (kThreads * g_i) mod n
   uint64_t shift64[kMcMax][QMC_DMAX];
   uint32_t shift32[kMcMax][QMC_DMAX];
-  float shiftf[kMcMax][QMC_DMAX];   // 2 Delta - 2 (fast FP32 sector path)
+  float2 shiftp[kMcMax / 2][QMC_DMAX];  // fast FP32 sector path: 2 Delta - 2 of shifts
+                                        // (2p, 2p + 1) side by side for packed adds
   R kor[8];                // Korobov z(s) = s^(a+1) sum_k kor[k] s^k on s <= 1/2;
                            // kor[7] = (2a+1)!/(a!)^2 (general kernel weight)
   R cU[kPolyCoefMax];      // nested-Horner U (dense kernels)
   R cF[kPolyCoefMax];      // nested-Horner F
+  float2 cp[kPairCoefMax];  // packed FP32 path: (c, c) pairs of U's slots, then of -F's
   R sep_c[QMC_DMAX];       // separable: (1 + c z) exp(b z), trig: h as R
   R sep_b[QMC_DMAX];
   // epsilon expansion of Eq. (7): orders f_0..f_{eps_orders-1} of
@@ -82,6 +85,37 @@ struct RuleParams {
   int32_t m_total;
   R eps_b[2];              // (bU, bF)
   R eps_inv[kEpsMax];      // 1 / k for k = 1..kEpsMax
+};
+
+// Shift constant 2 Delta_k - 2 of dimension i in the paired layout.
+template <typename R>
+__host__ __device__ inline float shift_tri(const RuleParams<R>& P, int k, int i) {
+  return (k & 1) ? P.shiftp[k >> 1][i].y : P.shiftp[k >> 1][i].x;
+}
+template <typename R>
+__host__ __device__ inline void set_shift_tri(RuleParams<R>& P, int k, int i, float v) {
+  if (k & 1) P.shiftp[k >> 1][i].y = v;
+  else P.shiftp[k >> 1][i].x = v;
+}
+
+// Packed FP32 path: (c, c) pairs of U's degree-1 nested-Horner slots, then of
+// -F's degree-2 slots (from cU, cF; negation is exact).
+template <typename R>
+__host__ __device__ inline void fill_pairs(RuleParams<R>& P, int d) {
+  const int nu = poly_slots(d, 1), nf = poly_slots(d, 2);
+  for (int s = 0; s < nu && s < kPairCoefMax; ++s) P.cp[s] = make_float2((float)P.cU[s], (float)P.cU[s]);
+  for (int s = 0; s < nf && nu + s < kPairCoefMax; ++s)
+    P.cp[nu + s] = make_float2(-(float)P.cF[s], -(float)P.cF[s]);
+}
+
+// Several integrands on one lattice (shared-lattice sweep): the rule's
+// parameters plus the (c, c) pairs of each integrand of this launch's chunk.
+constexpr int kMultiChunk = 8;  // integrands fused into one launch
+struct MultiParams {
+  RuleParams<float> base;
+  int32_t s_base;   // first integrand of this launch
+  int32_t count;    // integrands of the plan (their sum is group `count`)
+  float2 cps[kMultiChunk][kPairCoefMax];  // U's then -F's slots, per integrand
 };
 
 // Sparse monomial table for the general kernel (any degree, d <= QMC_DMAX).

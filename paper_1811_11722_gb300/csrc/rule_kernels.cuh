@@ -123,7 +123,37 @@ struct DensePolys {
     U = poly_dense<D, KU>(P.cU, z);
     F = poly_dense<D, KF>(P.cF, z);
   }
+  // packed: U and -F on coordinate pairs from the (c, c) pairs
+  template <int D, int KU, int KF>
+  __device__ static __forceinline__ void eval2(const RuleParams<float>& P, const float2* z, float2& U, float2& Fn) {
+    U = poly_dense2<D, KU>(P.cp, z);
+    Fn = poly_dense2<D, KF>(P.cp + poly_slots(D, KU), z);
+  }
 };
+
+// Packed FP32 sector path applies to U of degree <= 1 and F of degree <= 2.
+template <typename R, int KU, int KF>
+constexpr bool kPacked = sizeof(R) == 4 && KU == 1 && KF == 2;
+
+// Shifts 2p and 2p + 1 at one point: the triangle coordinates start with one
+// packed add, the abs steps are scalar (abs is a free operand modifier of a
+// scalar add), U and -F are packed Horner chains, then -U^2 F and the
+// reciprocal (recip_neg2) are packed.
+template <int D, int TR, int ALPHA, int KU, int KF, class POLY>
+__device__ __forceinline__ float2 sector_value2(const RuleParams<float>& P, const float* base, int p) {
+  float2 z[D];
+  float wa = 1.0f, wb = 1.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const float2 t = add2(make_float2(base[i], base[i]), P.shiftp[p][i]);
+    z[i] = make_float2(coord_tri_t<TR, ALPHA>(t.x, P.kor, wa), coord_tri_t<TR, ALPHA>(t.y, P.kor, wb));
+  }
+  float2 U, Fn;
+  POLY::template eval2<D, KU, KF>(P, z, U, Fn);
+  float2 v = recip_neg2(mul2(mul2(U, U), Fn));
+  if constexpr (TR == TR_KOROBOV) v = mul2(v, make_float2(wa, wb));
+  return v;
+}
 
 template <typename R, int D, int TR, int ALPHA, int KU, int KF, class POLY = DensePolys>
 __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename SecBase<R>::T* base, int k) {
@@ -131,7 +161,7 @@ __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename
   R w = R(1);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], P.shiftf[k][i], P.kor, w);
+    if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], shift_tri(P, k, i), P.kor, w);
     else z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
   }
   R U, F;
@@ -149,7 +179,7 @@ __device__ __forceinline__ R eps_point(const RuleParams<R>& P, const typename Se
   R w = R(1);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], P.shiftf[k][i], P.kor, w);
+    if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], shift_tri(P, k, i), P.kor, w);
     else z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
   }
   DensePolys::template eval<D, 1, 2, R>(P, z, U, F);
@@ -166,7 +196,7 @@ __device__ __forceinline__ typename SecBase<R>::T sec_base(uint32_t idx, const R
 
 template <typename R>
 __device__ __forceinline__ double sec_coord_used(const RuleParams<R>& P, typename SecBase<R>::T b, int k, int i) {
-  if constexpr (sizeof(R) == 4) return coord_tri_used(b, P.shiftf[k][i]);
+  if constexpr (sizeof(R) == 4) return coord_tri_used(b, shift_tri(P, k, i));
   else return coord_used<R>(b + shift_of(P, k, i));
 }
 
@@ -223,6 +253,19 @@ __device__ __forceinline__ void block_epilogue(Acc<R>* acc, int mk, unsigned nba
 // shared memory (MC * kThreads float2) and only the short float runs stay in
 // registers, which frees two thirds of the accumulator registers for higher
 // occupancy.
+// Packed runs -> the per-shift accumulators' runs (which then fold as usual).
+template <int MC, typename R>
+__device__ __forceinline__ void unpack_runs(float2* run2, Acc<R>* acc) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int p = 0; p < MC / 2; ++p) {
+      acc[2 * p].run += run2[p].x;
+      acc[2 * p + 1].run += run2[p].y;
+      run2[p] = make_float2(0.0f, 0.0f);
+    }
+  }
+}
+
 template <typename R, int D, int MC, int TR, int ALPHA, int KU, int KF, bool CHECK, class POLY, bool SMACC = false>
 __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __restrict__ partial,
                                             unsigned long long* __restrict__ counters, const SampleIO& sio) {
@@ -236,6 +279,11 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
 #pragma unroll
   for (int kk = 0; kk < MC; ++kk) acc[kk].init();
   constexpr bool kSm = SMACC && sizeof(R) == 4;
+  // packed path: the float runs of shifts (2p, 2p + 1) in one register pair
+  constexpr bool kPack = kPacked<R, KU, KF> && MC % 2 == 0;
+  float2 run2[kPack ? MC / 2 : 1];
+#pragma unroll
+  for (int p = 0; p < (kPack ? MC / 2 : 1); ++p) run2[p] = make_float2(0.0f, 0.0f);
   extern __shared__ float2 accsm[];  // [MC][kThreads] (hi, lo), used when kSm
   if constexpr (kSm) {
 #pragma unroll
@@ -255,20 +303,35 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
       typename SecBase<R>::T base[D];
 #pragma unroll
       for (int i = 0; i < D; ++i) base[i] = sec_base<R>(idx[i], P.rc);
+      if constexpr (kPack) {
 #pragma unroll
-      for (int kk = 0; kk < MC; ++kk) {
-        R v = sector_value<R, D, TR, ALPHA, KU, KF, POLY>(P, base, kk);
-        if constexpr (CHECK) {
-          const bool ok = finite_(v);
-          nbad += (ok || kk >= P.m_launch) ? 0u : 1u;  // padded rows are not counted
-          v = ok ? v : R(0);
+        for (int p = 0; p < MC / 2; ++p) {
+          float2 v = sector_value2<D, TR, ALPHA, KU, KF, POLY>(P, base, p);
+          if constexpr (CHECK) {
+            const bool oka = finite_(v.x), okb = finite_(v.y);
+            nbad += (oka || 2 * p >= P.m_launch) ? 0u : 1u;  // padded rows are not counted
+            nbad += (okb || 2 * p + 1 >= P.m_launch) ? 0u : 1u;
+            v = make_float2(oka ? v.x : 0.0f, okb ? v.y : 0.0f);
+          }
+          run2[p] = add2(run2[p], v);
         }
-        acc[kk].add(v);
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < MC; ++kk) {
+          R v = sector_value<R, D, TR, ALPHA, KU, KF, POLY>(P, base, kk);
+          if constexpr (CHECK) {
+            const bool ok = finite_(v);
+            nbad += (ok || kk >= P.m_launch) ? 0u : 1u;  // padded rows are not counted
+            v = ok ? v : R(0);
+          }
+          acc[kk].add(v);
+        }
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
       if constexpr (sizeof(R) == 4) {
         if ((s & (kFoldG - 1)) == kFoldG - 1) {
+          if constexpr (kPack) unpack_runs<MC>(run2, acc);
 #pragma unroll
           for (int kk = 0; kk < MC; ++kk) {
             if constexpr (kSm) {
@@ -284,6 +347,7 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
       }
     }
   }
+  if constexpr (kPack) unpack_runs<MC>(run2, acc);  // the last partial run
   if constexpr (kSm) {
 #pragma unroll
     for (int kk = 0; kk < MC; ++kk) {
@@ -714,6 +778,116 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   eps_epilogue<R, MC, NE>(acc, nbad, P, partial, counters);
+}
+
+
+// -------------------------------------------- several integrands, one lattice --
+//
+// SC integrands of one dimension on the same (n, g, shifts, transform): per
+// point the lattice indices and bases, per shift pair the triangle
+// coordinates are computed once and shared by the SC packed evaluations
+// (POLYS::eval2(M, s, ...) gives U_s and -F_s).  Integrand s of this launch is
+// integrand s_base + s of the plan; its per-shift CTA slots are group
+// s_base + s of [groups][m_total][nblk][2], and its non-finite values are
+// counted in counters[2 (s_base + s)] and in the sum's counters[2 count].
+template <int D, int MC, int SC, int TR, int ALPHA, bool CHECK, class POLYS>
+__device__ __forceinline__ void multi_body(const MultiParams& M, double* __restrict__ partial,
+                                           unsigned long long* __restrict__ counters) {
+  static_assert(MC % 2 == 0, "shift pairs");
+  const RuleParams<float>& P = M.base;
+  const uint32_t n = (uint32_t)P.n;
+  float2 run2[SC][MC / 2];
+  Acc<float> acc[SC][MC];
+  unsigned nbad[SC];
+#pragma unroll
+  for (int s = 0; s < SC; ++s) {
+    nbad[s] = 0;
+#pragma unroll
+    for (int p = 0; p < MC / 2; ++p) run2[s][p] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) acc[s][kk].init();
+  }
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+    uint32_t idx[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
+    for (int st = 0; st < steps; ++st) {
+      float base[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) base[i] = sec_base<float>(idx[i], P.rc);
+#pragma unroll
+      for (int p = 0; p < MC / 2; ++p) {
+        float2 z[D];
+        float wa = 1.0f, wb = 1.0f;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const float2 t = add2(make_float2(base[i], base[i]), P.shiftp[p][i]);
+          z[i] = make_float2(coord_tri_t<TR, ALPHA>(t.x, P.kor, wa), coord_tri_t<TR, ALPHA>(t.y, P.kor, wb));
+        }
+        const float2 w = make_float2(wa, wb);
+#pragma unroll
+        for (int s = 0; s < SC; ++s) {
+          float2 U, Fn;
+          POLYS::eval2(M, s, z, U, Fn);  // s is a constant once the loop is unrolled
+          float2 v = recip_neg2(mul2(mul2(U, U), Fn));
+          if constexpr (TR == TR_KOROBOV) v = mul2(v, w);
+          if constexpr (CHECK) {
+            const bool oka = finite_(v.x), okb = finite_(v.y);
+            nbad[s] += (oka || 2 * p >= P.m_launch) ? 0u : 1u;
+            nbad[s] += (okb || 2 * p + 1 >= P.m_launch) ? 0u : 1u;
+            v = make_float2(oka ? v.x : 0.0f, okb ? v.y : 0.0f);
+          }
+          run2[s][p] = add2(run2[s][p], v);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
+      if ((st & (kFoldG - 1)) == kFoldG - 1) {
+#pragma unroll
+        for (int s = 0; s < SC; ++s) {
+          unpack_runs<MC>(run2[s], acc[s]);
+#pragma unroll
+          for (int kk = 0; kk < MC; ++kk) acc[s][kk].fold();
+        }
+      }
+    }
+  }
+  __shared__ double red[kThreads / 32][SC * MC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long bad_all = 0;
+#pragma unroll
+  for (int s = 0; s < SC; ++s) {
+    unpack_runs<MC>(run2[s], acc[s]);
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) {
+      double t = acc[s][kk].warp_total();
+      if (lane == 0) red[warp][s * MC + kk] = t;
+    }
+    if constexpr (CHECK) {
+      unsigned long long bad = warp_sum_u64((unsigned long long)nbad[s]);
+      bad_all += bad;
+      if (lane == 0 && bad) atomicAdd(&counters[2 * (M.s_base + s)], bad);
+    }
+  }
+  if constexpr (CHECK) {
+    if (lane == 0 && bad_all) atomicAdd(&counters[2 * M.count], bad_all);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < SC * MC; t += kThreads) {
+    const int s = t / MC, kk = t % MC;
+    if (kk >= P.m_launch) continue;
+    double acc_s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) acc_s += red[w][t];
+    const size_t slot = (((size_t)(M.s_base + s) * P.m_total + P.k_base + kk) * P.nblk + blockIdx.x) * 2;
+    partial[slot] = acc_s;
+    partial[slot + 1] = 0.0;
+  }
 }
 
 }  // namespace qmc

@@ -262,6 +262,24 @@ def config3(count: int = 256, m: int = 16, seed: int = SEED_BASE + 3, transform:
     return probs
 
 
+def config3_shared(count: int = 32, d: int = 6, n: int = N_C2, m: int = 16, seed: int = SEED_BASE + 6,
+                   transform: str = "baker", alpha: int = 0, precision: str = "fp32") -> List[Problem]:
+    """Shared-lattice variant of configuration 3: `count` sectors of one dimension d
+    on one lattice (n, m shifts) with configuration 3's term counts, T_U ~ U{4..10},
+    T_F ~ U{6..20}; every problem carries the same shift table."""
+    rng = SplitMix64(seed)
+    shifts = make_shifts(rng, m, d)
+    probs = []
+    for s in range(count):
+        tu = rng.randint(4, 10)
+        tf = rng.randint(6, 20)
+        U = random_poly(rng, d, tu, 0)
+        F = random_poly(rng, d, 0, tf)
+        probs.append(Problem(f"shared_sector_{s}", d, n, m, shifts, transform, alpha=alpha, kind="sector",
+                             U=U, F=F, aU=-2, aF=-1, precision=precision, gamma=product_weights(d)))
+    return probs
+
+
 def config4(n: int = N_C4, m: int = 20, seed: int = SEED_BASE + 4, precision: str = "fp64",
             lam: float = 0.1) -> Problem:
     """Complex-valued sector: d=5, U = c0 + 5 deg-1, F = c0 + 10 deg-2 with 3 coefficients

@@ -128,6 +128,8 @@ def lib():
                                               ctypes.POINTER(vp)]
             L.qmc_sample_points_eps.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_eps, i32, vp, vp,
                                                 vp, vp]
+            L.qmc_integrate_multi.argtypes = [i32, u64, i32, vp, vp, qmc_transform, i32, vp, vp, vp, vp]
+            L.qmc_multi_plan_create.argtypes = [i32, u64, i32, vp, vp, qmc_transform, i32, vp, ctypes.POINTER(vp)]
             L.qmc_last_error.restype = ctypes.c_char_p
             L.qmc_version.restype = i32
             for name in ("qmc_make_lattice", "qmc_integrate", "qmc_plan_create", "qmc_plan_execute",
@@ -136,7 +138,7 @@ def lib():
                          "qmc_batch_plan_tune", "qmc_sample_points", "qmc_cv_train", "qmc_integrate_cv",
                          "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts", "qmc_measure_peaks",
                          "qmc_integrate_to_tolerance", "qmc_integrate_eps", "qmc_eps_plan_create",
-                         "qmc_sample_points_eps"):
+                         "qmc_sample_points_eps", "qmc_integrate_multi", "qmc_multi_plan_create"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -440,6 +442,48 @@ def qmc_sample_points_eps(d, n, m, g, shifts, t, f: Integrand, eps: qmc_eps, j, 
     _check(lib().qmc_sample_points_eps(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, ctypes.byref(eps), j.shape[0],
                                        _ptr(j), _ptr(k), _ptr(vals), ctypes.c_void_p(stream)))
     return vals
+
+
+# ------------------------------------------- several integrands, one lattice --
+
+def _integrand_array(fs):
+    arr = (qmc_integrand * len(fs))()
+    for s, f in enumerate(fs):
+        arr[s] = f.s
+    return arr
+
+
+def qmc_integrate_multi(d, n, m, g, shifts, t, fs, want_per_shift=False, stream=0):
+    """Integrands fs (list of Integrand) on one lattice.  Returns (results
+    [len(fs) + 1], the last for their sum; per_shift[len(fs) + 1, m, 2] or None)."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    arr = _integrand_array(fs)
+    res = (qmc_result * (len(fs) + 1))()
+    ps = np.zeros((len(fs) + 1, m, 2)) if want_per_shift else None
+    rc = lib().qmc_integrate_multi(d, n, m, _ptr(g), _ptr(shifts), t, len(fs), arr, res, _ptr(ps),
+                                   ctypes.c_void_p(stream))
+    _check(rc, allow_warnings=True)
+    return list(res), ps
+
+
+class MultiPlan(Plan):
+    """qmc_multi_plan_create; execute() returns len(fs) + 1 results."""
+
+    def __init__(self, d, n, m, g, shifts, t, fs):
+        self.m = m
+        self._fs = list(fs)
+        self.orders = len(fs) + 1
+        g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+        shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+        arr = _integrand_array(fs)
+        h = ctypes.c_void_p()
+        _check(lib().qmc_multi_plan_create(d, n, m, _ptr(g), _ptr(shifts), t, len(fs), arr, ctypes.byref(h)))
+        self.h = h
+
+
+def qmc_multi_plan_create(d, n, m, g, shifts, t, fs) -> MultiPlan:
+    return MultiPlan(d, n, m, g, shifts, t, fs)
 
 
 # --------------------------------------------------------- control variate --

@@ -131,6 +131,38 @@ def test_eps_validation_rejects_bad_arguments(Q, case):
     assert ei.value.status == Q.QMC_EINVAL
 
 
+@pytest.mark.parametrize("case,status", [("count0", "EINVAL"), ("fp64", "EUNSUPPORTED"), ("dmismatch", "EINVAL"),
+                                         ("deg3", "EUNSUPPORTED"), ("alpha2", "EUNSUPPORTED"), ("d9", "EUNSUPPORTED")])
+def test_multi_validation(Q, case, status):
+    """The shared-lattice entry point checks every integrand on the host."""
+    d, n, m = 3, 101, 4
+    coef = np.array([1.0, 0.5])
+    expo = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.uint8)
+    t = Q.transform("baker")
+    fs = [Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP32EVAL, (coef, expo), (coef, expo)) for _ in range(3)]
+    if case == "count0":
+        fs = []
+    elif case == "fp64":
+        fs[1] = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP64, (coef, expo), (coef, expo))
+    elif case == "dmismatch":
+        fs[2] = Q.Integrand(Q.QMC_F_SECTOR, 2, Q.QMC_FP32EVAL, (coef, expo[:, :2]), (coef, expo[:, :2]))
+    elif case == "deg3":
+        fs[0] = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP32EVAL, (coef, expo),
+                            (coef, np.array([[0, 0, 0], [1, 1, 1]], np.uint8)))
+    elif case == "alpha2":
+        t = Q.transform("korobov", 2)
+    elif case == "d9":
+        d = 9
+        e9 = np.zeros((2, 9), np.uint8)
+        e9[1, 0] = 1
+        fs = [Q.Integrand(Q.QMC_F_SECTOR, 9, Q.QMC_FP32EVAL, (coef, e9), (coef, e9))]
+    g = np.arange(1, d + 1, dtype=np.uint64)
+    shifts = np.full((m, d), 0.25)
+    with pytest.raises(Q.QmcError) as ei:
+        Q.qmc_integrate_multi(d, n, m, g, shifts, t, fs)
+    assert ei.value.status == getattr(Q, "QMC_" + status)
+
+
 def test_make_lattice_rejects_composite(Q):
     with pytest.raises(Q.QmcError):
         Q.qmc_make_lattice(3, 1001, [1.0, 0.25, 1 / 9])

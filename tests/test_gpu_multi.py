@@ -1,0 +1,119 @@
+"""GPU parity of the shared-lattice sweep: several sector integrands of one
+dimension on the same (n, g, shifts, transform), evaluated by one fused
+kernel, against the oracle for each integrand and for their sum.
+
+Tolerances are those of the FP32EVAL path (per-shift Q^(k) within 2e-7
+relative of the oracle).  Against the single-integrand kernel the per-point
+values are the same floating-point operations in the same order, so only
+the grouping of the compensated run sums differs (1e-8 relative)."""
+import numpy as np
+import pytest
+
+from paper_1811_11722_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_1811_11722_gb300 import build, qmc
+    build.build_library()
+    return qmc
+
+
+def oracle_sum(oracle_lib, probs, g, nthreads=1):
+    """Per-integrand oracle results and the sum's Eq. (2)/(3) from the summed
+    per-shift sums."""
+    refs = [oracle_lib.integrate(p, g, nthreads=nthreads) for p in probs]
+    sums = np.sum([r["sums"] for r in refs], axis=0)
+    q, mean, var = oracle_lib.estimate(sums, probs[0].n)
+    return refs, {"q": q, "mean": mean, "err": np.sqrt(var)}
+
+
+@pytest.mark.parametrize("transform,alpha", [("baker", 0), ("korobov", 3), ("none", 0)])
+def test_multi_vs_oracle(Q, oracle_lib, nthreads, transform, alpha):
+    """11 integrands (a full chunk of 8 and a ragged chunk of 3), d = 6,
+    n = 100003 (many tiles, ragged tail), m = 9 (an odd last shift pair)."""
+    probs = I.config3_shared(count=11, d=6, n=100003, m=9, transform=transform, alpha=alpha)
+    g = I.random_generating_vector(I.SplitMix64(61), 6, probs[0].n)
+    fs = [Q.integrand_from_problem(p, "fp32") for p in probs]
+    res, ps = Q.qmc_integrate_multi(6, probs[0].n, 9, g, probs[0].shifts, Q.transform(transform, alpha), fs,
+                                    want_per_shift=True)
+    assert len(res) == 12
+    refs, tot = oracle_sum(oracle_lib, probs, g, nthreads)
+    for s in range(11):
+        assert res[s].status == 0 and res[s].nonfinite == 0
+        assert np.all(np.abs(ps[s, :, 0] - refs[s]["q"][:, 0]) <= 2e-7 * np.abs(refs[s]["q"][:, 0])), s
+        assert abs(res[s].mean[0] - refs[s]["mean"][0]) <= 2e-7 * abs(refs[s]["mean"][0]), s
+    assert np.all(np.abs(ps[11, :, 0] - tot["q"][:, 0]) <= 2e-7 * np.abs(tot["q"][:, 0]))
+    assert abs(res[11].mean[0] - tot["mean"][0]) <= 2e-7 * abs(tot["mean"][0])
+    # the sum's per-shift values are the integrands' per-shift values added
+    assert np.allclose(ps[11, :, 0], ps[:11, :, 0].sum(axis=0), rtol=1e-13, atol=0)
+
+
+def test_multi_matches_single_integrand_kernel(Q):
+    """The fused sweep against one qmc_integrate per integrand (d = 8, two chunks)."""
+    probs = I.config3_shared(count=16, d=8, n=1000003, m=16)
+    g = I.random_generating_vector(I.SplitMix64(62), 8, probs[0].n)
+    fs = [Q.integrand_from_problem(p, "fp32") for p in probs]
+    t = Q.transform("baker")
+    res, ps = Q.qmc_integrate_multi(8, probs[0].n, 16, g, probs[0].shifts, t, fs, want_per_shift=True)
+    for s, f in enumerate(fs):
+        one, ps1 = Q.qmc_integrate(8, probs[0].n, 16, g, probs[0].shifts, t, f, want_per_shift=True)
+        assert np.all(np.abs(ps[s, :, 0] - ps1[:, 0]) <= 1e-8 * np.abs(ps1[:, 0])), s
+        assert abs(res[s].err[0] - one.err[0]) <= 1e-3 * one.err[0] + 1e-9 * abs(one.mean[0]), s
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 7])
+def test_multi_all_dims(Q, oracle_lib, d):
+    probs = I.config3_shared(count=5, d=d, n=20011, m=4, transform="korobov", alpha=3)
+    g = I.random_generating_vector(I.SplitMix64(63 + d), d, probs[0].n)
+    fs = [Q.integrand_from_problem(p, "fp32") for p in probs]
+    res, ps = Q.qmc_integrate_multi(d, probs[0].n, 4, g, probs[0].shifts, Q.transform("korobov", 3), fs,
+                                    want_per_shift=True)
+    refs, tot = oracle_sum(oracle_lib, probs, g)
+    for s in range(5):
+        assert np.all(np.abs(ps[s, :, 0] - refs[s]["q"][:, 0]) <= 4e-7 * np.abs(refs[s]["q"][:, 0])), (d, s)
+    assert np.all(np.abs(ps[5, :, 0] - tot["q"][:, 0]) <= 4e-7 * np.abs(tot["q"][:, 0]))
+
+
+def test_multi_nonfinite_counted_per_integrand(Q, oracle_lib):
+    """One integrand's F has no constant term, so 1/F is infinite where z = 0;
+    it counts those points, the others count none, the sum counts them all."""
+    d, n, m = 2, 1009, 4
+    rng = I.SplitMix64(64)
+    sh = I.make_shifts(rng, m, d)
+    sh[0] = 0.0
+    good = [I.Problem(f"ok{s}", d, n, m, sh, "baker", kind="sector", U=I.random_poly(rng, d, 2, 0),
+                      F=I.random_poly(rng, d, 0, 3)) for s in range(3)]
+    bad = I.Problem("nf", d, n, m, sh, "baker", kind="sector",
+                    U=I.Poly(np.array([1.0]), np.zeros((1, d), np.uint8)),
+                    F=I.Poly(np.array([1.0, 1.0]), np.array([[2, 0], [0, 2]], np.uint8)))
+    probs = good[:2] + [bad] + good[2:]
+    g = np.array([1, 17], dtype=np.uint64)
+    fs = [Q.integrand_from_problem(p, "fp32") for p in probs]
+    res, ps = Q.qmc_integrate_multi(d, n, m, g, sh, Q.transform("baker"), fs, want_per_shift=True)
+    refs = [oracle_lib.integrate(p, g) for p in probs]
+    nf = int(refs[2]["nonfinite"].sum())
+    assert nf > 0
+    for s in range(4):
+        assert res[s].nonfinite == int(refs[s]["nonfinite"].sum()), s
+    assert res[2].status == Q.QMC_ENONFINITE and res[0].status == 0
+    assert res[4].nonfinite == nf and res[4].status == Q.QMC_ENONFINITE
+    assert np.all(np.abs(ps[2, :, 0] - refs[2]["q"][:, 0]) <= 2e-7 * np.abs(refs[2]["q"][:, 0]))
+
+
+def test_multi_plan_replay(Q):
+    """A shared-lattice plan replays bit-identically."""
+    probs = I.config3_shared(count=9, d=6, n=1000003, m=8)
+    g = I.random_generating_vector(I.SplitMix64(65), 6, probs[0].n)
+    fs = [Q.integrand_from_problem(p, "fp32") for p in probs]
+    plan = Q.qmc_multi_plan_create(6, probs[0].n, 8, g, probs[0].shifts, Q.transform("baker"), fs)
+    a = plan.execute()
+    b = plan.execute()
+    assert len(a) == 10
+    assert all(x.mean[0] == y.mean[0] and x.err[0] == y.err[0] for x, y in zip(a, b))
+    desc = plan.describe()
+    assert desc["orders"] == "10" and desc["specialised"] == "1"
+    assert plan.launches() == 4 * 2 + 1
+    plan.destroy()

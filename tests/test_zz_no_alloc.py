@@ -38,10 +38,16 @@ def test_noalloc_matches_integrate_twice(Q, precision, transform, alpha, tol):
 
 
 def test_noalloc_rejects_oversized_request(Q):
-    """More shifts than the fixed scratch array holds is refused, not truncated."""
-    p = I.config2(n=16777213, m=1024)
-    p.shifts = I.make_shifts(I.SplitMix64(5), 1024, p.d)
-    g = I.random_generating_vector(I.SplitMix64(78), p.d, p.n)
+    """More shift slots than the fixed scratch array holds is refused, not
+    truncated.  A d = 2 FP64 sector kernel keeps several CTAs per SM, so
+    m = 1024 shifts need m x (CTAs of one wave) x 16 B > 4 MiB of slots."""
+    rng = I.SplitMix64(5)
+    d, n, m = 2, 16777213, 1024
+    U = I.random_poly(rng, d, 2, 0)
+    F = I.random_poly(rng, d, 0, 3)
+    p = I.Problem("big", d, n, m, I.make_shifts(rng, m, d), "baker", kind="sector", U=U, F=F)
+    g = I.random_generating_vector(I.SplitMix64(78), d, n)
     with pytest.raises(Q.QmcError) as ei:
-        Q.qmc_integrate_noalloc(p.d, p.n, p.m, g, p.shifts, Q.transform("baker"), Q.integrand_from_problem(p, "fp32"))
+        Q.qmc_integrate_noalloc(d, n, m, g, p.shifts, Q.transform("baker"), Q.integrand_from_problem(p, "fp64"))
     assert ei.value.status == Q.QMC_EINVAL
+    assert "scratch" in Q.qmc_last_error()
