@@ -44,7 +44,7 @@ FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 # DRAM traffic of the lattice kernel from one ncu capture of this workload;
 # valid only while the kernel sources hash to KERNEL_SHA (else reported null).
-NCU_TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"kernel_sha": "100a4644a8a24f73", "bytes_per_launch": 61700}
 
 
 def kernel_sha() -> str:

@@ -379,6 +379,23 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
       for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
       for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
       if (base.tr == TR_KOROBOV) base.value_scale = std::pow((double)base.kor[7], (double)d);
+      if (fp32 && !tune.no_jit && jit_enabled()) {
+        // run-time specialised, packed, exactly `orders` orders; one logarithm
+        // per value when U, F > 0 on the cube and bF = -bU
+        fill_pairs(base, d);
+        const int NE = eps->orders;
+        const int jmc = NE <= 2 ? 16 : (NE <= 3 ? 8 : 4);
+        const bool positive = base.check_finite == 0;
+        const bool log1 = positive && eps->bF == -eps->bU;
+        void* fn = nullptr;
+        int occ = 0;
+        if (jit_eps_f32(d, jmc, NE, base.tr, base.tr == TR_KOROBOV ? 3 : 0, log1, !positive, cu, cf, &fn, &occ) ==
+            QMC_OK) {
+          jit_fn = fn;
+          jit_occ = occ;
+          mc = jmc;
+        }
+      }
     } else {
       general = true;
     }
@@ -417,8 +434,9 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
         void* fn = nullptr;
         int occ = 0;
         size_t sm = 0;
-        if (jit_sector_f32(d, mc, base.tr, base.tr == TR_KOROBOV ? 3 : 0, base.check_finite != 0, cu, cf, &fn,
-                           &occ, &sm) == QMC_OK) {
+        const bool smacc = tune.smacc < 0 ? jit_smacc() : tune.smacc != 0;
+        if (jit_sector_f32(d, mc, base.tr, base.tr == TR_KOROBOV ? 3 : 0, base.check_finite != 0, cu, cf, smacc,
+                           tune.minb, &fn, &occ, &sm) == QMC_OK) {
           jit_fn = fn;
           jit_occ = occ;
           jit_smem = sm;
@@ -701,8 +719,16 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
   Plan* pl = reinterpret_cast<Plan*>(plan);
   cudaStream_t st = (cudaStream_t)stream;
   const SavedProblem& sp = pl->saved;
-  std::vector<int> cands;
-  if (sp.f.precision == QMC_FP32EVAL && sp.f.kind == QMC_F_SECTOR && sp.eps.orders == 0) cands = {8, 16, 32};
+  // candidates (shifts per launch, accumulators in shared memory, min CTAs per SM)
+  struct Cand {
+    int mc, smacc, minb;
+  };
+  std::vector<Cand> cands;
+  if (sp.f.precision == QMC_FP32EVAL && sp.f.kind == QMC_F_SECTOR && sp.eps.orders == 0) {
+    cands = {{8, 0, 0}, {16, 0, 0}, {32, 0, 0}};
+    if (pl->launches.size() && pl->launches[0].cufunc)  // register-pressure variants of the specialised kernel
+      cands.insert(cands.end(), {{16, 0, 2}, {16, 1, 2}, {32, 1, 0}, {32, 1, 2}});
+  }
   if (cands.empty()) {
     if (shifts_per_launch_out) *shifts_per_launch_out = pl->mc;
     return QMC_OK;
@@ -712,12 +738,14 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
   qmc_result* dres = nullptr;
   QMC_CUDA(cudaMalloc(&dres, sizeof(qmc_result)));
   float best = 1e30f;
-  int best_mc = pl->mc;
+  Cand best_c{pl->mc, pl->tune.smacc, pl->tune.minb};
   int rc = QMC_OK;
-  for (int mc : cands) {
+  for (const Cand& cd : cands) {
     Plan trial;
     TuneChoice tc = pl->tune;
-    tc.mc = mc;
+    tc.mc = cd.mc;
+    tc.smacc = cd.smacc;
+    tc.minb = cd.minb;
     rc = plan_build(&trial, sp.d, sp.n, sp.m, sp.g.data(), sp.shifts.data(), sp.t, &sp.f, tc);
     if (rc == QMC_EUNSUPPORTED) {
       rc = QMC_OK;
@@ -740,16 +768,18 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
     if (rc) break;
     if (tot < best) {
       best = tot;
-      best_mc = mc;
+      best_c = cd;
     }
   }
   cudaFree(dres);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;
-  if (best_mc != pl->mc) {
+  if (best_c.mc != pl->mc || best_c.smacc != pl->tune.smacc || best_c.minb != pl->tune.minb) {
     TuneChoice tc = pl->tune;
-    tc.mc = best_mc;
+    tc.mc = best_c.mc;
+    tc.smacc = best_c.smacc;
+    tc.minb = best_c.minb;
     Plan fresh;
     rc = plan_build(&fresh, sp.d, sp.n, sp.m, sp.g.data(), sp.shifts.data(), sp.t, &sp.f, tc);
     if (rc) return rc;
@@ -841,9 +871,10 @@ int qmc_plan_describe(qmc_plan plan, char* buf, int32_t len) {
     L = v;
   }
   snprintf(buf, (size_t)len,
-           "d=%d n=%llu m=%d complex=%d orders=%d shifts_per_launch=%d launches=%zu specialised=%d ctas=%d L=%d",
+           "d=%d n=%llu m=%d complex=%d orders=%d shifts_per_launch=%d launches=%zu specialised=%d ctas=%d L=%d "
+           "smem_acc=%d min_ctas=%d",
            pl->d, (unsigned long long)pl->n, pl->m, pl->is_complex, pl->orders, pl->mc, pl->launches.size() + 1,
-           (ln && ln->cufunc) ? 1 : 0, pl->nblk, L);
+           (ln && ln->cufunc) ? 1 : 0, pl->nblk, L, (ln && ln->smem) ? 1 : 0, pl->tune.minb);
   return QMC_OK;
 }
 

@@ -210,7 +210,7 @@ __device__ __forceinline__ double coord_f64(uint64_t X, const double* kor, int a
 // before the wrap.  (An add with one constant operand encodes directly; an
 // FMA with an immediate 2 and a constant would first load the constant.)
 // Then v = |t| - 1 = +-(2 {y} - 1), so the baker map is
-// z = 1 - |2 {y} - 1| = 1 - |v| with no wrap test at all, and
+// z = 1 - |2 {y} - 1| = 1 - |v| = min(|t|, 2 - |t|) with no wrap test at all, and
 // s = min({y}, 1 - {y}) = (1 - |v|) / 2; {y} > 1/2 exactly when t and v have
 // the same sign.
 __device__ __forceinline__ float base2_f32(uint64_t p64) {
@@ -224,10 +224,13 @@ __device__ __forceinline__ float coord_tri_t(float t, const float* kor, float& w
   if constexpr (TR == TR_NONE) {
     return __fmaf_rn(0.5f, t, t < 0.0f ? 1.0f : 0.0f);
   } else {
-    const float v = fabsf(t) - 1.0f;
     if constexpr (TR == TR_BAKER) {
-      return 1.0f - fabsf(v);
+      // 1 - ||t| - 1| = min(|t|, 2 - |t|): one FP32 add and a min (ALU pipe),
+      // and exact: |t| < 1 is returned as is, 2 - |t| is exact for |t| in [1, 2)
+      const float a = fabsf(t);
+      return fminf(a, 2.0f - a);
     } else {
+      const float v = fabsf(t) - 1.0f;
       const float s = __fmaf_rn(-0.5f, fabsf(v), 0.5f);
       const bool upper = t * v > 0.0f;
       return korobov_apply<ALPHA>(s, upper, kor, 0, w);

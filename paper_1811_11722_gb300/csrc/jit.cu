@@ -245,13 +245,9 @@ static int jit_compile(const std::string& src, const char* name, size_t smem, vo
   return QMC_OK;
 }
 
-// Compile (or fetch) the specialised FP32 sector kernel.  Returns QMC_OK and
-// the CUfunction / occupancy, or an error code (the caller falls back).
-int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
-                   const std::vector<double>& cf, void** fn_out, int* occ_out, size_t* smem_out) {
-  const bool smacc = jit_smacc();
-  const size_t smem = smacc ? (size_t)MC * kThreads * 8 : 0;
-  *smem_out = smem;
+// The include line and the GenPolys policy (scalar eval for point sampling,
+// packed eval2 for the rule) of one integrand.
+static std::string gen_polys(int D, const std::vector<double>& cu, const std::vector<double>& cf) {
   std::string src;
   src += "#include \"rule_kernels.cuh\"\n";
   src += "namespace qmc {\nstruct GenPolys {\n";
@@ -264,7 +260,33 @@ int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vect
   src += "                                               float2& Fn) {\n";
   src += poly_code2(D, cu, cf);
   src += "  }\n};\n}  // namespace qmc\n";
-  src += "extern \"C\" __global__ void __launch_bounds__(256) qmc_jit_sector(\n";
+  return src;
+}
+
+// Compile (or fetch) the specialised FP32 epsilon-order kernel (eps_body2):
+// NE orders, MC shifts per launch, one logarithm per value when log1.
+int jit_eps_f32(int D, int MC, int NE, int TR, int ALPHA, bool log1, bool check, const std::vector<double>& cu,
+                const std::vector<double>& cf, void** fn_out, int* occ_out) {
+  std::string src = gen_polys(D, cu, cf);
+  src += "extern \"C\" __global__ void __launch_bounds__(256) qmc_jit_eps(\n";
+  src += "    const __grid_constant__ qmc::RuleParams<float> P, double* __restrict__ partial,\n";
+  src += "    unsigned long long* __restrict__ counters, const qmc::SampleIO sio) {\n";
+  src += "  qmc::eps_body2<" + std::to_string(D) + ", " + std::to_string(MC) + ", " + std::to_string(NE) + ", " +
+         std::to_string(TR) + ", " + std::to_string(ALPHA) + ", " + (log1 ? "true" : "false") + ", " +
+         (check ? "true" : "false") + ", qmc::GenPolys>(P, partial, counters, sio);\n}\n";
+  return jit_compile(src, "qmc_jit_eps", 0, fn_out, occ_out);
+}
+
+// Compile (or fetch) the specialised FP32 sector kernel.  Returns QMC_OK and
+// the CUfunction / occupancy, or an error code (the caller falls back).
+int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
+                   const std::vector<double>& cf, bool smacc, int minb, void** fn_out, int* occ_out,
+                   size_t* smem_out) {
+  const size_t smem = smacc ? (size_t)MC * kThreads * 8 : 0;
+  *smem_out = smem;
+  std::string src = gen_polys(D, cu, cf);
+  src += "extern \"C\" __global__ void __launch_bounds__(256" + (minb > 0 ? ", " + std::to_string(minb) : "") +
+         ") qmc_jit_sector(\n";
   src += "    const __grid_constant__ qmc::RuleParams<float> P, double* __restrict__ partial,\n";
   src += "    unsigned long long* __restrict__ counters, const qmc::SampleIO sio) {\n";
   src += "  qmc::sector_body<float, " + std::to_string(D) + ", " + std::to_string(MC) + ", " + std::to_string(TR) +

@@ -30,6 +30,9 @@ struct TuneChoice {
   bool no_jit = false; // keep the template kernel (no run-time specialisation)
   int max_ctas = 0;    // cap on CTAs of each launch (batched sectors run side by side)
   bool force_general = false;
+  int smacc = -1;      // specialised kernel: accumulator pairs in shared memory (1), registers (0),
+                       // -1: the QMC_JIT_SMACC default
+  int minb = 0;        // specialised kernel: minimum resident CTAs per SM in its launch bounds (0: none)
 };
 
 // Deep copy of a problem's host inputs (so a plan can be rebuilt by the tuner).
@@ -104,10 +107,13 @@ int plan_execute(Plan* pl, qmc_result* out, double* per_shift, cudaStream_t stre
 bool jit_enabled();
 bool jit_smacc();
 int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
-                   const std::vector<double>& cf, void** fn_out, int* occ_out, size_t* smem_out);
+                   const std::vector<double>& cf, bool smacc, int minb, void** fn_out, int* occ_out,
+                   size_t* smem_out);
 int jit_multi_f32(int D, int MC, int TR, int ALPHA, bool check,
                   const std::vector<std::pair<std::vector<double>, std::vector<double>>>& polys, void** fn_out,
                   int* occ_out);
+int jit_eps_f32(int D, int MC, int NE, int TR, int ALPHA, bool log1, bool check, const std::vector<double>& cu,
+                const std::vector<double>& cf, void** fn_out, int* occ_out);
 int device_sms();
 int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream);
 int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraphNode_t* node);

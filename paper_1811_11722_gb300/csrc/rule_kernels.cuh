@@ -725,6 +725,118 @@ __global__ void __launch_bounds__(kThreads)
   eps_epilogue<R, MC, NE>(acc, nbad, P, partial, counters);
 }
 
+// Run-time specialised form (FP32, packed shift pairs, POLY from the code
+// generator, NE = the plan's orders exactly).  LOG1: the host has shown U > 0
+// and F > 0 on the cube and bF = -bU, so L = bU log(U / F) with
+// U / F = U (U^2) v0 from values already at hand: one logarithm per value.
+// Otherwise L takes both logarithms, and every order counts its own NaN/Inf.
+template <int D, int MC, int NE, int TR, int ALPHA, bool LOG1, bool CHECK, class POLY>
+__device__ __forceinline__ void eps_body2(const RuleParams<float>& P, double* __restrict__ partial,
+                                          unsigned long long* __restrict__ counters, const SampleIO& sio) {
+  static_assert(MC % 2 == 0, "shift pairs");
+  if (sio.count > 0) {  // single terms: the scalar evaluation
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sio.count) return;
+    const uint64_t j = sio.j[s];
+    const int k = sio.k[s];
+    float base[D], z[D];
+    float w = 1.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      uint32_t idx = lattice_index(j, P.g[i], P.n);
+      base[i] = sec_base<float>(idx, P.rc);
+      if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
+      if (sio.coord) sio.coord[(size_t)s * D + i] = sec_coord_used<float>(P, base[i], k, i);
+      z[i] = coord_tri<TR, ALPHA>(base[i], shift_tri(P, k, i), P.kor, w);
+    }
+    float U, F;
+    POLY::template eval<D, 1, 2, float>(P, z, U, F);
+    float v = recip(U * U * F);
+    if constexpr (TR == TR_KOROBOV) v *= w;
+    const float L = P.eps_b[0] * log_(U) + P.eps_b[1] * log_(F);
+    for (int o = 0; o < P.eps_orders; ++o) {
+      sio.values[(size_t)s * sio.stride + o] = (double)v * P.value_scale;
+      v = v * L * P.eps_inv[o];
+    }
+    return;
+  }
+  const uint32_t n = (uint32_t)P.n;
+  float2 run2[NE][MC / 2];
+  Acc<float> acc[NE][MC];
+  unsigned nbad[NE];
+#pragma unroll
+  for (int o = 0; o < NE; ++o) {
+    nbad[o] = 0;
+#pragma unroll
+    for (int p = 0; p < MC / 2; ++p) run2[o][p] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int kk = 0; kk < MC; ++kk) acc[o][kk].init();
+  }
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+    uint32_t idx[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
+    for (int st = 0; st < steps; ++st) {
+      float base[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) base[i] = sec_base<float>(idx[i], P.rc);
+#pragma unroll
+      for (int p = 0; p < MC / 2; ++p) {
+        float2 z[D];
+        float wa = 1.0f, wb = 1.0f;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const float2 t = add2(make_float2(base[i], base[i]), P.shiftp[p][i]);
+          z[i] = make_float2(coord_tri_t<TR, ALPHA>(t.x, P.kor, wa), coord_tri_t<TR, ALPHA>(t.y, P.kor, wb));
+        }
+        float2 U, Fn;
+        POLY::template eval2<D, 1, 2>(P, z, U, Fn);
+        const float2 uu = mul2(U, U);
+        float2 v = recip_neg2(mul2(uu, Fn));
+        float2 L;
+        if constexpr (LOG1) {
+          const float2 r = mul2(mul2(U, uu), v);  // U / F
+          L = make_float2(P.eps_b[0] * log_(r.x), P.eps_b[0] * log_(r.y));
+        } else {
+          L = make_float2(P.eps_b[0] * log_(U.x) + P.eps_b[1] * log_(-Fn.x),
+                          P.eps_b[0] * log_(U.y) + P.eps_b[1] * log_(-Fn.y));
+        }
+        if constexpr (TR == TR_KOROBOV) v = mul2(v, make_float2(wa, wb));
+#pragma unroll
+        for (int o = 0; o < NE; ++o) {
+          if constexpr (CHECK) {
+            const bool oka = finite_(v.x), okb = finite_(v.y);
+            nbad[o] += (oka || 2 * p >= P.m_launch) ? 0u : 1u;
+            nbad[o] += (okb || 2 * p + 1 >= P.m_launch) ? 0u : 1u;
+            run2[o][p] = add2(run2[o][p], make_float2(oka ? v.x : 0.0f, okb ? v.y : 0.0f));
+          } else {
+            run2[o][p] = add2(run2[o][p], v);
+          }
+          if (o + 1 < NE) v = mul2(v, mul2(L, make_float2(P.eps_inv[o], P.eps_inv[o])));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
+      if ((st & (kFoldG - 1)) == kFoldG - 1) {
+#pragma unroll
+        for (int o = 0; o < NE; ++o) {
+          unpack_runs<MC>(run2[o], acc[o]);
+#pragma unroll
+          for (int kk = 0; kk < MC; ++kk) acc[o][kk].fold();
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < NE; ++o) unpack_runs<MC>(run2[o], acc[o]);
+  eps_epilogue<float, MC, NE>(acc, nbad, P, partial, counters);
+}
+
 // Any integer powers, sparse U and F, runtime d and transform: the general
 // kernel's evaluation with the orders added (NE = kEpsMax, MC = kEpsAcc / NE).
 template <typename R>

@@ -100,7 +100,13 @@ def test_multi_nonfinite_counted_per_integrand(Q, oracle_lib):
         assert res[s].nonfinite == int(refs[s]["nonfinite"].sum()), s
     assert res[2].status == Q.QMC_ENONFINITE and res[0].status == 0
     assert res[4].nonfinite == nf and res[4].status == Q.QMC_ENONFINITE
-    assert np.all(np.abs(ps[2, :, 0] - refs[2]["q"][:, 0]) <= 2e-7 * np.abs(refs[2]["q"][:, 0]))
+    # 1/F ~ 1/|z|^2 near the left-out point: FP32 coordinates (2^-24 absolute)
+    # put ~2 dz/|z| relative error on such values, so the comparison is with the
+    # single-integrand FP32 kernel, which does the same arithmetic
+    one, ps1 = Q.qmc_integrate(d, n, m, g, sh, Q.transform("baker"), fs[2], want_per_shift=True)
+    assert one.nonfinite == nf
+    assert np.all(np.abs(ps[2, :, 0] - ps1[:, 0]) <= 1e-8 * np.abs(ps1[:, 0]))
+    assert np.all(np.abs(ps[2, :, 0] - refs[2]["q"][:, 0]) <= 1e-4 * np.abs(refs[2]["q"][:, 0]))
 
 
 def test_multi_plan_replay(Q):
