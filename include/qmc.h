@@ -348,6 +348,35 @@ int qmc_integrate_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, con
 #endif
 
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
+/* Embedded rank-1 lattices in base 2 (automatic n without discarding work).
+ * One generating vector g serves every size 2^k, log2_nmin <= k <= log2_nmax:
+ * the size-2^k lattice is {j g / 2^k}, the points of size 2n include those of
+ * size n, and the others form the size-n lattice shifted by g / (2n).
+ * qmc_make_lattice_embedded builds g component by component (g_1 = 1, odd
+ * components) minimising max_k 4^k e^2_{2^k}(g), with e^2 the worst-case
+ * error of qmc_make_lattice at each size; candidates for a component are all
+ * odd z < 2^(log2_nmax - 1) when `candidates` covers them, else that many drawn
+ * by SplitMix64 from `seed` (ties to the smallest z).  Host only; sizes up to
+ * 2^30.  g_out: [d] host. */
+int qmc_make_lattice_embedded(int32_t d, int32_t log2_nmin, int32_t log2_nmax, const double* gamma,
+                              int32_t candidates, uint64_t seed, uint64_t* g_out);
+/* Doubling n until Eq. (3)'s relative error meets rel_tol: level 0 applies the
+ * rule with n = 2^log2_n0 points; level l >= 1 evaluates only the new points
+ * of n = 2^(log2_n0 + l), as the rule of the previous size on shifts
+ * Delta + g / n, and averages it with the previous per-shift values, so the
+ * estimate at every level is exactly the size-2^(log2_n0 + l) rule.
+ *   levels     1..31 - log2_n0 sizes;  g [d] odd components, for the largest size
+ *   per_shift  optional [m][2] host: the per-shift values of the returned level
+ *   level_out  the level that produced *out
+ * Shifts, transform and integrand as for qmc_integrate; `out` is host memory.
+ * Returns QMC_OK when the tolerance was met (or the level's NaN/Inf warning),
+ * else the last level's estimate with status QMC_ETIMEOUT. */
+int qmc_integrate_extensible(int32_t d, int32_t log2_n0, int32_t levels, const uint64_t* g, int32_t m,
+                             const double* shifts, qmc_transform t, const qmc_integrand* f, double rel_tol,
+                             qmc_result* out, double* per_shift, int32_t* level_out, void* stream);
+#endif
+
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
 /* Eq. (2)/(3) from per-shift values alone: Qbar and sigma^2 (two-pass,
  * compensated) over m values Q^(k) given as per_shift [m][2] (re, im), host
  * memory; host only, no GPU.  Combines independent shift sets (from several

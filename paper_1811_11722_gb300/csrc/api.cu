@@ -376,6 +376,10 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
       mc = kEpsAcc / ne;
       auto cu = pack_dense(f->U, d, 1);
       auto cf = pack_dense(f->F, d, 2);
+      if (fp32) {
+        prescale_slots(cu.data(), d, 1, fx_sigma(base.tr));
+        prescale_slots(cf.data(), d, 2, fx_sigma(base.tr));
+      }
       for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
       for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
       if (base.tr == TR_KOROBOV) base.value_scale = std::pow((double)base.kor[7], (double)d);
@@ -426,6 +430,10 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
     if (func) {
       auto cu = pack_dense(f->U, d, KU);
       auto cf = pack_dense(f->F, d, KF);
+      if (fp32) {  // the FP32 kernels hand the polynomials z / fx_sigma (exact powers of two)
+        prescale_slots(cu.data(), d, KU, fx_sigma(base.tr));
+        prescale_slots(cf.data(), d, KF, fx_sigma(base.tr));
+      }
       for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
       for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
       if (fp32 && KU == 1 && KF == 2) fill_pairs(base, d);
@@ -506,9 +514,7 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
       for (int i = 0; i < d; ++i) {
         const int src = kk < mk ? k0 + kk : k0;
         uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
-        P.shift64[kk][i] = s64;
-        P.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
-        set_shift_tri(P, kk, i, (float)(2.0 * shifts[(size_t)src * d + i] - 2.0));
+        set_shift(P, kk, i, s64);
       }
     Launch ln;
     ln.func = func;
@@ -832,6 +838,56 @@ int qmc_integrate_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, con
   }
   out->status = QMC_ETIMEOUT;
   return fail(QMC_ETIMEOUT, "relative error %.3g not reached after %d lattices", rel_tol, levels);
+}
+
+int qmc_integrate_extensible(int32_t d, int32_t log2_n0, int32_t levels, const uint64_t* g, int32_t m,
+                             const double* shifts, qmc_transform t, const qmc_integrand* f, double rel_tol,
+                             qmc_result* out, double* per_shift, int32_t* level_out, void* stream) {
+  if (levels < 1 || log2_n0 < 1 || log2_n0 + levels - 1 > 30 || !g || !shifts || !out || !(rel_tol > 0.0) ||
+      m < 2 || d < 1 || d > QMC_DMAX)
+    return fail(QMC_EINVAL, "bad extensible-lattice arguments");
+  if (is_device_pointer(out) || (per_shift && is_device_pointer(per_shift)))
+    return fail(QMC_EINVAL, "the results must be host memory");
+  for (int i = 0; i < d; ++i)
+    if ((g[i] & 1) == 0) return fail(QMC_EINVAL, "g[%d] must be odd (a unit modulo every power of two)", i);
+  std::vector<double> q((size_t)m * 2), qn((size_t)m * 2), sh2((size_t)m * d);
+  std::vector<uint64_t> gl(d);
+  int rc = QMC_OK;
+  uint64_t nonfinite = 0, deform = 0;
+  for (int l = 0; l < levels; ++l) {
+    const uint64_t n = 1ull << (log2_n0 + (l == 0 ? 0 : l - 1));  // the size of the rule evaluated at this level
+    for (int i = 0; i < d; ++i) gl[i] = g[i] % n == 0 ? 1 : g[i] % n;  // n = 2: every odd g is 1
+    const double* sh = shifts;
+    if (l > 0) {
+      // the points of size 2n that are not in size n: the size-n lattice shifted by g / (2n)
+      const double two_n = (double)(2 * n);
+      for (int k = 0; k < m; ++k)
+        for (int i = 0; i < d; ++i) {
+          double v = shifts[(size_t)k * d + i] + (double)(g[i] % (2 * n)) / two_n;
+          sh2[(size_t)k * d + i] = v >= 1.0 ? v - 1.0 : v;
+        }
+      sh = sh2.data();
+    }
+    qmc_result r;
+    rc = qmc_integrate(d, n, m, gl.data(), sh, t, f, &r, l == 0 ? q.data() : qn.data(), stream);
+    if (rc != QMC_OK && rc != QMC_ENONFINITE && rc != QMC_EDEFORM) return rc;
+    if (l > 0)
+      for (size_t u = 0; u < q.size(); ++u) q[u] = 0.5 * (q[u] + qn[u]);
+    nonfinite += r.nonfinite;
+    deform += r.deform_violations;
+    rc = qmc_combine_shifts(m, q.data(), out);  // Eq. (3) on the per-shift values of size 2^(log2_n0 + l)
+    if (rc) return rc;
+    out->nonfinite = nonfinite;
+    out->deform_violations = deform;
+    out->status = nonfinite ? QMC_ENONFINITE : (deform ? QMC_EDEFORM : QMC_OK);
+    if (level_out) *level_out = l;
+    if (per_shift) std::memcpy(per_shift, q.data(), q.size() * sizeof(double));
+    const double mag = std::hypot(out->mean[0], out->mean[1]);
+    const double err = std::hypot(out->err[0], out->err[1]);
+    if (mag > 0.0 && err <= rel_tol * mag) return out->status;
+  }
+  out->status = QMC_ETIMEOUT;
+  return fail(QMC_ETIMEOUT, "relative error %.3g not reached by n = 2^%d", rel_tol, log2_n0 + levels - 1);
 }
 
 int qmc_combine_shifts(int32_t m, const double* per_shift, qmc_result* out) {

@@ -398,9 +398,7 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
       for (int i = 0; i < d; ++i) {
         const int src = kk < mk ? k0 + kk : k0;
         uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
-        C->base.shift64[kk][i] = s64;
-        C->base.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
-        set_shift_tri(C->base, kk, i, (float)(2.0 * shifts[(size_t)src * d + i] - 2.0));
+        set_shift(C->base, kk, i, s64);
       }
     Launch ln;
     ln.func = func;

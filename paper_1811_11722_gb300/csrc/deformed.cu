@@ -79,9 +79,7 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
     for (int kk = 0; kk < mk; ++kk)
       for (int i = 0; i < d; ++i) {
         uint64_t s64 = shift_fixed64(shifts[(size_t)(k0 + kk) * d + i]);
-        P.shift64[kk][i] = s64;
-        P.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
-        set_shift_tri(P, kk, i, (float)(2.0 * shifts[(size_t)(k0 + kk) * d + i] - 2.0));
+        set_shift(P, kk, i, s64);
       }
     Launch ln;
     ln.func = func;

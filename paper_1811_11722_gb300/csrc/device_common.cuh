@@ -75,15 +75,20 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// 1 / x for both halves, given y = -x: q = rcp.approx(y) ~ -1/x, one Newton
-// step in the form q (y q - 2) = (1/x)(1 - e^2) for q = (1 + e)/y.  Taking
-// -x as input (the host negates F's coefficients) leaves no negation on the
-// packed path.
+// 1 / x for both halves, given y = -x (the host negates F's coefficients, so
+// -U^2 F comes out of the packed chains): r = rcp.approx(x), the negation an
+// operand modifier of the scalar reciprocal; e = 1 - x r = fma(y, r, 1),
+// small and exact before its one rounding; then the Newton step r + r e.
+// These are the operations of recip(float), which returns the correctly
+// rounded reciprocal (exhaustively checked over a binade).  A form that
+// rounds y r - 2 ~ -1 + e to float instead would quantise e, itself about
+// one ulp, and bias the values by ~1e-8.
 __device__ __forceinline__ float2 recip_neg2(float2 y) {
-  float2 q;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q.x) : "f"(y.x));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q.y) : "f"(y.y));
-  return mul2(q, fma2(y, q, make_float2(-2.0f, -2.0f)));
+  float2 r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(-y.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(-y.y));
+  const float2 e = fma2(y, r, make_float2(1.0f, 1.0f));
+  return fma2(r, e, r);
 }
 
 template <typename R>
@@ -202,51 +207,46 @@ __device__ __forceinline__ double coord_f64(uint64_t X, const double* kor, int a
   }
 }
 
-// Float-domain coordinates of the fast FP32 sector path.  With the point's
-// doubled base b2 = 2 frac(idx/n) (the 32-bit fraction rounded to 23 bits and
-// placed in a float mantissa, integer and FMA pipes only; doubling is exact)
-// and the shift constant c = 2 Delta - 2,
-// one add gives t = 2 (b + Delta) - 2 in [-2, 2), i.e. y = b + Delta in [0, 2)
-// before the wrap.  (An add with one constant operand encodes directly; an
-// FMA with an immediate 2 and a constant would first load the constant.)
-// Then v = |t| - 1 = +-(2 {y} - 1), so the baker map is
-// z = 1 - |2 {y} - 1| = 1 - |v| = min(|t|, 2 - |t|) with no wrap test at all, and
-// s = min({y}, 1 - {y}) = (1 - |v|) / 2; {y} > 1/2 exactly when t and v have
-// the same sign.
-__device__ __forceinline__ float base2_f32(uint64_t p64) {
-  const uint32_t X = frac32(p64) + 0x100u;         // round to 23 bits (wraps to 0 near 1: periodic)
-  return __fmaf_rn(2.0f, unit_f32(X), -2.0f);      // 2 (x + 1) - 2 = 2x, exact
+// FP32 sector coordinates in 32-bit fixed point, on the integer pipe.
+// Per point and dimension the base B is the fraction idx/n rounded to 32 bits
+// plus a dither (below); per shift X = B + D wraps modulo 1 by itself, and
+//   baker:  M = |(int32) X| = 2^32 min(x, 1 - x), z = M 2^-31,
+//   none:   z = X 2^-32,
+//   Korobov: s = M 2^-32 = min(x, 1 - x), the upper half when X >= 2^31.
+// Each coordinate is rounded to float once, from the exact integer, so z
+// carries a relative (not an absolute 2^-24) rounding error.  For baker and
+// none the power of two goes into the polynomial coefficients (the host
+// prescales them), so the float the kernel uses is M or X itself.
+__device__ __forceinline__ uint32_t base32(uint64_t p64) { return (uint32_t)((p64 + 0x80000000ull) >> 32); }
+
+// Rounding a coordinate that sits on the lattice to float repeats the same
+// few rounding errors in a pattern tied to the lattice (at n ~ 2^24 the point
+// spacing matches the float grid), which biases the sum.  A dither of
+// [-64, 64) units of 2^-32, one per (point, dimension) from a Weyl sequence
+// in j (an odd multiplier per dimension), spans the coarsest float spacing of
+// M (2^7 units) and makes the rounding unbiased; it moves the point by at most
+// 1.5e-8.  It is zero at j = 0, so the lattice point at the origin (a zero
+// shift) stays exactly there.
+__device__ __forceinline__ uint32_t dither32(uint64_t j, int i) {
+  const uint32_t h = (uint32_t)j * (0x9E3779B9u ^ ((uint32_t)i * 0x632BE5AAu));
+  return ((h >> 25) ^ 64u) - 64u;  // two's complement in [-64, 64); 0 for j = 0
 }
 
-// The triangle coordinate from t = b2 + c.
+// X read as a signed 32-bit integer is 2^32 (x - [x >= 1/2]), so
+// |float((int32) X)| = 2^32 min(x, 1 - x), rounded once (rounding is symmetric,
+// and X = 2^31, x = 1/2, converts exactly to -2^31).
 template <int TR, int ALPHA>
-__device__ __forceinline__ float coord_tri_t(float t, const float* kor, float& w) {
+__device__ __forceinline__ float coord_fx(uint32_t X, const float* kor, float& w) {
   if constexpr (TR == TR_NONE) {
-    return __fmaf_rn(0.5f, t, t < 0.0f ? 1.0f : 0.0f);
+    return __uint2float_rn(X);  // z 2^32
   } else {
+    const float a = fabsf(__int2float_rn((int32_t)X));
     if constexpr (TR == TR_BAKER) {
-      // 1 - ||t| - 1| = min(|t|, 2 - |t|): one FP32 add and a min (ALU pipe),
-      // and exact: |t| < 1 is returned as is, 2 - |t| is exact for |t| in [1, 2)
-      const float a = fabsf(t);
-      return fminf(a, 2.0f - a);
+      return a;  // z 2^31
     } else {
-      const float v = fabsf(t) - 1.0f;
-      const float s = __fmaf_rn(-0.5f, fabsf(v), 0.5f);
-      const bool upper = t * v > 0.0f;
-      return korobov_apply<ALPHA>(s, upper, kor, 0, w);
+      return korobov_apply<ALPHA>(a * 0x1p-32f, (int32_t)X < 0, kor, 0, w);
     }
   }
-}
-
-template <int TR, int ALPHA>
-__device__ __forceinline__ float coord_tri(float b2, float c, const float* kor, float& w) {
-  return coord_tri_t<TR, ALPHA>(b2 + c, kor, w);
-}
-
-// The coordinate {y} the triangle form stands for, as a double (sampling output).
-__device__ __forceinline__ double coord_tri_used(float b2, float c) {
-  const double t = (double)(b2 + c);
-  return 0.5 * t + (t < 0.0 ? 1.0 : 0.0);
 }
 
 // ----------------------------------------------------------- polynomials --

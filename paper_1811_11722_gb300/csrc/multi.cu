@@ -64,7 +64,11 @@ int build_multi_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
   const int TR = base.tr, ALPHA = kor3 ? 3 : 0;
   // dense slots of every integrand
   std::vector<std::pair<std::vector<double>, std::vector<double>>> polys(count);
-  for (int s = 0; s < count; ++s) polys[s] = {pack_dense(fs[s].U, d, 1), pack_dense(fs[s].F, d, 2)};
+  for (int s = 0; s < count; ++s) {
+    polys[s] = {pack_dense(fs[s].U, d, 1), pack_dense(fs[s].F, d, 2)};
+    prescale_slots(polys[s].first.data(), d, 1, fx_sigma(TR));  // coordinates arrive divided by fx_sigma
+    prescale_slots(polys[s].second.data(), d, 2, fx_sigma(TR));
+  }
   // one specialised kernel per integrand chunk, compiled on all host cores
   const int chunks = (count + kMultiChunk - 1) / kMultiChunk;
   std::vector<void*> fn(chunks, nullptr);
@@ -123,7 +127,7 @@ int build_multi_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
       for (int kk = 0; kk < kMultiMc; ++kk)  // rows mk.. repeat row k0 (evaluated, never written back)
         for (int i = 0; i < d; ++i) {
           const int src = kk < mk ? k0 + kk : k0;
-          set_shift_tri(M->base, kk, i, (float)(2.0 * shifts[(size_t)src * d + i] - 2.0));
+          set_shift(M->base, kk, i, shift_fixed64(shifts[(size_t)src * d + i]));
         }
       M->s_base = c * kMultiChunk;
       M->count = count;

@@ -117,7 +117,11 @@ static int noalloc_run(int32_t d, uint64_t n, int32_t m, const uint64_t* g, cons
   if (rc) return rc;
   rc = pack_dense_into<R>(f->F, d, 2, P.cF);
   if (rc) return rc;
-  if (fp32) fill_pairs(P, d);
+  if (fp32) {  // the FP32 kernels hand the polynomials z / fx_sigma (exact powers of two)
+    prescale_slots(P.cU, d, 1, fx_sigma(P.tr));
+    prescale_slots(P.cF, d, 2, fx_sigma(P.tr));
+    fill_pairs(P, d);
+  }
   if (P.tr == TR_KOROBOV) {
     double s = 1.0;
     for (int i = 0; i < d; ++i) s *= (double)P.kor[7];
@@ -160,9 +164,7 @@ static int noalloc_run(int32_t d, uint64_t n, int32_t m, const uint64_t* g, cons
       for (int i = 0; i < d; ++i) {
         const int src = kk < mk ? k0 + kk : k0;
         const uint64_t s64 = shift_fixed64(shifts[(size_t)src * d + i]);
-        P.shift64[kk][i] = s64;
-        P.shift32[kk][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
-        set_shift_tri(P, kk, i, (float)(2.0 * shifts[(size_t)src * d + i] - 2.0));
+        set_shift(P, kk, i, s64);
       }
     void* args[4] = {&P, &partial, &counters, &none};
     e = cudaLaunchKernel(func, dim3(nblk), dim3(kThreads), args, 0, st);

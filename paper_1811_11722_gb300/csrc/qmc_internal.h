@@ -69,8 +69,7 @@ struct RuleParams {
   uint32_t gstep[QMC_DMAX];     // (kThreads * g_i) mod n
   uint64_t shift64[kMcMax][QMC_DMAX];
   uint32_t shift32[kMcMax][QMC_DMAX];
-  float2 shiftp[kMcMax / 2][QMC_DMAX];  // fast FP32 sector path: 2 Delta - 2 of shifts
-                                        // (2p, 2p + 1) side by side for packed adds
+  uint32_t shiftx[kMcMax][QMC_DMAX];    // FP32 sector path: Delta rounded to 32-bit fixed point
   R kor[8];                // Korobov z(s) = s^(a+1) sum_k kor[k] s^k on s <= 1/2;
                            // kor[7] = (2a+1)!/(a!)^2 (general kernel weight)
   R cU[kPolyCoefMax];      // nested-Horner U (dense kernels)
@@ -87,15 +86,49 @@ struct RuleParams {
   R eps_inv[kEpsMax];      // 1 / k for k = 1..kEpsMax
 };
 
-// Shift constant 2 Delta_k - 2 of dimension i in the paired layout.
+// Shift row k, dimension i, from its 64-bit fixed-point value s64 =
+// round(Delta 2^64): the u64 copy (FP64 paths), the 32-bit copy with the
+// 2^-24 rounding offset of the 23-bit float conversion folded in (FP32
+// separable, general and deformed paths), and the plain 32-bit rounding
+// (FP32 sector paths).
 template <typename R>
-__host__ __device__ inline float shift_tri(const RuleParams<R>& P, int k, int i) {
-  return (k & 1) ? P.shiftp[k >> 1][i].y : P.shiftp[k >> 1][i].x;
+__host__ __device__ inline void set_shift(RuleParams<R>& P, int k, int i, uint64_t s64) {
+  P.shift64[k][i] = s64;
+  P.shift32[k][i] = (uint32_t)((s64 + 0x80000000ull) >> 32) + 0x100u;
+  P.shiftx[k][i] = (uint32_t)((s64 + 0x80000000ull) >> 32);
 }
-template <typename R>
-__host__ __device__ inline void set_shift_tri(RuleParams<R>& P, int k, int i, float v) {
-  if (k & 1) P.shiftp[k >> 1][i].y = v;
-  else P.shiftp[k >> 1][i].x = v;
+
+// Scale nested-Horner slots (poly_dense order) by sigma^degree, so that the
+// polynomial takes its coordinates divided by sigma.  sigma is a power of
+// two, so the scaled evaluation rounds exactly as the unscaled one.
+template <typename T>
+__host__ __device__ inline void prescale_slots(T* c, int D, int K, double sigma) {
+  const double s1 = sigma, s2 = sigma * sigma, s3 = s2 * sigma;
+  if (K == 1) {
+    for (int i = 0; i < D; ++i) c[1 + i] = (T)((double)c[1 + i] * s1);
+    return;
+  }
+  int off = 1;
+  for (int i = 0; i < D; ++i) {
+    c[off] = (T)((double)c[off] * s1);
+    ++off;
+    for (int j = i; j < D; ++j) {
+      c[off] = (T)((double)c[off] * s2);
+      ++off;
+      if (K == 3)
+        for (int k = j; k < D; ++k) {
+          c[off] = (T)((double)c[off] * s3);
+          ++off;
+        }
+    }
+  }
+}
+
+// Coordinate scale of the FP32 sector path per transform code (the kernels
+// hand U and F the coordinate divided by it): none 2^-32, baker 2^-31,
+// Korobov 1 (its z is computed in float from s).
+__host__ __device__ inline double fx_sigma(int tr) {
+  return tr == TR_NONE ? 0x1p-32 : (tr == TR_BAKER ? 0x1p-31 : 1.0);
 }
 
 // Packed FP32 path: (c, c) pairs of U's degree-1 nested-Horner slots, then of

@@ -83,12 +83,13 @@ __device__ __forceinline__ typename FixT<R>::T shift_of(const RuleParams<R>& P, 
   else return P.shift64[k][i];
 }
 
-// Per-point base of the fast sector path: float frac for FP32, fixed point for FP64.
+// Per-point base of the fast sector path: 32-bit fixed point (dithered) for
+// FP32, 64-bit fixed point for FP64.
 template <typename R>
 struct SecBase;
 template <>
 struct SecBase<float> {
-  using T = float;
+  using T = uint32_t;
 };
 template <>
 struct SecBase<double> {
@@ -135,19 +136,17 @@ struct DensePolys {
 template <typename R, int KU, int KF>
 constexpr bool kPacked = sizeof(R) == 4 && KU == 1 && KF == 2;
 
-// Shifts 2p and 2p + 1 at one point: the triangle coordinates start with one
-// packed add, the abs steps are scalar (abs is a free operand modifier of a
-// scalar add), U and -F are packed Horner chains, then -U^2 F and the
-// reciprocal (recip_neg2) are packed.
+// Shifts 2p and 2p + 1 at one point: the fixed-point coordinates (integer add,
+// one conversion each), U and -F as packed Horner chains, then -U^2 F and the
+// reciprocal (recip_neg2) packed.
 template <int D, int TR, int ALPHA, int KU, int KF, class POLY>
-__device__ __forceinline__ float2 sector_value2(const RuleParams<float>& P, const float* base, int p) {
+__device__ __forceinline__ float2 sector_value2(const RuleParams<float>& P, const uint32_t* base, int p) {
   float2 z[D];
   float wa = 1.0f, wb = 1.0f;
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    const float2 t = add2(make_float2(base[i], base[i]), P.shiftp[p][i]);
-    z[i] = make_float2(coord_tri_t<TR, ALPHA>(t.x, P.kor, wa), coord_tri_t<TR, ALPHA>(t.y, P.kor, wb));
-  }
+  for (int i = 0; i < D; ++i)
+    z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], P.kor, wa),
+                       coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p + 1][i], P.kor, wb));
   float2 U, Fn;
   POLY::template eval2<D, KU, KF>(P, z, U, Fn);
   float2 v = recip_neg2(mul2(mul2(U, U), Fn));
@@ -161,7 +160,7 @@ __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename
   R w = R(1);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], shift_tri(P, k, i), P.kor, w);
+    if constexpr (sizeof(R) == 4) z[i] = coord_fx<TR, ALPHA>(base[i] + P.shiftx[k][i], P.kor, w);
     else z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
   }
   R U, F;
@@ -179,7 +178,7 @@ __device__ __forceinline__ R eps_point(const RuleParams<R>& P, const typename Se
   R w = R(1);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    if constexpr (sizeof(R) == 4) z[i] = coord_tri<TR, ALPHA>(base[i], shift_tri(P, k, i), P.kor, w);
+    if constexpr (sizeof(R) == 4) z[i] = coord_fx<TR, ALPHA>(base[i] + P.shiftx[k][i], P.kor, w);
     else z[i] = coord<R, TR, ALPHA>(base[i] + shift_of(P, k, i), P.kor, P.alpha, w);
   }
   DensePolys::template eval<D, 1, 2, R>(P, z, U, F);
@@ -188,15 +187,17 @@ __device__ __forceinline__ R eps_point(const RuleParams<R>& P, const typename Se
   return v;
 }
 
+// Per-point base of coordinate i at point j (FP32: 32-bit fixed point plus the
+// dither of point j, dimension i; FP64: 64-bit fixed point).
 template <typename R>
-__device__ __forceinline__ typename SecBase<R>::T sec_base(uint32_t idx, const Recip& rc) {
-  if constexpr (sizeof(R) == 4) return base2_f32(frac64(idx, rc));
+__device__ __forceinline__ typename SecBase<R>::T sec_base(uint32_t idx, const Recip& rc, uint64_t j, int i) {
+  if constexpr (sizeof(R) == 4) return base32(frac64(idx, rc)) + dither32(j, i);
   else return frac64(idx, rc);
 }
 
 template <typename R>
 __device__ __forceinline__ double sec_coord_used(const RuleParams<R>& P, typename SecBase<R>::T b, int k, int i) {
-  if constexpr (sizeof(R) == 4) return coord_tri_used(b, shift_tri(P, k, i));
+  if constexpr (sizeof(R) == 4) return (double)(uint32_t)(b + P.shiftx[k][i]) * 0x1p-32;
   else return coord_used<R>(b + shift_of(P, k, i));
 }
 
@@ -211,7 +212,7 @@ __device__ void sector_sample(const RuleParams<R>& P, const SampleIO& sio) {
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     uint32_t idx = lattice_index(j, P.g[i], P.n);
-    base[i] = sec_base<R>(idx, P.rc);
+    base[i] = sec_base<R>(idx, P.rc, j, i);
     if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
     if (sio.coord) sio.coord[(size_t)s * D + i] = sec_coord_used<R>(P, base[i], k, i);
   }
@@ -302,7 +303,7 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
     for (int s = 0; s < steps; ++s) {
       typename SecBase<R>::T base[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) base[i] = sec_base<R>(idx[i], P.rc);
+      for (int i = 0; i < D; ++i) base[i] = sec_base<R>(idx[i], P.rc, j0 + (uint64_t)s * kThreads, i);
       if constexpr (kPack) {
 #pragma unroll
         for (int p = 0; p < MC / 2; ++p) {
@@ -673,7 +674,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       uint32_t idx = lattice_index(j, P.g[i], P.n);
-      base[i] = sec_base<R>(idx, P.rc);
+      base[i] = sec_base<R>(idx, P.rc, j, i);
       if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
       if (sio.coord) sio.coord[(size_t)s * D + i] = sec_coord_used<R>(P, base[i], k, i);
     }
@@ -707,7 +708,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int s = 0; s < steps; ++s) {
       BT base[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) base[i] = sec_base<R>(idx[i], P.rc);
+      for (int i = 0; i < D; ++i) base[i] = sec_base<R>(idx[i], P.rc, j0 + (uint64_t)s * kThreads, i);
 #pragma unroll
       for (int kk = 0; kk < MC; ++kk) {
         R U, F;
@@ -739,15 +740,16 @@ __device__ __forceinline__ void eps_body2(const RuleParams<float>& P, double* __
     if (s >= sio.count) return;
     const uint64_t j = sio.j[s];
     const int k = sio.k[s];
-    float base[D], z[D];
+    uint32_t base[D];
+    float z[D];
     float w = 1.0f;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       uint32_t idx = lattice_index(j, P.g[i], P.n);
-      base[i] = sec_base<float>(idx, P.rc);
+      base[i] = sec_base<float>(idx, P.rc, j, i);
       if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
       if (sio.coord) sio.coord[(size_t)s * D + i] = sec_coord_used<float>(P, base[i], k, i);
-      z[i] = coord_tri<TR, ALPHA>(base[i], shift_tri(P, k, i), P.kor, w);
+      z[i] = coord_fx<TR, ALPHA>(base[i] + P.shiftx[k][i], P.kor, w);
     }
     float U, F;
     POLY::template eval<D, 1, 2, float>(P, z, U, F);
@@ -782,18 +784,17 @@ __device__ __forceinline__ void eps_body2(const RuleParams<float>& P, double* __
 #pragma unroll
     for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
     for (int st = 0; st < steps; ++st) {
-      float base[D];
+      uint32_t base[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) base[i] = sec_base<float>(idx[i], P.rc);
+      for (int i = 0; i < D; ++i) base[i] = sec_base<float>(idx[i], P.rc, j0 + (uint64_t)st * kThreads, i);
 #pragma unroll
       for (int p = 0; p < MC / 2; ++p) {
         float2 z[D];
         float wa = 1.0f, wb = 1.0f;
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-          const float2 t = add2(make_float2(base[i], base[i]), P.shiftp[p][i]);
-          z[i] = make_float2(coord_tri_t<TR, ALPHA>(t.x, P.kor, wa), coord_tri_t<TR, ALPHA>(t.y, P.kor, wb));
-        }
+        for (int i = 0; i < D; ++i)
+          z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], P.kor, wa),
+                             coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p + 1][i], P.kor, wb));
         float2 U, Fn;
         POLY::template eval2<D, 1, 2>(P, z, U, Fn);
         const float2 uu = mul2(U, U);
@@ -929,18 +930,17 @@ __device__ __forceinline__ void multi_body(const MultiParams& M, double* __restr
 #pragma unroll
     for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
     for (int st = 0; st < steps; ++st) {
-      float base[D];
+      uint32_t base[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) base[i] = sec_base<float>(idx[i], P.rc);
+      for (int i = 0; i < D; ++i) base[i] = sec_base<float>(idx[i], P.rc, j0 + (uint64_t)st * kThreads, i);
 #pragma unroll
       for (int p = 0; p < MC / 2; ++p) {
         float2 z[D];
         float wa = 1.0f, wb = 1.0f;
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-          const float2 t = add2(make_float2(base[i], base[i]), P.shiftp[p][i]);
-          z[i] = make_float2(coord_tri_t<TR, ALPHA>(t.x, P.kor, wa), coord_tri_t<TR, ALPHA>(t.y, P.kor, wb));
-        }
+        for (int i = 0; i < D; ++i)
+          z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], P.kor, wa),
+                             coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p + 1][i], P.kor, wb));
         const float2 w = make_float2(wa, wb);
 #pragma unroll
         for (int s = 0; s < SC; ++s) {

@@ -130,6 +130,9 @@ def lib():
                                                 vp, vp]
             L.qmc_integrate_multi.argtypes = [i32, u64, i32, vp, vp, qmc_transform, i32, vp, vp, vp, vp]
             L.qmc_multi_plan_create.argtypes = [i32, u64, i32, vp, vp, qmc_transform, i32, vp, ctypes.POINTER(vp)]
+            L.qmc_make_lattice_embedded.argtypes = [i32, i32, i32, vp, i32, u64, vp]
+            L.qmc_integrate_extensible.argtypes = [i32, i32, i32, vp, i32, vp, qmc_transform, P_int, ctypes.c_double,
+                                                   vp, vp, vp, vp]
             L.qmc_last_error.restype = ctypes.c_char_p
             L.qmc_version.restype = i32
             for name in ("qmc_make_lattice", "qmc_integrate", "qmc_plan_create", "qmc_plan_execute",
@@ -138,7 +141,8 @@ def lib():
                          "qmc_batch_plan_tune", "qmc_sample_points", "qmc_cv_train", "qmc_integrate_cv",
                          "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts", "qmc_measure_peaks",
                          "qmc_integrate_to_tolerance", "qmc_integrate_eps", "qmc_eps_plan_create",
-                         "qmc_sample_points_eps", "qmc_integrate_multi", "qmc_multi_plan_create"):
+                         "qmc_sample_points_eps", "qmc_integrate_multi", "qmc_multi_plan_create", "qmc_make_lattice_embedded",
+                         "qmc_integrate_extensible"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -407,6 +411,32 @@ def qmc_sample_points(d, n, m, g, shifts, t, f: Integrand, j, k, want_idx=True, 
     _check(lib().qmc_sample_points(d, n, m, _ptr(g), _ptr(shifts), t, f.ref, cnt, _ptr(j), _ptr(k), _ptr(vals),
                                    _ptr(idx), _ptr(crd), ctypes.c_void_p(stream)))
     return vals, idx, crd
+
+
+# --------------------------------------------------- embedded lattices --
+
+def qmc_make_lattice_embedded(d: int, log2_nmin: int, log2_nmax: int, gamma, candidates: int = 1 << 30,
+                              seed: int = 0) -> np.ndarray:
+    gamma = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+    g = np.zeros(d, dtype=np.uint64)
+    _check(lib().qmc_make_lattice_embedded(d, log2_nmin, log2_nmax, _ptr(gamma), int(min(candidates, 2**31 - 1)),
+                                           seed, _ptr(g)))
+    return g
+
+
+def qmc_integrate_extensible(d, log2_n0, levels, g, m, shifts, t, f: Integrand, rel_tol, stream=0):
+    """Returns (qmc_result, level reached, per_shift[m, 2], tolerance met)."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    res = qmc_result()
+    ps = np.zeros((m, 2))
+    lvl = ctypes.c_int32(-1)
+    rc = lib().qmc_integrate_extensible(d, log2_n0, levels, _ptr(g), m, _ptr(shifts), t, f.ref, float(rel_tol),
+                                        ctypes.byref(res), _ptr(ps), ctypes.byref(lvl), ctypes.c_void_p(stream))
+    if rc == QMC_ETIMEOUT:
+        return res, int(lvl.value), ps, False
+    _check(rc, allow_warnings=True)
+    return res, int(lvl.value), ps, True
 
 
 # ------------------------------------------------------- epsilon expansion --

@@ -185,3 +185,53 @@ def test_make_lattice_matches_oracle_cbc(Q, oracle_lib, n):
     assert abs(e_lib - e_ref) <= 1e-12 * e_ref
     if n >= 101:
         assert np.array_equal(g, ref)
+
+
+# ------------------------------------------------------ embedded lattices --
+
+def _embedded_T(oracle_lib, g, gamma, kmin, K):
+    """max_k 4^k e^2_{2^k}(g) with the oracle's worst-case error."""
+    s = len(g)
+    return max(4.0 ** k * oracle_lib.cbc_error(s, 1 << k, np.asarray(g, dtype=np.uint64) % (1 << k), gamma[:s])
+               for k in range(kmin, K + 1))
+
+
+def test_embedded_lattice_exhaustive_matches_oracle(Q, oracle_lib):
+    """All odd candidates at N = 2^8 (sizes 2^3..2^8), d = 3: every component
+    attains the minimum of the oracle-evaluated criterion.  Symmetric
+    candidates (z and -z^-1 mod N give mirrored lattices) tie to ~1e-13, where
+    rounding picks one, so the minimum is matched to 1e-10 relative."""
+    d, kmin, K = 3, 3, 8
+    gam = I.product_weights(d)
+    g = Q.qmc_make_lattice_embedded(d, kmin, K, gam)
+    assert g[0] == 1 and np.all(g % 2 == 1) and np.all(g < (1 << (K - 1)))
+    for s in range(1, d):
+        cands = list(range(1, 1 << (K - 1), 2))
+        T = np.array([_embedded_T(oracle_lib, list(g[:s]) + [z], gam, kmin, K) for z in cands])
+        chosen = T[cands.index(int(g[s]))]
+        assert chosen <= T.min() * (1 + 1e-10), (s, g[s], cands[int(np.argmin(T))], chosen, T.min())
+        # every candidate clearly better than the chosen one would be a mistake
+        assert np.sum(T < chosen * (1 - 1e-10)) == 0
+
+
+def test_embedded_lattice_subset_is_deterministic(Q, oracle_lib):
+    """With a drawn candidate subset the vector depends only on the seed, and it
+    beats the degenerate vector g = (1, 1, ..., 1) at every embedded size."""
+    d, kmin, K = 4, 6, 14
+    gam = I.product_weights(d)
+    a = Q.qmc_make_lattice_embedded(d, kmin, K, gam, candidates=32, seed=7)
+    b = Q.qmc_make_lattice_embedded(d, kmin, K, gam, candidates=32, seed=7)
+    c = Q.qmc_make_lattice_embedded(d, kmin, K, gam, candidates=32, seed=8)
+    assert np.array_equal(a, b) and a[0] == 1 and np.all(a % 2 == 1)
+    assert not np.array_equal(a, c)
+    for k in range(kmin, K + 1):
+        n = 1 << k
+        assert oracle_lib.cbc_error(d, n, a % n, gam) < oracle_lib.cbc_error(d, n, np.ones(d, np.uint64), gam)
+
+
+@pytest.mark.parametrize("args", [(0, 3, 8), (17, 3, 8), (3, 0, 8), (3, 9, 8), (3, 3, 31)])
+def test_embedded_lattice_validation(Q, args):
+    d, kmin, K = args
+    with pytest.raises(Q.QmcError) as ei:
+        Q.qmc_make_lattice_embedded(d, kmin, K, np.ones(max(d, 1)))
+    assert ei.value.status == Q.QMC_EINVAL

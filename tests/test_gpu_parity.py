@@ -144,7 +144,8 @@ def test_sector_d6_fp32(Q, oracle_lib, nthreads, transform, alpha):
     g = I.random_generating_vector(I.SplitMix64(8), 6, p.n)
     gpu, ps = gpu_run(Q, p, g, "fp32")
     ref = oracle_lib.integrate(p, g, nthreads=nthreads)
-    assert np.all(np.abs(ps[:, 0] - ref["q"][:, 0]) <= 2e-7 * np.abs(ref["q"][:, 0]))
+    rel = np.abs(ps[:, 0] - ref["q"][:, 0]) / np.abs(ref["q"][:, 0])
+    assert np.all(rel <= 2e-7), (int(np.argmax(rel)), float(rel.max()), ps[:, 0].tolist())
     assert abs(gpu["mean"][0] - ref["mean"][0]) <= 2e-7 * abs(ref["mean"][0])
 
 
@@ -295,7 +296,8 @@ def test_config2_full_size_fp32_vs_oracle(Q, oracle_lib, lattices, nthreads):
     g = gvec(lattices, p)
     gpu, ps = gpu_run(Q, p, g, "fp32")
     ref = oracle_lib.integrate(p, g, nthreads=nthreads)
-    assert np.all(np.abs(ps[:, 0] - ref["q"][:, 0]) <= 2e-7 * np.abs(ref["q"][:, 0]))
+    rel = np.abs(ps[:, 0] - ref["q"][:, 0]) / np.abs(ref["q"][:, 0])
+    assert np.all(rel <= 2e-7), (int(np.argmax(rel)), float(rel.max()), ps[:, 0].tolist())
     assert abs(gpu["mean"][0] - ref["mean"][0]) <= 2e-7 * abs(ref["mean"][0])
     g64, ps64 = gpu_run(Q, p, g, "fp64")
     assert_fp64_parity(g64, ps64, ref)
@@ -607,3 +609,73 @@ def test_integrate_to_tolerance(Q):
     assert direct.mean[0] == res.mean[0]
     res, lvl, ok = Q.qmc_integrate_to_tolerance(6, ladder[:2], gs[:2], 16, p.shifts, t, f, 1e-16)
     assert not ok and lvl == 1 and res.status == Q.QMC_ETIMEOUT
+
+
+def test_fp32_rounding_unbiased_at_full_size(Q, lattices):
+    """At n = 16777213 the lattice spacing equals the float grid of the
+    coordinates, so rounding them to float repeats a lattice-tied pattern of
+    errors.  The FP32 path rounds each coordinate once from 32-bit fixed point
+    with a per-point dither; its per-shift values must then agree with the FP64
+    path to 2e-10 relative (the QMC scatter between shifts is ~5e-9), and the
+    mean to a tenth of the FP64 error estimate."""
+    p = I.config2(n=16777213, m=32)
+    g = gvec(lattices, p)
+    t = Q.transform(p.transform, p.alpha)
+    r32, ps32 = Q.qmc_integrate(p.d, p.n, p.m, g, p.shifts, t, Q.integrand_from_problem(p, "fp32"),
+                                want_per_shift=True)
+    r64, ps64 = Q.qmc_integrate(p.d, p.n, p.m, g, p.shifts, t, Q.integrand_from_problem(p, "fp64"),
+                                want_per_shift=True)
+    q = abs(r64.mean[0])
+    assert np.all(np.abs(ps32[:, 0] - ps64[:, 0]) <= 2e-10 * q), np.max(np.abs(ps32[:, 0] - ps64[:, 0])) / q
+    assert abs(r32.mean[0] - r64.mean[0]) <= 0.1 * r64.err[0]
+
+
+@pytest.mark.parametrize("transform,alpha", [("baker", 0), ("korobov", 3), ("none", 0)])
+def test_fp32_fold_and_origin_points(Q, oracle_lib, transform, alpha):
+    """FP32 coordinates at the fold x = 1/2 (fixed point 2^31, the most
+    negative 32-bit integer when read as signed) and at the origin: point j = 0
+    under shifts with coordinates 0.5 and 0.0 exactly, against the oracle."""
+    p = I.config2(n=100003, m=4)
+    p.transform, p.alpha = transform, alpha
+    p.shifts = np.array([[0.5] * 6, [0.0] * 6, [0.5, 0.0, 0.5, 0.0, 0.5, 0.0], [0.25, 0.5, 0.75, 0.0, 0.5, 0.125]])
+    g = I.random_generating_vector(I.SplitMix64(9), 6, p.n)
+    js = np.zeros(4, dtype=np.uint64)
+    ks = np.arange(4, dtype=np.int32)
+    vals, _, crd = Q.qmc_sample_points(p.d, p.n, p.m, g, p.shifts, Q.transform(transform, alpha),
+                                       Q.integrand_from_problem(p, "fp32"), js, ks)
+    for s in range(4):
+        v, _, ox, _, _ = oracle_lib.point(p, g, int(ks[s]), 0)
+        assert np.array_equal(crd[s], ox), (s, crd[s], ox)
+        assert abs(vals[s, 0] - v[0]) <= 4e-6 * abs(v[0]) + 1e-300, (s, vals[s, 0], v[0])
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-9)])
+def test_extensible_levels_reproduce_the_direct_rule(Q, oracle_lib, precision, tol):
+    """Doubling from n = 2^10 to 2^14 by evaluating only the new half of the
+    points each time gives the size-2^14 rule itself (per shift), and the
+    oracle's value for it."""
+    p = I.config2(n=1 << 14, m=8)
+    g = Q.qmc_make_lattice_embedded(6, 10, 14, p.gamma, candidates=64, seed=3)
+    t = Q.transform(p.transform, p.alpha)
+    f = Q.integrand_from_problem(p, precision)
+    res, lvl, ps, ok = Q.qmc_integrate_extensible(6, 10, 5, g, 8, p.shifts, t, f, 1e-300)
+    assert not ok and lvl == 4 and res.status == Q.QMC_ETIMEOUT
+    direct, ps_d = Q.qmc_integrate(6, 1 << 14, 8, g % (1 << 14), p.shifts, t, f, want_per_shift=True)
+    assert np.all(np.abs(ps[:, 0] - ps_d[:, 0]) <= tol * np.abs(ps_d[:, 0]))
+    ref = oracle_lib.integrate(p, g % (1 << 14))
+    assert np.all(np.abs(ps[:, 0] - ref["q"][:, 0]) <= (1e-12 if precision == "fp64" else 2e-7) * np.abs(ref["q"][:, 0]))
+
+
+def test_extensible_stops_at_tolerance(Q):
+    """The doubling stops at the first size whose Eq. (3) relative error meets
+    the target; the previous size did not."""
+    p = I.config2(m=16)
+    g = Q.qmc_make_lattice_embedded(6, 12, 24, p.gamma, candidates=32, seed=1)
+    t = Q.transform(p.transform, p.alpha)
+    f = Q.integrand_from_problem(p, "fp32")
+    res, lvl, ps, ok = Q.qmc_integrate_extensible(6, 12, 13, g, 16, p.shifts, t, f, 1e-7)
+    assert ok and 0 < lvl <= 12
+    assert res.err[0] <= 1e-7 * abs(res.mean[0])
+    n_prev = 1 << (12 + lvl - 1)
+    prev, _ = Q.qmc_integrate(6, n_prev, 16, g % n_prev, p.shifts, t, f)
+    assert prev.err[0] > 1e-7 * abs(prev.mean[0])
