@@ -84,6 +84,10 @@ def _configure(L):
     L.orc_cv_integral.restype = dbl
     L.orc_cv_loss_grad.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp]
     L.orc_cv_loss_grad.restype = dbl
+    L.orc_cv_loss_grad_bf16.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp]
+    L.orc_cv_loss_grad_bf16.restype = dbl
+    L.orc_bf16.argtypes = [dbl]
+    L.orc_bf16.restype = dbl
     return L
 
 
@@ -268,6 +272,21 @@ def cv_loss_grad(d, R, K, F, x, h, a):
     grad = np.zeros(R * d * K)
     loss = lib().orc_cv_loss_grad(d, R, K, F, h.shape[0], _ptr(x), _ptr(h), _ptr(a), _ptr(grad))
     return float(loss), grad
+
+
+def cv_loss_grad_bf16(d, R, K, F, x, h, a):
+    """(loss, grad[R*d*K]) of the fit with BF16-rounded contraction operands, FP64 sums."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    h = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+    grad = np.zeros(R * d * K)
+    loss = lib().orc_cv_loss_grad_bf16(d, R, K, F, h.shape[0], _ptr(x), _ptr(h), _ptr(a), _ptr(grad))
+    return float(loss), grad
+
+
+def bf16(v: float) -> float:
+    """v rounded to float, then to bfloat16 (nearest, ties to even)."""
+    return float(lib().orc_bf16(float(v)))
 
 
 def cbc_error(d: int, n: int, g, gamma) -> float:

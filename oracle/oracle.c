@@ -381,6 +381,64 @@ double orc_cv_loss_grad(int d, int R, int K, int F, int P, const double* x, cons
   return neum_get(&loss) / (double)P;
 }
 
+/* The fit's contractions on BF16 operands (the configuration's "BF16
+ * inputs, FP32 accumulate" for training the surrogate): the same loss and
+ * gradient as orc_cv_loss_grad, with every operand of the two contractions
+ * rounded first to float and then to bfloat16 (round to nearest, ties to
+ * even) -- the basis values cos(F pi k x), the parameters a, and the factor
+ * 2 e prod_{i' != i} C_ri' / P of the gradient -- and their exact products
+ * summed in FP64. */
+double orc_bf16(double v) {
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u) return (double)f; /* Inf / NaN kept */
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+double orc_cv_loss_grad_bf16(int d, int R, int K, int F, int P, const double* x, const double* h, const float* a,
+                             double* grad) {
+  int na = R * d * K;
+  for (int q = 0; q < na; ++q) grad[q] = 0.0;
+  double* C = (double*)malloc(sizeof(double) * R * d);
+  double* cs = (double*)malloc(sizeof(double) * d * K);
+  double* ab = (double*)malloc(sizeof(double) * na);
+  for (int q = 0; q < na; ++q) ab[q] = orc_bf16((double)a[q]);
+  neum_t loss = {0, 0};
+  for (int j = 0; j < P; ++j) {
+    const double* xj = x + (size_t)j * d;
+    for (int i = 0; i < d; ++i)
+      for (int k = 0; k < K; ++k) cs[i * K + k] = orc_bf16(cos((double)F * M_PI * (double)k * xj[i]));
+    double g = 0.0;
+    for (int r = 0; r < R; ++r) {
+      double prod = 1.0;
+      for (int i = 0; i < d; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += ab[(r * d + i) * K + k] * cs[i * K + k];
+        C[r * d + i] = s;
+        prod *= s;
+      }
+      g += prod;
+    }
+    double e = g - h[j];
+    neum_add(&loss, e * e);
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < d; ++i) {
+        double other = 1.0;
+        for (int i2 = 0; i2 < d; ++i2)
+          if (i2 != i) other *= C[r * d + i2];
+        const double dg = orc_bf16(2.0 * e * other / (double)P);
+        for (int k = 0; k < K; ++k) grad[(r * d + i) * K + k] += dg * cs[i * K + k];
+      }
+  }
+  free(C);
+  free(cs);
+  free(ab);
+  return neum_get(&loss) / (double)P;
+}
+
 /* ------------------------------------------------------------- the rule --- */
 
 /* Lattice index of Eq. (2): idx_i = ((j-1) g_i) mod n with j-1 = jm1, exact in 128 bits. */

@@ -15,11 +15,22 @@
 // rule's estimate beside the control-variate one and the caller keeps
 // whichever has the smaller Eq. (3) error.
 //
-// Training kernels (FP32 CUDA cores, FP64 loss):
-//   cv_basis     B[i][j][k] = cos(F pi k x_ji) for the pilot points
-//   cv_forward   C_ri(x_j), g_j, e_j = 2 (g_j - h_j)/P, D[i][j][r] = e_j prod_{i'!=i} C_ri'
+// Training kernels.  The two contractions of the fit run on tensor cores
+// (warp-level BF16 MMA, FP32 accumulation); the loss is summed in FP64:
+//   cv_basis     B[i][j][k] = cos(F pi k x_ji) for the pilot points, rounded to
+//                BF16, in two layouts: Bf[i][j][k] (forward) and Bt[i][k][j]
+//                (backward); padding points j >= P are zero rows
+//   cv_forward   C_ri(x_j) = sum_k B a, g_j, e_j = 2 (g_j - h_j)/P and the factor
+//                D[i][j][r] = e_j prod_{i'!=i} C_ri' (BF16, as DgT[i][r][j])
 //   cv_backward  grad_part[c][i][r][k] = sum_{j in chunk c} D[i][j][r] B[i][j][k]
 //   cv_adam      grad = sum_c grad_part (fixed order), Adam step, cosine-decayed rate
+// Each contraction is, per dimension, (points x 32) (32 x 16) forward and
+// (16 x points) (points x 32) backward: 16 or 32 output columns.  The
+// warp-level MMA keeps a point's 16 values C_ri in the registers of the lanes
+// that multiply them across dimensions and differentiate the product, so
+// nothing between the contraction and the loss goes through memory.  The
+// estimator (the lattice rule with g subtracted) keeps FP32 basis values, as
+// its bias would otherwise exceed the rule's error.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,48 +51,69 @@ __global__ void cv_iota_kernel(uint64_t* j, int P) {
   if (t < P) j[t] = (uint64_t)t;
 }
 
-__global__ void cv_basis_kernel(const double* __restrict__ x, int P, int d, float freq, float* __restrict__ B) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (i, j)
-  if (t >= P * d) return;
-  const int i = t / P, j = t % P;
-  const double xv = x[(size_t)j * d + i];
-  float* out = B + ((size_t)i * P + j) * kCvK;
+__global__ void cv_basis_kernel(const double* __restrict__ x, int P, int Ppad, int d, float freq,
+                                uint16_t* __restrict__ Bf, uint16_t* __restrict__ Bt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (i, j), j fastest: Bt stores coalesce
+  if (t >= Ppad * d) return;
+  const int i = t / Ppad, j = t % Ppad;
+  const double xv = j < P ? x[(size_t)j * d + i] : 0.0;
+  uint16_t* out = Bf + ((size_t)i * Ppad + j) * kCvK;
 #pragma unroll 4
-  for (int k = 0; k < kCvK; ++k) out[k] = (float)cospi((double)freq * (double)k * xv);
+  for (int k = 0; k < kCvK; ++k) {
+    const uint16_t b = j < P ? bf16_bits((float)cospi((double)freq * (double)k * xv)) : (uint16_t)0;
+    out[k] = b;
+    Bt[((size_t)i * kCvK + k) * Ppad + j] = b;
+  }
 }
 
-// grid (chunks, d); thread t owns outputs (r, k) = (t / 16, 2 (t % 16) + {0, 1}).
-__global__ void __launch_bounds__(256)
-    cv_backward_kernel(const float* __restrict__ B, const float* __restrict__ Dg, int P, int d,
+// Backward pass on tensor cores: grid (chunks, d), 4 warps per CTA, warp w
+// taking a quarter of the chunk's points in steps of 16.  Per step, A is the
+// factor DgT[i][r][j] (16 r x 16 points) and B the basis Bt[i][k][j]
+// (16 points x 32 k, four k-tiles); the 16 x 32 gradient block of dimension i
+// accumulates in FP32 registers, and the four warps' blocks are added in a
+// fixed order through shared memory.
+__global__ void __launch_bounds__(128)
+    cv_backward_kernel(const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ DgT, int Ppad, int d,
                        float* __restrict__ grad_part) {
-  __shared__ float ds[64][kCvR];
-  __shared__ float bs[64][kCvK + 1];
+  __shared__ float blk[4][kCvR][kCvK];
   const int c = blockIdx.x, i = blockIdx.y;
-  const int r = threadIdx.x / 16, k0 = 2 * (threadIdx.x % 16);
-  const int j_begin = c * kCvChunk, j_end = min(P, j_begin + kCvChunk);
-  float g0 = 0.0f, g1 = 0.0f;
-  for (int jt = j_begin; jt < j_end; jt += 64) {
-    const int cnt = min(64, j_end - jt);
-    __syncthreads();
-    for (int q = threadIdx.x; q < 64 * kCvR; q += 256) {
-      const int jj = q / kCvR, rr = q % kCvR;
-      ds[jj][rr] = jj < cnt ? Dg[((size_t)i * P + jt + jj) * kCvR + rr] : 0.0f;
-    }
-    for (int q = threadIdx.x; q < 64 * kCvK; q += 256) {
-      const int jj = q / kCvK, kk = q % kCvK;
-      bs[jj][kk] = jj < cnt ? B[((size_t)i * P + jt + jj) * kCvK + kk] : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int jj = 0; jj < 64; ++jj) {
-      const float dv = ds[jj][r];
-      g0 = fmaf(dv, bs[jj][k0], g0);
-      g1 = fmaf(dv, bs[jj][k0 + 1], g1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int quarter = kCvChunk / 4;
+  const int jb = c * kCvChunk + warp * quarter, je = min(Ppad, jb + quarter);
+  float acc[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[nt][v] = 0.0f;
+  const uint16_t* dA = DgT + ((size_t)i * kCvR + g) * Ppad;
+  const uint16_t* dB = dA + 8 * (size_t)Ppad;
+  for (int j0 = jb; j0 < je; j0 += 16) {
+    const int j = j0 + 2 * t;
+    const uint32_t a0 = *reinterpret_cast<const uint32_t*>(dA + j);
+    const uint32_t a1 = *reinterpret_cast<const uint32_t*>(dB + j);
+    const uint32_t a2 = *reinterpret_cast<const uint32_t*>(dA + j + 8);
+    const uint32_t a3 = *reinterpret_cast<const uint32_t*>(dB + j + 8);
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const uint16_t* bp = Bt + ((size_t)i * kCvK + 8 * nt + g) * Ppad + j;
+      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bp);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bp + 8);
+      mma_bf16_16x8x16(acc[nt], a0, a1, a2, a3, b0, b1);
     }
   }
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    blk[warp][g][8 * nt + 2 * t] = acc[nt][0];
+    blk[warp][g][8 * nt + 2 * t + 1] = acc[nt][1];
+    blk[warp][g + 8][8 * nt + 2 * t] = acc[nt][2];
+    blk[warp][g + 8][8 * nt + 2 * t + 1] = acc[nt][3];
+  }
+  __syncthreads();
   float* out = grad_part + (size_t)c * (kCvR * d * kCvK);
-  out[(r * d + i) * kCvK + k0] = g0;
-  out[(r * d + i) * kCvK + k0 + 1] = g1;
+  for (int q = threadIdx.x; q < kCvR * kCvK; q += blockDim.x) {
+    const int r = q / kCvK, k = q % kCvK;
+    out[(r * d + i) * kCvK + k] = ((blk[0][r][k] + blk[1][r][k]) + blk[2][r][k]) + blk[3][r][k];
+  }
 }
 
 __global__ void cv_adam_kernel(const float* __restrict__ grad_part, int nchunk, int npar, float* __restrict__ a,
@@ -114,10 +146,10 @@ static const void* cv_forward_for(int d) {
   }
 }
 
-static void cv_forward(int d, int P, const float* B, const double* hv, const float* a, float* Dg, double* lp,
-                       cudaStream_t st) {
-  void* args[6] = {(void*)&B, (void*)&hv, (void*)&a, (void*)&P, (void*)&Dg, (void*)&lp};
-  cudaLaunchKernel(cv_forward_for(d), dim3((P + 255) / 256), dim3(256), args, 0, st);
+static void cv_forward(int d, int P, int Ppad, const uint16_t* Bf, const double* hv, const float* a, uint16_t* DgT,
+                       double* lp, cudaStream_t st) {
+  void* args[7] = {(void*)&Bf, (void*)&hv, (void*)&a, (void*)&P, (void*)&Ppad, (void*)&DgT, (void*)&lp};
+  cudaLaunchKernel(cv_forward_for(d), dim3(Ppad / kCvTile), dim3(128), args, 0, st);
 }
 
 static float bf16_round(float v) {
@@ -132,11 +164,12 @@ static float bf16_round(float v) {
 
 // Device buffers of one fit: pilot coordinates and values, basis, parameters.
 struct CvFit {
-  int d = 0, P = 0, nchunk = 0, npar = 0;
+  int d = 0, P = 0, Ppad = 0, nchunk = 0, npar = 0;
   double* x = nullptr;       // [P][d]
   double* hv = nullptr;      // [P][2] (value, 0)
-  float* B = nullptr;        // [d][P][K]
-  float* Dg = nullptr;       // [d][P][R]
+  uint16_t* Bf = nullptr;    // [d][Ppad][K] BF16
+  uint16_t* Bt = nullptr;    // [d][K][Ppad] BF16
+  uint16_t* DgT = nullptr;   // [d][R][Ppad] BF16
   float* a = nullptr;
   float* m1 = nullptr;
   float* m2 = nullptr;
@@ -149,12 +182,13 @@ struct CvFit {
   int alloc(int d_, int P_) {
     d = d_;
     P = P_;
-    nchunk = (P + kCvChunk - 1) / kCvChunk;
+    Ppad = (P + kCvTile - 1) / kCvTile * kCvTile;
+    nchunk = (Ppad + kCvChunk - 1) / kCvChunk;
     npar = kCvR * d * kCvK;
-    const int nlp = (P + 255) / 256;
-    size_t sz[] = {(size_t)P * d * 8, (size_t)P * 2 * 8, (size_t)d * P * kCvK * 4, (size_t)d * P * kCvR * 4,
-                   (size_t)npar * 4,  (size_t)npar * 4, (size_t)npar * 4,        (size_t)nchunk * npar * 4,
-                   (size_t)nlp * 8};
+    const int nlp = Ppad / kCvTile;
+    size_t sz[] = {(size_t)P * d * 8,      (size_t)P * 2 * 8, (size_t)d * Ppad * kCvK * 2, (size_t)d * kCvK * Ppad * 2,
+                   (size_t)d * kCvR * Ppad * 2, (size_t)npar * 4, (size_t)npar * 4,      (size_t)npar * 4,
+                   (size_t)nchunk * npar * 4, (size_t)nlp * 8};
     size_t total = 0;
     for (size_t s : sz) total += (s + 255) & ~(size_t)255;
     if (cudaMalloc(&block, total) != cudaSuccess) {
@@ -162,9 +196,9 @@ struct CvFit {
       return fail(QMC_ENOMEM, "control-variate fit buffers (%zu bytes)", total);
     }
     char* p = (char*)block;
-    void** dst[] = {(void**)&x, (void**)&hv, (void**)&B, (void**)&Dg, (void**)&a, (void**)&m1, (void**)&m2,
-                    (void**)&grad_part, (void**)&loss_part};
-    for (int q = 0; q < 9; ++q) {
+    void** dst[] = {(void**)&x,  (void**)&hv, (void**)&Bf, (void**)&Bt,        (void**)&DgT,
+                    (void**)&a,  (void**)&m1, (void**)&m2, (void**)&grad_part, (void**)&loss_part};
+    for (int q = 0; q < 10; ++q) {
       *dst[q] = p;
       p += (sz[q] + 255) & ~(size_t)255;
     }
@@ -173,7 +207,7 @@ struct CvFit {
 };
 
 static double cv_loss_host(const CvFit& F, cudaStream_t st) {
-  const int nlp = (F.P + 255) / 256;
+  const int nlp = F.Ppad / kCvTile;
   std::vector<double> lp(nlp);
   cudaMemcpyAsync(lp.data(), F.loss_part, nlp * 8, cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -211,9 +245,9 @@ int qmc_cv_loss_grad(int32_t d, const qmc_cv_config* cfg, int32_t P, const doubl
   cudaMemcpyAsync(F.x, x, (size_t)P * d * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(F.hv, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(F.a, a, (size_t)F.npar * 4, cudaMemcpyHostToDevice, st);
-  cv_basis_kernel<<<(P * d + 255) / 256, 256, 0, st>>>(F.x, P, d, (float)cfg->freq_step, F.B);
-  cv_forward(d, P, F.B, F.hv, F.a, F.Dg, F.loss_part, st);
-  cv_backward_kernel<<<dim3(F.nchunk, d), 256, 0, st>>>(F.B, F.Dg, P, d, F.grad_part);
+  cv_basis_kernel<<<(F.Ppad * d + 255) / 256, 256, 0, st>>>(F.x, P, F.Ppad, d, (float)cfg->freq_step, F.Bf, F.Bt);
+  cv_forward(d, P, F.Ppad, F.Bf, F.hv, F.a, F.DgT, F.loss_part, st);
+  cv_backward_kernel<<<dim3(F.nchunk, d), 128, 0, st>>>(F.Bt, F.DgT, F.Ppad, d, F.grad_part);
   std::vector<float> gp((size_t)F.nchunk * F.npar);
   cudaMemcpyAsync(gp.data(), F.grad_part, gp.size() * 4, cudaMemcpyDeviceToHost, st);
   *loss_out = cv_loss_host(F, st);
@@ -277,7 +311,7 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
     cudaError_t e = cudaLaunchKernel(ln.func, dim3((P + 255) / 256), dim3(kThreads), args, 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "pilot evaluation");
   }
-  cv_basis_kernel<<<(P * d + 255) / 256, 256, 0, st>>>(F.x, P, d, (float)cfg->freq_step, F.B);
+  cv_basis_kernel<<<(F.Ppad * d + 255) / 256, 256, 0, st>>>(F.x, P, F.Ppad, d, (float)cfg->freq_step, F.Bf, F.Bt);
   // pilot mean for the initial constant terms
   std::vector<double> hv(2 * (size_t)P);
   cudaMemcpyAsync(hv.data(), F.hv, hv.size() * 8, cudaMemcpyDeviceToHost, st);
@@ -312,13 +346,13 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
   cudaMemsetAsync(F.m2, 0, (size_t)F.npar * 4, st);
   double first = 0.0, last = 0.0;
   for (int step = 1; step <= cfg->steps; ++step) {
-    cv_forward(d, P, F.B, F.hv, F.a, F.Dg, F.loss_part, st);
+    cv_forward(d, P, F.Ppad, F.Bf, F.hv, F.a, F.DgT, F.loss_part, st);
     if (step == 1) first = cv_loss_host(F, st);
-    cv_backward_kernel<<<dim3(F.nchunk, d), 256, 0, st>>>(F.B, F.Dg, P, d, F.grad_part);
+    cv_backward_kernel<<<dim3(F.nchunk, d), 128, 0, st>>>(F.Bt, F.DgT, F.Ppad, d, F.grad_part);
     const float lr = (float)(0.5 * cfg->lr * (1.0 + std::cos(M_PI * (double)(step - 1) / (double)cfg->steps)));
     cv_adam_kernel<<<(F.npar + 255) / 256, 256, 0, st>>>(F.grad_part, F.nchunk, F.npar, F.a, F.m1, F.m2, step, lr);
   }
-  cv_forward(d, P, F.B, F.hv, F.a, F.Dg, F.loss_part, st);
+  cv_forward(d, P, F.Ppad, F.Bf, F.hv, F.a, F.DgT, F.loss_part, st);
   last = cv_loss_host(F, st);
   std::vector<float> af(F.npar);
   cudaMemcpyAsync(af.data(), F.a, (size_t)F.npar * 4, cudaMemcpyDeviceToHost, st);

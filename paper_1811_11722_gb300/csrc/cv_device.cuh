@@ -11,6 +11,27 @@ constexpr int kCvK = 32;
 constexpr int kCvDMax = 8;
 constexpr int kCvMc = 8;            // shifts per estimator launch
 constexpr int kCvChunk = 2048;      // pilot points per backward CTA
+constexpr int kCvTile = 64;         // pilot points per forward CTA (4 warps x 16); the pilot is padded to it
+
+// Warp-level tensor-core product D = A B + C, A 16x16 (row), B 16x8 (col),
+// BF16 operands packed two per 32-bit register, FP32 accumulation.  Lane l
+// (group g = l / 4, t = l % 4) holds A[g][2t..2t+1] (a0), A[g+8][2t..] (a1),
+// A[g][2t+8..] (a2), A[g+8][2t+8..] (a3); B[2t..2t+1][g] (b0), B[2t+8..][g]
+// (b1); D[g][2t..2t+1] (c0, c1) and D[g+8][2t..2t+1] (c2, c3).
+__device__ __forceinline__ void mma_bf16_16x8x16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                                 uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// float -> bfloat16 bits, round to nearest even (finite inputs)
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+  const uint32_t u = __float_as_uint(v);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
 
 struct CvParams {
   RuleParams<float> base;
@@ -169,71 +190,97 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Forward pass of the fit on tensor cores.  Warp w of the CTA takes pilot
+// points j0 .. j0 + 15.  Per dimension i, C_i = Bf_i a_i^T, with the basis
+// Bf[i][j][k] (BF16, k contiguous) as A (16 points x 32 k, two k-steps) and
+// the parameters a[r][i][k] (BF16, from shared memory) as B (32 k x 16 r,
+// two r-tiles).  A lane holds the same (point, r) positions of C for every
+// dimension, so the product over dimensions, g = sum_r prod_i C_ri, the loss
+// and the gradient factor 2 e prod_{i' != i} C_ri' / P all stay in its
+// registers; only the sum over r needs the other three lanes of its group.
+// The factor goes out as BF16 in the layout the backward pass reads,
+// DgT[i][r][j] (j contiguous).  Rows j >= P (padding) carry zero basis rows,
+// add nothing to the loss and get a zero factor.
 template <int D>
-__global__ void __launch_bounds__(256)
-    cv_forward_kernel(const float* __restrict__ B, const double* __restrict__ hv, const float* __restrict__ a, int P,
-                      float* __restrict__ Dg, double* __restrict__ loss_part) {
-  __shared__ float as[kCvR * D * kCvK];
-  __shared__ double red[8];
-  for (int q = threadIdx.x; q < kCvR * D * kCvK; q += blockDim.x) as[q] = a[q];
+__global__ void __launch_bounds__(128)
+    cv_forward_kernel(const uint16_t* __restrict__ Bf, const double* __restrict__ hv, const float* __restrict__ a,
+                      int P, int Ppad, uint16_t* __restrict__ DgT, double* __restrict__ loss_part) {
+  __shared__ __align__(16) uint16_t as[kCvR * D * kCvK];
+  __shared__ double red[4];
+  for (int q = threadIdx.x; q < kCvR * D * kCvK; q += blockDim.x) as[q] = bf16_bits(a[q]);
   __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  double l2 = 0.0;
-  if (j < P) {
-    float C[D][kCvR];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int j0 = blockIdx.x * kCvTile + warp * 16;
+  float C[D][2][4];  // [dimension][r-tile][fragment]
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      float b[kCvK];
-      const float4* bp = reinterpret_cast<const float4*>(B + ((size_t)i * P + j) * kCvK);
+  for (int i = 0; i < D; ++i) {
+    const uint16_t* rowA = Bf + ((size_t)i * Ppad + j0 + g) * kCvK;
+    const uint16_t* rowB = rowA + 8 * kCvK;
 #pragma unroll
-      for (int q = 0; q < kCvK / 4; ++q) {
-        float4 v = bp[q];
-        b[4 * q] = v.x;
-        b[4 * q + 1] = v.y;
-        b[4 * q + 2] = v.z;
-        b[4 * q + 3] = v.w;
-      }
+    for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-      for (int r = 0; r < kCvR; ++r) {
-        float s = 0.0f;
+      for (int v = 0; v < 4; ++v) C[i][nt][v] = 0.0f;
 #pragma unroll
-        for (int k = 0; k < kCvK; ++k) s = fmaf(as[(r * D + i) * kCvK + k], b[k], s);
-        C[i][r] = s;
+    for (int ks = 0; ks < 2; ++ks) {
+      const int k = 16 * ks + 2 * t;
+      const uint32_t a0 = *reinterpret_cast<const uint32_t*>(rowA + k);
+      const uint32_t a1 = *reinterpret_cast<const uint32_t*>(rowB + k);
+      const uint32_t a2 = *reinterpret_cast<const uint32_t*>(rowA + k + 8);
+      const uint32_t a3 = *reinterpret_cast<const uint32_t*>(rowB + k + 8);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const uint16_t* ap = as + ((8 * nt + g) * D + i) * kCvK + k;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(ap);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(ap + 8);
+        mma_bf16_16x8x16(C[i][nt], a0, a1, a2, a3, b0, b1);
       }
     }
-    float g = 0.0f;
+  }
+  // g for rows j0 + g (fragments 0, 1) and j0 + g + 8 (fragments 2, 3)
+  float prod[2][4];
 #pragma unroll
-    for (int r = 0; r < kCvR; ++r) {
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
       float p = 1.0f;
 #pragma unroll
-      for (int i = 0; i < D; ++i) p *= C[i][r];
-      g += p;
+      for (int i = 0; i < D; ++i) p *= C[i][nt][v];
+      prod[nt][v] = p;
     }
-    const double err = (double)g - hv[2 * (size_t)j];
-    l2 = err * err;
-    const float e = (float)(2.0 * err / (double)P);
+  float gA = prod[0][0] + prod[0][1] + prod[1][0] + prod[1][1];
+  float gB = prod[0][2] + prod[0][3] + prod[1][2] + prod[1][3];
+  gA += __shfl_xor_sync(0xffffffffu, gA, 1);
+  gA += __shfl_xor_sync(0xffffffffu, gA, 2);
+  gB += __shfl_xor_sync(0xffffffffu, gB, 1);
+  gB += __shfl_xor_sync(0xffffffffu, gB, 2);
+  const int jA = j0 + g, jB = j0 + g + 8;
+  const double errA = jA < P ? (double)gA - hv[2 * (size_t)jA] : 0.0;
+  const double errB = jB < P ? (double)gB - hv[2 * (size_t)jB] : 0.0;
+  double l2 = t == 0 ? errA * errA + errB * errB : 0.0;
+  const float eA = (float)(2.0 * errA / (double)P), eB = (float)(2.0 * errB / (double)P);
+  // factor per (dimension, position): e * prefix * suffix over the other dimensions
 #pragma unroll
-    for (int r = 0; r < kCvR; ++r) {
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float e = v < 2 ? eA : eB;
+      const int j = v < 2 ? jA : jB;
+      const int r = 8 * nt + 2 * t + (v & 1);
       float pre[D + 1];
-      pre[0] = 1.0f;
+      pre[0] = e;
 #pragma unroll
-      for (int i = 0; i < D; ++i) pre[i + 1] = pre[i] * C[i][r];
+      for (int i = 0; i < D; ++i) pre[i + 1] = pre[i] * C[i][nt][v];
       float suf = 1.0f;
 #pragma unroll
       for (int i = D - 1; i >= 0; --i) {
-        Dg[((size_t)i * P + j) * kCvR + r] = e * pre[i] * suf;
-        suf *= C[i][r];
+        DgT[((size_t)i * kCvR + r) * Ppad + j] = bf16_bits(pre[i] * suf);
+        suf *= C[i][nt][v];
       }
     }
-  }
   l2 = warp_sum_d(l2);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
+  if (lane == 0) red[warp] = l2;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    loss_part[blockIdx.x] = s;
-  }
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
 }
 
 // One explicit specialisation per d, each compiled in its own unit.

@@ -461,18 +461,26 @@ def _cv_cfg(Q, steps=300, freq=1, seed=7):
     return cfg
 
 
-def test_cv_gradient_matches_oracle(Q, oracle_lib):
-    """Training kernels' loss and gradient against the oracle's FP64 chain rule."""
+@pytest.mark.parametrize("d,P", [(8, 3000), (3, 1000), (1, 77)])
+def test_cv_gradient_matches_oracle(Q, oracle_lib, d, P):
+    """Training kernels (BF16 tensor-core contractions, FP32 accumulation)
+    against the oracle's chain rule on the same BF16-rounded operands with FP64
+    sums: what differs is FP32 accumulation and, rarely, the BF16 rounding of a
+    gradient factor computed in FP32 instead of FP64.  Pilot sizes that are
+    not multiples of the 64-point tile check the padding.  Against the all-FP64
+    fit the difference stays within BF16's resolution."""
     rng = np.random.default_rng(11)
-    d, P = 8, 3000
     a = (rng.normal(size=16 * d * 32) * 0.05).astype(np.float32)
     a[[(r * d + i) * 32 for r in range(16) for i in range(d)]] = 0.8
     x = rng.random((P, d))
     h = rng.random(P)
     loss, grad = Q.qmc_cv_loss_grad(d, _cv_cfg(Q), x, h, a)
-    lref, gref = oracle_lib.cv_loss_grad(d, 16, 32, 1, x, h, a)
+    lref, gref = oracle_lib.cv_loss_grad_bf16(d, 16, 32, 1, x, h, a)
     assert abs(loss - lref) <= 1e-5 * lref
     assert np.max(np.abs(grad - gref)) <= 2e-4 * np.max(np.abs(gref))
+    l64, g64 = oracle_lib.cv_loss_grad(d, 16, 32, 1, x, h, a)
+    assert abs(loss - l64) <= 2e-2 * l64
+    assert np.max(np.abs(grad - g64)) <= 2e-2 * np.max(np.abs(g64))
 
 
 def test_cv_training_and_estimator_parity(Q, oracle_lib, nthreads):
@@ -649,11 +657,14 @@ def test_fp32_fold_and_origin_points(Q, oracle_lib, transform, alpha):
         assert abs(vals[s, 0] - v[0]) <= 4e-6 * abs(v[0]) + 1e-300, (s, vals[s, 0], v[0])
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-9)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-8)])
 def test_extensible_levels_reproduce_the_direct_rule(Q, oracle_lib, precision, tol):
     """Doubling from n = 2^10 to 2^14 by evaluating only the new half of the
     points each time gives the size-2^14 rule itself (per shift), and the
-    oracle's value for it."""
+    oracle's value for it.  In FP32 the two evaluations give a point different
+    dithers (its index differs between the half-size rule and the direct one),
+    so they differ by the per-point rounding noise, ~2e-7 rms averaged over
+    16384 points (~2e-9 rms)."""
     p = I.config2(n=1 << 14, m=8)
     g = Q.qmc_make_lattice_embedded(6, 10, 14, p.gamma, candidates=64, seed=3)
     t = Q.transform(p.transform, p.alpha)

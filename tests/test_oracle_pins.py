@@ -490,3 +490,50 @@ def test_eps_expansion_d1_against_quad(oracle_lib):
     full, _ = quad(lambda x: (a + b * x) ** (-2 + bU * eps) * (c + e * x * x) ** (-1 + bF * eps), 0, 1,
                    epsabs=1e-15, epsrel=1e-13)
     assert abs(total - full) < 2 * eps ** 5 * 10 + 1e-10
+
+
+# ------------------------------------------- BF16 operands of the fit --
+
+def test_bf16_rounding_matches_torch(oracle_lib):
+    """The oracle's bfloat16 rounding (float first, then nearest-even to 8
+    mantissa bits) against torch's float32 -> bfloat16 conversion."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.normal(size=2000) * 10.0 ** rng.integers(-8, 8, 2000),
+                        [0.0, -0.0, 1.0, -1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 65504.0, 1e-30]])
+    ref = torch.tensor(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([oracle_lib.bf16(x) for x in v])
+    assert np.array_equal(got, ref)
+
+
+def test_cv_fit_bf16_exact_operands(oracle_lib):
+    """With operands that bfloat16 holds exactly (parameters on a 1/64 grid,
+    points where every cos(pi k x) is 0, +-1/2 or +-1) the BF16 fit has the FP64
+    fit's loss; its gradient differs only by the rounding of the factor
+    2 e prod C / P, at most 2^-8 relative per term."""
+    rng = np.random.default_rng(6)
+    d, R, K, P = 3, 16, 32, 40
+    a = (rng.integers(-32, 33, R * d * K) / 64.0).astype(np.float32)
+    x = rng.choice([0.0, 0.5, 1.0 / 3.0, 2.0 / 3.0, 1.0], size=(P, d))
+    h = rng.random(P)
+    l64, g64 = oracle_lib.cv_loss_grad(d, R, K, 1, x, h, a)
+    l16, g16 = oracle_lib.cv_loss_grad_bf16(d, R, K, 1, x, h, a)
+    assert abs(l16 - l64) <= 1e-12 * l64
+    # bound each gradient entry by the sum of |terms| (FP64 fit with |a|, |cos|, |e| is an upper bound proxy)
+    assert np.max(np.abs(g16 - g64)) <= 2.0 ** -8 * np.max(np.abs(g64)) * 4
+    assert np.max(np.abs(g16 - g64)) > 0.0  # the factor's rounding does act
+
+
+def test_cv_fit_bf16_close_to_fp64(oracle_lib):
+    """For generic points the BF16 fit stays within BF16's resolution of the
+    FP64 fit (loss within 2%, gradient within 2% of its largest entry)."""
+    rng = np.random.default_rng(7)
+    d, R, K, P = 4, 16, 32, 200
+    a = (rng.normal(size=R * d * K) * 0.05).astype(np.float32)
+    a[[(r * d + i) * K for r in range(R) for i in range(d)]] = 0.8
+    x = rng.random((P, d))
+    h = rng.random(P)
+    l64, g64 = oracle_lib.cv_loss_grad(d, R, K, 1, x, h, a)
+    l16, g16 = oracle_lib.cv_loss_grad_bf16(d, R, K, 1, x, h, a)
+    assert abs(l16 - l64) <= 2e-2 * l64
+    assert np.max(np.abs(g16 - g64)) <= 2e-2 * np.max(np.abs(g64))
