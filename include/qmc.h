@@ -354,10 +354,12 @@ int qmc_integrate_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, con
  * size n, and the others form the size-n lattice shifted by g / (2n).
  * qmc_make_lattice_embedded builds g component by component (g_1 = 1, odd
  * components) minimising max_k 4^k e^2_{2^k}(g), with e^2 the worst-case
- * error of qmc_make_lattice at each size; candidates for a component are all
- * odd z < 2^(log2_nmax - 1) when `candidates` covers them, else that many drawn
- * by SplitMix64 from `seed` (ties to the smallest z).  Host only; sizes up to
- * 2^30.  g_out: [d] host. */
+ * error of qmc_make_lattice at each size.  When `candidates` covers all odd
+ * z < 2^(log2_nmax - 1), all of them are searched at once (cyclic correlations
+ * over the powers of 5 by FFT, O(N log N) per component, the best few then
+ * recomputed exactly); otherwise `candidates` odd z drawn by SplitMix64 from
+ * `seed` are evaluated directly.  Ties go to the smallest z.  Host only; sizes
+ * up to 2^30.  g_out: [d] host. */
 int qmc_make_lattice_embedded(int32_t d, int32_t log2_nmin, int32_t log2_nmax, const double* gamma,
                               int32_t candidates, uint64_t seed, uint64_t* g_out);
 /* Doubling n until Eq. (3)'s relative error meets rel_tol: level 0 applies the

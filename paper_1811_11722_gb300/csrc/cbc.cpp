@@ -129,6 +129,110 @@ static double candidate_sum(uint64_t n, const std::vector<double>& p, uint64_t z
   return s + c;
 }
 
+
+
+
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// max_k 4^k e^2_k for the vector so far (products p over the N points)
+// extended by component z with weight gamma.
+static double embedded_criterion(const std::vector<double>& p, int K, int kmin, uint64_t z, double gamma) {
+  const uint64_t N = 1ull << K;
+  // sums of the terms by the number of trailing zero bits of J (J = 0 in every level)
+  std::vector<double> bucket(K + 1, 0.0);
+  for (uint64_t J = 0; J < N; ++J) {
+    const uint64_t r = (J * z) & (N - 1);
+    const double term = p[J] * (1.0 + gamma * bern2((double)r / (double)N));
+    const int v = J == 0 ? K : std::min(K, __builtin_ctzll(J));
+    bucket[v] += term;
+  }
+  double worst = -1e300, level_sum = 0.0;
+  for (int k = 0; k <= K; ++k) {  // level k holds the J with at least K - k trailing zeros
+    level_sum += bucket[K - k];
+    if (k < kmin) continue;
+    const double e2 = level_sum / (double)(1ull << k) - 1.0;
+    worst = std::max(worst, std::ldexp(e2, 2 * k));
+  }
+  return worst;
+}
+
+constexpr int kRerankEmb = 16;
+
+// The criterion max_k 4^k e^2_k of every candidate z = 5^b mod N (b < N/4,
+// reported as min(z, N - z)), from the per-v cyclic correlations.
+static void embedded_all(const std::vector<double>& p, int K, int kmin, double gamma, std::vector<uint64_t>& zs,
+                         std::vector<double>& crit) {
+  const uint64_t N = 1ull << K;
+  const uint64_t L0 = N / 4;
+  zs.resize(L0);
+  crit.assign(L0, 0.0);
+  // level sums S_v(b), accumulated into per-k partial sums below
+  std::vector<std::vector<double>> T(K);
+  for (int v = 0; v < K; ++v) {
+    const uint64_t Nv = N >> v;
+    if (Nv < 8) continue;  // small groups: direct sums below
+    const uint64_t L = Nv / 4;
+    int logL = 0;
+    while ((1ull << logL) < L) ++logL;
+    std::vector<cd> q(L), w(L);
+    uint64_t pw = 1;  // 5^a mod Nv
+    for (uint64_t a = 0; a < L; ++a) {
+      q[a] = cd(p[(pw << v)] + p[((Nv - pw) << v)], 0.0);
+      w[a] = cd(1.0 + gamma * bern2((double)pw / (double)Nv), 0.0);
+      pw = (pw * 5) & (Nv - 1);
+    }
+    std::vector<cd> tw(std::max<uint64_t>(1, L / 2));
+    for (uint64_t k = 0; k < L / 2; ++k) tw[k] = std::polar(1.0, -2.0 * M_PI * (double)k / (double)L);
+    fft(q, tw, logL, false);
+    fft(w, tw, logL, false);
+    for (uint64_t f = 0; f < L; ++f) q[f] = std::conj(q[f]) * w[f];
+    fft(q, tw, logL, true);
+    T[v].resize(L);
+    for (uint64_t b = 0; b < L; ++b) T[v][b] = q[b].real() / (double)L;
+  }
+  parallel_for(L0, [&](size_t lo, size_t hi) {
+    std::vector<double> lv(K + 1);
+    uint64_t z = 1;  // 5^lo mod N
+    {
+      uint64_t base = 5, e = lo;
+      while (e) {
+        if (e & 1) z = (z * base) & (N - 1);
+        base = (base * base) & (N - 1);
+        e >>= 1;
+      }
+    }
+    for (size_t b = lo; b < hi; ++b) {
+      // contribution of the points with v trailing zero bits; J = 0 in every level
+      for (int v = 0; v < K; ++v) {
+        const uint64_t Nv = N >> v;
+        double s;
+        if (Nv >= 8) {
+          s = T[v][b & (Nv / 4 - 1)];
+        } else {
+          s = 0.0;
+          for (uint64_t u = 1; u < Nv; u += 2)
+            s += p[u << v] * (1.0 + gamma * bern2((double)((u * z) & (Nv - 1)) / (double)Nv));
+        }
+        lv[v] = s;
+      }
+      double level_sum = p[0] * (1.0 + gamma * bern2(0.0)), worst = -1e300;
+      for (int k = 0; k <= K; ++k) {  // size 2^k holds the points with v >= K - k
+        if (k > 0) level_sum += lv[K - k];
+        if (k < kmin) continue;
+        worst = std::max(worst, std::ldexp(level_sum / (double)(1ull << k) - 1.0, 2 * k));
+      }
+      crit[b] = worst;
+      zs[b] = std::min(z, N - z);
+      z = (z * 5) & (N - 1);
+    }
+  });
+}
+
 }  // namespace qmc
 
 using namespace qmc;
@@ -225,6 +329,95 @@ extern "C" int qmc_make_lattice(int32_t d, uint64_t n, const double* gamma, uint
     }
   } catch (const std::bad_alloc&) {
     return fail(QMC_ENOMEM, "host memory for the CBC search");
+  }
+  return QMC_OK;
+}
+
+// Embedded (extensible) rank-1 lattices in base 2, for growing n without
+// discarding earlier work.
+//
+// With N = 2^K and one generating vector g, the lattice of size 2^k uses the
+// points J = j 2^(K-k) of the size-N lattice: {j g / 2^k} = {J g / N}.  The
+// point sets are nested, and the points of size 2n that are not in size n
+// form the size-n lattice shifted by g / (2n).  A rule can therefore double n
+// by evaluating one more size-n rule and averaging it, shift by shift, with
+// the previous level (qmc_integrate_extensible).
+//
+// The vector is built component by component as in the CBC search for one n
+// (same space and weights, e^2_k = -1 + 2^-k sum_{J : 2^(K-k) | J} prod_i
+// (1 + gamma_i B2({J g_i / N}))), choosing each component to minimise the
+// worst scaled error over the embedded sizes, max_k 4^k e^2_k.  The e^2 of a
+// good lattice decays roughly like n^-2, so the scaling keeps every size in
+// play.  The candidates for a component are the odd z in [1, N/2) (z and
+// N - z give the same errors; even z would not be units mod 2^k), all of them
+// or a SplitMix64-drawn subset.
+//
+// All candidates at once.  Write J = 2^v u with u odd.  Modulo N_v = N / 2^v
+// the odd residues are +-5^a (a < L_v = N_v / 4) and B2 is symmetric, so for
+// z = +-5^b the points with that v contribute
+//   T_v(b) = sum_a q_v[a] w_v[(a + b) mod L_v],
+//   q_v[a] = p[2^v 5^a] + p[2^v (N_v - 5^a)],  w_v[c] = 1 + gamma B2(5^c mod N_v / N_v),
+// a cyclic correlation of length L_v done by FFT.  Every embedded size 2^k
+// uses the same T_v (those with v >= K - k), so one set of correlations per
+// component gives every candidate's criterion in O(N log N); the kRerankEmb
+// best are then recomputed exactly (term by term) and the smallest wins.
+
+extern "C" int qmc_make_lattice_embedded(int32_t d, int32_t log2_nmin, int32_t log2_nmax, const double* gamma,
+                                         int32_t candidates, uint64_t seed, uint64_t* g_out) {
+  if (d < 1 || d > QMC_DMAX) return fail(QMC_EINVAL, "d=%d outside [1, %d]", d, QMC_DMAX);
+  if (log2_nmin < 1 || log2_nmax < log2_nmin || log2_nmax > 30)
+    return fail(QMC_EINVAL, "embedded sizes 2^%d..2^%d: need 1 <= min <= max <= 30", log2_nmin, log2_nmax);
+  if (!gamma || !g_out || candidates < 1) return fail(QMC_EINVAL, "null weights/output or no candidates");
+  for (int i = 0; i < d; ++i)
+    if (!(gamma[i] > 0.0) || !std::isfinite(gamma[i])) return fail(QMC_EINVAL, "gamma[%d] must be positive", i);
+  const int K = log2_nmax;
+  const uint64_t N = 1ull << K;
+  std::vector<double> p(N, 1.0);
+  auto extend = [&](uint64_t z, double gam) {
+    for (uint64_t J = 0; J < N; ++J) p[J] *= 1.0 + gam * bern2((double)((J * z) & (N - 1)) / (double)N);
+  };
+  g_out[0] = 1;
+  extend(1, gamma[0]);
+  const uint64_t odd_count = N / 4 > 0 ? N / 4 : 1;  // odd z in [1, N/2)
+  for (int s = 1; s < d; ++s) {
+    std::vector<uint64_t> cand;
+    if ((uint64_t)candidates >= odd_count && K >= 5) {
+      // every odd candidate, by the correlations; the best few re-ranked exactly
+      std::vector<uint64_t> zs;
+      std::vector<double> cr;
+      embedded_all(p, K, log2_nmin, gamma[s], zs, cr);
+      std::vector<size_t> order(zs.size());
+      for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+      const size_t top = std::min<size_t>(kRerankEmb, order.size());
+      std::partial_sort(order.begin(), order.begin() + top, order.end(), [&](size_t x, size_t y) {
+        return cr[x] < cr[y] || (cr[x] == cr[y] && zs[x] < zs[y]);
+      });
+      for (size_t q = 0; q < top; ++q) cand.push_back(zs[order[q]]);
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    } else if ((uint64_t)candidates >= odd_count) {
+      for (uint64_t z = 1; z < std::max<uint64_t>(N / 2, 2); z += 2) cand.push_back(z);
+    } else {
+      uint64_t st = seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(s + 1));
+      while ((int)cand.size() < candidates) {
+        const uint64_t z = 2 * (splitmix64(st) % odd_count) + 1;
+        if (std::find(cand.begin(), cand.end(), z) == cand.end()) cand.push_back(z);
+      }
+      std::sort(cand.begin(), cand.end());
+    }
+    std::vector<double> crit(cand.size());
+    const unsigned nt = std::max(1u, std::min<unsigned>(64u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned w = 0; w < nt; ++w)
+      th.emplace_back([&, w] {
+        for (size_t c = w; c < cand.size(); c += nt) crit[c] = embedded_criterion(p, K, log2_nmin, cand[c], gamma[s]);
+      });
+    for (auto& x : th) x.join();
+    size_t best = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+      if (crit[c] < crit[best]) best = c;  // strict: ties go to the smaller z
+    g_out[s] = cand[best];
+    extend(cand[best], gamma[s]);
   }
   return QMC_OK;
 }
