@@ -173,7 +173,10 @@ int qmc_plan_launches(qmc_plan plan, int32_t* launches_out);
 #endif
 /* Autotuner: times the plan on `stream` with each specialised shift-chunk
  * size (shifts evaluated per point by one launch: 8, 16 or 32 for FP32EVAL
- * sector integrands; other plans have one choice) and keeps the fastest.
+ * sector integrands, with register-pressure variants of the run-time
+ * specialised kernel; other plans have one choice) and keeps the fastest.
+ * QMC_TUNE_VERBOSE=1 in the environment prints each candidate's time to
+ * stderr.
  * Reports the choice in *shifts_per_launch_out (may be NULL).  Synchronises
  * the device. */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -314,9 +315,13 @@ int choose_grid(const void* func, size_t smem, uint64_t n, int& nblk, int& L, ui
   int sms = device_sm_count();
   if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
   int occ = 0;
-  QMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, kThreads, smem));
-  if (occ < 1) occ = 1;
-  if (occupancy_override > 0) occ = std::min(occ, occupancy_override);
+  if (func) {
+    QMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, kThreads, smem));
+    if (occ < 1) occ = 1;
+    if (occupancy_override > 0) occ = std::min(occ, occupancy_override);
+  } else {
+    occ = std::max(1, occupancy_override);  // a run-time compiled kernel: the caller's occupancy
+  }
   uint64_t want = (uint64_t)sms * occ;
   uint64_t per = (n + want * kThreads - 1) / (want * kThreads);
   const uint64_t Lmax = 512;
@@ -481,7 +486,9 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
 
   int nblk = 0, L = 0;
   uint64_t tiles = 0;
-  int rc = choose_grid(func, 0, n, nblk, L, tiles, jit_fn ? (tune.occupancy > 0 ? std::min(tune.occupancy, jit_occ) : jit_occ)
+  // a run-time specialised kernel has its own occupancy (registers, shared memory), not the template's
+  int rc = choose_grid(jit_fn ? nullptr : func, 0, n, nblk, L, tiles,
+                       jit_fn ? (tune.occupancy > 0 ? std::min(tune.occupancy, jit_occ) : jit_occ)
                                                           : tune.occupancy);
   if (rc) return rc;
   if (tune.max_ctas > 0 && nblk > tune.max_ctas) {
@@ -733,7 +740,7 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
   if (sp.f.precision == QMC_FP32EVAL && sp.f.kind == QMC_F_SECTOR && sp.eps.orders == 0) {
     cands = {{8, 0, 0}, {16, 0, 0}, {32, 0, 0}};
     if (pl->launches.size() && pl->launches[0].cufunc)  // register-pressure variants of the specialised kernel
-      cands.insert(cands.end(), {{16, 0, 2}, {16, 1, 2}, {32, 1, 0}, {32, 1, 2}});
+      cands.insert(cands.end(), {{16, 0, 2}, {16, 1, 2}, {32, 1, 0}, {32, 1, 2}, {32, 0, 2}});
   }
   if (cands.empty()) {
     if (shifts_per_launch_out) *shifts_per_launch_out = pl->mc;
@@ -746,6 +753,8 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
   float best = 1e30f;
   Cand best_c{pl->mc, pl->tune.smacc, pl->tune.minb};
   int rc = QMC_OK;
+  const char* ve = std::getenv("QMC_TUNE_VERBOSE");  // per-candidate times on stderr
+  const bool verbose = ve && ve[0] == '1';
   for (const Cand& cd : cands) {
     Plan trial;
     TuneChoice tc = pl->tune;
@@ -772,6 +781,10 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
     }
     plan_free(&trial, nullptr);
     if (rc) break;
+    if (verbose)
+      std::fprintf(stderr, "qmc_plan_tune: shifts_per_launch=%d smem_acc=%d min_ctas=%d ctas=%d specialised=%d: %.4f ms\n",
+                   cd.mc, cd.smacc, cd.minb, trial.nblk, (!trial.launches.empty() && trial.launches[0].cufunc) ? 1 : 0,
+                   tot / 3.0f);
     if (tot < best) {
       best = tot;
       best_c = cd;
