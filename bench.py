@@ -224,8 +224,15 @@ def extras(qmc, I, torch):
         plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, qmc.transform(p.transform, p.alpha),
                         qmc.integrand_from_problem(p, prec))
         t = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream, reps=3)
-        out[f"c4_deformed_d5_{prec}"] = {"evals_per_s": p.n * p.m / t, "ms": 1e3 * t}
+        r = plan.execute()
+        out[f"c4_deformed_d5_{prec}"] = {"evals_per_s": p.n * p.m / t, "ms": 1e3 * t,
+                                         "mean": [r.mean[0], r.mean[1]], "err": [r.err[0], r.err[1]]}
         plan.destroy()
+    c32, c64 = out["c4_deformed_d5_fp32"], out["c4_deformed_d5_fp64"]
+    mag = abs(complex(*c64["mean"]))
+    out["c4_fp32_vs_fp64"] = {"rel_diff": abs(complex(*c32["mean"]) - complex(*c64["mean"])) / mag,
+                              "rel_err_estimate_fp64": abs(complex(*c64["err"])) / mag,
+                              "rel_err_estimate_fp32": abs(complex(*c32["err"])) / mag}
     # precision of the FP32 evaluation on the benchmark's workload: |Q_FP32 - Q_FP64| / |Qbar|
     # against the Eq. (3) error estimate, same lattice and shifts
     p = I.config2()
