@@ -36,6 +36,12 @@ MUTATIONS = {
                           [pins.test_deformation_lambda_invariance, pins.test_deformation_at_corners]),
     "cv_integral_term": ("for (int i = 0; i < d; ++i) p *= (double)a[(r * d + i) * K];",
                          "for (int i = 1; i < d; ++i) p *= (double)a[(r * d + i) * K];", [pins.test_cv_integral_closed_form]),
+    "bf16_ties_away": ("u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;", "u = (u + 0x8000u) & 0xFFFF0000u;",
+                       [pins.test_bf16_rounding_matches_torch]),
+    "bf16_factor_unrounded": ("const double dg = orc_bf16(2.0 * e * other / (double)P);",
+                              "const double dg = 2.0 * e * other / (double)P;", [pins.test_cv_fit_bf16_exact_operands]),
+    "eps_factorial_dropped": ("for (int k = 1; k <= p->eps_order; ++k) c *= L / (double)k;",
+                              "for (int k = 1; k <= p->eps_order; ++k) c *= L;", [pins.test_eps_expansion_d1_against_quad]),
 }
 
 
