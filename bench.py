@@ -298,6 +298,31 @@ def extras(qmc, I, torch):
     for pl in plans:
         pl.destroy()
     bp.destroy()
+    # control-variate estimator Q[f - g] + int g (surrogate contracted on tensor
+    # cores) on the configuration-5 integrand at n = 16777213, m = 16: one fit
+    # (2000 Adam steps, pilot n = 65537), then the estimator per transform
+    # beside the plain rule on the same points
+    p = I.config5(n=16777213, m=16)
+    g = I.random_generating_vector(I.SplitMix64(5), p.d, p.n)
+    gp = qmc.qmc_make_lattice(p.d, I.N_PILOT, p.gamma)
+    f_ = qmc.integrand_from_problem(p, "fp32")
+    cfg = qmc.qmc_cv_config()
+    cfg.R, cfg.K, cfg.freq_step, cfg.steps, cfg.lr, cfg.seed = 16, 32, 1, 2000, 1e-2, 7
+    a, _ = qmc.qmc_cv_train(p.d, I.N_PILOT, gp, I.make_shifts(I.SplitMix64(54), 1, p.d)[0], qmc.transform("none"),
+                            f_, cfg, stream=sh)
+    for name, tt in (("none", qmc.transform("none")), ("korobov3", qmc.transform("korobov", 3))):
+        res = {}
+        t = device_time(lambda: res.update(r=qmc.qmc_integrate_cv(p.d, p.n, p.m, g, p.shifts, tt, f_, cfg, a,
+                                                                  stream=sh)[0]), stream, reps=3)
+        plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, tt, f_)
+        tp = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream, reps=3)
+        plan.destroy()
+        r = res["r"]
+        out[f"c5_cv_estimator_{name}"] = {
+            "evals_per_s": p.n * p.m / t, "ms": 1e3 * t, "plain_rule_ms": 1e3 * tp, "cost_vs_plain_rule": t / tp,
+            "tf32_mma_tflops": p.d * 2048 * p.n * p.m / t / 1e12,
+            "err_cv": r.err[0], "err_plain_same_points": r.err[1], "gain_same_points": r.err[1] / r.err[0],
+            "note": "one TF32 m16n8k8 MMA (2048 flops) per point and dimension: head and remainder of the basis"}
     return out
 
 

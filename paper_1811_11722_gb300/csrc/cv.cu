@@ -28,9 +28,13 @@
 // (16 x points) (points x 32) backward: 16 or 32 output columns.  The
 // warp-level MMA keeps a point's 16 values C_ri in the registers of the lanes
 // that multiply them across dimensions and differentiate the product, so
-// nothing between the contraction and the loss goes through memory.  The
-// estimator (the lattice rule with g subtracted) keeps FP32 basis values, as
-// its bias would otherwise exceed the rule's error.
+// nothing between the contraction and the loss goes through memory.
+//
+// Estimator kernel (cv_tc_kernel, cv_device.cuh).  The lattice rule with g
+// subtracted evaluates the surrogate's per-dimension contraction on tensor
+// cores too, as TF32 warp MMAs on a head/remainder split of each basis value,
+// which keeps FP32 accuracy: a BF16 basis there would bias Q[f - g] beyond
+// the rule's error.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -393,11 +397,16 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
   std::unique_ptr<CvParams> C(new CvParams());
   std::memset(C.get(), 0, sizeof(CvParams));
   fill_common(C->base, d, n, g, t, f);
+  // the integrand on the FP32 sector path's fixed-point coordinates: U and F
+  // take z / fx_sigma (exact powers of two folded into the coefficients)
   auto cu = pack_dense(f->U, d, 1);
   auto cf = pack_dense(f->F, d, 2);
+  prescale_slots(cu.data(), d, 1, fx_sigma(C->base.tr));
+  prescale_slots(cf.data(), d, 2, fx_sigma(C->base.tr));
   for (size_t i = 0; i < cu.size(); ++i) C->base.cU[i] = (float)cu[i];
   for (size_t i = 0; i < cf.size(); ++i) C->base.cF[i] = (float)cf[i];
   C->base.value_scale = 1.0;
+  C->sigma = (float)fx_sigma(C->base.tr);
   const int npar = kCvR * d * kCvK;
   for (int q = 0; q < npar; ++q) C->a[q] = a[q];
   C->freq = (float)cfg->freq_step;
@@ -412,7 +421,10 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
   pl.n = n;
   pl.m = m;
   pl.is_complex = 1;
-  pl.final_scale = 1.0;
+  // Korobov weights go in unnormalised (u^3 per factor); their constant
+  // (2a+1)!/(a!)^2 per dimension is applied to both sums in FP64, before int g
+  // is added
+  pl.final_scale = C->base.tr == TR_KOROBOV ? std::pow((double)C->base.kor[7], (double)d) : 1.0;
   pl.offset[0] = gint;
   pl.mc = kCvMc;
   int nblk = 0, L = 0;

@@ -9,9 +9,9 @@ namespace qmc {
 
 template <>
 const void* cv_estimator_ptr<QMC_D>(int tr, int alpha) {
-  if (tr == TR_BAKER) return (const void*)&cv_sector_kernel<QMC_D, TR_BAKER, 0>;
-  if (tr == TR_KOROBOV && alpha == 3) return (const void*)&cv_sector_kernel<QMC_D, TR_KOROBOV, 3>;
-  if (tr == TR_NONE) return (const void*)&cv_sector_kernel<QMC_D, TR_NONE, 0>;
+  if (tr == TR_BAKER) return (const void*)&cv_tc_kernel<QMC_D, TR_BAKER, 0>;
+  if (tr == TR_KOROBOV && alpha == 3) return (const void*)&cv_tc_kernel<QMC_D, TR_KOROBOV, 3>;
+  if (tr == TR_NONE) return (const void*)&cv_tc_kernel<QMC_D, TR_NONE, 0>;
   return nullptr;
 }
 
