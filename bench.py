@@ -297,6 +297,20 @@ def extras(qmc, I, torch):
                                    "note": "generating vectors drawn at random (any valid g; throughput only)"}
     for pl in plans:
         pl.destroy()
+    # the same 256 sectors as one persistent launch (work items from a device
+    # counter, coefficients staged in shared memory, no run-time compilation)
+    t0 = time.perf_counter()
+    pp = qmc.BatchPlan(tuples, persistent=True)
+    pbuild_s = time.perf_counter() - t0
+    pw = pp.tune(sh)
+    tpp = device_time(lambda: pp.execute(out=dev_res, stream=sh), stream, reps=3)
+    rp = [r.as_dict() for r in pp.execute()]
+    rg = [r.as_dict() for r in bp.execute()]
+    out["c3_batch_256_sectors_persistent"] = {
+        "evals_per_s": evals / tpp, "ms": 1e3 * tpp, "points_per_item": pw, "plan_build_s": pbuild_s,
+        "launches": pp.launches(), "ms_graph": 1e3 * t, "graph_plan_build_s": build_s,
+        "max_rel_diff_vs_graph": max(abs(a["mean"][0] - b["mean"][0]) / abs(b["mean"][0]) for a, b in zip(rp, rg))}
+    pp.destroy()
     bp.destroy()
     # control-variate estimator Q[f - g] + int g (surrogate contracted on tensor
     # cores) on the configuration-5 integrand at n = 16777213, m = 16: one fit

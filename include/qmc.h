@@ -230,13 +230,31 @@ int qmc_batch_plan_create(int32_t count, const qmc_problem* problems, qmc_batch_
 int qmc_batch_plan_execute(qmc_batch_plan plan, qmc_result* out, double* per_shift, void* stream);
 int qmc_batch_plan_destroy(qmc_batch_plan plan);
 #endif
+/* The same batch as ONE persistent launch (the rule of Eq. (2) for every
+ * problem, Eq. (3) per problem): CTAs take work items (problem, chunk of 8
+ * shifts, chunk of `chunk_points` consecutive j) from a device counter, stage
+ * the problem's rule into shared memory and sweep the chunk; item q of a
+ * problem writes its fixed slots, so results do not depend on the order in
+ * which CTAs take items.  Coefficients are read from shared memory (no
+ * per-problem code specialisation), so each problem must be an FP32EVAL
+ * SECTOR integrand U^-2 F^-1 with deg U <= 1, deg F <= 2, d <= 8 and transform
+ * none, baker or Korobov 3 (else QMC_EUNSUPPORTED).  The plan replays one
+ * CUDA graph: counter reset, the persistent kernel, the final pass.
+ *   chunk_points  points per work item, a multiple of 256 in [256, 2^24];
+ *                 0 = 65536 (qmc_batch_plan_tune sweeps 2^14..2^18)
+ * Execute, launches, tune and destroy are those of qmc_batch_plan_create. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+int qmc_batch_plan_create_persistent(int32_t count, const qmc_problem* problems, uint32_t chunk_points,
+                                     qmc_batch_plan* plan_out);
+#endif
 /* Kernel launches in one replay (rule kernels + the final pass). */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_batch_plan_launches(qmc_batch_plan plan, int32_t* launches_out);
 #endif
 /* Autotuner: times the graph on `stream` for evaluations-per-CTA budgets
- * 2^18..2^24 (the per-problem grid is ceil(n m / budget) CTAs), rebuilds the
- * plan with the fastest and reports it in *work_per_cta_out (may be NULL).
+ * 2^18..2^24 (the per-problem grid is ceil(n m / budget) CTAs), or, for a
+ * persistent plan, for work items of 2^14..2^18 points, rebuilds the plan
+ * with the fastest and reports it in *work_per_cta_out (may be NULL).
  * `problems` must describe the same batch the plan was created from.
  * Synchronises `stream`. */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */

@@ -43,7 +43,7 @@ def _units():
         units.append((f"misc_{real}.o", "kernels_misc.cu", [f"-DQMC_REAL={real}"]))
     for d in SECTOR_DIMS:
         units.append((f"cv_{d}.o", "cv_inst.cu", [f"-DQMC_D={d}"]))
-    for src in ("finalize.cu", "api.cu", "deformed.cu", "batch.cu", "cbc.cpp", "cv.cu", "noalloc.cu", "jit.cu", "probe.cu", "multi.cu"):
+    for src in ("finalize.cu", "api.cu", "deformed.cu", "batch.cu", "cbc.cpp", "cv.cu", "noalloc.cu", "jit.cu", "probe.cu", "multi.cu", "persist.cu"):
         if os.path.exists(os.path.join(CSRC, src)):
             units.append((os.path.splitext(src)[0] + ".o", src, []))
     return units

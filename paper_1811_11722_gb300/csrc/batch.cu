@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <string>
 #include <thread>
 #include <cstring>
@@ -42,6 +43,23 @@ struct BatchPlan {
   std::vector<FinalizeArgs> fin_host;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // persistent mode: one launch over (descriptor, j-chunk) work items
+  bool persistent = false;
+  uint32_t chunk = 1u << 16;
+  struct Sector {
+    int m = 0;
+    uint64_t n = 0;
+    int nitems = 0;
+    double final_scale = 1.0;
+  };
+  std::vector<Sector> psec;
+  std::vector<int> pdesc_sector;         // descriptor -> sector
+  std::vector<PersistDesc> pdesc;
+  std::vector<PersistItem> pitems;
+  PersistDesc* pdesc_dev = nullptr;
+  PersistItem* pitems_dev = nullptr;
+  unsigned* pnext_dev = nullptr;
+  int pgrid = 0;
 };
 
 static void batch_release(BatchPlan* bp) {
@@ -198,6 +216,236 @@ static int batch_graph(BatchPlan* bp) {
   return QMC_OK;
 }
 
+// ---------------------------------------------------------- persistent --
+
+static bool poly_positive_host(const qmc_poly& p, int d) {
+  bool has_const = false;
+  for (int t = 0; t < p.nterms; ++t) {
+    int deg = 0;
+    for (int i = 0; i < d; ++i) deg += p.expo[(size_t)t * d + i];
+    if (p.coef[t] < 0.0) return false;
+    if (deg == 0 && p.coef[t] > 0.0) has_const = true;
+  }
+  return has_const;
+}
+
+// Descriptors (one per sector and chunk of kPersistMc shifts) and the work
+// list, longest items first.
+static int persist_build(BatchPlan* bp, int32_t count, const qmc_problem* problems, uint32_t chunk) {
+  if (count < 1 || count > 65536) return fail(QMC_EINVAL, "batch count=%d outside [1, 65536]", count);
+  if (!problems) return fail(QMC_EINVAL, "null problems");
+  if (chunk < (uint32_t)kThreads || chunk % kThreads != 0 || chunk > (1u << 24))
+    return fail(QMC_EINVAL, "chunk of %u points: a multiple of %d in [%d, 2^24]", chunk, kThreads, kThreads);
+  bp->count = count;
+  bp->persistent = true;
+  bp->chunk = chunk;
+  bp->psec.assign(count, BatchPlan::Sector());
+  bp->pdesc.clear();
+  bp->pdesc_sector.clear();
+  bp->pitems.clear();
+  bp->ps_off.clear();
+  bp->total_m = 0;
+  bp->max_m = 0;
+  struct Cost {
+    double c;
+    PersistItem it;
+  };
+  std::vector<Cost> costs;
+  for (int s = 0; s < count; ++s) {
+    const qmc_problem& q = problems[s];
+    int rc = validate_problem(q.d, q.n, q.m, q.g, q.shifts, q.t, q.f);
+    if (rc) {
+      const std::string why = qmc_last_error();
+      return fail(rc, "problem %d: %s", s, why.c_str());
+    }
+    const qmc_integrand& f = *q.f;
+    const bool tr_ok = q.t.kind != QMC_TRANSFORM_KOROBOV || q.t.alpha == 3;
+    if (f.kind != QMC_F_SECTOR || f.precision != QMC_FP32EVAL || f.aU != -2 || f.aF != -1 || q.d > kDFast ||
+        poly_degree(f.U, q.d) > 1 || poly_degree(f.F, q.d) > 2 || !tr_ok)
+      return fail(QMC_EUNSUPPORTED,
+                  "problem %d: the persistent batch takes FP32EVAL U^-2 F^-1 sectors, deg U <= 1, deg F <= 2, "
+                  "d <= %d, transform none, baker or Korobov 3", s, kDFast);
+    RuleParams<float> base;
+    fill_common(base, q.d, q.n, q.g, q.t, &f);
+    auto cu = pack_dense(f.U, q.d, 1);
+    auto cf = pack_dense(f.F, q.d, 2);
+    prescale_slots(cu.data(), q.d, 1, fx_sigma(base.tr));
+    prescale_slots(cf.data(), q.d, 2, fx_sigma(base.tr));
+    for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (float)cu[i];
+    for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (float)cf[i];
+    fill_pairs(base, q.d);
+    base.check_finite = (poly_positive_host(f.U, q.d) && poly_positive_host(f.F, q.d)) ? 0 : 1;
+    base.m_total = q.m;
+    BatchPlan::Sector& sec = bp->psec[s];
+    sec.m = q.m;
+    sec.n = q.n;
+    sec.nitems = (int)((q.n + chunk - 1) / chunk);
+    sec.final_scale = base.tr == TR_KOROBOV ? std::pow((double)base.kor[7], (double)q.d) : 1.0;
+    bp->ps_off.push_back((size_t)bp->total_m * 2);
+    bp->total_m += q.m;
+    bp->max_m = std::max(bp->max_m, q.m);
+    const double per_point = (double)(poly_slots(q.d, 1) + poly_slots(q.d, 2) + 2 * q.d);
+    for (int k0 = 0; k0 < q.m; k0 += kPersistMc) {
+      const int mk = std::min(kPersistMc, q.m - k0);
+      PersistDesc D;
+      std::memset(&D, 0, sizeof(D));
+      D.P = base;
+      D.P.m_launch = mk;
+      D.P.k_base = k0;
+      for (int kk = 0; kk < kPersistMc; ++kk)  // rows mk.. repeat row k0 (evaluated, never written back)
+        for (int i = 0; i < q.d; ++i)
+          set_shift(D.P, kk, i, shift_fixed64(q.shifts[(size_t)(kk < mk ? k0 + kk : k0) * q.d + i]));
+      D.nitems = sec.nitems;
+      const uint32_t di = (uint32_t)bp->pdesc.size();
+      bp->pdesc.push_back(D);
+      bp->pdesc_sector.push_back(s);
+      for (int it = 0; it < sec.nitems; ++it) {
+        const uint64_t pts = std::min<uint64_t>(chunk, q.n - (uint64_t)it * chunk);
+        costs.push_back({(double)pts * per_point * kPersistMc, PersistItem{di, (uint32_t)it}});
+      }
+    }
+  }
+  if (costs.size() > 0xFFFFFFF0ull) return fail(QMC_EINVAL, "too many work items (%zu)", costs.size());
+  std::stable_sort(costs.begin(), costs.end(), [](const Cost& a, const Cost& b) { return a.c > b.c; });
+  bp->pitems.reserve(costs.size());
+  for (const Cost& c : costs) bp->pitems.push_back(c.it);
+  bp->launches = 2;  // the persistent kernel and the final pass
+  return QMC_OK;
+}
+
+static int persist_alloc(BatchPlan* bp) {
+  size_t bytes = 0;
+  std::vector<size_t> part_off(bp->count), cnt_off(bp->count);
+  for (int i = 0; i < bp->count; ++i) {
+    part_off[i] = bytes;
+    bytes += (size_t)bp->psec[i].m * bp->psec[i].nitems * 2 * sizeof(double);
+  }
+  for (int i = 0; i < bp->count; ++i) {
+    cnt_off[i] = bytes;
+    bytes += 2 * sizeof(unsigned long long);
+  }
+  const size_t next_off = bytes;
+  bytes += 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t res_off = bytes;
+  bytes += (size_t)bp->count * sizeof(qmc_result);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t ps_off = bytes;
+  bytes += (size_t)bp->total_m * 2 * sizeof(double);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t fin_off = bytes;
+  bytes += (size_t)bp->count * sizeof(FinalizeArgs);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t desc_off = bytes;
+  bytes += bp->pdesc.size() * sizeof(PersistDesc);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t item_off = bytes;
+  bytes += bp->pitems.size() * sizeof(PersistItem);
+  cudaError_t e = cudaMalloc(&bp->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QMC_ENOMEM, "persistent batch workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  char* base = (char*)bp->ws;
+  bp->res_dev = (qmc_result*)(base + res_off);
+  bp->ps_dev = (double*)(base + ps_off);
+  bp->fin_dev = (FinalizeArgs*)(base + fin_off);
+  bp->pdesc_dev = (PersistDesc*)(base + desc_off);
+  bp->pitems_dev = (PersistItem*)(base + item_off);
+  bp->pnext_dev = (unsigned*)(base + next_off);
+  bp->fin_host.resize(bp->count);
+  for (int i = 0; i < bp->count; ++i) {
+    const BatchPlan::Sector& sec = bp->psec[i];
+    FinalizeArgs& A = bp->fin_host[i];
+    std::memset(&A, 0, sizeof(A));
+    A.partial = (double*)(base + part_off[i]);
+    A.nblk = sec.nitems;
+    A.m = sec.m;
+    A.is_complex = 0;
+    A.dn = (double)sec.n;
+    A.value_scale = sec.final_scale;
+    A.counters = (unsigned long long*)(base + cnt_off[i]);
+    A.result = bp->res_dev + i;
+    A.per_shift = bp->ps_dev + bp->ps_off[i];
+  }
+  for (size_t q = 0; q < bp->pdesc.size(); ++q) {
+    const int s = bp->pdesc_sector[q];
+    bp->pdesc[q].partial = (double*)(base + part_off[s]);
+    bp->pdesc[q].counters = (unsigned long long*)(base + cnt_off[s]);
+  }
+  e = cudaMemcpy(bp->fin_dev, bp->fin_host.data(), (size_t)bp->count * sizeof(FinalizeArgs), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(bp->pdesc_dev, bp->pdesc.data(), bp->pdesc.size() * sizeof(PersistDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(bp->pitems_dev, bp->pitems.data(), bp->pitems.size() * sizeof(PersistItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(base + cnt_off[0], 0, (size_t)bp->count * 2 * sizeof(unsigned long long) + 16);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent batch descriptors");
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persist_kernel_ptr(), kThreads, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent kernel occupancy");
+  const int sms = device_sms();
+  if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
+  bp->pgrid = (int)std::min<uint64_t>((uint64_t)sms * (uint64_t)std::max(occ, 1), bp->pitems.size());
+  return QMC_OK;
+}
+
+// counter reset -> persistent kernel -> final pass
+static int persist_graph(BatchPlan* bp) {
+  cudaError_t e = cudaGraphCreate(&bp->graph, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+  cudaMemsetParams mp;
+  std::memset(&mp, 0, sizeof(mp));
+  mp.dst = bp->pnext_dev;
+  mp.value = 0;
+  mp.elementSize = 4;
+  mp.width = 1;
+  mp.height = 1;
+  mp.pitch = 4;
+  cudaGraphNode_t mnode;
+  e = cudaGraphAddMemsetNode(&mnode, bp->graph, nullptr, 0, &mp);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddMemsetNode");
+  PersistArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.descs = bp->pdesc_dev;
+  A.items = bp->pitems_dev;
+  A.nitems = (uint32_t)bp->pitems.size();
+  A.chunk = bp->chunk;
+  A.next = bp->pnext_dev;
+  void* kargs[1] = {&A};
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.func = (void*)persist_kernel_ptr();
+  kp.gridDim = dim3(bp->pgrid);
+  kp.blockDim = dim3(kThreads);
+  kp.kernelParams = kargs;
+  cudaGraphNode_t knode;
+  e = cudaGraphAddKernelNode(&knode, bp->graph, &mnode, 1, &kp);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddKernelNode (persistent kernel)");
+  FinalizeArgs* fin = bp->fin_dev;
+  void* fargs[1] = {&fin};
+  cudaKernelNodeParams fp;
+  std::memset(&fp, 0, sizeof(fp));
+  fp.func = (void*)finalize_batch_ptr();
+  fp.gridDim = dim3(bp->count);
+  fp.blockDim = dim3(256);
+  fp.sharedMemBytes = (unsigned)((size_t)bp->max_m * 2 * sizeof(double));
+  fp.kernelParams = fargs;
+  cudaGraphNode_t fnode;
+  e = cudaGraphAddKernelNode(&fnode, bp->graph, &knode, 1, &fp);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddKernelNode (final pass)");
+  e = cudaGraphInstantiate(&bp->exec, bp->graph, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return QMC_OK;
+}
+
+static int persist_create(BatchPlan* bp, int32_t count, const qmc_problem* problems, uint32_t chunk) {
+  int rc = persist_build(bp, count, problems, chunk);
+  if (rc) return rc;
+  rc = persist_alloc(bp);
+  if (rc) return rc;
+  return persist_graph(bp);
+}
+
 static int batch_create(BatchPlan* bp, int32_t count, const qmc_problem* problems, uint64_t work_per_cta) {
   int rc = batch_build(bp, count, problems, work_per_cta);
   if (rc) return rc;
@@ -253,6 +501,21 @@ int qmc_batch_plan_create(int32_t count, const qmc_problem* problems, qmc_batch_
   return QMC_OK;
 }
 
+int qmc_batch_plan_create_persistent(int32_t count, const qmc_problem* problems, uint32_t chunk_points,
+                                     qmc_batch_plan* plan_out) {
+  if (!plan_out) return fail(QMC_EINVAL, "null plan_out");
+  *plan_out = nullptr;
+  std::unique_ptr<BatchPlan> bp(new BatchPlan());
+  bp->src.assign(problems, problems + (problems && count > 0 ? count : 0));
+  int rc = persist_create(bp.get(), count, problems, chunk_points ? chunk_points : (1u << 16));
+  if (rc) {
+    batch_release(bp.get());
+    return rc;
+  }
+  *plan_out = reinterpret_cast<qmc_batch_plan>(bp.release());
+  return QMC_OK;
+}
+
 int qmc_batch_plan_execute(qmc_batch_plan plan, qmc_result* out, double* per_shift, void* stream) {
   if (!plan) return fail(QMC_EINVAL, "null plan");
   return batch_execute(reinterpret_cast<BatchPlan*>(plan), out, per_shift, (cudaStream_t)stream);
@@ -281,12 +544,14 @@ int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* 
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return fail(QMC_ECUDA, "events");
   std::vector<qmc_result> scratch(bp->count);
   float best_ms = 1e30f;
-  uint64_t best_w = bp->work_per_cta;
+  const bool pers = bp->persistent;
+  uint64_t best_w = pers ? bp->chunk : bp->work_per_cta;
   int rc = QMC_OK;
-  for (int lw = 18; lw <= 24 && rc == QMC_OK; ++lw) {
+  // graph mode: evaluations per CTA 2^18..2^24; persistent mode: points per work item 2^14..2^18
+  for (int lw = pers ? 14 : 18; lw <= (pers ? 18 : 24) && rc == QMC_OK; ++lw) {
     const uint64_t w = 1ull << lw;
     BatchPlan trial;
-    rc = batch_create(&trial, bp->count, problems, w);
+    rc = pers ? persist_create(&trial, bp->count, problems, (uint32_t)w) : batch_create(&trial, bp->count, problems, w);
     if (rc) break;
     float tot = 0.0f;
     for (int rep = 0; rep < 4 && rc == QMC_OK; ++rep) {
@@ -308,10 +573,10 @@ int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* 
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;
-  if (best_w != bp->work_per_cta) {
+  if (best_w != (pers ? (uint64_t)bp->chunk : bp->work_per_cta)) {
     cudaStreamSynchronize(st);
     batch_release(bp);
-    rc = batch_create(bp, bp->count, problems, best_w);
+    rc = pers ? persist_create(bp, bp->count, problems, (uint32_t)best_w) : batch_create(bp, bp->count, problems, best_w);
     if (rc) return rc;
   }
   if (work_per_cta_out) *work_per_cta_out = best_w;

@@ -75,6 +75,7 @@ inline const void* general_eps_ptr(bool fp32) {
 // batched form takes a device array of FinalizeArgs, one CTA per problem.
 const void* finalize_ptr();
 const void* finalize_batch_ptr();
+const void* persist_kernel_ptr();  // batched sectors in one persistent launch (persist.cu)
 
 // Arguments of the final pass.
 struct FinalizeArgs {

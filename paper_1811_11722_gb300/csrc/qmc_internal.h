@@ -151,6 +151,32 @@ struct MultiParams {
   float2 cps[kMultiChunk][kPairCoefMax];  // U's then -F's slots, per integrand
 };
 
+// Batched sectors in one persistent launch.  A descriptor is one sector's
+// rule for one chunk of up to kPersistMc shifts (FP32 packed sector path:
+// prescaled dense slots and their (c, c) pairs, shift rows padded with the
+// chunk's first row); a work item is (descriptor, j-chunk).  CTAs take items
+// from a counter in any order; item q of a sector writes the fixed slots
+// [k][q] of that sector, so the result does not depend on the order.
+constexpr int kPersistMc = 8;
+struct alignas(16) PersistDesc {
+  RuleParams<float> P;
+  double* partial;                // the sector's slots [m][nitems][2]
+  unsigned long long* counters;   // the sector's counters [2]
+  int32_t nitems;                 // j-chunks of the sector
+  int32_t pad[3];
+};
+struct PersistItem {
+  uint32_t desc;  // descriptor
+  uint32_t item;  // j-chunk of its sector: points [item * chunk, min(n, (item + 1) * chunk))
+};
+struct PersistArgs {
+  const PersistDesc* descs;
+  const PersistItem* items;
+  uint32_t nitems;
+  uint32_t chunk;   // points per item, a multiple of kThreads
+  unsigned* next;   // item counter, zero at launch
+};
+
 // Sparse monomial table for the general kernel (any degree, d <= QMC_DMAX).
 template <typename R>
 struct SparsePoly {

@@ -112,6 +112,7 @@ def lib():
                                                      ctypes.c_double, vp, ctypes.POINTER(i32), vp]
             L.qmc_integrate_batch.argtypes = [i32, vp, vp, vp, vp]
             L.qmc_batch_plan_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
+            L.qmc_batch_plan_create_persistent.argtypes = [i32, vp, ctypes.c_uint32, ctypes.POINTER(vp)]
             L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
             L.qmc_batch_plan_destroy.argtypes = [vp]
             L.qmc_batch_plan_launches.argtypes = [vp, ctypes.POINTER(i32)]
@@ -142,7 +143,7 @@ def lib():
                          "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts", "qmc_measure_peaks",
                          "qmc_integrate_to_tolerance", "qmc_integrate_eps", "qmc_eps_plan_create",
                          "qmc_sample_points_eps", "qmc_integrate_multi", "qmc_multi_plan_create", "qmc_make_lattice_embedded",
-                         "qmc_integrate_extensible"):
+                         "qmc_integrate_extensible", "qmc_batch_plan_create_persistent"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -356,12 +357,19 @@ def qmc_integrate_batch(problems, stream=0, want_per_shift=False):
 
 
 class BatchPlan:
-    """qmc_batch_plan_create / _execute / _destroy."""
+    """qmc_batch_plan_create (a graph of per-problem kernels) or, with
+    persistent=True, qmc_batch_plan_create_persistent (one persistent launch,
+    `chunk` points per work item, 0 = the library default); _execute /
+    _destroy."""
 
-    def __init__(self, problems):
+    def __init__(self, problems, persistent=False, chunk=0):
         self.b = _Batch(problems)
         h = ctypes.c_void_p()
-        _check(lib().qmc_batch_plan_create(self.b.count, ctypes.cast(self.b.arr, ctypes.c_void_p), ctypes.byref(h)))
+        arr = ctypes.cast(self.b.arr, ctypes.c_void_p)
+        if persistent:
+            _check(lib().qmc_batch_plan_create_persistent(self.b.count, arr, int(chunk), ctypes.byref(h)))
+        else:
+            _check(lib().qmc_batch_plan_create(self.b.count, arr, ctypes.byref(h)))
         self.h = h
 
     def execute(self, out=None, per_shift=None, stream=0):

@@ -163,6 +163,46 @@ def test_multi_validation(Q, case, status):
     assert ei.value.status == getattr(Q, "QMC_" + status)
 
 
+@pytest.mark.parametrize("case,status", [("chunk100", "EINVAL"), ("fp64", "EUNSUPPORTED"), ("deg3", "EUNSUPPORTED"),
+                                         ("alpha2", "EUNSUPPORTED"), ("d9", "EUNSUPPORTED"),
+                                         ("powers", "EUNSUPPORTED"), ("bad_g", "EINVAL")])
+def test_persistent_batch_validation(Q, case, status):
+    """The persistent batch checks every problem on the host, before any
+    device work (so these run without a GPU)."""
+    d, n, m = 3, 101, 4
+    coef = np.array([1.0, 0.5])
+    expo = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.uint8)
+    t = Q.transform("baker")
+    g = np.arange(1, d + 1, dtype=np.uint64)
+    shifts = np.full((m, d), 0.25)
+    f = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP32EVAL, (coef, expo), (coef, expo))
+    probs = [(d, n, m, g, shifts, t, f), (d, n, m, g, shifts, t, f)]
+    chunk = 0
+    if case == "chunk100":
+        chunk = 100
+    elif case == "fp64":
+        probs[1] = (d, n, m, g, shifts, t, Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP64, (coef, expo), (coef, expo)))
+    elif case == "deg3":
+        f3 = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP32EVAL, (coef, expo),
+                         (coef, np.array([[0, 0, 0], [1, 1, 1]], np.uint8)))
+        probs[0] = (d, n, m, g, shifts, t, f3)
+    elif case == "alpha2":
+        probs[1] = (d, n, m, g, shifts, Q.transform("korobov", 2), f)
+    elif case == "d9":
+        e9 = np.zeros((2, 9), np.uint8)
+        e9[1, 0] = 1
+        probs[0] = (9, n, m, np.arange(1, 10, dtype=np.uint64), np.full((m, 9), 0.25), t,
+                    Q.Integrand(Q.QMC_F_SECTOR, 9, Q.QMC_FP32EVAL, (coef, e9), (coef, e9)))
+    elif case == "powers":
+        probs[1] = (d, n, m, g, shifts, t, Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP32EVAL, (coef, expo), (coef, expo),
+                                                       -1, -1))
+    elif case == "bad_g":
+        probs[1] = (d, n, m, np.array([1, 101, 3], dtype=np.uint64), shifts, t, f)
+    with pytest.raises(Q.QmcError) as ei:
+        Q.BatchPlan(probs, persistent=True, chunk=chunk)
+    assert ei.value.status == getattr(Q, "QMC_" + status)
+
+
 def test_make_lattice_rejects_composite(Q):
     with pytest.raises(Q.QmcError):
         Q.qmc_make_lattice(3, 1001, [1.0, 0.25, 1 / 9])

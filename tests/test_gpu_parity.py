@@ -425,6 +425,72 @@ def test_batch_plan_graph_replay_and_tune(Q):
     bp.destroy()
 
 
+def test_persistent_batch_matches_oracle_and_graph(Q, oracle_lib, nthreads):
+    """One persistent launch over a mixed batch of FP32 sectors (d = 1..8;
+    baker, none and Korobov 3; m = 5, 16 and 21, so shift chunks of 8 with
+    padded rows; a non-positive F, so the non-finite check is on): every
+    problem's per-shift values match the oracle, and the graph batch on the
+    same problems within the grouping of the compensated sums.  Chunks of
+    1024 points leave ragged last items."""
+    sect = I.config3(count=9)
+    trs = [("baker", 0), ("none", 0), ("korobov", 3)]
+    ms = [5, 16, 21]
+    probs = []
+    for s, p in enumerate(sect):
+        p.n = I.prev_prime(20000 + 3000 * s)
+        p.transform, p.alpha = trs[s % 3]
+        p = I.with_shifts(p, ms[s % 3], 1200 + s)
+        probs.append(p)
+    d1 = I.Problem("d1", 1, 10007, 4, I.make_shifts(I.SplitMix64(5), 4, 1), "baker", kind="sector",
+                   U=I.random_poly(I.SplitMix64(6), 1, 1, 0), F=I.random_poly(I.SplitMix64(7), 1, 0, 1),
+                   precision="fp32", gamma=I.product_weights(1))
+    probs.append(d1)
+    neg = I.config3(count=3, seed=I.SEED_BASE + 78)[2]
+    neg.n = I.prev_prime(30000)
+    neg.F.coef[-1] = -0.05  # F may vanish inside the cube: CHECK path
+    probs.append(neg)
+    gs = [I.random_generating_vector(I.SplitMix64(800 + i), p.d, p.n) for i, p in enumerate(probs)]
+    tuples = [_batch_tuple(Q, p, g, "fp32") for p, g in zip(probs, gs)]
+    total_m = sum(p.m for p in probs)
+    pp = Q.BatchPlan(tuples, persistent=True, chunk=1024)
+    assert pp.launches() == 2
+    ps_p = np.zeros(2 * total_m)
+    res_p = pp.execute(per_shift=ps_p)
+    ps_p2 = np.zeros(2 * total_m)
+    pp.execute(per_shift=ps_p2)
+    assert np.array_equal(ps_p, ps_p2)  # replays are deterministic
+    pp.destroy()
+    res_g, ps_g = Q.qmc_integrate_batch(tuples, want_per_shift=True)
+    off = 0
+    for p, g, r, rg in zip(probs, gs, res_p, res_g):
+        q = ps_p[2 * off: 2 * (off + p.m)].reshape(p.m, 2)
+        qg = ps_g[2 * off: 2 * (off + p.m)].reshape(p.m, 2)
+        off += p.m
+        assert r.status == rg.status, p.name
+        assert r.nonfinite == rg.nonfinite, p.name
+        assert np.all(np.abs(q[:, 0] - qg[:, 0]) <= 1e-8 * np.abs(qg[:, 0])), p.name
+        ref = oracle_lib.integrate(p, g, nthreads=nthreads)
+        assert np.all(np.abs(q[:, 0] - ref["q"][:, 0]) <= 4e-7 * np.abs(ref["q"][:, 0])), p.name
+
+
+def test_persistent_batch_tune(Q):
+    """The tuner sweeps the work-item size of a persistent plan and keeps
+    results within FP32 rounding."""
+    sect = I.config3(count=12)
+    for s, p in enumerate(sect):
+        p.n = I.prev_prime(60000 + 9000 * s)
+    gs = [I.random_generating_vector(I.SplitMix64(950 + i), p.d, p.n) for i, p in enumerate(sect)]
+    tuples = [_batch_tuple(Q, p, g) for p, g in zip(sect, gs)]
+    pp = Q.BatchPlan(tuples, persistent=True)
+    a = [r.as_dict() for r in pp.execute()]
+    w = pp.tune()
+    assert (1 << 14) <= w <= (1 << 18)
+    b = [r.as_dict() for r in pp.execute()]
+    for x, y in zip(a, b):
+        assert abs(x["mean"][0] - y["mean"][0]) <= 1e-7 * abs(x["mean"][0])
+    pp.destroy()
+
+
 def test_config3_full_batch_sampled(Q, oracle_lib, nthreads):
     """The full batched-sector configuration (256 sectors, ~9.3e9 evaluations):
     every status OK, and the six smallest sectors checked against the oracle."""
@@ -433,6 +499,13 @@ def test_config3_full_batch_sampled(Q, oracle_lib, nthreads):
     tuples = [_batch_tuple(Q, p, g) for p, g in zip(sect, gs)]
     res, ps = Q.qmc_integrate_batch(tuples, want_per_shift=True)
     assert all(r.status == 0 for r in res)
+    # the same batch as one persistent launch: every sector's per-shift values
+    # agree with the graph's within the grouping of the compensated sums
+    pp = Q.BatchPlan(tuples, persistent=True)
+    ps_p = np.zeros_like(ps)
+    assert all(r.status == 0 for r in pp.execute(per_shift=ps_p))
+    pp.destroy()
+    assert np.all(np.abs(ps_p[0::2] - ps[0::2]) <= 1e-8 * np.abs(ps[0::2]))
     offs = np.cumsum([0] + [p.m for p in sect])
     for i in sorted(range(len(sect)), key=lambda i: sect[i].n)[:6]:
         ref = oracle_lib.integrate(sect[i], gs[i], nthreads=nthreads)
