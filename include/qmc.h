@@ -283,8 +283,9 @@ typedef struct {
 
 /* Fit the surrogate on the GPU to f at the n_pilot points of one shifted
  * lattice (g_pilot, shift_pilot [d]) on the untransformed cube (f evaluated in
- * FP64 by the rule's own kernel; t is not used here), mean squared error,
- * FP32 training kernels.
+ * FP64 by the rule's own kernel; t is not used here), mean squared error;
+ * the fit's contractions run on tensor cores (BF16 operands, FP32
+ * accumulation).
  *   a_out     [R*d*K] host, the parameters rounded to bfloat16 (stored as float)
  *   loss_out  optional [2] host: loss before the first and after the last step
  * Synchronises `stream`. */
@@ -301,7 +302,10 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
  * the same points (the fallback: keep whichever error is smaller).
  * per_shift (optional, [m*2]) gets the two per-shift values.  Supports
  * FP32EVAL sector integrands U^-2 F^-1 with deg U <= 1, deg F <= 2, d <= 8,
- * transform none, baker or Korobov 3. */
+ * transform none, baker or Korobov 3.  f is evaluated as by the FP32 sector
+ * kernels; g's per-dimension contraction runs on tensor cores (TF32 products
+ * of the parameters with a head/remainder split of each basis value, degree 0
+ * added in FP32), which keeps g to FP32 accuracy. */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                      qmc_transform t, const qmc_integrand* f, const qmc_cv_config* cfg, const float* a,
