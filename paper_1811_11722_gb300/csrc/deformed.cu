@@ -37,11 +37,12 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
     worst = std::max(worst, 0.25 * f->lambda * row);
   }
   const bool fast = worst < 1.0 && t.kind == QMC_TRANSFORM_KOROBOV && t.alpha == 3 && !tune.force_general;
+  const bool u_linear = poly_degree(f->U, d) <= 1;  // U on its degree-1 slots only
   const void* func = nullptr;
   switch (d) {
 #define QMC_D_CASE(DD) \
   case DD:             \
-    func = deformed_ptr<R, DD>(fast); \
+    func = deformed_ptr<R, DD>(fast, u_linear); \
     break;
     QMC_D_CASE(1) QMC_D_CASE(2) QMC_D_CASE(3) QMC_D_CASE(4) QMC_D_CASE(5) QMC_D_CASE(6) QMC_D_CASE(7)
     QMC_D_CASE(8)
@@ -49,7 +50,7 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
     default: break;
   }
   if (!func) return fail(QMC_EUNSUPPORTED, "no deformed kernel for d=%d", d);
-  auto cu = pack_dense(f->U, d, 2);
+  auto cu = pack_dense(f->U, d, u_linear ? 1 : 2);
   for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
   for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
   base.value_scale = 1.0;  // transform weights normalised per factor in this kernel

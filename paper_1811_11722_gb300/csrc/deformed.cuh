@@ -78,6 +78,19 @@ __device__ __forceinline__ Cx<R> poly2_complex(const R* c, const Cx<R>* z) {
   return acc;
 }
 
+// Complex evaluation of a degree-1 polynomial with real coefficients
+// (nested layout c0, l_0 .. l_{D-1}).
+template <int D, typename R>
+__device__ __forceinline__ Cx<R> poly1_complex(const R* c, const Cx<R>* z) {
+  Cx<R> acc{c[0], R(0)};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    acc.re = fma_(c[1 + i], z[i].re, acc.re);
+    acc.im = fma_(c[1 + i], z[i].im, acc.im);
+  }
+  return acc;
+}
+
 template <typename R>
 __device__ __forceinline__ R cmag1(R re, R im) {
   return fabs(re) + fabs(im);
@@ -136,8 +149,9 @@ __device__ __forceinline__ Cx<R> det_ipm(R (&M)[D][D]) {
 
 // Weighted complex value at one point and shift; *bad set when Im F(w) > 0.
 // FAST: compile-time Korobov weight 3 and no pivoting (host-checked);
-// otherwise the runtime transform and pivoted LU.
-template <typename R, int D, bool FAST = false>
+// otherwise the runtime transform and pivoted LU.  KU: degree of U (1 or 2),
+// with cU in that degree's nested layout.
+template <typename R, int D, bool FAST = false, int KU = 2>
 __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const typename FixT<R>::T* base, int k,
                                                 bool& bad) {
   R y[D];
@@ -179,7 +193,9 @@ __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const ty
     }
   }
   const Cx<R> dJ = det_ipm<D, R, !FAST>(M);
-  const Cx<R> U = poly2_complex<D, R>(P.cU, z);
+  Cx<R> U;
+  if constexpr (KU == 1) U = poly1_complex<D, R>(P.cU, z);
+  else U = poly2_complex<D, R>(P.cU, z);
   const Cx<R> F = poly2_complex<D, R>(cF, z);
   bad = F.im > R(0);
   Cx<R> v;
@@ -192,7 +208,7 @@ __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const ty
 
 constexpr int kMcDeformed = 8;
 
-template <typename R, int D, bool FAST = false>
+template <typename R, int D, bool FAST = false, int KU = 2>
 __global__ void __launch_bounds__(kThreads)
     deformed_kernel(const __grid_constant__ RuleParams<R> P, double* __restrict__ partial,
                     unsigned long long* __restrict__ counters, const SampleIO sio) {
@@ -211,7 +227,7 @@ __global__ void __launch_bounds__(kThreads)
       if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<R>(base[i] + shift_of(P, k, i));
     }
     bool bad;
-    Cx<R> v = deformed_value<R, D, FAST>(P, base, k, bad);
+    Cx<R> v = deformed_value<R, D, FAST, KU>(P, base, k, bad);
     sio.values[2 * (size_t)s] = (double)v.re * P.value_scale;
     sio.values[2 * (size_t)s + 1] = (double)v.im * P.value_scale;
     return;
@@ -244,7 +260,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int i = 0; i < D; ++i) base[i] = fix_base<R>(idx[i], P.rc);
         bool bad;
-        Cx<R> v = deformed_value<R, D, FAST>(P, base, kk, bad);
+        Cx<R> v = deformed_value<R, D, FAST, KU>(P, base, kk, bad);
         ndef += bad ? 1u : 0u;
         if (P.check_finite) {
           const bool ok = finite_(v.re) && finite_(v.im);

@@ -37,8 +37,8 @@ QMC_DECL_EPS(double, 5) QMC_DECL_EPS(double, 6) QMC_DECL_EPS(double, 7) QMC_DECL
 // and unpivoted LU (host-checked dominance); otherwise runtime transform and
 // pivoted LU.
 template <typename R, int D>
-const void* deformed_ptr(bool fast);
-#define QMC_DECL_DEF(R, D) template <> const void* deformed_ptr<R, D>(bool);
+const void* deformed_ptr(bool fast, bool u_linear);
+#define QMC_DECL_DEF(R, D) template <> const void* deformed_ptr<R, D>(bool, bool);
 QMC_DECL_DEF(float, 1) QMC_DECL_DEF(float, 2) QMC_DECL_DEF(float, 3) QMC_DECL_DEF(float, 4)
 QMC_DECL_DEF(float, 5) QMC_DECL_DEF(float, 6) QMC_DECL_DEF(float, 7) QMC_DECL_DEF(float, 8)
 QMC_DECL_DEF(double, 1) QMC_DECL_DEF(double, 2) QMC_DECL_DEF(double, 3) QMC_DECL_DEF(double, 4)

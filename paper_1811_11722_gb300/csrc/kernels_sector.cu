@@ -61,8 +61,12 @@ const void* eps_ptr<QMC_REAL, QMC_D>(int ne, int tr) {
 }
 
 template <>
-const void* deformed_ptr<QMC_REAL, QMC_D>(bool fast) {
-  return fast ? (const void*)&deformed_kernel<QMC_REAL, QMC_D, true> : (const void*)&deformed_kernel<QMC_REAL, QMC_D, false>;
+const void* deformed_ptr<QMC_REAL, QMC_D>(bool fast, bool u_linear) {
+  if (u_linear)
+    return fast ? (const void*)&deformed_kernel<QMC_REAL, QMC_D, true, 1>
+                : (const void*)&deformed_kernel<QMC_REAL, QMC_D, false, 1>;
+  return fast ? (const void*)&deformed_kernel<QMC_REAL, QMC_D, true, 2>
+              : (const void*)&deformed_kernel<QMC_REAL, QMC_D, false, 2>;
 }
 
 }  // namespace qmc
