@@ -353,8 +353,10 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
     <= 2^(e/2)), each level a fresh rule with its CBC vector; lattice
     construction is a precompute and is not timed, everything else is.
     Compares the plain rule on the prime ladder, the embedded base-2 lattices
-    (each level adds only the new half of the points) and the control variate
+    (each level adds only the new half of the points), the sum of 32 sectors as
+    one fused sweep against one rule per sector, and the control variate
     (training included)."""
+    import numpy as np
     out = {}
     ladder = [n for n in I.ladder_primes() if n >= 65521]
     sh = torch.cuda.current_stream().cuda_stream
@@ -370,9 +372,16 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
             self[n] = qmc.qmc_make_lattice(self.d, n, self.gamma)
             return self[n]
 
+    caches = {}
+
+    def lat_for(p):
+        if p.d not in caches:
+            caches[p.d] = lattices(p.d, p.gamma)
+        return caches[p.d]
+
     # plain rule on the single-sector workload and on the d=8 Korobov-3 sector
     for name, p in (("sector_d6_baker_fp32", I.config2()), ("sector_d8_korobov3_fp32", I.config5())):
-        lat = lattices(p.d, p.gamma)
+        lat = lat_for(p)
         f = qmc.integrand_from_problem(p, "fp32")
         t = qmc.transform(p.transform, p.alpha)
         # the integrand's kernel is compiled at run time on first use: a precompute, like the lattices
@@ -396,9 +405,40 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
         out[name + "_embedded"] = {"n": 1 << (16 + lvl), "rel_err": r.err[0] / abs(r.mean[0]), "mean": r.mean[0],
                                    "wall_s": time.perf_counter() - t0, "reached": bool(ok),
                                    "points_evaluated_per_shift": 1 << (16 + lvl)}
+    # integrand-sum batching: the sum of the 32 d = 6 sectors of the shared-lattice
+    # variant of configuration 3 (Korobov 3), one fused sweep per level
+    # (qmc_integrate_multi) against one rule per sector (qmc_integrate, per-shift
+    # values summed, Eq. (3) by qmc_combine_shifts); the same points either way
+    probs = I.config3_shared(transform="korobov", alpha=3)
+    fs = [qmc.integrand_from_problem(q) for q in probs]
+    sh6, m6, tb = probs[0].shifts, probs[0].m, qmc.transform("korobov", 3)
+    lat = lat_for(probs[0])
+    n0 = ladder[0]
+    qmc.qmc_integrate_multi(6, n0, m6, lat[n0], sh6, tb, fs, stream=sh)  # run-time compilation: a precompute
+    for f_ in fs:
+        qmc.qmc_integrate(6, n0, m6, lat[n0], sh6, tb, f_, stream=sh)
+    for mode in ("fused", "one_rule_per_sector"):
+        wall, rec = 0.0, None
+        for n in ladder:
+            gn = lat[n]
+            t0 = time.perf_counter()
+            if mode == "fused":
+                r = qmc.qmc_integrate_multi(6, n, m6, gn, sh6, tb, fs, stream=sh)[0][-1]
+            else:
+                tot = np.zeros((m6, 2))
+                for f_ in fs:
+                    tot += qmc.qmc_integrate(6, n, m6, gn, sh6, tb, f_, stream=sh, want_per_shift=True)[1]
+                r = qmc.qmc_combine_shifts(tot)
+            wall += time.perf_counter() - t0
+            rel = r.err[0] / abs(r.mean[0])
+            rec = {"n": n, "rel_err": rel, "mean": r.mean[0], "wall_s": wall}
+            if rel <= tol or wall > budget_s:
+                break
+        rec["reached"] = rec["rel_err"] <= tol
+        out[f"sum_32_sectors_d6_korobov3_fp32_{mode}"] = rec
     # control variate on the d=8 sector (pilot n=65537, 2000 Adam steps), both bases
     p = I.config5()
-    lat = lattices(p.d, p.gamma)
+    lat = lat_for(p)
     gp = qmc.qmc_make_lattice(p.d, I.N_PILOT, p.gamma)
     f = qmc.integrand_from_problem(p, "fp32")
     t = qmc.transform(p.transform, p.alpha)
