@@ -138,3 +138,26 @@ def test_cv_gain_by_transform(Q):
         gains[name] = r["err"][1] / r["err"][0]
         print(f"{name}: err cv {r['err'][0]:.3e} plain {r['err'][1]:.3e} gain {gains[name]:.2f}")
     assert gains["none"] >= 2.0
+
+
+@pytest.mark.slow
+def test_cv_estimator_full_size(Q, oracle_lib, nthreads):
+    """The estimator at the size the benchmark times it (configuration-5
+    integrand, d = 8, Korobov 3, n = 16777213; two shifts, one launch): both
+    per-shift sums against the oracle over all 16.7M points, and the
+    surrogate's own quadrature int g - Q^(k)[g] to 5e-8 of int g, as for the
+    small cases."""
+    p = I.with_shifts(I.config5(n=16777213, m=2), 2, 61)
+    g = Q.qmc_make_lattice(8, p.n, p.gamma)
+    a = _params(oracle_lib, 8, seed=62)
+    f = Q.integrand_from_problem(p, "fp32")
+    _, ps = Q.qmc_integrate_cv(8, p.n, p.m, g, p.shifts, Q.transform("korobov", 3), f, _cfg(Q), a)
+    gint = oracle_lib.cv_integral(8, R, K, a)
+    ref_plain = oracle_lib.integrate(p, g, nthreads=nthreads)["q"][:, 0]
+    p.cv = {"R": R, "K": K, "F": 1, "a": a}
+    ref_cv = oracle_lib.integrate(p, g, nthreads=nthreads)["q"][:, 0] + gint
+    dev_plain = np.max(np.abs(ps[:, 1] - ref_plain) / np.abs(ref_plain))
+    dev_cv = np.max(np.abs(ps[:, 0] - ref_cv) / (np.abs(ref_plain) + abs(gint)))
+    dev_quad = np.max(np.abs((ps[:, 0] - ps[:, 1]) - (ref_cv - ref_plain))) / abs(gint)
+    print(f"full size: plain {dev_plain:.2e}, cv {dev_cv:.2e}, surrogate quadrature {dev_quad:.2e}")
+    assert dev_plain <= 2e-7 and dev_cv <= 2e-7 and dev_quad <= 5e-8
