@@ -123,3 +123,32 @@ def test_multi_plan_replay(Q):
     assert desc["orders"] == "10" and desc["specialised"] == "1"
     assert plan.launches() == 4 * 2 + 1
     plan.destroy()
+
+
+@pytest.mark.slow
+def test_multi_full_size(Q, oracle_lib, nthreads):
+    """The fused sweep at the size the benchmark times it (32 sectors, d = 6,
+    n = 16777213, m = 16, baker): every integrand's per-shift values against
+    the same integrands run one kernel each (a graph batch, 1e-8: the same
+    per-point values, grouped differently), the sum group equal to the sum of
+    the integrands, and two integrands' first two shifts against the oracle
+    over all 16.7M points (2e-7)."""
+    import dataclasses
+    probs = I.config3_shared()
+    n, m = probs[0].n, probs[0].m
+    g = I.random_generating_vector(I.SplitMix64(64), 6, n)
+    fs = [Q.integrand_from_problem(p, "fp32") for p in probs]
+    t = Q.transform("baker")
+    res, ps = Q.qmc_integrate_multi(6, n, m, g, probs[0].shifts, t, fs, want_per_shift=True)
+    assert all(r.status == 0 for r in res)
+    bp = Q.BatchPlan([(6, n, m, g, probs[0].shifts, t, f) for f in fs])
+    ps_b = np.zeros(2 * m * len(fs))
+    bp.execute(per_shift=ps_b)
+    bp.destroy()
+    ps_b = ps_b.reshape(len(fs), m, 2)
+    assert np.all(np.abs(ps[:32, :, 0] - ps_b[:, :, 0]) <= 1e-8 * np.abs(ps_b[:, :, 0]))
+    assert np.allclose(ps[32, :, 0], ps[:32, :, 0].sum(axis=0), rtol=1e-13, atol=0)
+    for s in (0, 31):
+        p2 = dataclasses.replace(probs[s], m=2, shifts=probs[s].shifts[:2].copy())
+        ref = oracle_lib.integrate(p2, g, nthreads=nthreads)["q"][:, 0]
+        assert np.all(np.abs(ps[s, :2, 0] - ref) <= 2e-7 * np.abs(ref)), s
