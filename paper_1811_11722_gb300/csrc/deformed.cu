@@ -53,6 +53,12 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
   auto cu = pack_dense(f->U, d, u_linear ? 1 : 2);
   for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
   for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (R)cf[i];
+  for (int k = 0; k < d; ++k)  // -lambda d2F/dy_k dy_l (constant: F has degree 2)
+    for (int l = 0; l < d; ++l) {
+      const int a = k < l ? k : l, b = k < l ? l : k;
+      const double h = (k == l ? 2.0 : 1.0) * cf[q_off_host(d, a, b)];
+      base.cF[kDefHessOff + k * d + l] = (R)(-f->lambda * h);
+    }
   base.value_scale = 1.0;  // transform weights normalised per factor in this kernel
   base.check_finite = 1;
   int nblk = 0, L = 0;

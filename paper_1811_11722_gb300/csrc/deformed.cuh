@@ -8,8 +8,8 @@
 //                                           + y_k (1 - y_k) d2F/dy_k dy_l]
 //   f    = U(w)^aU F(w)^aF det J,   value = f * prod_i (transform weight)
 // F (and U) are dense polynomials of degree <= 2 in nested Horner form, so
-// dF/dy is a linear form and d2F a constant symmetric matrix read from the
-// same coefficients at compile-time offsets.  J = I + i M with M real; its
+// dF/dy is a linear form read from F's coefficients at compile-time offsets,
+// and -lambda d2F is a constant matrix the host tabulates after them.  J = I + i M with M real; its
 // determinant comes from LU factorisation with partial pivoting done by
 // conditional row swaps in registers (no dynamic register indexing).
 //
@@ -17,6 +17,7 @@
 // dwarfs the index work it would share), keeping one complex matrix live.
 #pragma once
 
+#include "kernel_table.h"
 #include "rule_kernels.cuh"
 
 namespace qmc {
@@ -71,9 +72,11 @@ __device__ __forceinline__ Cx<R> poly2_complex(const R* c, const Cx<R>* z) {
       r.re = fma_(q, z[j].re, r.re);
       r.im = fma_(q, z[j].im, r.im);
     }
-    Cx<R> t = cmul(z[i], r);
-    acc.re += t.re;
-    acc.im += t.im;
+    // acc += z_i r, as four fused steps
+    acc.re = fma_(z[i].re, r.re, acc.re);
+    acc.re = fma_(-z[i].im, r.im, acc.re);
+    acc.im = fma_(z[i].re, r.im, acc.im);
+    acc.im = fma_(z[i].im, r.re, acc.im);
   }
   return acc;
 }
@@ -133,10 +136,11 @@ __device__ __forceinline__ Cx<R> det_ipm(R (&M)[D][D]) {
     for (int r = c + 1; r < D; ++r) {
       const Cx<R> f = cmul(Cx<R>{ar[r][c], ai[r][c]}, inv);
 #pragma unroll
-      for (int q = c + 1; q < D; ++q) {
-        const Cx<R> t = cmul(f, Cx<R>{ar[c][q], ai[c][q]});
-        ar[r][q] -= t.re;
-        ai[r][q] -= t.im;
+      for (int q = c + 1; q < D; ++q) {  // a_rq -= f a_cq, as four fused steps
+        ar[r][q] = fma_(-f.re, ar[c][q], ar[r][q]);
+        ar[r][q] = fma_(f.im, ai[c][q], ar[r][q]);
+        ai[r][q] = fma_(-f.re, ai[c][q], ai[r][q]);
+        ai[r][q] = fma_(-f.im, ar[c][q], ai[r][q]);
       }
     }
   }
@@ -176,6 +180,7 @@ __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const ty
     gr[kk] = s;
   }
   const R lam = P.lam;
+  const R* nH = cF + kDefHessOff;  // -lambda times the Hessian of F (host table)
   Cx<R> z[D];
   R M[D][D];
 #pragma unroll
@@ -183,14 +188,8 @@ __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const ty
     const R a = fma_(-y[kk], y[kk], y[kk]);  // y (1 - y)
     z[kk] = {y[kk], -lam * a * gr[kk]};
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-      const int lo = kk < l ? kk : l, hi = kk < l ? l : kk;
-      const R q = cF[q_off(D, lo, hi)];
-      const R h2 = (kk == l) ? R(2) * q : q;
-      R v = a * h2;
-      if (kk == l) v = fma_(fma_(R(-2), y[kk], R(1)), gr[kk], v);
-      M[kk][l] = -lam * v;
-    }
+    for (int l = 0; l < D; ++l) M[kk][l] = a * nH[kk * D + l];
+    M[kk][kk] = fma_(-lam * fma_(R(-2), y[kk], R(1)), gr[kk], M[kk][kk]);
   }
   const Cx<R> dJ = det_ipm<D, R, !FAST>(M);
   Cx<R> U;

@@ -38,6 +38,11 @@ QMC_DECL_EPS(double, 5) QMC_DECL_EPS(double, 6) QMC_DECL_EPS(double, 7) QMC_DECL
 // pivoted LU.
 template <typename R, int D>
 const void* deformed_ptr(bool fast, bool u_linear);
+// Deformed sector kernels: the Hessian of F times -lambda, [k][l] with row
+// stride d, kept in RuleParams::cF after F's nested-Horner slots.
+constexpr int kDefHessOff = 64;
+static_assert(kDefHessOff >= poly_slots(kDFast, 2) && kDefHessOff + kDFast * kDFast <= kPolyCoefMax,
+              "deformed Hessian table placement");
 #define QMC_DECL_DEF(R, D) template <> const void* deformed_ptr<R, D>(bool, bool);
 QMC_DECL_DEF(float, 1) QMC_DECL_DEF(float, 2) QMC_DECL_DEF(float, 3) QMC_DECL_DEF(float, 4)
 QMC_DECL_DEF(float, 5) QMC_DECL_DEF(float, 6) QMC_DECL_DEF(float, 7) QMC_DECL_DEF(float, 8)

@@ -356,6 +356,28 @@ def test_config4_deformed_fp32(Q, oracle_lib, nthreads):
     assert np.all(np.abs((ps[:, 0] + 1j * ps[:, 1]) - (ref["q"][:, 0] + 1j * ref["q"][:, 1])) <= 2e-6 * scale)
 
 
+@pytest.mark.slow
+def test_config4_full_size(Q, oracle_lib, nthreads):
+    """Configuration 4 at its full size (n = 4194301, m = 20), the launch
+    configuration the benchmark times, in both precisions.
+    * The first two shifts of each against the oracle over every point: FP64
+      within 1e-12, FP32 within the small case's 2e-6.
+    * The FP32 mean's distance from the FP64 mean within a quarter of the
+      Eq. (3) error estimate of each part."""
+    import dataclasses
+    p = _c4(n=4194301)
+    g = I.random_generating_vector(I.SplitMix64(4), 5, p.n)
+    g64, ps64 = gpu_run(Q, p, g, "fp64")
+    g32, ps32 = gpu_run(Q, p, g, "fp32")
+    p2 = dataclasses.replace(p, m=2, shifts=p.shifts[:2].copy())
+    ref = oracle_lib.integrate(p2, g, nthreads=nthreads)["q"]
+    rc = ref[:, 0] + 1j * ref[:, 1]
+    assert np.all(np.abs((ps64[:2, 0] + 1j * ps64[:2, 1]) - rc) <= 1e-12 * np.abs(rc))
+    assert np.all(np.abs((ps32[:2, 0] + 1j * ps32[:2, 1]) - rc) <= 2e-6 * np.abs(rc))
+    for part in (0, 1):
+        assert abs(g32["mean"][part] - g64["mean"][part]) <= 0.25 * g64["err"][part], part
+
+
 def test_deformed_lambda_zero_equals_real_kernel(Q):
     """With lambda = 0 the contour is the real cube and J = I: the complex
     kernel reproduces the real sector kernel (positive F) to rounding."""
