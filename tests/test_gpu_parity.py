@@ -243,6 +243,40 @@ def test_edge_sizes(Q, oracle_lib, n, d, m):
     assert_fp64_parity(gpu, ps, oracle_lib.integrate(p, g))
 
 
+@pytest.mark.slow
+def test_largest_n(Q, oracle_lib, nthreads):
+    """n = 2^31 - 1, the largest lattice the library takes, at d = 2. The
+    index products j g reach 2^62 and the fixed-point reciprocal of n is at
+    its precision limit.
+    * Points at both ends of the index range: indices bit-exact, FP64
+      values within 1e-12.
+    * The first shift's Q^(1) over all 2.1e9 points against the oracle: FP64
+      within 1e-12, FP32 within 2e-7."""
+    n, d = 2147483647, 2
+    rng = I.SplitMix64(2024)
+    U = I.random_poly(rng, d, 2, 0)
+    F = I.random_poly(rng, d, 0, 2)
+    sh = I.make_shifts(rng, 2, d)
+    p = I.Problem("largest_n", d, n, 2, sh, "baker", kind="sector", U=U, F=F)
+    g = np.array([1, 1432590847], dtype=np.uint64)
+    t = Q.transform("baker")
+    js = np.array([0, 1, 2, 1 << 30, (1 << 31) - 3, n - 2, n - 1], dtype=np.uint64)
+    ks = np.array([0, 1, 0, 1, 0, 1, 0], dtype=np.int32)
+    vals, idx, _ = Q.qmc_sample_points(d, n, 2, g, sh, t, Q.integrand_from_problem(p, "fp64"), js, ks,
+                                       want_coord=False)
+    for s in range(len(js)):
+        v, oi, _, _, _ = oracle_lib.point(p, g, int(ks[s]), int(js[s]))
+        assert np.array_equal(idx[s], oi), s
+        assert abs(vals[s][0] - v[0]) <= 1e-12 * abs(v[0]), s
+    _, ps64 = gpu_run(Q, p, g, "fp64")
+    _, ps32 = gpu_run(Q, p, g, "fp32")
+    sums, nonf, _ = oracle_lib.rule_sums(p, g, 0, n, nthreads=nthreads, shifts=sh[:1])
+    assert int(nonf.sum()) == 0
+    ref = sums[0, 0] / n
+    assert abs(ps64[0, 0] - ref) <= 1e-12 * abs(ref)
+    assert abs(ps32[0, 0] - ref) <= 2e-7 * abs(ref)
+
+
 def test_nonfinite_values_counted(Q, oracle_lib):
     """F without a constant term vanishes at z = 0: 1/F is infinite there.  Both
     sides leave those points out and count them."""
