@@ -252,7 +252,8 @@ uint64_t shift_fixed64(double delta) {
   return (uint64_t)v;
 }
 
-static bool poly_positive(const qmc_poly& p, int d) {
+// Positive on the cube: a positive constant term and no negative coefficient.
+bool poly_positive(const qmc_poly& p, int d) {
   bool has_const = false;
   for (int t = 0; t < p.nterms; ++t) {
     int deg = 0;

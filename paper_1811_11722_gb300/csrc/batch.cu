@@ -218,17 +218,6 @@ static int batch_graph(BatchPlan* bp) {
 
 // ---------------------------------------------------------- persistent --
 
-static bool poly_positive_host(const qmc_poly& p, int d) {
-  bool has_const = false;
-  for (int t = 0; t < p.nterms; ++t) {
-    int deg = 0;
-    for (int i = 0; i < d; ++i) deg += p.expo[(size_t)t * d + i];
-    if (p.coef[t] < 0.0) return false;
-    if (deg == 0 && p.coef[t] > 0.0) has_const = true;
-  }
-  return has_const;
-}
-
 // Descriptors (one per sector and chunk of kPersistMc shifts) and the work
 // list, longest items first.
 static int persist_build(BatchPlan* bp, int32_t count, const qmc_problem* problems, uint32_t chunk) {
@@ -273,8 +262,7 @@ static int persist_build(BatchPlan* bp, int32_t count, const qmc_problem* proble
     prescale_slots(cf.data(), q.d, 2, fx_sigma(base.tr));
     for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (float)cu[i];
     for (size_t i = 0; i < cf.size(); ++i) base.cF[i] = (float)cf[i];
-    fill_pairs(base, q.d);
-    base.check_finite = (poly_positive_host(f.U, q.d) && poly_positive_host(f.F, q.d)) ? 0 : 1;
+    fill_pairs(base, q.d);  // check_finite: set by fill_common (off when U, F > 0 on the cube)
     base.m_total = q.m;
     BatchPlan::Sector& sec = bp->psec[s];
     sec.m = q.m;

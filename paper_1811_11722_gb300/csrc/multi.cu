@@ -25,17 +25,6 @@ namespace {
 
 constexpr int kMultiMc = 2;  // shifts per launch: SC x MC run sums stay in registers
 
-bool poly_is_positive(const qmc_poly& p, int d) {
-  bool has_const = false;
-  for (int t = 0; t < p.nterms; ++t) {
-    int deg = 0;
-    for (int i = 0; i < d; ++i) deg += p.expo[(size_t)t * d + i];
-    if (p.coef[t] < 0.0) return false;
-    if (deg == 0 && p.coef[t] > 0.0) has_const = true;
-  }
-  return has_const;
-}
-
 int build_multi_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                      const qmc_transform& t, int32_t count, const qmc_integrand* fs) {
   if (count < 1 || count > QMC_MULTI_MAX || !fs)
@@ -51,7 +40,7 @@ int build_multi_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
       return fail(QMC_EUNSUPPORTED,
                   "integrand %d: the shared-lattice kernel takes FP32EVAL U^-2 F^-1, deg U <= 1, deg F <= 2, d <= %d", s,
                   kDFast);
-    if (!poly_is_positive(f.U, d) || !poly_is_positive(f.F, d)) check = true;
+    if (!poly_positive(f.U, d) || !poly_positive(f.F, d)) check = true;
   }
   const bool kor3 = t.kind == QMC_TRANSFORM_KOROBOV && t.alpha == 3;
   if (t.kind == QMC_TRANSFORM_KOROBOV && !kor3)

@@ -82,6 +82,7 @@ bool prime_check(uint64_t n);
 int validate_problem(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                      const qmc_transform& t, const qmc_integrand* f);
 int poly_degree(const qmc_poly& p, int d);
+bool poly_positive(const qmc_poly& p, int d);
 std::vector<double> pack_dense(const qmc_poly& p, int D, int K);
 Recip reciprocal(uint64_t n);
 void korobov_coefs(int alpha, double* kor);
