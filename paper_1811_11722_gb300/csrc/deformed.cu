@@ -1,11 +1,31 @@
 // Plan builder for contour-deformed (complex) sector integrands.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
+#include "deformed.cuh"
 #include "plan.h"
 
 namespace qmc {
+
+// QMC_DEFORMED_PACKED=0 keeps FP32 plans on the one-shift kernel.
+static bool deformed_packed_enabled() {
+  const char* e = std::getenv("QMC_DEFORMED_PACKED");
+  return !(e && e[0] == '0');
+}
+
+// The packed FP32 variant (two shifts per instruction), d <= kDef2DMax.
+static const void* deformed2_ptr(int d) {
+  switch (d) {
+    case 1: return (const void*)&deformed2_kernel<1>;
+    case 2: return (const void*)&deformed2_kernel<2>;
+    case 3: return (const void*)&deformed2_kernel<3>;
+    case 4: return (const void*)&deformed2_kernel<4>;
+    case 5: return (const void*)&deformed2_kernel<5>;
+    default: return nullptr;
+  }
+}
 
 constexpr int kMcDef = 8;  // shifts per launch (matches the kernel's shared accumulators)
 
@@ -38,6 +58,9 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
   }
   const bool fast = worst < 1.0 && t.kind == QMC_TRANSFORM_KOROBOV && t.alpha == 3 && !tune.force_general;
   const bool u_linear = poly_degree(f->U, d) <= 1;  // U on its degree-1 slots only
+  // FP32 with two shifts per instruction: the FAST variant, U^-2 F^-1, d <= kDef2DMax
+  const bool packed = sizeof(R) == 4 && fast && u_linear && d <= kDef2DMax && f->aU == -2 && f->aF == -1 &&
+                      deformed_packed_enabled();
   const void* func = nullptr;
   switch (d) {
 #define QMC_D_CASE(DD) \
@@ -49,6 +72,7 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
 #undef QMC_D_CASE
     default: break;
   }
+  if (packed) func = deformed2_ptr(d);
   if (!func) return fail(QMC_EUNSUPPORTED, "no deformed kernel for d=%d", d);
   auto cu = pack_dense(f->U, d, u_linear ? 1 : 2);
   for (size_t i = 0; i < cu.size(); ++i) base.cU[i] = (R)cu[i];
@@ -59,6 +83,18 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
       const double h = (k == l ? 2.0 : 1.0) * cf[q_off_host(d, a, b)];
       base.cF[kDefHessOff + k * d + l] = (R)(-f->lambda * h);
     }
+  if (packed) {  // (c, c) pairs: U's linear slots, F's slots, then the Hessian of F, k-major
+    int o = 0;
+    for (size_t i = 0; i < cu.size(); ++i, ++o) base.cp[o] = make_float2((float)cu[i], (float)cu[i]);
+    for (size_t i = 0; i < cf.size(); ++i, ++o) base.cp[o] = make_float2((float)cf[i], (float)cf[i]);
+    for (int k = 0; k < d; ++k)
+      for (int l = 0; l < d; ++l, ++o) {
+        const int a = k < l ? k : l, b = k < l ? l : k;
+        const float h = (float)((k == l ? 2.0 : 1.0) * cf[q_off_host(d, a, b)]);
+        base.cp[o] = make_float2(h, h);
+      }
+    if (o > kPairCoefMax) return fail(QMC_EUNSUPPORTED, "deformed: %d coefficient pairs", o);
+  }
   base.value_scale = 1.0;  // transform weights normalised per factor in this kernel
   base.check_finite = 1;
   int nblk = 0, L = 0;

@@ -306,4 +306,218 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// --------------------------------------------- packed FP32, two shifts --
+//
+// The FAST variant (Korobov 3, unpivoted LU, U of degree 1) for FP32 with
+// two shifts per instruction: every real quantity of a (point, shift) is a
+// float2 holding shifts 2p and 2p + 1, and the arithmetic is f32x2.  The
+// coefficients come as (c, c) pairs from the launch parameters (cp):
+// U's 1 + d linear slots, F's nested degree-2 slots, then the Hessian of F
+// (2 q_kk on the diagonal) k-major, which fits for d <= kDef2DMax.
+constexpr int kDef2DMax = 5;
+
+struct Cx2 {
+  float2 re, im;
+};
+
+__device__ __forceinline__ float2 neg2(float2 a) { return mul2(a, make_float2(-1.0f, -1.0f)); }
+
+__device__ __forceinline__ Cx2 cmul2(const Cx2& a, const Cx2& b) {
+  return {fma2(neg2(a.im), b.im, mul2(a.re, b.re)), fma2(a.re, b.im, mul2(a.im, b.re))};
+}
+
+// 1 / a: (re, -im) / |a|^2 with the correctly rounded packed reciprocal
+__device__ __forceinline__ Cx2 crecip2(const Cx2& a) {
+  const float2 rn = recip_neg2(fma2(a.re, a.re, mul2(a.im, a.im)));  // -1 / |a|^2
+  return {mul2(a.re, neg2(rn)), mul2(a.im, rn)};
+}
+
+template <int D>
+__device__ __forceinline__ Cx2 deformed_value2(const RuleParams<float>& P, const uint32_t* base, int p, bool& bad_a,
+                                               bool& bad_b) {
+  float2 y[D];
+  float wa = 1.0f, wb = 1.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+    y[i] = make_float2(coord<float, TR_KOROBOV, 0>(base[i] + P.shift32[2 * p][i], P.kor, 3, wa),
+                       coord<float, TR_KOROBOV, 0>(base[i] + P.shift32[2 * p + 1][i], P.kor, 3, wb));
+  const float2* cu = P.cp;
+  const float2* cf = P.cp + 1 + D;
+  const float2* H = cf + poly_slots(D, 2);
+  const float2 nlam = make_float2(-P.lam, -P.lam);
+  const float2 one = make_float2(1.0f, 1.0f), zero = make_float2(0.0f, 0.0f);
+  Cx2 z[D];
+  float2 ar[D][D], ai[D][D];  // J = I + i M
+#pragma unroll
+  for (int kk = 0; kk < D; ++kk) {
+    float2 gr = cf[l_off(D, kk)];  // dF/dy_kk
+#pragma unroll
+    for (int j = 0; j < D; ++j) gr = fma2(H[kk * D + j], y[j], gr);
+    const float2 na = mul2(nlam, fma2(neg2(y[kk]), y[kk], y[kk]));  // -lambda y (1 - y)
+    z[kk] = {y[kk], mul2(na, gr)};
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      ar[kk][l] = kk == l ? one : zero;
+      ai[kk][l] = mul2(na, H[kk * D + l]);
+    }
+    ai[kk][kk] = fma2(mul2(nlam, fma2(y[kk], make_float2(-2.0f, -2.0f), one)), gr, ai[kk][kk]);
+  }
+  // det J by LU without pivoting (J diagonally dominant, shown by the host)
+  Cx2 dJ{one, zero};
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const Cx2 piv{ar[c][c], ai[c][c]};
+    dJ = cmul2(dJ, piv);
+    if (c + 1 < D) {
+      const Cx2 inv = crecip2(piv);
+#pragma unroll
+      for (int r = c + 1; r < D; ++r) {
+        const Cx2 f = cmul2(Cx2{ar[r][c], ai[r][c]}, inv);
+        const float2 frn = neg2(f.re), fin = neg2(f.im);
+#pragma unroll
+        for (int q = c + 1; q < D; ++q) {  // a_rq -= f a_cq, as four fused steps
+          ar[r][q] = fma2(frn, ar[c][q], ar[r][q]);
+          ar[r][q] = fma2(f.im, ai[c][q], ar[r][q]);
+          ai[r][q] = fma2(frn, ai[c][q], ai[r][q]);
+          ai[r][q] = fma2(fin, ar[c][q], ai[r][q]);
+        }
+      }
+    }
+  }
+  // U (degree 1) and F (degree 2) at w, real coefficients
+  Cx2 U{cu[0], zero};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    U.re = fma2(cu[1 + i], z[i].re, U.re);
+    U.im = fma2(cu[1 + i], z[i].im, U.im);
+  }
+  Cx2 F{cf[0], zero};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Cx2 r{cf[l_off(D, i)], zero};
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      const float2 q = cf[q_off(D, i, j)];
+      r.re = fma2(q, z[j].re, r.re);
+      r.im = fma2(q, z[j].im, r.im);
+    }
+    const float2 nzi = neg2(z[i].im);
+    F.re = fma2(z[i].re, r.re, F.re);
+    F.re = fma2(nzi, r.im, F.re);
+    F.im = fma2(z[i].re, r.im, F.im);
+    F.im = fma2(z[i].im, r.re, F.im);
+  }
+  bad_a = F.im.x > 0.0f;  // the contour left the allowed half-plane, Im F(w) > 0
+  bad_b = F.im.y > 0.0f;
+  Cx2 v = cmul2(dJ, crecip2(cmul2(cmul2(U, U), F)));
+  const float2 w = make_float2(wa, wb);
+  v.re = mul2(v.re, w);
+  v.im = mul2(v.im, w);
+  return v;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 2)  // two CTAs per SM: 128 registers, no spills at d = 5
+    deformed2_kernel(const __grid_constant__ RuleParams<float> P, double* __restrict__ partial,
+                     unsigned long long* __restrict__ counters, const SampleIO sio) {
+  if (sio.count > 0) {  // sampling: the scalar path of the same variant, one (point, shift) per thread
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sio.count) return;
+    const uint64_t j = sio.j[s];
+    const int k = sio.k[s];
+    uint32_t base[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      uint32_t idx = lattice_index(j, P.g[i], P.n);
+      base[i] = fix_base<float>(idx, P.rc);
+      if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
+      if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<float>(base[i] + P.shift32[k][i]);
+    }
+    bool bad;
+    Cx<float> v = deformed_value<float, D, true, 1>(P, base, k, bad);
+    sio.values[2 * (size_t)s] = (double)v.re * P.value_scale;
+    sio.values[2 * (size_t)s + 1] = (double)v.im * P.value_scale;
+    return;
+  }
+  __shared__ double accs[2][kMcDeformed][kThreads];
+  const uint32_t n = (uint32_t)P.n;
+  const int mk = P.m_launch;
+  for (int kk = 0; kk < kMcDeformed; ++kk) {
+    accs[0][kk][threadIdx.x] = 0.0;
+    accs[1][kk][threadIdx.x] = 0.0;
+  }
+  unsigned nbad = 0, ndef = 0;
+  const uint64_t tile_pts = (uint64_t)kThreads * (uint64_t)P.L;
+  for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    const uint64_t j0 = tile * tile_pts + threadIdx.x;
+    if (j0 >= P.n) continue;
+    uint64_t left = (P.n - j0 + kThreads - 1) / kThreads;
+    const int steps = left < (uint64_t)P.L ? (int)left : P.L;
+#pragma unroll 1
+    for (int kk = 0; kk < mk; kk += 2) {
+      const bool has_b = kk + 1 < mk;  // an odd last shift: the pair's second row is evaluated, not kept
+      uint32_t idx[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) idx[i] = lattice_index(j0, P.g[i], P.n);
+      Acc<float> are_a, aim_a, are_b, aim_b;
+      are_a.init();
+      aim_a.init();
+      are_b.init();
+      aim_b.init();
+#pragma unroll 1
+      for (int s = 0; s < steps; ++s) {
+        uint32_t base[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) base[i] = fix_base<float>(idx[i], P.rc);
+        bool bad_a, bad_b;
+        Cx2 v = deformed_value2<D>(P, base, kk >> 1, bad_a, bad_b);
+        ndef += (bad_a ? 1u : 0u) + ((bad_b && has_b) ? 1u : 0u);
+        const bool ok_a = finite_(v.re.x) && finite_(v.im.x);
+        const bool ok_b = finite_(v.re.y) && finite_(v.im.y);
+        nbad += (ok_a ? 0u : 1u) + ((ok_b || !has_b) ? 0u : 1u);
+        are_a.add(ok_a ? v.re.x : 0.0f);
+        aim_a.add(ok_a ? v.im.x : 0.0f);
+        are_b.add(ok_b ? v.re.y : 0.0f);
+        aim_b.add(ok_b ? v.im.y : 0.0f);
+#pragma unroll
+        for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
+        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+          are_a.fold();
+          aim_a.fold();
+          are_b.fold();
+          aim_b.fold();
+        }
+      }
+      accs[0][kk][threadIdx.x] += are_a.thread_total();
+      accs[1][kk][threadIdx.x] += aim_a.thread_total();
+      if (has_b) {
+        accs[0][kk + 1][threadIdx.x] += are_b.thread_total();
+        accs[1][kk + 1][threadIdx.x] += aim_b.thread_total();
+      }
+    }
+  }
+  __shared__ double red[kThreads / 32][kMcDeformed][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int kk = 0; kk < mk; ++kk) {
+    const double tr = warp_sum_d(accs[0][kk][threadIdx.x]);
+    const double ti = warp_sum_d(accs[1][kk][threadIdx.x]);
+    if (lane == 0) {
+      red[warp][kk][0] = tr;
+      red[warp][kk][1] = ti;
+    }
+  }
+  unsigned long long b1 = warp_sum_u64((unsigned long long)nbad);
+  unsigned long long b2 = warp_sum_u64((unsigned long long)ndef);
+  if (lane == 0 && b1) atomicAdd(&counters[0], b1);
+  if (lane == 0 && b2) atomicAdd(&counters[1], b2);
+  __syncthreads();
+  if (threadIdx.x < 2 * mk) {
+    const int kk = threadIdx.x >> 1, part = threadIdx.x & 1;
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][kk][part];
+    partial[((size_t)(P.k_base + kk) * P.nblk + blockIdx.x) * 2 + part] = s;
+  }
+}
+
 }  // namespace qmc

@@ -412,6 +412,30 @@ def test_config4_full_size(Q, oracle_lib, nthreads):
         assert abs(g32["mean"][part] - g64["mean"][part]) <= 0.25 * g64["err"][part], part
 
 
+@pytest.mark.parametrize("d", [2, 3, 5])
+def test_deformed_packed_matches_one_shift_kernel(Q, oracle_lib, nthreads, monkeypatch, d):
+    """The FP32 deformed kernel that evaluates two shifts per instruction
+    against the one-shift kernel (QMC_DEFORMED_PACKED=0) and the oracle.
+    m = 7 leaves the last shift unpaired.  The two kernels differ only in
+    rounding (a packed reciprocal), so their per-shift values agree far
+    inside the FP32 bound, and both count the same contour violations."""
+    rng = I.SplitMix64(4400 + d)
+    U = I.random_poly(rng, d, d, 0)
+    F = I.random_poly(rng, d, 0, 2 * d, neg_quad=1)
+    p = I.Problem(f"def_d{d}", d, 50021, 7, I.make_shifts(rng, 7, d), "korobov", alpha=3,
+                  kind="sector_deformed", U=U, F=F, lam=0.1, precision="fp32")
+    g = I.random_generating_vector(rng, d, p.n)
+    a, pa = gpu_run(Q, p, g, "fp32")
+    monkeypatch.setenv("QMC_DEFORMED_PACKED", "0")
+    b, pb = gpu_run(Q, p, g, "fp32")
+    ca, cb = pa[:, 0] + 1j * pa[:, 1], pb[:, 0] + 1j * pb[:, 1]
+    assert np.all(np.abs(ca - cb) <= 1e-6 * np.abs(cb))
+    assert a["deform_violations"] == b["deform_violations"] and a["nonfinite"] == b["nonfinite"]
+    ref = oracle_lib.integrate(p, g, nthreads=nthreads)
+    rc = ref["q"][:, 0] + 1j * ref["q"][:, 1]
+    assert np.all(np.abs(ca - rc) <= 2e-6 * np.abs(rc))
+
+
 def test_deformed_lambda_zero_equals_real_kernel(Q):
     """With lambda = 0 the contour is the real cube and J = I: the complex
     kernel reproduces the real sector kernel (positive F) to rounding."""
