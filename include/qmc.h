@@ -75,7 +75,12 @@ typedef struct {
  * SECTOR         f = U(z)^aU F(z)^aF                   (Eq. 7 at eps = 0)
  * SECTOR_DEFORMED f = U(w)^aU F(w)^aF det(dw/dz), with the contour
  *                w_k = z_k - i lambda z_k (1 - z_k) dF/dz_k (Sec. 3 Feynman
- *                prescription; vanishes at z_k in {0, 1}); F of degree <= 2
+ *                prescription; vanishes at z_k in {0, 1}); F of degree <= 2.
+ *                FP32EVAL with Korobov 3, U of degree 1, powers (-2, -1),
+ *                d <= 5 and J diagonally dominant on the cube evaluates two
+ *                shifts per instruction; QMC_DEFORMED_PACKED=0 in the
+ *                environment keeps one shift per thread (same results to
+ *                FP32 rounding)
  * TRIG           f = cos(2 pi h . z)                   (dual-lattice check) */
 enum {
   QMC_F_CONST = 0,
