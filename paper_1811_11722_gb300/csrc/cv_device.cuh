@@ -189,7 +189,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         const float U = poly_dense<D, 1>(P.cU, zf);
         const float F = poly_dense<D, 2>(P.cF, zf);
         float h = recip(U * U * F);
-        if constexpr (TR == TR_KOROBOV) h *= w;
+        if constexpr (TR == TR_KOROBOV) {
+          w = korobov_weight_fx(w);
+          h *= w;
+        }
         const bool fin = finite_(h);
         const bool ok = valid && fin;
         nbad += (valid && !fin) ? 1u : 0u;
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         apl.add(hv);
 #pragma unroll
         for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+        if ((s & fold_mask<TR>()) == fold_mask<TR>()) {
           acv.fold();
           apl.fold();
         }

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
         if constexpr (sizeof(R) == 4) {
-          if ((s & (kFoldG - 1)) == kFoldG - 1) {
+          if ((s & (FAST ? 0 : fold_mask_rt(P.tr))) == (FAST ? 0 : fold_mask_rt(P.tr))) {  // FAST: Korobov 3
             are.fold();
             aim.fold();
           }
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 2)  // two CTAs per SM: 128 register
         aim_b.add(ok_b ? v.im.y : 0.0f);
 #pragma unroll
         for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+        {  // Korobov-weighted values: every value into the (hi, lo) pairs
           are_a.fold();
           aim_a.fold();
           are_b.fold();

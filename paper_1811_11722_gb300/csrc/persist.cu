@@ -50,7 +50,7 @@ __device__ __noinline__ void persist_item(const RuleParams<float>& P, uint64_t j
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-      if ((s & (kFoldG - 1)) == kFoldG - 1) {
+      if ((s & fold_mask<TR>()) == fold_mask<TR>()) {
         unpack_runs<MC>(run2, acc);
 #pragma unroll
         for (int kk = 0; kk < MC; ++kk) acc[kk].fold();

@@ -24,6 +24,19 @@ namespace qmc {
 
 constexpr int kFoldG = 8;
 
+// Steps between folds of the FP32 run sums into their (hi, lo) pairs, as a
+// mask: fold when (step & mask) == mask.  Korobov-weighted values span many
+// binades (the weight vanishes at the faces), and a float run drops those
+// below half an ulp of its running sum, always downward: -1.4e-9 of the
+// integral at n ~ 4e6, d = 6.  They go into the pair one by one (mask 0, every
+// step; the Fast2Sum keeps each value's rounding error).  Baker and untransformed
+// values stay within a few binades and keep runs of kFoldG.
+template <int TR>
+__host__ __device__ constexpr int fold_mask() {
+  return TR == TR_KOROBOV ? 0 : kFoldG - 1;
+}
+__device__ __forceinline__ int fold_mask_rt(int tr) { return tr == TR_KOROBOV ? 0 : kFoldG - 1; }
+
 template <typename R>
 struct Acc;
 
@@ -150,7 +163,7 @@ __device__ __forceinline__ float2 sector_value2(const RuleParams<float>& P, cons
   float2 U, Fn;
   POLY::template eval2<D, KU, KF>(P, z, U, Fn);
   float2 v = recip_neg2(mul2(mul2(U, U), Fn));
-  if constexpr (TR == TR_KOROBOV) v = mul2(v, make_float2(wa, wb));
+  if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(make_float2(wa, wb)));
   return v;
 }
 
@@ -166,7 +179,10 @@ __device__ __forceinline__ R sector_value(const RuleParams<R>& P, const typename
   R U, F;
   POLY::template eval<D, KU, KF, R>(P, z, U, F);
   R v = recip(U * U * F);
-  if constexpr (TR == TR_KOROBOV) v *= w;
+  if constexpr (TR == TR_KOROBOV) {
+    if constexpr (sizeof(R) == 4) v *= korobov_weight_fx(w);
+    else v *= w;
+  }
   return v;
 }
 
@@ -183,7 +199,10 @@ __device__ __forceinline__ R eps_point(const RuleParams<R>& P, const typename Se
   }
   DensePolys::template eval<D, 1, 2, R>(P, z, U, F);
   R v = recip(U * U * F);
-  if constexpr (TR == TR_KOROBOV) v *= w;
+  if constexpr (TR == TR_KOROBOV) {
+    if constexpr (sizeof(R) == 4) v *= korobov_weight_fx(w);
+    else v *= w;
+  }
   return v;
 }
 
@@ -331,7 +350,7 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
       if constexpr (sizeof(R) == 4) {
-        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+        if ((s & fold_mask<TR>()) == fold_mask<TR>()) {
           if constexpr (kPack) unpack_runs<MC>(run2, acc);
 #pragma unroll
           for (int kk = 0; kk < MC; ++kk) {
@@ -472,7 +491,7 @@ __global__ void __launch_bounds__(kThreads)
         }
       }
       if constexpr (sizeof(R) == 4) {
-        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+        if ((s & fold_mask<TR>()) == fold_mask<TR>()) {
 #pragma unroll
           for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
         }
@@ -580,7 +599,7 @@ __global__ void __launch_bounds__(kThreads)
         }
       }
       if constexpr (sizeof(R) == 4) {
-        if ((s & (kFoldG - 1)) == kFoldG - 1) {
+        if ((s & fold_mask_rt(P.tr)) == fold_mask_rt(P.tr)) {
 #pragma unroll
           for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
         }
@@ -719,7 +738,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
       if constexpr (sizeof(R) == 4) {
-        if ((s & (kFoldG - 1)) == kFoldG - 1) eps_fold<R, MC, NE>(acc);
+        if ((s & fold_mask<TR>()) == fold_mask<TR>()) eps_fold<R, MC, NE>(acc);
       }
     }
   }
@@ -754,7 +773,7 @@ __device__ __forceinline__ void eps_body2(const RuleParams<float>& P, double* __
     float U, F;
     POLY::template eval<D, 1, 2, float>(P, z, U, F);
     float v = recip(U * U * F);
-    if constexpr (TR == TR_KOROBOV) v *= w;
+    if constexpr (TR == TR_KOROBOV) v *= korobov_weight_fx(w);
     const float L = P.eps_b[0] * log_(U) + P.eps_b[1] * log_(F);
     for (int o = 0; o < P.eps_orders; ++o) {
       sio.values[(size_t)s * sio.stride + o] = (double)v * P.value_scale;
@@ -807,7 +826,7 @@ __device__ __forceinline__ void eps_body2(const RuleParams<float>& P, double* __
           L = make_float2(P.eps_b[0] * log_(U.x) + P.eps_b[1] * log_(-Fn.x),
                           P.eps_b[0] * log_(U.y) + P.eps_b[1] * log_(-Fn.y));
         }
-        if constexpr (TR == TR_KOROBOV) v = mul2(v, make_float2(wa, wb));
+        if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(make_float2(wa, wb)));
 #pragma unroll
         for (int o = 0; o < NE; ++o) {
           if constexpr (CHECK) {
@@ -823,7 +842,7 @@ __device__ __forceinline__ void eps_body2(const RuleParams<float>& P, double* __
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-      if ((st & (kFoldG - 1)) == kFoldG - 1) {
+      if ((st & fold_mask<TR>()) == fold_mask<TR>()) {
 #pragma unroll
         for (int o = 0; o < NE; ++o) {
           unpack_runs<MC>(run2[o], acc[o]);
@@ -886,7 +905,7 @@ __global__ void __launch_bounds__(kThreads)
         }
       }
       if constexpr (sizeof(R) == 4) {
-        if ((s & (kFoldG - 1)) == kFoldG - 1) eps_fold<R, MC, NE>(acc);
+        if ((s & fold_mask_rt(P.tr)) == fold_mask_rt(P.tr)) eps_fold<R, MC, NE>(acc);
       }
     }
   }
@@ -941,7 +960,8 @@ __device__ __forceinline__ void multi_body(const MultiParams& M, double* __restr
         for (int i = 0; i < D; ++i)
           z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], P.kor, wa),
                              coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p + 1][i], P.kor, wb));
-        const float2 w = make_float2(wa, wb);
+        float2 w = make_float2(wa, wb);
+        if constexpr (TR == TR_KOROBOV) w = korobov_weight_fx2(w);
 #pragma unroll
         for (int s = 0; s < SC; ++s) {
           float2 U, Fn;
@@ -959,7 +979,7 @@ __device__ __forceinline__ void multi_body(const MultiParams& M, double* __restr
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-      if ((st & (kFoldG - 1)) == kFoldG - 1) {
+      if ((st & fold_mask<TR>()) == fold_mask<TR>()) {
 #pragma unroll
         for (int s = 0; s < SC; ++s) {
           unpack_runs<MC>(run2[s], acc[s]);

@@ -772,6 +772,39 @@ def test_integrate_to_tolerance(Q):
     assert not ok and lvl == 1 and res.status == Q.QMC_ETIMEOUT
 
 
+@pytest.mark.slow
+def test_time_to_tolerance_true_error(Q, oracle_lib, nthreads):
+    """The walks to 1e-8 relative error that the benchmark times land within
+    their own error estimate of the true integral. Two walks:
+    * the plain rule on the prime ladder (configuration-2 integrand, baker);
+    * the embedded base-2 lattices (configuration-5 integrand, Korobov 3).
+    Each is checked against tensor Gauss-Legendre of the untransformed
+    integrand, converged (two node counts agree to 1e-11)."""
+    p = I.config2()
+    ladder = [n for n in I.ladder_primes() if 100000 < n < 20000000]
+    gs = [Q.qmc_make_lattice(6, n, p.gamma) for n in ladder]
+    res, lvl, ok = Q.qmc_integrate_to_tolerance(6, ladder, gs, p.m, p.shifts, Q.transform("baker"),
+                                                Q.integrand_from_problem(p, "fp32"), 1e-8)
+    assert ok and res.err[0] <= 1e-8 * abs(res.mean[0])
+    gl_a = oracle_lib.gauss_legendre(p, 12, nthreads=nthreads)[0]
+    gl_b = oracle_lib.gauss_legendre(p, 16, nthreads=nthreads)[0]
+    assert abs(gl_a - gl_b) <= 1e-11 * abs(gl_b)
+    print(f"C2 ladder: n = {ladder[lvl]}, |Q - I| / |I| = {abs(res.mean[0] - gl_b) / abs(gl_b):.2e}, "
+          f"estimate {res.err[0] / abs(res.mean[0]):.2e}")
+    assert abs(res.mean[0] - gl_b) <= 4 * res.err[0]
+    p5 = I.config5()
+    ge = Q.qmc_make_lattice_embedded(8, 16, 25, p5.gamma)
+    r, lvl5, _, ok5 = Q.qmc_integrate_extensible(8, 16, 10, ge, p5.m, p5.shifts, Q.transform("korobov", 3),
+                                                 Q.integrand_from_problem(p5, "fp32"), 1e-8)
+    assert ok5 and r.err[0] <= 1e-8 * abs(r.mean[0])
+    gl9 = oracle_lib.gauss_legendre(p5, 9, nthreads=nthreads)[0]
+    gl10 = oracle_lib.gauss_legendre(p5, 10, nthreads=nthreads)[0]
+    assert abs(gl9 - gl10) <= 1e-11 * abs(gl10)
+    print(f"C5 embedded: n = 2^{16 + lvl5}, |Q - I| / |I| = {abs(r.mean[0] - gl10) / abs(gl10):.2e}, "
+          f"estimate {r.err[0] / abs(r.mean[0]):.2e}")
+    assert abs(r.mean[0] - gl10) <= 4 * r.err[0]
+
+
 def test_fp32_rounding_unbiased_at_full_size(Q, lattices):
     """At n = 16777213 the lattice spacing equals the float grid of the
     coordinates, so rounding them to float repeats a lattice-tied pattern of
@@ -789,6 +822,34 @@ def test_fp32_rounding_unbiased_at_full_size(Q, lattices):
     q = abs(r64.mean[0])
     assert np.all(np.abs(ps32[:, 0] - ps64[:, 0]) <= 2e-10 * q), np.max(np.abs(ps32[:, 0] - ps64[:, 0])) / q
     assert abs(r32.mean[0] - r64.mean[0]) <= 0.1 * r64.err[0]
+
+
+@pytest.mark.parametrize("cfg", ["c2", "c5"])
+def test_fp32_korobov_weight_unbiased_at_full_size(Q, cfg):
+    """The Korobov-3 FP32 path: its weight is a product of d factors
+    u = s(1 - s) cubed.  Rounding u * u * u per factor in float is biased low
+    (the low bits of a square are not uniform); that summed to -3.0e-9 (d = 6)
+    and -4.6e-9 (d = 8) relative against the FP64 rule, above the rule's own
+    error at 1e-8 targets.  The FP32 path multiplies the factors and cubes the
+    product once with an exact square.  Korobov values also span many binades,
+    and float runs dropped the smallest (-1.4e-9 more); each value now goes
+    into the compensated pair on its own.  What remains is the FP32 rounding of
+    the coordinates and of z, which grows with d.  At n = 16777213 the FP32 and
+    FP64 per-shift values must agree on average to 1e-10 d and each to
+    2.5e-10 d.  That is measured at -4.2e-10 (d = 6) and -6.5e-10 (d = 8), a
+    twentieth of the rule's error estimate there; before the two changes it was
+    -3.0e-9 and -4.6e-9."""
+    p = (I.config2(n=16777213, m=16) if cfg == "c2" else I.config5(n=16777213, m=16))
+    g = Q.qmc_make_lattice(p.d, p.n, p.gamma)
+    t = Q.transform("korobov", 3)
+    _, ps32 = Q.qmc_integrate(p.d, p.n, p.m, g, p.shifts, t, Q.integrand_from_problem(p, "fp32"),
+                              want_per_shift=True)
+    _, ps64 = Q.qmc_integrate(p.d, p.n, p.m, g, p.shifts, t, Q.integrand_from_problem(p, "fp64"),
+                              want_per_shift=True)
+    rel = (ps32[:, 0] - ps64[:, 0]) / ps64[:, 0]
+    print(f"{cfg}: FP32 - FP64 per shift, mean {rel.mean():.2e}, max |.| {np.abs(rel).max():.2e}")
+    assert abs(rel.mean()) <= 1e-10 * p.d
+    assert np.all(np.abs(rel) <= 2.5e-10 * p.d)
 
 
 @pytest.mark.parametrize("transform,alpha", [("baker", 0), ("korobov", 3), ("none", 0)])
