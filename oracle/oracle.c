@@ -450,17 +450,17 @@ uint64_t orc_index(uint64_t jm1, uint64_t g, uint64_t n) {
  * value = f(z) prod_i w_i.  Optional dumps of idx, x, z. */
 int orc_point(const orc_problem* p, uint64_t n, const uint64_t* g, const double* shift, uint64_t jm1,
               double* val, uint64_t* idx_out, double* x_out, double* z_out, int* bad) {
-  double z[ORC_DMAX];
+  double x[ORC_DMAX], z[ORC_DMAX];
   double wprod = 1.0;
   for (int i = 0; i < p->d; ++i) {
     uint64_t idx = orc_index(jm1, g[i], n);
     double y = (double)idx / (double)n + shift[i];
-    double x = (y >= 1.0) ? y - 1.0 : y;
+    x[i] = (y >= 1.0) ? y - 1.0 : y;
     double w;
-    z[i] = orc_transform(p->tkind, p->alpha, x, &w);
+    z[i] = orc_transform(p->tkind, p->alpha, x[i], &w);
     wprod *= w;
     if (idx_out) idx_out[i] = idx;
-    if (x_out) x_out[i] = x;
+    if (x_out) x_out[i] = x[i];
     if (z_out) z_out[i] = z[i];
   }
   double f[2];

@@ -19,7 +19,7 @@ MUTATIONS = {
                      [lambda o: pins.test_korobov_transform(o, 3)]),
     "index_modulus": ("% (unsigned __int128)n);", "% (unsigned __int128)(n + 1));",
                       [pins.test_index_exact_bigint]),
-    "no_wrap": ("double x = (y >= 1.0) ? y - 1.0 : y;", "double x = y;",
+    "no_wrap": ("x[i] = (y >= 1.0) ? y - 1.0 : y;", "x[i] = y;",
                 [lambda o: pins.test_rule_matches_exact_rationals(o, "none", 0, 13, 2)]),
     "variance_denominator": ("var[part] = neum_get(&v) / ((double)m * (double)(m - 1));",
                              "var[part] = neum_get(&v) / ((double)m * (double)m);", [pins.test_variance_estimate]),
@@ -40,6 +40,23 @@ MUTATIONS = {
                        [pins.test_bf16_rounding_matches_torch]),
     "bf16_factor_unrounded": ("const double dg = orc_bf16(2.0 * e * other / (double)P);",
                               "const double dg = 2.0 * e * other / (double)P;", [pins.test_cv_fit_bf16_exact_operands]),
+    "cv_g_at_x": ("val[0] -= orc_cv_g(p->d, p->cvR, p->cvK, p->cvF, p->cva, z) * wprod;",
+                  "val[0] -= orc_cv_g(p->d, p->cvR, p->cvK, p->cvF, p->cva, x) * wprod;",
+                  [lambda o: pins.test_cv_surrogate_equal_to_integrand_cancels(o, "korobov", 3, 1),
+                   lambda o: pins.test_cv_estimator_unbiased_with_nonzero_surrogate(o, "korobov", 3, 1)]),
+    "cv_weight_dropped": ("val[0] -= orc_cv_g(p->d, p->cvR, p->cvK, p->cvF, p->cva, z) * wprod;",
+                          "val[0] -= orc_cv_g(p->d, p->cvR, p->cvK, p->cvF, p->cva, z);",
+                          [lambda o: pins.test_cv_surrogate_equal_to_integrand_cancels(o, "korobov", 3, 2),
+                           lambda o: pins.test_cv_estimator_unbiased_with_nonzero_surrogate(o, "korobov", 3, 2)]),
+    "cv_sign": ("val[0] -= orc_cv_g(", "val[0] += orc_cv_g(",
+                [lambda o: pins.test_cv_surrogate_equal_to_integrand_cancels(o, "none", 0, 1),
+                 lambda o: pins.test_cv_estimator_unbiased_with_nonzero_surrogate(o, "baker", 0, 1)]),
+    "cv_basis_frequency": ("cos((double)F * M_PI * (double)k * x[i]);", "cos(M_PI * (double)k * x[i]);",
+                           [lambda o: pins.test_cv_surrogate_equal_to_integrand_cancels(o, "baker", 0, 2)]),
+    "nonfinite_not_counted": ("c->nonfinite[k] += 1;", "c->nonfinite[k] += 0;",
+                              [lambda o: pins.test_nonfinite_values_counted_and_left_out(o, "none", 0)]),
+    "nonfinite_summed": ("c->nonfinite[k] += 1;\n        continue;", "c->nonfinite[k] += 1;",
+                         [lambda o: pins.test_nonfinite_values_counted_and_left_out(o, "korobov", 3)]),
     "eps_factorial_dropped": ("for (int k = 1; k <= p->eps_order; ++k) c *= L / (double)k;",
                               "for (int k = 1; k <= p->eps_order; ++k) c *= L;", [pins.test_eps_expansion_d1_against_quad]),
 }

@@ -464,6 +464,135 @@ def test_cv_estimator_zero_surrogate_is_plain_rule(oracle_lib):
     assert np.array_equal(plain["q"], cv["q"])
 
 
+def _cv_exact_surrogate(d, R, K, F, axis, freq):
+    """Parameters whose rank 0 is cos(F pi k z_axis) with F k = 2 freq (so it
+    equals cos(2 pi freq z_axis), the trig integrand with h = freq e_axis) and
+    whose other ranks are zero."""
+    a = np.zeros((R, d, K), np.float32)
+    assert (2 * freq) % F == 0 and 2 * freq // F < K
+    for i in range(d):
+        a[0, i, 0] = 1.0
+    a[0, axis, 0] = 0.0
+    a[0, axis, 2 * freq // F] = 1.0
+    return a.ravel()
+
+
+@pytest.mark.parametrize("transform,alpha", [("none", 0), ("baker", 0), ("korobov", 3), ("korobov", 5)])
+@pytest.mark.parametrize("F", [1, 2])
+def test_cv_surrogate_equal_to_integrand_cancels(oracle_lib, transform, alpha, F):
+    """With g = f the summand (f - g)(z(x)) prod w vanishes at every point, so
+    every per-shift Q[f - g] is zero (to rounding) and the estimator returns
+    int g = int f = 0 with zero variance.  f = cos(2 pi h.z) with h = 13 e_1
+    on the n = 13 lattice: h is in the dual lattice (h.g = 13 = 0 mod 13), so
+    without a transform the plain rule gives cos(2 pi h.Delta_k), far from 0
+    (a sign slip in the subtraction doubles it).  Evaluating g at x instead of
+    z, or leaving out the transform weight, leaves a Korobov-weighted
+    cosine integral of order 0.1 per shift."""
+    d, R, K, n, m, freq = 3, 2, 32, 13, 4, 13
+    rng = I.SplitMix64(401 + F)
+    h = np.zeros(d, np.int32)
+    h[1] = freq
+    p = I.Problem("trig_cv", d, n, m, I.make_shifts(rng, m, d), transform, alpha=alpha, kind="trig", h=h)
+    g = np.array([1, 1, 5], dtype=np.uint64)
+    plain = oracle_lib.integrate(p, g)
+    if transform == "none":
+        for k in range(m):
+            assert abs(plain["q"][k, 0] - math.cos(2 * math.pi * freq * p.shifts[k, 1])) < 1e-12
+    p.cv = {"R": R, "K": K, "F": F, "a": _cv_exact_surrogate(d, R, K, F, 1, freq)}
+    assert oracle_lib.cv_integral(d, R, K, p.cv["a"]) == 0.0
+    r = oracle_lib.integrate(p, g)
+    assert np.all(np.abs(r["q"][:, 0]) < 1e-13), r["q"][:, 0]
+    assert r["var"][0] < 1e-26
+
+
+def _cv_generic_params(d, R, K, seed):
+    """Surrogate parameters of the integrand's scale: constant terms near 0.8
+    (so int g ~ R 0.8^d is not small), the rest N(0, 0.05)."""
+    rng = np.random.default_rng(seed)
+    a = rng.normal(0.0, 0.05, size=(R, d, K))
+    a[:, :, 0] = 0.7 + 0.2 * rng.random((R, d))
+    return a.astype(np.float32).ravel()
+
+
+@pytest.mark.parametrize("transform,alpha", [("baker", 0), ("korobov", 3)])
+@pytest.mark.parametrize("F", [1, 2])
+def test_cv_estimator_unbiased_with_nonzero_surrogate(oracle_lib, transform, alpha, F):
+    """Q[f - g] + int g estimates int f for any g (the shift average of the
+    rule is unbiased for every integrable summand): a d = 3 sector integrand
+    with a rank-2, K = 4 surrogate whose int g is about 1 agrees with tensor
+    Gauss-Legendre of f within six Eq. (3) error estimates, under baker and
+    Korobov 3.  Evaluating g at x instead of z (Korobov), dropping the weight
+    from the g term (Korobov), or adding g instead of subtracting it moves the
+    estimate by O(0.1)-O(1), far outside the error."""
+    from oracle.cbc import cbc_fast
+    d, R, K, n, m = 3, 2, 4, 32749, 8
+    p = small_sector(d, 71, transform=transform, alpha=alpha, n=n, m=m)
+    gl = oracle_lib.gauss_legendre(p, 24)[0]
+    g = cbc_fast(d, n, I.product_weights(d))
+    a = _cv_generic_params(d, R, K, seed=72 + F)
+    gint = oracle_lib.cv_integral(d, R, K, a)
+    assert 0.5 < gint < 2.0
+    p.cv = {"R": R, "K": K, "F": F, "a": a}
+    r = oracle_lib.integrate(p, g, nthreads=4)
+    est = r["mean"][0] + gint
+    assert abs(est - gl) < 6 * r["err"][0] + 1e-12, (est, gl, r["err"][0])
+    # the surrogate term is live: every shift's Q[f - g] differs from Q[f] by about int g
+    plain = oracle_lib.integrate(small_sector(d, 71, transform=transform, alpha=alpha, n=n, m=m), g, nthreads=4)
+    assert np.all(np.abs(plain["q"][:, 0] - r["q"][:, 0]) > 0.5 * gint)
+
+
+# ------------------------------------------------------- non-finite values --
+
+def _exact_value(p, g, shift, j, zf, wf):
+    """Term j of Eq. (2) in exact rationals for U = c0 + c1 z_0, F = z_1 (no
+    constant, so F = 0 where x_1 = 0): returns None where F = 0 (the value is
+    infinite, or 0 x infinite under Korobov), else the exact weighted value."""
+    xs = []
+    for i in range(p.d):
+        y = Fraction((j * int(g[i])) % p.n, p.n) + Fraction(shift[i])
+        xs.append(y - 1 if y >= 1 else y)
+    z = [zf(x) for x in xs]
+    w = Fraction(1)
+    for x in xs:
+        w *= wf(x)
+    Fv = Fraction(p.F.coef[0]) * z[1]
+    if Fv == 0:
+        return None
+    Uv = Fraction(p.U.coef[0]) + Fraction(p.U.coef[1]) * z[0]
+    return w / (Uv * Uv * Fv)
+
+
+@pytest.mark.parametrize("transform,alpha", [("none", 0), ("korobov", 3)])
+def test_nonfinite_values_counted_and_left_out(oracle_lib, transform, alpha):
+    """Reading R10 (points with a non-finite value are counted per shift and
+    left out of the sum): on the n = 16 lattice with g = (1, 4), F = z_1 has
+    no constant term and vanishes wherever x_1 = {4j/16 + Delta_1} = 0.  The
+    count per shift equals a brute-force count in exact rationals (4, 4 and 0
+    for the three dyadic shifts), and each per-shift sum equals the exact sum
+    of the remaining terms.  Without a transform the value there is +inf;
+    under Korobov 3 the weight is 0 too, and 0 x inf is NaN."""
+    d, n = 2, 16
+    g = np.array([1, 4], dtype=np.uint64)
+    shifts = np.array([[0.125, 0.25], [0.5, 0.0], [0.3125, 0.0625]])
+    U = I.Poly(np.array([0.75, 1.25]), np.array([[0, 0], [1, 0]], dtype=np.uint8))
+    F = I.Poly(np.array([1.5]), np.array([[0, 1]], dtype=np.uint8))
+    p = I.Problem("nonfinite", d, n, 3, shifts, transform, alpha=alpha, kind="sector", U=U, F=F, aU=-2, aF=-1)
+    if transform == "korobov":
+        zf, wf = _korobov_exact(alpha)
+    else:
+        zf, wf = (lambda t: t), (lambda t: Fraction(1))
+    sums, nonf, _ = oracle_lib.rule_sums(p, g)
+    want_counts = []
+    for k in range(p.m):
+        vals = [_exact_value(p, g, shifts[k], j, zf, wf) for j in range(n)]
+        want_counts.append(sum(v is None for v in vals))
+        exact = sum((v for v in vals if v is not None), Fraction(0))
+        assert np.isfinite(sums[k, 0])
+        assert abs(sums[k, 0] - float(exact)) <= 1e-14 * abs(float(exact)), (k, sums[k, 0], float(exact))
+    assert want_counts == [4, 4, 0]
+    assert [int(c) for c in nonf] == want_counts
+
+
 # -------------------------------------------------------- epsilon expansion --
 
 def test_eps_expansion_d1_against_quad(oracle_lib):
