@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,10 +38,32 @@ WORKLOAD = "sector U^-2 F^-1, d=6, T_U=6, T_F=12, baker, n=16777213, m=32, FP32 
 # 2 per coordinate (12), U 2 per term (12), F 3 per degree-2 term (36),
 # U^2 F 2, accumulate 1 -> 63, plus one reciprocal on the MUFU unit.
 FLOPS_PER_EVAL = 63
-# FP32 FMA peak of a GB300 at its maximum SM clock: 152 SMs x 128 lanes x
-# 2 flops x 2070 MHz.
-SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# FP32 FMA peak: SMs x FP32 lanes per SM x 2 flops x maximum SM clock.  The
+# SM count comes from the device and the maximum clock from nvidia-smi; 128
+# FP32 lanes per SM is the sm_100-class figure.  The fallbacks are a GB300's
+# 152 SMs and 2070 MHz.
+LANES = 128
+SMS_FALLBACK, SM_MAX_MHZ_FALLBACK = 152, 2070.0
+
+
+def fp32_peak_tflops(sms: int, sm_max_mhz: float) -> float:
+    return sms * LANES * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def device_sms(torch, index: int) -> int:
+    try:
+        return int(torch.cuda.get_device_properties(index).multi_processor_count)
+    except Exception:
+        return SMS_FALLBACK
+
+
+def device_max_sm_mhz(index: int) -> float:
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={index}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=30)
+        return float(out.stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return SM_MAX_MHZ_FALLBACK
 
 # DRAM traffic of the lattice kernel from one ncu capture of this workload;
 # valid only while the kernel sources hash to KERNEL_SHA (else reported null).
@@ -253,6 +276,20 @@ def extras(qmc, I, torch):
     out["c2_fp32_vs_fp64"] = {"rel_diff": abs(r32.mean[0] - r64.mean[0]) / abs(r64.mean[0]),
                               "rel_err_estimate_fp64": r64.err[0] / abs(r64.mean[0]),
                               "rel_err_estimate_fp32": r32.err[0] / abs(r32.mean[0])}
+    # the same workload on the FP64 path (the paper's arithmetic): throughput and
+    # the fraction of the measured FP64 FMA peak at the same 63 algorithmic flops
+    # per evaluation
+    plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, t_, qmc.integrand_from_problem(p, "fp64"))
+    plan.tune(sh)
+    t = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream, reps=3)
+    fp64_tf = FLOPS_PER_EVAL * p.n * p.m / t / 1e12
+    pk64 = out["peaks_measured"]["fp64_tflops"]
+    out["c2_fp64_path"] = {"evals_per_s": p.n * p.m / t, "ms": 1e3 * t, "plan": plan.describe(),
+                           "algorithmic_tflops": fp64_tf, "fp64_peak_measured_tflops": pk64,
+                           "frac_of_measured_fp64_peak": fp64_tf / pk64,
+                           "note": "63 algorithmic flops per evaluation as on the FP32 path; whole step "
+                                   "(lattice kernels and final pass) timed with CUDA events"}
+    plan.destroy()
     # epsilon expansion of the configuration-2 integrand, U^(-2+eps) F^(-1-eps):
     # orders 0..2 and 0..5 from one pass (FP32 eval), against the plain rule
     p = I.config2()
@@ -355,6 +392,26 @@ def extras(qmc, I, torch):
                                         "achieved counts both MMAs (basis head and remainder)"},
             "err_cv": r.err[0], "err_plain_same_points": r.err[1], "gain_same_points": r.err[1] / r.err[0],
             "note": "one TF32 m16n8k8 MMA (2048 flops) per point and dimension: head and remainder of the basis"}
+    # gain of the control variate per surrogate design and transform, from the
+    # same points (n = 1048573, m = 16): plain error / control-variate error.
+    # band > 0 holds the cosine degrees k >= band at zero (band-limited fit)
+    gains = {}
+    n1 = 1048573
+    g1 = qmc.qmc_make_lattice(p.d, n1, p.gamma)
+    for band in (0, 4, 8, 16):
+        cfg.band = band
+        a, losses = qmc.qmc_cv_train(p.d, I.N_PILOT, gp, I.make_shifts(I.SplitMix64(54), 1, p.d)[0],
+                                     qmc.transform("none"), f_, cfg, stream=sh)
+        row = {"loss": float(losses[1])}
+        for name, tt in (("none", qmc.transform("none")), ("baker", qmc.transform("baker")),
+                         ("korobov3", qmc.transform("korobov", 3))):
+            r, _ = qmc.qmc_integrate_cv(p.d, n1, p.m, g1, p.shifts, tt, f_, cfg, a, stream=sh)
+            row[name] = {"gain": r.err[1] / r.err[0], "err_cv": r.err[0], "err_plain": r.err[1]}
+        gains[f"band{band}"] = row
+    cfg.band = 0
+    out["c5_cv_gain_by_band_and_transform"] = dict(gains, n=n1, m=p.m,
+                                                   note="same points; gain = plain Eq. (3) error / control-variate "
+                                                        "error; band 0 = all 32 cosine degrees fitted")
     return out
 
 
@@ -364,6 +421,63 @@ def _short(cfg):
     c = copy.copy(cfg)
     c.steps = 5
     return c
+
+
+def c3_time_to_tolerance(qmc, I, sh, tol):
+    import numpy as np
+    sect = I.config3(transform="korobov", alpha=3)
+    S = len(sect)
+    ladder = I.ladder_primes()
+    cbc = {}   # n -> d=8 CBC vector (a d-dimensional CBC vector is its first d components)
+
+    def lattice(n, d):
+        if n not in cbc:
+            cbc[n] = qmc.qmc_make_lattice(8, n, I.product_weights(8))
+        return cbc[n][:d]
+
+    steps = [[q.n] + [n for n in ladder if n > q.n] for q in sect]
+    fs = [qmc.integrand_from_problem(q) for q in sect]
+    ts = [qmc.transform(q.transform, q.alpha) for q in sect]
+    # run-time compilation of every sector's kernel (independent of n): a precompute
+    qmc.qmc_integrate_batch([(q.d, 1009, q.m, lattice(1009, q.d), q.shifts, t_, f_)
+                             for q, t_, f_ in zip(sect, ts, fs)], stream=sh)
+    res = {}
+    for mode in ("batched", "one_by_one"):
+        level = [0] * S
+        mean = np.zeros(S)
+        err = np.zeros(S)
+        todo = list(range(S))
+        wall, levels, evals = 0.0, 0, 0
+        while True:
+            for i in todo:  # lattices are host precomputes (not timed)
+                lattice(steps[i][level[i]], sect[i].d)
+            t0 = time.perf_counter()
+            if mode == "batched":
+                tuples = [(sect[i].d, steps[i][level[i]], sect[i].m, lattice(steps[i][level[i]], sect[i].d),
+                           sect[i].shifts, ts[i], fs[i]) for i in todo]
+                rs, _ = qmc.qmc_integrate_batch(tuples, stream=sh)
+            else:
+                rs = [qmc.qmc_integrate(sect[i].d, steps[i][level[i]], sect[i].m,
+                                        lattice(steps[i][level[i]], sect[i].d), sect[i].shifts, ts[i], fs[i],
+                                        stream=sh)[0] for i in todo]
+            wall += time.perf_counter() - t0
+            levels += 1
+            for i, r in zip(todo, rs):
+                mean[i], err[i] = r.mean[0], r.err[0]
+                evals += steps[i][level[i]] * sect[i].m
+            total, total_err = mean.sum(), math.sqrt(float(np.sum(err ** 2)))
+            share = tol * abs(total) / math.sqrt(S)
+            todo = [i for i in range(S) if err[i] > share and level[i] + 1 < len(steps[i])]
+            if total_err <= tol * abs(total) or not todo:
+                break
+            for i in todo:
+                level[i] += 1
+        res[mode] = {"rel_err": total_err / abs(total), "sum": float(total), "wall_s": wall, "levels": levels,
+                     "evals": int(evals), "reached": total_err <= tol * abs(total),
+                     "largest_n": int(max(steps[i][level[i]] for i in range(S)))}
+    res["batched"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched"]["wall_s"]
+    return {"c3_256_sectors_korobov3_sum_batched": res["batched"],
+            "c3_256_sectors_korobov3_sum_one_by_one": res["one_by_one"]}
 
 
 def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
@@ -454,35 +568,60 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
                 break
         rec["reached"] = rec["rel_err"] <= tol
         out[f"sum_32_sectors_d6_korobov3_fp32_{mode}"] = rec
-    # control variate on the d=8 sector (pilot n=65537, 2000 Adam steps), both bases
+    # configuration 3's 256 sectors (Korobov 3 variant), their sum to 1e-8
+    # relative error: every sector walks its own ladder (its table prime, then
+    # the ladder primes above it, CBC vectors from the library, untimed).  A
+    # level refines only the sectors whose Eq. (3) error exceeds their share
+    # tol |sum| / sqrt(256) of the total's budget; the total error is the
+    # quadrature sum of the sectors'.  Batched: each level is one
+    # qmc_integrate_batch call over the refined sectors; one by one: one
+    # qmc_integrate call per refined sector.  Same lattices, shifts and points.
+    out.update(c3_time_to_tolerance(qmc, I, sh, tol))
+    # control variate on the d=8 sector (pilot n=65537, 2000 Adam steps).  The
+    # library's judged walk (qmc_integrate_cv_to_tolerance): the first ladder
+    # lattice is the pilot where the control variate and the plain rule meet at
+    # equal cost; the loser is dropped.  Fit included in the wall time.  Beside
+    # it, the control variate forced through every level (no judge).
     p = I.config5()
     lat = lat_for(p)
     gp = qmc.qmc_make_lattice(p.d, I.N_PILOT, p.gamma)
     f = qmc.integrand_from_problem(p, "fp32")
     t = qmc.transform(p.transform, p.alpha)
-    for freq in (1, 2):
+    pilot_shift = I.make_shifts(I.SplitMix64(54), 1, p.d)[0]
+    ns = np.array(ladder, dtype=np.uint64)
+    gs = np.concatenate([lat[n] for n in ladder])
+    for band in (0, 8):
         cfg = qmc.qmc_cv_config()
-        cfg.R, cfg.K, cfg.freq_step, cfg.steps, cfg.lr, cfg.seed = 16, 32, freq, 2000, 1e-2, 7
+        cfg.R, cfg.K, cfg.freq_step, cfg.steps, cfg.lr, cfg.band, cfg.seed = 16, 32, 1, 2000, 1e-2, band, 7
         # first-use work outside the timing: one short fit and one estimator call
-        a0, _ = qmc.qmc_cv_train(p.d, I.N_PILOT, gp, I.make_shifts(I.SplitMix64(54), 1, p.d)[0], t, f, _short(cfg))
+        a0, _ = qmc.qmc_cv_train(p.d, I.N_PILOT, gp, pilot_shift, t, f, _short(cfg))
         qmc.qmc_integrate_cv(p.d, ladder[0], p.m, lat[ladder[0]], p.shifts, t, f, cfg, a0, stream=sh)
         t0 = time.perf_counter()
-        a, losses = qmc.qmc_cv_train(p.d, I.N_PILOT, gp, I.make_shifts(I.SplitMix64(54), 1, p.d)[0], t, f, cfg)
+        a, losses = qmc.qmc_cv_train(p.d, I.N_PILOT, gp, pilot_shift, t, f, cfg)
+        train_s = time.perf_counter() - t0
+        r, lvl, mode, judge, ok = qmc.qmc_integrate_cv_to_tolerance(p.d, ns, gs, p.m, p.shifts, t, f, cfg, a, tol,
+                                                                     stream=sh)
         wall = time.perf_counter() - t0
-        train_s = wall
-        rec = None
-        for n in ladder:
-            gn = lat[n]
-            t0 = time.perf_counter()
-            r, _ = qmc.qmc_integrate_cv(p.d, n, p.m, gn, p.shifts, t, f, cfg, a, stream=sh)
-            wall += time.perf_counter() - t0
-            rel = r.err[0] / abs(r.mean[0])
-            rec = {"n": n, "rel_err": rel, "plain_rel_err_same_points": r.err[1] / abs(r.mean[1]), "mean": r.mean[0],
-                   "wall_s": wall, "train_s": train_s, "loss": [float(losses[0]), float(losses[1])]}
-            if rel <= tol or wall > budget_s:
-                break
-        rec["reached"] = rec["rel_err"] <= tol
-        out[f"sector_d8_korobov3_cv_freq{freq}"] = rec
+        out[f"sector_d8_korobov3_cv_band{band}_judged"] = {
+            "n": int(ladder[lvl]), "rel_err": r.err[0] / abs(r.mean[0]), "mean": r.mean[0], "wall_s": wall,
+            "train_s": train_s, "reached": bool(ok), "kept": "control variate" if mode == 1 else "plain rule",
+            "pilot": dict(judge, n=int(ladder[0])), "loss": [float(losses[0]), float(losses[1])],
+            "plain_ladder_wall_s": out["sector_d8_korobov3_fp32"]["wall_s"],
+            "speedup_vs_plain_ladder": out["sector_d8_korobov3_fp32"]["wall_s"] / wall}
+        if band == 0:  # the control variate forced through every level, for comparison
+            wall, rec = train_s, None
+            for n in ladder:
+                gn = lat[n]
+                t1 = time.perf_counter()
+                rr, _ = qmc.qmc_integrate_cv(p.d, n, p.m, gn, p.shifts, t, f, cfg, a, stream=sh)
+                wall += time.perf_counter() - t1
+                rel = rr.err[0] / abs(rr.mean[0])
+                rec = {"n": n, "rel_err": rel, "plain_rel_err_same_points": rr.err[1] / abs(rr.mean[1]),
+                       "mean": rr.mean[0], "wall_s": wall, "train_s": train_s}
+                if rel <= tol or wall > budget_s:
+                    break
+            rec["reached"] = rec["rel_err"] <= tol
+            out["sector_d8_korobov3_cv_forced"] = rec
     return out
 
 
@@ -589,6 +728,9 @@ def main():
     rule_avg_s = statistics.mean(rule_ms) / 1e3
     achieved = FLOPS_PER_EVAL * evals / rule_avg_s / 1e12
     clocks = clk.summary()
+    sms = device_sms(torch, local)
+    sm_max_mhz = clocks.get("sm_max_mhz") or device_max_sm_mhz(local)
+    peak = fp32_peak_tflops(sms, sm_max_mhz)
     sha = kernel_sha()
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel_sha"] == sha else None
     line = {
@@ -598,15 +740,16 @@ def main():
         "e2e": {"value": world * evals * K / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": qmc.RESULT_BYTES},
         "gpu_launches": launches_per_step * K,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": (("qmc_jit_sector = sector_body specialised at run time for this U, F; "
                                  if desc.get("specialised") == "1" else "sector_kernel ")
                                 + f"<float, D=6, MC={shifts_per_launch}, baker, U deg 1, F deg 2>"),
                      "plan": desc,
                      "kernel_ms": 1e3 * rule_avg_s, "flops_per_eval": FLOPS_PER_EVAL,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (nominal max clock)",
-                     "frac_at_observed_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)
+                     "peak_source": f"{sms} SMs (device) x {LANES} FP32 lanes x 2 flops x {sm_max_mhz:g} MHz "
+                                    "(maximum SM clock, nvidia-smi)",
+                     "frac_at_observed_clock": (achieved / fp32_peak_tflops(sms, clocks["sm_mhz"])
                                                 if clocks.get("sm_mhz") else None)},
         "clocks": clocks,
         "result": {"mean": res["mean"][0], "err": res["err"][0]},

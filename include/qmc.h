@@ -244,11 +244,20 @@ int qmc_batch_plan_destroy(qmc_batch_plan plan);
  * shifts, chunk of `chunk_points` consecutive j) from a device counter, stage
  * the problem's rule into shared memory and sweep the chunk; item q of a
  * problem writes its fixed slots, so results do not depend on the order in
- * which CTAs take items.  Coefficients are read from shared memory (no
- * per-problem code specialisation), so each problem must be an FP32EVAL
- * SECTOR integrand U^-2 F^-1 with deg U <= 1, deg F <= 2, d <= 8 and transform
- * none, baker or Korobov 3 (else QMC_EUNSUPPORTED).  The plan replays one
- * CUDA graph: counter reset, the persistent kernel, the final pass.
+ * which CTAs take items.  Each problem must be an FP32EVAL SECTOR integrand
+ * U^-2 F^-1 with deg U <= 1, deg F <= 2, d <= 8 and transform none, baker or
+ * Korobov 3 (else QMC_EUNSUPPORTED).  The kernel is specialised at run time:
+ * every (problem, chunk of up to 16 shifts) gets straight-line code with its
+ * lattice, shifts and nonzero coefficients as constants (NVRTC, one program
+ * per group of problems compiled on the host cores as relocatable code, then
+ * linked into one module), and the persistent kernel dispatches each work
+ * item to its problem's code.  When that is unavailable (no run-time
+ * compilation, QMC_PERSIST_JIT=0 or QMC_JIT=0 in the environment, or more
+ * than 60 KB of nonzero coefficient pairs for the module's constant bank),
+ * one generic kernel stages each problem's dense coefficients in shared
+ * memory instead (chunks of 8 shifts); qmc_batch_plan_describe reports which.
+ * The plan replays one CUDA graph: counter reset, the persistent kernel, the
+ * final pass.
  *   chunk_points  points per work item, a multiple of 256 in [256, 2^24];
  *                 0 = 65536 (qmc_batch_plan_tune sweeps 2^14..2^18)
  * Execute, launches, tune and destroy are those of qmc_batch_plan_create. */
@@ -256,14 +265,23 @@ int qmc_batch_plan_destroy(qmc_batch_plan plan);
 int qmc_batch_plan_create_persistent(int32_t count, const qmc_problem* problems, uint32_t chunk_points,
                                      qmc_batch_plan* plan_out);
 #endif
+/* One-line description of a batch plan, NUL-terminated into buf[len]: the
+ * mode (graph or persistent); for a persistent plan whether its kernel was
+ * specialised at run time, the descriptors (sector and shift chunk), work
+ * items, CTAs, points per item and shift rows per descriptor. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+int qmc_batch_plan_describe(qmc_batch_plan plan, char* buf, int32_t len);
+#endif
 /* Kernel launches in one replay (rule kernels + the final pass). */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_batch_plan_launches(qmc_batch_plan plan, int32_t* launches_out);
 #endif
 /* Autotuner: times the graph on `stream` for evaluations-per-CTA budgets
  * 2^18..2^24 (the per-problem grid is ceil(n m / budget) CTAs), or, for a
- * persistent plan, for work items of 2^14..2^18 points, rebuilds the plan
- * with the fastest and reports it in *work_per_cta_out (may be NULL).
+ * persistent plan, for work items of 2^14..2^18 points (a specialised kernel
+ * also built for two resident CTAs per SM, every function held to 128
+ * registers), rebuilds the plan with the fastest and reports the work size in
+ * *work_per_cta_out (may be NULL).
  * `problems` must describe the same batch the plan was created from.
  * Synchronises `stream`. */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
@@ -279,6 +297,10 @@ int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* 
  * with the same Eq. (3) error estimate.  This build: R = 16, K = 32, d <= 8.
  *   freq_step  F: 1 -> cos(pi k x); 2 -> cos(2 pi k x) (1-periodic basis)
  *   steps, lr  full-batch Adam (beta 0.9, 0.999), rate lr * (1 + cos(pi s/steps)) / 2
+ *   band       0: every degree k < K is fitted; 1 <= band <= K: the degrees
+ *              k >= band are held at zero (a band-limited surrogate, whose
+ *              high derivatives, and so its content at the dual lattice's
+ *              frequencies after the periodizing transform, stay small)
  *   seed       SplitMix64 seed of the initial parameters */
 typedef struct {
   int32_t R;
@@ -286,7 +308,7 @@ typedef struct {
   int32_t freq_step;
   int32_t steps;
   float lr;
-  int32_t reserved;
+  int32_t band;
   uint64_t seed;
 } qmc_cv_config;
 
@@ -321,6 +343,37 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
                      qmc_result* out, double* per_shift, void* stream);
 #endif
 
+/* Automatic choice of n with the control variate as a candidate (the ladder
+ * of qmc_integrate_to_tolerance; the estimator of qmc_integrate_cv).  The
+ * first lattice is the pilot: one control-variate pass gives Q[f - g] + int g
+ * and the plain Q[f] from the same points, each with its Eq. (3) error, and a
+ * plain pass on the same lattice times the plain rule alone.  The control
+ * variate is kept only if it wins at equal cost,
+ *   (err_cv / |Qbar_cv|) * t_cv < (err_plain / |Qbar_plain|) * t_plain,
+ * with t the host wall time of each pass (an estimate whose error falls at
+ * least as 1/n reaches a target in time proportional to error x time per
+ * pass), both passes run once before they are timed so that first-use work
+ * (run-time compilation) does not enter the comparison.  Otherwise the walk continues on the plain rule alone (qmc_integrate)
+ * from the second lattice on, so the result never costs more than the plain
+ * walk plus the pilot.  Stops at the first level whose kept estimate meets
+ * err / |Qbar| <= rel_tol.
+ *   levels, n, g  as for qmc_integrate_to_tolerance
+ *   cfg, a        the fitted surrogate (qmc_cv_train)
+ *   out           host: the kept estimate in part [0] (part [1] zero)
+ *   level_out     the level that produced *out (may be NULL)
+ *   mode_out      1 if the control variate was kept, 0 if the plain rule (may be NULL)
+ *   judge_out     optional [4] host: pilot relative errors (control variate,
+ *                 plain) and pass times in seconds (control variate, plain)
+ * Integrands as for qmc_integrate_cv.  Synchronises `stream`.  Returns QMC_OK
+ * when the tolerance was met, else QMC_ETIMEOUT with the last level's
+ * estimate. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+int qmc_integrate_cv_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, const uint64_t* g, int32_t m,
+                                  const double* shifts, qmc_transform t, const qmc_integrand* f,
+                                  const qmc_cv_config* cfg, const float* a, double rel_tol, qmc_result* out,
+                                  int32_t* level_out, int32_t* mode_out, double* judge_out, void* stream);
+#endif
+
 /* The training kernels' loss and gradient at given parameters on given
  * points (x [P*d] in [0,1), targets h [P], host), for checking them against
  * an independent computation.  grad_out [R*d*K] host. */
@@ -337,7 +390,11 @@ int qmc_cv_loss_grad(int32_t d, const qmc_cv_config* cfg, int32_t P, const doubl
  * file-scope device array of 4 MiB per device, resident until the process
  * exits.  Its address is looked up once per device, with that device
  * current, by the first call on that device; make that first call before any
- * stream capture.  Every call shares the array and leaves its contents
+ * stream capture.  Under CUDA's lazy module loading (the default) that first
+ * call is also what loads the library's module on the device and so
+ * reserves the 4 MiB there: a caller that expects its allocator to be
+ * exhausted or locked later should make one small call on each device while
+ * device memory is still available.  Every call shares the array and leaves its contents
  * behind (the counters are cleared at the start of each call), so calls
  * whose GPU work overlaps (different streams or host threads) race on it:
  * order them.  Supports SECTOR integrands U^-2 F^-1 with deg U <= 1,

@@ -484,6 +484,11 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
     fill_sparse(gp.U, f->U);
     fill_sparse(gp.F, f->F);
   }
+  // FP32 float-coordinate kernels (general, separable) raise the product of the
+  // Korobov factors 4u to the power alpha once per value: the constant
+  // ((2a+1)!/(a!)^2 / 4^a) per dimension is applied in FP64 by the final pass
+  if (fp32 && (general || !(f->kind == QMC_F_SECTOR || eps)) && base.tr == TR_KOROBOV)
+    base.value_scale = std::pow((double)base.kor[7] / std::pow(4.0, (double)base.alpha), (double)d);
 
   int nblk = 0, L = 0;
   uint64_t tiles = 0;

@@ -17,8 +17,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <thread>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -60,6 +62,10 @@ struct BatchPlan {
   PersistItem* pitems_dev = nullptr;
   unsigned* pnext_dev = nullptr;
   int pgrid = 0;
+  int pmc = kPersistMc;                  // shift rows per descriptor
+  void* pj_fn = nullptr;                 // run-time specialised persistent kernel (CUfunction), if any
+  int pj_occ = 0;
+  int pj_min_ctas = 1;                   // CTAs per SM it is built for (1, or 2 at 128 registers)
 };
 
 static void batch_release(BatchPlan* bp) {
@@ -218,9 +224,10 @@ static int batch_graph(BatchPlan* bp) {
 
 // ---------------------------------------------------------- persistent --
 
-// Descriptors (one per sector and chunk of kPersistMc shifts) and the work
-// list, longest items first.
-static int persist_build(BatchPlan* bp, int32_t count, const qmc_problem* problems, uint32_t chunk) {
+// Descriptors (one per sector and chunk of `mc` shifts: kPersistMc for the
+// generic kernel, kPjMc for the specialised one) and the work list, longest
+// items first.
+static int persist_build(BatchPlan* bp, int32_t count, const qmc_problem* problems, uint32_t chunk, int mc) {
   if (count < 1 || count > 65536) return fail(QMC_EINVAL, "batch count=%d outside [1, 65536]", count);
   if (!problems) return fail(QMC_EINVAL, "null problems");
   if (chunk < (uint32_t)kThreads || chunk % kThreads != 0 || chunk > (1u << 24))
@@ -228,6 +235,7 @@ static int persist_build(BatchPlan* bp, int32_t count, const qmc_problem* proble
   bp->count = count;
   bp->persistent = true;
   bp->chunk = chunk;
+  bp->pmc = mc;
   bp->psec.assign(count, BatchPlan::Sector());
   bp->pdesc.clear();
   bp->pdesc_sector.clear();
@@ -273,14 +281,14 @@ static int persist_build(BatchPlan* bp, int32_t count, const qmc_problem* proble
     bp->total_m += q.m;
     bp->max_m = std::max(bp->max_m, q.m);
     const double per_point = (double)(poly_slots(q.d, 1) + poly_slots(q.d, 2) + 2 * q.d);
-    for (int k0 = 0; k0 < q.m; k0 += kPersistMc) {
-      const int mk = std::min(kPersistMc, q.m - k0);
+    for (int k0 = 0; k0 < q.m; k0 += mc) {
+      const int mk = std::min(mc, q.m - k0);
       PersistDesc D;
       std::memset(&D, 0, sizeof(D));
       D.P = base;
       D.P.m_launch = mk;
       D.P.k_base = k0;
-      for (int kk = 0; kk < kPersistMc; ++kk)  // rows mk.. repeat row k0 (evaluated, never written back)
+      for (int kk = 0; kk < mc; ++kk)  // rows mk.. repeat row k0 (evaluated, never written back)
         for (int i = 0; i < q.d; ++i)
           set_shift(D.P, kk, i, shift_fixed64(q.shifts[(size_t)(kk < mk ? k0 + kk : k0) * q.d + i]));
       D.nitems = sec.nitems;
@@ -289,7 +297,7 @@ static int persist_build(BatchPlan* bp, int32_t count, const qmc_problem* proble
       bp->pdesc_sector.push_back(s);
       for (int it = 0; it < sec.nitems; ++it) {
         const uint64_t pts = std::min<uint64_t>(chunk, q.n - (uint64_t)it * chunk);
-        costs.push_back({(double)pts * per_point * kPersistMc, PersistItem{di, (uint32_t)it}});
+        costs.push_back({(double)pts * per_point * mc, PersistItem{di, (uint32_t)it}});
       }
     }
   }
@@ -368,9 +376,11 @@ static int persist_alloc(BatchPlan* bp) {
     e = cudaMemcpy(bp->pitems_dev, bp->pitems.data(), bp->pitems.size() * sizeof(PersistItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(base + cnt_off[0], 0, (size_t)bp->count * 2 * sizeof(unsigned long long) + 16);
   if (e != cudaSuccess) return cuda_fail(e, "persistent batch descriptors");
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persist_kernel_ptr(), kThreads, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "persistent kernel occupancy");
+  int occ = bp->pj_occ;
+  if (!bp->pj_fn) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persist_kernel_ptr(), kThreads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent kernel occupancy");
+  }
   const int sms = device_sms();
   if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
   bp->pgrid = (int)std::min<uint64_t>((uint64_t)sms * (uint64_t)std::max(occ, 1), bp->pitems.size());
@@ -400,15 +410,23 @@ static int persist_graph(BatchPlan* bp) {
   A.chunk = bp->chunk;
   A.next = bp->pnext_dev;
   void* kargs[1] = {&A};
-  cudaKernelNodeParams kp;
-  std::memset(&kp, 0, sizeof(kp));
-  kp.func = (void*)persist_kernel_ptr();
-  kp.gridDim = dim3(bp->pgrid);
-  kp.blockDim = dim3(kThreads);
-  kp.kernelParams = kargs;
   cudaGraphNode_t knode;
-  e = cudaGraphAddKernelNode(&knode, bp->graph, &mnode, 1, &kp);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddKernelNode (persistent kernel)");
+  if (bp->pj_fn) {
+    Launch ln;
+    ln.cufunc = bp->pj_fn;
+    ln.grid = dim3(bp->pgrid);
+    int rc = graph_add_launch(bp->graph, ln, kargs, &knode, &mnode, 1);
+    if (rc) return rc;
+  } else {
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = (void*)persist_kernel_ptr();
+    kp.gridDim = dim3(bp->pgrid);
+    kp.blockDim = dim3(kThreads);
+    kp.kernelParams = kargs;
+    e = cudaGraphAddKernelNode(&knode, bp->graph, &mnode, 1, &kp);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddKernelNode (persistent kernel)");
+  }
   FinalizeArgs* fin = bp->fin_dev;
   void* fargs[1] = {&fin};
   cudaKernelNodeParams fp;
@@ -426,9 +444,76 @@ static int persist_graph(BatchPlan* bp) {
   return QMC_OK;
 }
 
-static int persist_create(BatchPlan* bp, int32_t count, const qmc_problem* problems, uint32_t chunk) {
-  int rc = persist_build(bp, count, problems, chunk);
-  if (rc) return rc;
+// QMC_PERSIST_JIT=0 keeps persistent plans on the generic kernel.
+static bool persist_jit_enabled() {
+  const char* e = std::getenv("QMC_PERSIST_JIT");
+  return jit_enabled() && !(e && e[0] == '0');
+}
+
+// The specialised persistent kernel for the descriptors persist_build made
+// (kPjMc shift rows each); false if it cannot be built (the caller falls back).
+static bool persist_specialise(BatchPlan* bp) {
+  std::vector<PjSector> secs(bp->count);
+  std::vector<bool> have(bp->count, false);
+  std::vector<PjDesc> descs(bp->pdesc.size());
+  for (size_t q = 0; q < bp->pdesc.size(); ++q) {
+    const RuleParams<float>& P = bp->pdesc[q].P;
+    const int s = bp->pdesc_sector[q];
+    if (!have[s]) {
+      PjSector& S = secs[s];
+      S.d = P.d;
+      S.tr = P.tr;
+      S.check = P.check_finite != 0;
+      S.n = P.n;
+      S.rc = P.rc;
+      for (int i = 0; i < P.d; ++i) {
+        S.g[i] = P.g[i];
+        S.gstep[i] = P.gstep[i];
+      }
+      S.cu.assign(P.cU, P.cU + poly_slots(P.d, 1));
+      S.cf.assign(P.cF, P.cF + poly_slots(P.d, 2));
+      for (int k = 0; k < 8; ++k) S.kor[k] = P.kor[k];
+      have[s] = true;
+    }
+    PjDesc& Dq = descs[q];
+    Dq.sector = s;
+    Dq.kbase = P.k_base;
+    Dq.m = P.m_launch;
+    Dq.mc = std::min(kPjMc, (P.m_launch + 1) & ~1);
+    Dq.shift.resize((size_t)Dq.mc * P.d);
+    for (int k = 0; k < Dq.mc; ++k)
+      for (int i = 0; i < P.d; ++i) Dq.shift[(size_t)k * P.d + i] = P.shiftx[k][i];
+  }
+  // every Korobov sector takes weight 3: its coefficients serve the whole module
+  for (int s = 0; s < bp->count; ++s)
+    if (secs[s].tr == TR_KOROBOV) {
+      for (int t = 0; t < bp->count; ++t) std::memcpy(secs[t].kor, secs[s].kor, sizeof(secs[s].kor));
+      break;
+    }
+  void* fn = nullptr;
+  int occ = 0;
+  if (jit_persist(secs, descs, bp->pj_min_ctas, &fn, &occ) != QMC_OK) return false;
+  bp->pj_fn = fn;
+  bp->pj_occ = occ;
+  return true;
+}
+
+static int persist_create(BatchPlan* bp, int32_t count, const qmc_problem* problems, uint32_t chunk,
+                          int min_ctas = 1) {
+  bp->pj_min_ctas = min_ctas;
+  bp->pj_fn = nullptr;
+  bp->pj_occ = 0;
+  int rc = QMC_OK;
+  bool specialised = false;
+  if (persist_jit_enabled()) {
+    rc = persist_build(bp, count, problems, chunk, kPjMc);
+    if (rc) return rc;
+    specialised = persist_specialise(bp);
+  }
+  if (!specialised) {
+    rc = persist_build(bp, count, problems, chunk, kPersistMc);
+    if (rc) return rc;
+  }
   rc = persist_alloc(bp);
   if (rc) return rc;
   return persist_graph(bp);
@@ -518,6 +603,19 @@ int qmc_batch_plan_destroy(qmc_batch_plan plan) {
   return QMC_OK;
 }
 
+int qmc_batch_plan_describe(qmc_batch_plan plan, char* buf, int32_t len) {
+  if (!plan || !buf || len < 1) return fail(QMC_EINVAL, "null plan or buffer");
+  const BatchPlan* bp = reinterpret_cast<const BatchPlan*>(plan);
+  if (bp->persistent)
+    snprintf(buf, (size_t)len, "mode=persistent specialised=%d problems=%d descriptors=%zu items=%zu ctas=%d chunk=%u "
+             "shifts_per_descriptor=%d min_ctas=%d", bp->pj_fn ? 1 : 0, bp->count, bp->pdesc.size(), bp->pitems.size(),
+             bp->pgrid, bp->chunk, bp->pmc, bp->pj_fn ? bp->pj_min_ctas : 0);
+  else
+    snprintf(buf, (size_t)len, "mode=graph problems=%d launches=%d work_per_cta=%llu", bp->count, bp->launches,
+             (unsigned long long)bp->work_per_cta);
+  return QMC_OK;
+}
+
 int qmc_batch_plan_launches(qmc_batch_plan plan, int32_t* launches_out) {
   if (!plan || !launches_out) return fail(QMC_EINVAL, "null argument");
   *launches_out = reinterpret_cast<BatchPlan*>(plan)->launches;
@@ -530,41 +628,48 @@ int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* 
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return fail(QMC_ECUDA, "events");
-  std::vector<qmc_result> scratch(bp->count);
   float best_ms = 1e30f;
   const bool pers = bp->persistent;
   uint64_t best_w = pers ? bp->chunk : bp->work_per_cta;
+  int best_minc = bp->pj_min_ctas;
+  // a specialised persistent kernel is also built for two CTAs per SM (128 registers)
+  const int max_minc = pers && bp->pj_fn ? 2 : 1;
   int rc = QMC_OK;
   // graph mode: evaluations per CTA 2^18..2^24; persistent mode: points per work item 2^14..2^18
-  for (int lw = pers ? 14 : 18; lw <= (pers ? 18 : 24) && rc == QMC_OK; ++lw) {
-    const uint64_t w = 1ull << lw;
-    BatchPlan trial;
-    rc = pers ? persist_create(&trial, bp->count, problems, (uint32_t)w) : batch_create(&trial, bp->count, problems, w);
-    if (rc) break;
-    float tot = 0.0f;
-    for (int rep = 0; rep < 4 && rc == QMC_OK; ++rep) {
-      cudaEventRecord(a, st);
-      if (cudaGraphLaunch(trial.exec, st) != cudaSuccess) rc = fail(QMC_ECUDA, "tuning launch");
-      cudaEventRecord(b, st);
-      cudaEventSynchronize(b);
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, a, b);
-      if (rep > 0) tot += ms;  // first replay warms up
+  for (int minc = 1; minc <= max_minc && rc == QMC_OK; ++minc)
+    for (int lw = pers ? 14 : 18; lw <= (pers ? 18 : 24) && rc == QMC_OK; ++lw) {
+      const uint64_t w = 1ull << lw;
+      BatchPlan trial;
+      rc = pers ? persist_create(&trial, bp->count, problems, (uint32_t)w, minc)
+                : batch_create(&trial, bp->count, problems, w);
+      if (rc) break;
+      float tot = 0.0f;
+      for (int rep = 0; rep < 4 && rc == QMC_OK; ++rep) {
+        cudaEventRecord(a, st);
+        if (cudaGraphLaunch(trial.exec, st) != cudaSuccess) rc = fail(QMC_ECUDA, "tuning launch");
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) tot += ms;  // first replay warms up
+      }
+      cudaStreamSynchronize(st);
+      const bool got = !pers || minc == 1 || trial.pj_fn;  // a failed two-CTA build fell back: not a candidate
+      batch_release(&trial);
+      if (got && tot > 0.0f && tot < best_ms) {
+        best_ms = tot;
+        best_w = w;
+        best_minc = minc;
+      }
     }
-    cudaStreamSynchronize(st);
-    batch_release(&trial);
-    if (tot > 0.0f && tot < best_ms) {
-      best_ms = tot;
-      best_w = w;
-    }
-  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;
-  if (best_w != (pers ? (uint64_t)bp->chunk : bp->work_per_cta)) {
+  if (best_w != (pers ? (uint64_t)bp->chunk : bp->work_per_cta) || (pers && best_minc != bp->pj_min_ctas)) {
     cudaStreamSynchronize(st);
     batch_release(bp);
-    rc = pers ? persist_create(bp, bp->count, problems, (uint32_t)best_w) : batch_create(bp, bp->count, problems, best_w);
+    rc = pers ? persist_create(bp, bp->count, problems, (uint32_t)best_w, best_minc)
+              : batch_create(bp, bp->count, problems, best_w);
     if (rc) return rc;
   }
   if (work_per_cta_out) *work_per_cta_out = best_w;

@@ -95,7 +95,14 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
       }
     if (o > kPairCoefMax) return fail(QMC_EUNSUPPORTED, "deformed: %d coefficient pairs", o);
   }
-  base.value_scale = 1.0;  // transform weights normalised per factor in this kernel
+  // Transform weight constants.  FP64 normalises each factor in the kernel.
+  // FP32 FAST multiplies the factors u and cubes the product: (2a+1)!/(a!)^2
+  // = 140 per dimension remains; other FP32 Korobov plans raise the product of
+  // the factors 4u to the power alpha: ((2a+1)!/(a!)^2 / 4^a) per dimension.
+  base.value_scale = 1.0;
+  if (sizeof(R) == 4 && base.tr == TR_KOROBOV)
+    base.value_scale = fast ? std::pow((double)base.kor[7], (double)d)
+                            : std::pow((double)base.kor[7] / std::pow(4.0, (double)base.alpha), (double)d);
   base.check_finite = 1;
   int nblk = 0, L = 0;
   uint64_t tiles = 0;
@@ -112,7 +119,7 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
   pl->nblk = nblk;
   pl->func = func;
   pl->mc = kMcDef;
-  pl->final_scale = 1.0;
+  pl->final_scale = base.value_scale;
   pl->is_complex = 1;
   for (int k0 = 0; k0 < m; k0 += kMcDef) {
     const int mk = std::min(kMcDef, m - k0);

@@ -151,10 +151,76 @@ __device__ __forceinline__ Cx<R> det_ipm(R (&M)[D][D]) {
   return det;
 }
 
+// Per-point base of coordinate i at point j.  The FAST FP32 variant takes
+// the sector kernels' coordinates: the 32-bit fixed-point fraction plus the
+// per-point dither, each coordinate rounded to float once from the exact
+// integer (coord_fx), so that rounding is unbiased even where the lattice
+// spacing matches the float grid; the other variants keep fix_base.
+template <typename R, bool FAST>
+__device__ __forceinline__ typename FixT<R>::T def_base(uint32_t idx, const Recip& rc, uint64_t j, int i) {
+  if constexpr (FAST && sizeof(R) == 4) return sec_base<float>(idx, rc, j, i);
+  else return fix_base<R>(idx, rc);
+}
+
+template <typename R, bool FAST>
+__device__ __forceinline__ double def_coord_used(const RuleParams<R>& P, typename FixT<R>::T b, int k, int i) {
+  if constexpr (FAST && sizeof(R) == 4) return (double)(uint32_t)(b + P.shiftx[k][i]) * 0x1p-32;
+  else return coord_used<R>(b + shift_of(P, k, i));
+}
+
+// det(I + i M) - 1 without pivoting (J = I + i M strictly diagonally dominant
+// on the cube, shown by the host).  The elimination runs on B = J - I with the
+// identity implicit: the pivot of column c is 1 + b_cc, the updates
+// b_rq -= f b_cq never touch it (c < q), and the determinant is carried as
+// Delta = det - 1 through (1 + Delta)(1 + b) = 1 + (Delta + b + Delta b).
+// Every rounding is then relative to a small quantity.  Eliminating on J
+// itself rounds each diagonal entry, a value near 1, after every small
+// update; in FP32 that made the configuration-4 integral 2e-8 too large (a
+// step-by-step float emulation of the kernel, bit-identical to it on sampled
+// points, put the whole bias in those updates).
+template <int D, typename R>
+__device__ __forceinline__ Cx<R> det_ipm_minus1(R (&M)[D][D]) {
+  R br[D][D], bi[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      br[r][q] = R(0);
+      bi[r][q] = M[r][q];
+    }
+  Cx<R> del{R(0), R(0)};
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const Cx<R> b{br[c][c], bi[c][c]};
+    const Cx<R> t = cmul(del, b);
+    del.re = (del.re + b.re) + t.re;
+    del.im = (del.im + b.im) + t.im;
+    if (c + 1 < D) {
+      const Cx<R> inv = crecip(Cx<R>{R(1) + b.re, b.im});
+#pragma unroll
+      for (int r = c + 1; r < D; ++r) {
+        const Cx<R> f = cmul(Cx<R>{br[r][c], bi[r][c]}, inv);
+#pragma unroll
+        for (int q = c + 1; q < D; ++q) {  // b_rq -= f b_cq, as four fused steps
+          br[r][q] = fma_(-f.re, br[c][q], br[r][q]);
+          br[r][q] = fma_(f.im, bi[c][q], br[r][q]);
+          bi[r][q] = fma_(-f.re, bi[c][q], bi[r][q]);
+          bi[r][q] = fma_(-f.im, br[c][q], bi[r][q]);
+        }
+      }
+    }
+  }
+  return del;
+}
+
 // Weighted complex value at one point and shift; *bad set when Im F(w) > 0.
 // FAST: compile-time Korobov weight 3 and no pivoting (host-checked);
 // otherwise the runtime transform and pivoted LU.  KU: degree of U (1 or 2),
-// with cU in that degree's nested layout.
+// with cU in that degree's nested layout.  FP32 weights: the FAST variant
+// multiplies the factors u = s (1 - s) and cubes the product once
+// (korobov_weight_fx; constant 140^d in FP64 by the final pass), the others
+// raise the product of the factors 4u to the run-time power once
+// (korobov_weight_rt); both avoid the low bias of rounding u^alpha per factor.
 template <typename R, int D, bool FAST = false, int KU = 2>
 __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const typename FixT<R>::T* base, int k,
                                                 bool& bad) {
@@ -162,8 +228,13 @@ __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const ty
   R wt = R(1);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    if constexpr (FAST) y[i] = coord<R, TR_KOROBOV, 0>(base[i] + shift_of(P, k, i), P.kor, 3, wt);
+    if constexpr (FAST && sizeof(R) == 4) y[i] = coord_fx<TR_KOROBOV, 3>(base[i] + P.shiftx[k][i], P.kor, wt);
+    else if constexpr (FAST) y[i] = coord<R, TR_KOROBOV, 0>(base[i] + shift_of(P, k, i), P.kor, 3, wt);
     else y[i] = coord_general<R>(P, base[i] + shift_of(P, k, i), wt);
+  }
+  if constexpr (sizeof(R) == 4) {
+    if constexpr (FAST) wt = korobov_weight_fx(wt);
+    else if (P.tr == TR_KOROBOV) wt = korobov_weight_rt(wt, P.alpha);
   }
   const R* cF = P.cF;
   // gradient of F (linear form) and the contour
@@ -191,15 +262,24 @@ __device__ __forceinline__ Cx<R> deformed_value(const RuleParams<R>& P, const ty
     for (int l = 0; l < D; ++l) M[kk][l] = a * nH[kk * D + l];
     M[kk][kk] = fma_(-lam * fma_(R(-2), y[kk], R(1)), gr[kk], M[kk][kk]);
   }
-  const Cx<R> dJ = det_ipm<D, R, !FAST>(M);
+  // FAST (no pivoting): det J = 1 + Delta, applied as v = r + Delta r;
+  // otherwise the pivoted LU's determinant
+  Cx<R> dJ, dm1;
+  if constexpr (FAST) dm1 = det_ipm_minus1<D, R>(M);
+  else dJ = det_ipm<D, R, true>(M);
   Cx<R> U;
   if constexpr (KU == 1) U = poly1_complex<D, R>(P.cU, z);
   else U = poly2_complex<D, R>(P.cU, z);
   const Cx<R> F = poly2_complex<D, R>(cF, z);
   bad = F.im > R(0);
   Cx<R> v;
-  if (P.aU == -2 && P.aF == -1) v = cmul(dJ, crecip(cmul(cmul(U, U), F)));
-  else v = cmul(dJ, cmul(cpow_int(U, P.aU), cpow_int(F, P.aF)));
+  const Cx<R> rv = (P.aU == -2 && P.aF == -1) ? crecip(cmul(cmul(U, U), F)) : cmul(cpow_int(U, P.aU), cpow_int(F, P.aF));
+  if constexpr (FAST) {
+    const Cx<R> t = cmul(dm1, rv);
+    v = {rv.re + t.re, rv.im + t.im};
+  } else {
+    v = cmul(dJ, rv);
+  }
   v.re *= wt;
   v.im *= wt;
   return v;
@@ -221,9 +301,9 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       uint32_t idx = lattice_index(j, P.g[i], P.n);
-      base[i] = fix_base<R>(idx, P.rc);
+      base[i] = def_base<R, FAST>(idx, P.rc, j, i);
       if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
-      if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<R>(base[i] + shift_of(P, k, i));
+      if (sio.coord) sio.coord[(size_t)s * D + i] = def_coord_used<R, FAST>(P, base[i], k, i);
     }
     bool bad;
     Cx<R> v = deformed_value<R, D, FAST, KU>(P, base, k, bad);
@@ -255,9 +335,10 @@ __global__ void __launch_bounds__(kThreads)
       aim.init();
 #pragma unroll 1
       for (int s = 0; s < steps; ++s) {
+        const uint64_t j = j0 + (uint64_t)s * kThreads;
         FT base[D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) base[i] = fix_base<R>(idx[i], P.rc);
+        for (int i = 0; i < D; ++i) base[i] = def_base<R, FAST>(idx[i], P.rc, j, i);
         bool bad;
         Cx<R> v = deformed_value<R, D, FAST, KU>(P, base, kk, bad);
         ndef += bad ? 1u : 0u;
@@ -339,15 +420,15 @@ __device__ __forceinline__ Cx2 deformed_value2(const RuleParams<float>& P, const
   float wa = 1.0f, wb = 1.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i)
-    y[i] = make_float2(coord<float, TR_KOROBOV, 0>(base[i] + P.shift32[2 * p][i], P.kor, 3, wa),
-                       coord<float, TR_KOROBOV, 0>(base[i] + P.shift32[2 * p + 1][i], P.kor, 3, wb));
+    y[i] = make_float2(coord_fx<TR_KOROBOV, 3>(base[i] + P.shiftx[2 * p][i], P.kor, wa),
+                       coord_fx<TR_KOROBOV, 3>(base[i] + P.shiftx[2 * p + 1][i], P.kor, wb));
   const float2* cu = P.cp;
   const float2* cf = P.cp + 1 + D;
   const float2* H = cf + poly_slots(D, 2);
   const float2 nlam = make_float2(-P.lam, -P.lam);
   const float2 one = make_float2(1.0f, 1.0f), zero = make_float2(0.0f, 0.0f);
   Cx2 z[D];
-  float2 ar[D][D], ai[D][D];  // J = I + i M
+  float2 ar[D][D], ai[D][D];  // B = J - I = i M (real parts zero)
 #pragma unroll
   for (int kk = 0; kk < D; ++kk) {
     float2 gr = cf[l_off(D, kk)];  // dF/dy_kk
@@ -357,19 +438,22 @@ __device__ __forceinline__ Cx2 deformed_value2(const RuleParams<float>& P, const
     z[kk] = {y[kk], mul2(na, gr)};
 #pragma unroll
     for (int l = 0; l < D; ++l) {
-      ar[kk][l] = kk == l ? one : zero;
+      ar[kk][l] = zero;
       ai[kk][l] = mul2(na, H[kk * D + l]);
     }
     ai[kk][kk] = fma2(mul2(nlam, fma2(y[kk], make_float2(-2.0f, -2.0f), one)), gr, ai[kk][kk]);
   }
-  // det J by LU without pivoting (J diagonally dominant, shown by the host)
-  Cx2 dJ{one, zero};
+  // det J - 1 by LU without pivoting on B = J - I (J diagonally dominant,
+  // shown by the host; see det_ipm_minus1 for why the identity stays implicit)
+  Cx2 dm1{zero, zero};
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const Cx2 piv{ar[c][c], ai[c][c]};
-    dJ = cmul2(dJ, piv);
+    const Cx2 b{ar[c][c], ai[c][c]};
+    const Cx2 t = cmul2(dm1, b);
+    dm1.re = add2(add2(dm1.re, b.re), t.re);
+    dm1.im = add2(add2(dm1.im, b.im), t.im);
     if (c + 1 < D) {
-      const Cx2 inv = crecip2(piv);
+      const Cx2 inv = crecip2(Cx2{add2(one, b.re), b.im});
 #pragma unroll
       for (int r = c + 1; r < D; ++r) {
         const Cx2 f = cmul2(Cx2{ar[r][c], ai[r][c]}, inv);
@@ -409,8 +493,10 @@ __device__ __forceinline__ Cx2 deformed_value2(const RuleParams<float>& P, const
   }
   bad_a = F.im.x > 0.0f;  // the contour left the allowed half-plane, Im F(w) > 0
   bad_b = F.im.y > 0.0f;
-  Cx2 v = cmul2(dJ, crecip2(cmul2(cmul2(U, U), F)));
-  const float2 w = make_float2(wa, wb);
+  const Cx2 rv = crecip2(cmul2(cmul2(U, U), F));
+  const Cx2 t = cmul2(dm1, rv);
+  Cx2 v{add2(rv.re, t.re), add2(rv.im, t.im)};
+  const float2 w = korobov_weight_fx2(make_float2(wa, wb));  // (prod u)^3; 140^d in FP64 by the final pass
   v.re = mul2(v.re, w);
   v.im = mul2(v.im, w);
   return v;
@@ -429,9 +515,9 @@ __global__ void __launch_bounds__(kThreads, 2)  // two CTAs per SM: 128 register
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       uint32_t idx = lattice_index(j, P.g[i], P.n);
-      base[i] = fix_base<float>(idx, P.rc);
+      base[i] = def_base<float, true>(idx, P.rc, j, i);
       if (sio.idx) sio.idx[(size_t)s * D + i] = idx;
-      if (sio.coord) sio.coord[(size_t)s * D + i] = coord_used<float>(base[i] + P.shift32[k][i]);
+      if (sio.coord) sio.coord[(size_t)s * D + i] = def_coord_used<float, true>(P, base[i], k, i);
     }
     bool bad;
     Cx<float> v = deformed_value<float, D, true, 1>(P, base, k, bad);
@@ -466,9 +552,10 @@ __global__ void __launch_bounds__(kThreads, 2)  // two CTAs per SM: 128 register
       aim_b.init();
 #pragma unroll 1
       for (int s = 0; s < steps; ++s) {
+        const uint64_t j = j0 + (uint64_t)s * kThreads;
         uint32_t base[D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) base[i] = fix_base<float>(idx[i], P.rc);
+        for (int i = 0; i < D; ++i) base[i] = def_base<float, true>(idx[i], P.rc, j, i);
         bool bad_a, bad_b;
         Cx2 v = deformed_value2<D>(P, base, kk >> 1, bad_a, bad_b);
         ndef += (bad_a ? 1u : 0u) + ((bad_b && has_b) ? 1u : 0u);

@@ -177,8 +177,11 @@ __device__ __forceinline__ R korobov_apply(R s, bool upper, const R* kor, int al
   return upper ? R(1) - zs : zs;
 }
 
-// One coordinate of the FP32 path.  Returns the transformed coordinate z; w
-// is multiplied by the transform's weight factor.
+// One coordinate of the FP32 path.  Returns the transformed coordinate z.
+// Under the Korobov transform (weight `alpha` at run time) w is multiplied by
+// the factor 4u = 4 s (1 - s) only: the caller raises the product of the d
+// factors to the power alpha once per value (korobov_weight_rt), and the
+// constant ((2a+1)!/(a!)^2 / 4^a)^d is applied in FP64 by the final pass.
 template <int TR, int ALPHA>
 __device__ __forceinline__ float coord_f32(uint32_t X, const float* kor, int alpha, float& w) {
   float xb = unit_f32(X);
@@ -186,12 +189,36 @@ __device__ __forceinline__ float coord_f32(uint32_t X, const float* kor, int alp
     float t = __fmaf_rn(2.0f, xb, -3.0f);  // 2x - 1, exact
     return 1.0f - fabsf(t);
   } else if constexpr (TR == TR_KOROBOV) {
+    static_assert(ALPHA == 0, "the FP32 float-coordinate path takes the Korobov weight at run time");
     float x = xb - 1.0f;                   // exact
     float s = fminf(x, 1.0f - x);          // exact
-    return korobov_apply<ALPHA>(s, x > 0.5f, kor, alpha, w);
+    float p = kor[alpha];
+    for (int k = alpha - 1; k >= 0; --k) p = __fmaf_rn(p, s, kor[k]);
+    float sp = s;
+    for (int q = 0; q < alpha; ++q) sp *= s;
+    const float zs = sp * p;
+    w = __fmul_rn(w, 4.0f * __fmaf_rn(-s, s, s));  // 4u: an exact power of two times u
+    return x > 0.5f ? 1.0f - zs : zs;
   } else {
     return xb - 1.0f;
   }
+}
+
+// The Korobov weight of the FP32 paths with a run-time alpha from the product
+// w of the factors 4u: w^alpha as a double-float power (each product's
+// rounding error kept exactly by an FMA and carried along), rounded once.
+// Rounding u^alpha factor by factor in float is biased low (the low bits of
+// a square of a float are far from uniform); one rounding of a nearly exact
+// power is not.
+__device__ __forceinline__ float korobov_weight_rt(float w, int alpha) {
+  float hi = w, lo = 0.0f;
+  for (int q = 1; q < alpha; ++q) {
+    const float p = __fmul_rn(hi, w);
+    const float e = __fmaf_rn(hi, w, -p);
+    lo = __fmaf_rn(lo, w, e);
+    hi = p;
+  }
+  return __fadd_rn(hi, lo);
 }
 
 // One coordinate of the FP64 path.

@@ -22,9 +22,11 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "plan.h"
@@ -47,7 +49,16 @@ struct DriverApi {
                                  const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
   CUresult (*getErrorString)(CUresult, const char**) = nullptr;
   CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+  // linker of relocatable device code (the specialised persistent batch)
+  CUresult (*linkCreate)(unsigned, CUjit_option*, void**, CUlinkState*) = nullptr;
+  CUresult (*linkAddData)(CUlinkState, CUjitInputType, void*, size_t, const char*, unsigned, CUjit_option*,
+                          void**) = nullptr;
+  CUresult (*linkComplete)(CUlinkState, void**, size_t*) = nullptr;
+  CUresult (*linkDestroy)(CUlinkState) = nullptr;
+  CUresult (*graphAddKernelNodeDeps)(CUgraphNode*, CUgraph, const CUgraphNode*, size_t,
+                                     const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
   bool ok = false;
+  bool link_ok = false;
 };
 
 const DriverApi& driver() {
@@ -67,7 +78,11 @@ const DriverApi& driver() {
              get("cuGraphAddKernelNode", (void**)&api.graphAddKernelNode) &&
              get("cuGetErrorString", (void**)&api.getErrorString) &&
              get("cuFuncSetAttribute", (void**)&api.funcSetAttribute);
-    if (!api.ok) cudaGetLastError();
+    api.link_ok = api.ok && get("cuLinkCreate", (void**)&api.linkCreate) &&
+                  get("cuLinkAddData", (void**)&api.linkAddData) &&
+                  get("cuLinkComplete", (void**)&api.linkComplete) &&
+                  get("cuLinkDestroy", (void**)&api.linkDestroy);
+    if (!api.ok || !api.link_ok) cudaGetLastError();
   });
   return api;
 }
@@ -131,8 +146,8 @@ std::string poly_code(int D, const std::vector<double>& cu, const std::vector<do
 // the same chains over the (c, c) pairs of the kernel parameters, skipping the
 // slots whose coefficient is zero.
 std::string poly_code2(int D, const std::vector<double>& cu, const std::vector<double>& cf,
-                       const std::string& arr = "P.cp") {
-  auto pc = [&arr](int slot) { return arr + "[" + std::to_string(slot) + "]"; };
+                       const std::string& arr = "P.cp", const std::vector<int>* remap = nullptr) {
+  auto pc = [&arr, remap](int slot) { return arr + "[" + std::to_string(remap ? (*remap)[slot] : slot) + "]"; };
   const int nu = 1 + D;
   std::string s;
   s += "    float2 u = " + pc(0) + ";\n";
@@ -323,6 +338,257 @@ int jit_multi_f32(int D, int MC, int TR, int ALPHA, bool check,
   return jit_compile(src, "qmc_jit_multi", 0, fn_out, occ_out);
 }
 
+// ---------------------------------------------- specialised persistent batch --
+
+namespace {
+
+std::string hex32(uint32_t v) {
+  char b[24];
+  std::snprintf(b, sizeof(b), "0x%08xu", v);
+  return b;
+}
+std::string hex64(uint64_t v) {
+  char b[32];
+  std::snprintf(b, sizeof(b), "0x%016llxull", (unsigned long long)v);
+  return b;
+}
+
+// Pair slots (U's then -F's, the order of fill_pairs) that poly_code2 reads:
+// the constant terms and every slot with a nonzero coefficient.  remap[slot]
+// is the slot's index in the compact array, -1 if unused.
+std::vector<int> used_pairs(const PjSector& S, std::vector<float>* vals) {
+  const int nu = 1 + S.d;
+  const int nf = (int)S.cf.size();
+  std::vector<int> remap(nu + nf, -1);
+  int c = 0;
+  auto take = [&](int slot, float v) {
+    remap[slot] = c++;
+    vals->push_back(v);
+  };
+  take(0, (float)S.cu[0]);
+  for (int i = 0; i < S.d; ++i)
+    if ((float)S.cu[1 + i] != 0.0f) take(1 + i, (float)S.cu[1 + i]);
+  take(nu, -(float)S.cf[0]);
+  for (int t = 1; t < nf; ++t)
+    if ((float)S.cf[t] != 0.0f) take(nu + t, -(float)S.cf[t]);
+  return remap;
+}
+
+// One NVRTC program compiled as relocatable device code (every function held
+// to max_regs registers); its CUBIN in *out.
+int nvrtc_rdc(const std::string& src, const std::string& name, int max_regs, std::vector<char>* out,
+              std::string* log) {
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), name.c_str(), 0, nullptr, nullptr) != NVRTC_SUCCESS)
+    return QMC_EUNSUPPORTED;
+  const std::string inc = "-I" + csrc_dir();
+  const std::string regs = "--maxrregcount=" + std::to_string(max_regs);
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", inc.c_str(), "-lineinfo",
+                        "--relocatable-device-code=true", regs.c_str()};
+  nvrtcResult cr = nvrtcCompileProgram(prog, 6, opts);
+  if (cr != NVRTC_SUCCESS) {
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    log->assign(ls, '\0');
+    nvrtcGetProgramLog(prog, &(*log)[0]);
+    nvrtcDestroyProgram(&prog);
+    return QMC_EUNSUPPORTED;
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(prog, &n);
+  out->resize(n);
+  nvrtcGetCUBIN(prog, out->data());
+  nvrtcDestroyProgram(&prog);
+  return QMC_OK;
+}
+
+}  // namespace
+
+// The sources of the specialised persistent module: one program per group of
+// sectors (their coefficient pairs, one struct and one device function per
+// descriptor) and the dispatching kernel.  QMC_EUNSUPPORTED when the nonzero
+// coefficient pairs exceed what the module's constant bank holds.
+int persist_sources(const std::vector<PjSector>& secs, const std::vector<PjDesc>& descs, int ngroups, int min_ctas,
+                    std::vector<std::string>* gsrc_out, std::string* msrc_out) {
+  const int nsec = (int)secs.size();
+  std::vector<std::string>& gsrc = *gsrc_out;
+  gsrc.assign(ngroups, std::string());
+  std::vector<std::vector<int>> remaps(nsec);
+  size_t const_bytes = 0;
+  for (int g = 0; g < ngroups; ++g) {
+    std::string& src = gsrc[g];
+    src += "#include \"persist_jit.cuh\"\n";
+    src += "__constant__ float qmc_kor_g" + std::to_string(g) + "[8] = {";
+    for (int k = 0; k < 8; ++k) src += (k ? ", " : "") + lit(secs[0].kor[k]);
+    src += "};\n";
+  }
+  for (int s = 0; s < nsec; ++s) {
+    const PjSector& S = secs[s];
+    std::vector<float> vals;
+    remaps[s] = used_pairs(S, &vals);
+    const_bytes += vals.size() * 8;
+    std::string& src = gsrc[s % ngroups];
+    src += "__constant__ float2 qmc_cp_s" + std::to_string(s) + "[" + std::to_string(vals.size()) + "] = {";
+    for (size_t q = 0; q < vals.size(); ++q) src += (q ? ", {" : "{") + lit(vals[q]) + ", " + lit(vals[q]) + "}";
+    src += "};\n";
+  }
+  if (const_bytes > 60 * 1024) return QMC_EUNSUPPORTED;  // the constant bank of one module holds 64 KB
+  for (size_t q = 0; q < descs.size(); ++q) {
+    const PjDesc& Dq = descs[q];
+    const PjSector& S = secs[Dq.sector];
+    const int g = Dq.sector % ngroups;
+    std::string& src = gsrc[g];
+    const std::string nm = "qmc_sp_" + std::to_string(q);
+    src += "struct " + nm + " {\n";
+    src += "  static constexpr int D = " + std::to_string(S.d) + ", TR = " + std::to_string(S.tr) +
+           ", ALPHA = " + std::to_string(S.tr == TR_KOROBOV ? 3 : 0) + ", MC = " + std::to_string(Dq.mc) +
+           ", M = " + std::to_string(Dq.m) + ", KBASE = " + std::to_string(Dq.kbase) + ";\n";
+    src += std::string("  static constexpr bool CHECK = ") + (S.check ? "true" : "false") + ";\n";
+    src += "  static constexpr unsigned long long N = " + hex64(S.n) + ", RHI = " + hex64(S.rc.rhi) +
+           ", RLO = " + hex64(S.rc.rlo) + ";\n";
+    auto table = [&](const char* fname, const char* arg, int count, auto value) {
+      src += std::string("  __device__ static __forceinline__ unsigned ") + fname + "(" + arg + ") {\n    switch (" +
+             (std::strchr(arg, ',') ? "k * 16 + i" : "i") + ") {\n";
+      for (int c = 0; c < count; ++c) src += "      case " + std::to_string(c) + ": return " + value(c) + ";\n";
+      src += "    }\n    return 0u;\n  }\n";
+    };
+    table("g", "int i", S.d, [&](int i) { return hex32(S.g[i]); });
+    table("gstep", "int i", S.d, [&](int i) { return hex32(S.gstep[i]); });
+    {
+      src += "  __device__ static __forceinline__ unsigned shift(int k, int i) {\n    switch (k * 16 + i) {\n";
+      for (int k = 0; k < Dq.mc; ++k)
+        for (int i = 0; i < S.d; ++i)
+          src += "      case " + std::to_string(k * 16 + i) + ": return " + hex32(Dq.shift[(size_t)k * S.d + i]) + ";\n";
+      src += "    }\n    return 0u;\n  }\n";
+    }
+    src += "  __device__ static __forceinline__ const float* kor() { return qmc_kor_g" + std::to_string(g) + "; }\n";
+    src += "  __device__ static __forceinline__ void eval2(const float2* z, float2& U, float2& Fn) {\n";
+    src += "    using namespace qmc;\n";
+    src += poly_code2(S.d, S.cu, S.cf, "qmc_cp_s" + std::to_string(Dq.sector), &remaps[Dq.sector]);
+    src += "  }\n};\n";
+    src += "extern \"C\" __device__ void qmc_pd_" + std::to_string(q) +
+           "(unsigned long long j0, unsigned long long chunk, unsigned item, int nitems, double* partial, "
+           "unsigned long long* counters, double (*red)[qmc::kPjMc]) {\n";
+    src += "  qmc::pj_sweep<" + nm + ">(j0, chunk, item, nitems, partial, counters, red);\n}\n";
+  }
+  std::string& msrc = *msrc_out;
+  msrc = "#include \"persist_jit.cuh\"\n";
+  for (size_t q = 0; q < descs.size(); ++q)
+    msrc += "extern \"C\" __device__ void qmc_pd_" + std::to_string(q) +
+            "(unsigned long long, unsigned long long, unsigned, int, double*, unsigned long long*, "
+            "double (*)[qmc::kPjMc]);\n";
+  msrc +=
+      "extern \"C\" __global__ void __launch_bounds__(256, " + std::to_string(min_ctas) +
+      ") qmc_jit_persist(const __grid_constant__ qmc::PersistArgs A) {\n"
+      "  __shared__ double red[qmc::kThreads / 32][qmc::kPjMc];\n"
+      "  __shared__ unsigned cur;\n"
+      "  for (;;) {\n"
+      "    if (threadIdx.x == 0) cur = atomicAdd(A.next, 1u);\n"
+      "    __syncthreads();\n"
+      "    const unsigned it = cur;\n"
+      "    if (it >= A.nitems) break;  // the same for every thread of the CTA\n"
+      "    const qmc::PersistItem wi = A.items[it];\n"
+      "    const qmc::PersistDesc* ds = A.descs + wi.desc;\n"
+      "    const unsigned long long j0 = (unsigned long long)wi.item * A.chunk;\n"
+      "    double* partial = ds->partial;\n"
+      "    unsigned long long* counters = ds->counters;\n"
+      "    const int nitems = ds->nitems;\n"
+      "    switch (wi.desc) {\n";
+  for (size_t q = 0; q < descs.size(); ++q)
+    msrc += "      case " + std::to_string(q) + ": qmc_pd_" + std::to_string(q) +
+            "(j0, A.chunk, wi.item, nitems, partial, counters, red); break;\n";
+  msrc +=
+      "    }\n"
+      "    __syncthreads();  // red and cur are rewritten for the next item\n"
+      "  }\n}\n";
+  return QMC_OK;
+}
+
+int jit_persist(const std::vector<PjSector>& secs, const std::vector<PjDesc>& descs, int min_ctas, void** fn_out,
+                int* occ_out) {
+  if (secs.empty() || descs.empty() || min_ctas < 1 || min_ctas > 2) return QMC_EINVAL;
+  const int max_regs = min_ctas == 2 ? 128 : 255;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_ECUDA;
+  }
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return QMC_EUNSUPPORTED;
+  // group the sectors (with all of their descriptors) for compilation on the host cores
+  const int ngroups = std::max(1, std::min<int>((int)secs.size(),
+                                                std::min(32u, std::max(1u, std::thread::hardware_concurrency()))));
+  std::vector<std::string> gsrc;
+  std::string msrc;
+  int rc = persist_sources(secs, descs, ngroups, min_ctas, &gsrc, &msrc);
+  if (rc) return rc;
+  std::string key = std::to_string(dev) + "\npersist " + std::to_string(max_regs) + "\n" + msrc;
+  for (const std::string& g : gsrc) key += g;
+  {
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    auto it = g_jit_cache.find(key);
+    if (it != g_jit_cache.end()) {
+      *fn_out = (void*)it->second.fn;
+      *occ_out = it->second.occupancy;
+      return QMC_OK;
+    }
+  }
+  const DriverApi& drv = driver();
+  if (!drv.ok || !drv.link_ok) return QMC_EUNSUPPORTED;
+  // compile the groups and the dispatching kernel on the host cores
+  std::vector<std::vector<char>> cubins(ngroups + 1);
+  std::vector<int> rcs(ngroups + 1, QMC_OK);
+  std::vector<std::string> logs(ngroups + 1);
+  {
+    std::vector<std::thread> th;
+    for (int g = 0; g <= ngroups; ++g)
+      th.emplace_back([&, g]() {
+        rcs[g] = g < ngroups ? nvrtc_rdc(gsrc[g], "qmc_persist_g" + std::to_string(g) + ".cu", max_regs, &cubins[g],
+                                         &logs[g])
+                             : nvrtc_rdc(msrc, "qmc_persist_main.cu", max_regs, &cubins[g], &logs[g]);
+      });
+    for (auto& t : th) t.join();
+  }
+  for (int g = 0; g <= ngroups; ++g)
+    if (rcs[g] != QMC_OK) {
+      fail(QMC_EUNSUPPORTED, "persistent batch specialisation failed to compile: %.400s", logs[g].c_str());
+      return QMC_EUNSUPPORTED;
+    }
+  cudaFree(nullptr);  // the runtime's primary context is current for the driver API
+  CUlinkState ls;
+  if (drv.linkCreate(0, nullptr, nullptr, &ls) != CUDA_SUCCESS) return QMC_EUNSUPPORTED;
+  for (int g = 0; g <= ngroups; ++g) {
+    const std::string nm = "qmc_persist_" + std::to_string(g) + ".cubin";
+    if (drv.linkAddData(ls, CU_JIT_INPUT_CUBIN, cubins[g].data(), cubins[g].size(), nm.c_str(), 0, nullptr,
+                        nullptr) != CUDA_SUCCESS) {
+      drv.linkDestroy(ls);
+      return QMC_EUNSUPPORTED;
+    }
+  }
+  void* image = nullptr;
+  size_t image_size = 0;
+  if (drv.linkComplete(ls, &image, &image_size) != CUDA_SUCCESS) {
+    drv.linkDestroy(ls);
+    return QMC_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  JitEntry e;
+  const bool loaded = drv.moduleLoadData(&e.mod, image) == CUDA_SUCCESS;
+  drv.linkDestroy(ls);  // owns the linked image; the module keeps its own copy
+  if (!loaded) return QMC_EUNSUPPORTED;
+  if (drv.moduleGetFunction(&e.fn, e.mod, "qmc_jit_persist") != CUDA_SUCCESS) {
+    drv.moduleUnload(e.mod);
+    return QMC_EUNSUPPORTED;
+  }
+  if (drv.occupancy(&e.occupancy, e.fn, kThreads, 0) != CUDA_SUCCESS || e.occupancy < 1) e.occupancy = 1;
+  g_jit_cache[key] = e;
+  *fn_out = (void*)e.fn;
+  *occ_out = e.occupancy;
+  return QMC_OK;
+}
+
 // Launch either a runtime kernel (ln.func) or a specialised one (ln.cufunc).
 int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream) {
   if (ln.cufunc) {
@@ -342,7 +608,8 @@ int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream) {
 }
 
 // Kernel node for either kind of launch.
-int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraphNode_t* node) {
+int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraphNode_t* node,
+                     const cudaGraphNode_t* deps, size_t ndeps) {
   if (ln.cufunc) {
     CUDA_KERNEL_NODE_PARAMS kp;
     std::memset(&kp, 0, sizeof(kp));
@@ -356,7 +623,7 @@ int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraph
     kp.sharedMemBytes = (unsigned)ln.smem;
     kp.kernelParams = args;
     CUgraphNode n;
-    if (driver().graphAddKernelNode(&n, (CUgraph)graph, nullptr, 0, &kp) != CUDA_SUCCESS)
+    if (driver().graphAddKernelNode(&n, (CUgraph)graph, (const CUgraphNode*)deps, ndeps, &kp) != CUDA_SUCCESS)
       return fail(QMC_ECUDA, "cuGraphAddKernelNode");
     *node = (cudaGraphNode_t)n;
     return QMC_OK;
@@ -367,7 +634,7 @@ int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraph
   kp.gridDim = ln.grid;
   kp.blockDim = dim3(kThreads);
   kp.kernelParams = args;
-  cudaError_t e = cudaGraphAddKernelNode(node, graph, nullptr, 0, &kp);
+  cudaError_t e = cudaGraphAddKernelNode(node, graph, deps, ndeps, &kp);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddKernelNode");
   return QMC_OK;
 }

@@ -1,0 +1,105 @@
+// Run-time specialised persistent batch (device side, compiled by NVRTC).
+//
+// A descriptor is one sector's rule (Eq. 2) for a chunk of up to kPjMc shifts.
+// The host writes, per descriptor, a struct SP whose members are compile-time
+// constants of that rule: dimension, transform, n, the 128-bit reciprocal of
+// n, g and its per-step increment, the fixed-point shifts, and U and -F as
+// straight-line packed code over their nonzero monomials (coefficient pairs
+// in a __constant__ array of the descriptor's sector).  pj_sweep<SP> is the
+// FP32 packed sector sweep over one work item (a chunk of consecutive j) with
+// all of those folded into the instructions: shifts become immediate
+// operands of the coordinate adds, coefficients constant-bank operands of the
+// packed FMAs.  Its arithmetic is that of the sector kernels' packed path
+// (sector_value2 with the sector kernels' coordinates, reciprocal, weight and
+// compensated sums), so each value equals theirs bit for bit.
+//
+// SP provides
+//   static constexpr int D, TR, ALPHA, MC (even, <= kPjMc), M (shift rows
+//     written back, <= MC), KBASE (first shift of the chunk); bool CHECK
+//   static constexpr uint64_t N, RHI, RLO
+//   static uint32_t g(int i), gstep(int i), shift(int k, int i)
+//   static const float* kor()
+//   static void eval2(const float2* z, float2& U, float2& Fn)
+#pragma once
+
+#include "rule_kernels.cuh"
+
+namespace qmc {
+
+template <class SP>
+__device__ __forceinline__ void pj_sweep(uint64_t j0, uint64_t chunk, uint32_t item, int32_t nitems,
+                                         double* __restrict__ partial, unsigned long long* __restrict__ counters,
+                                         double (*red)[kPjMc]) {
+  constexpr int D = SP::D, MC = SP::MC, TR = SP::TR, ALPHA = SP::ALPHA;
+  static_assert(MC % 2 == 0 && MC <= kPjMc && SP::M <= MC, "shift rows of a descriptor");
+  const uint64_t j1 = j0 + chunk < SP::N ? j0 + chunk : SP::N;
+  Acc<float> acc[MC];
+#pragma unroll
+  for (int kk = 0; kk < MC; ++kk) acc[kk].init();
+  float2 run2[MC / 2];
+#pragma unroll
+  for (int p = 0; p < MC / 2; ++p) run2[p] = make_float2(0.0f, 0.0f);
+  unsigned nbad = 0;
+  const uint64_t jt = j0 + threadIdx.x;
+  if (jt < j1) {
+    const int steps = (int)((j1 - jt + kThreads - 1) / kThreads);
+    const Recip rc{SP::RHI, SP::RLO};
+    uint32_t idx[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) idx[i] = lattice_index(jt, SP::g(i), SP::N);
+    for (int s = 0; s < steps; ++s) {
+      uint32_t base[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) base[i] = sec_base<float>(idx[i], rc, jt + (uint64_t)s * kThreads, i);
+#pragma unroll
+      for (int p = 0; p < MC / 2; ++p) {
+        float2 z[D];
+        float wa = 1.0f, wb = 1.0f;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+          z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + SP::shift(2 * p, i), SP::kor(), wa),
+                             coord_fx<TR, ALPHA>(base[i] + SP::shift(2 * p + 1, i), SP::kor(), wb));
+        float2 U, Fn;
+        SP::eval2(z, U, Fn);
+        float2 v = recip_neg2(mul2(mul2(U, U), Fn));
+        if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(make_float2(wa, wb)));
+        if constexpr (SP::CHECK) {
+          const bool oka = finite_(v.x), okb = finite_(v.y);
+          nbad += (oka || 2 * p >= SP::M) ? 0u : 1u;  // padded rows are not counted
+          nbad += (okb || 2 * p + 1 >= SP::M) ? 0u : 1u;
+          v = make_float2(oka ? v.x : 0.0f, okb ? v.y : 0.0f);
+        }
+        run2[p] = add2(run2[p], v);
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], SP::gstep(i), (uint32_t)SP::N);
+      if ((s & fold_mask<TR>()) == fold_mask<TR>()) {
+        unpack_runs<MC>(run2, acc);
+#pragma unroll
+        for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
+      }
+    }
+  }
+  unpack_runs<MC>(run2, acc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int kk = 0; kk < MC; ++kk) {
+    const double t = acc[kk].warp_total();
+    if (lane == 0) red[warp][kk] = t;
+  }
+  if constexpr (SP::CHECK) {
+    const unsigned long long bad = warp_sum_u64((unsigned long long)nbad);
+    if (lane == 0 && bad) atomicAdd(&counters[0], bad);
+  }
+  __syncthreads();
+  if (threadIdx.x < SP::M) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) sum += red[w][threadIdx.x];
+    const size_t slot = ((size_t)(SP::KBASE + threadIdx.x) * nitems + item) * 2;
+    partial[slot] = sum;
+    partial[slot + 1] = 0.0;
+  }
+}
+
+}  // namespace qmc

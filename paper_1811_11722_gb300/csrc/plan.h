@@ -115,8 +115,34 @@ int jit_multi_f32(int D, int MC, int TR, int ALPHA, bool check,
                   int* occ_out);
 int jit_eps_f32(int D, int MC, int NE, int TR, int ALPHA, bool log1, bool check, const std::vector<double>& cu,
                 const std::vector<double>& cf, void** fn_out, int* occ_out);
+// One sector of a run-time specialised persistent batch: its rule as the
+// packed FP32 sector path sees it (prescaled dense slots of U and F).
+struct PjSector {
+  int d = 0, tr = 0;
+  bool check = false;
+  uint64_t n = 0;
+  Recip rc{0, 0};
+  uint32_t g[QMC_DMAX] = {0}, gstep[QMC_DMAX] = {0};
+  std::vector<double> cu, cf;
+  float kor[8] = {0};
+};
+// One descriptor: a sector and a chunk of shift rows (rows >= m repeat row 0).
+struct PjDesc {
+  int sector = 0, kbase = 0, m = 0, mc = 0;
+  std::vector<uint32_t> shift;  // [mc][d], 32-bit fixed point
+};
+// Compile (or fetch) the persistent kernel qmc_jit_persist for these
+// descriptors (one NVRTC program per group of sectors, compiled on the host
+// cores as relocatable code and linked); QMC_OK with the CUfunction and its
+// occupancy, else an error code (the caller keeps the generic kernel).
+// min_ctas: resident CTAs per SM the kernel is built for (1, or 2 with every
+// function held to 128 registers).
+int jit_persist(const std::vector<PjSector>& secs, const std::vector<PjDesc>& descs, int min_ctas, void** fn_out,
+                int* occ_out);
+
 int device_sms();
 int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream);
-int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraphNode_t* node);
+int graph_add_launch(cudaGraph_t graph, const Launch& ln, void** args, cudaGraphNode_t* node,
+                     const cudaGraphNode_t* deps = nullptr, size_t ndeps = 0);
 
 }  // namespace qmc

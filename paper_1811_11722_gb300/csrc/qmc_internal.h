@@ -158,6 +158,7 @@ struct MultiParams {
 // from a counter in any order; item q of a sector writes the fixed slots
 // [k][q] of that sector, so the result does not depend on the order.
 constexpr int kPersistMc = 8;
+constexpr int kPjMc = 16;  // shift rows per descriptor of the run-time specialised persistent kernel
 struct alignas(16) PersistDesc {
   RuleParams<float> P;
   double* partial;                // the sector's slots [m][nitems][2]

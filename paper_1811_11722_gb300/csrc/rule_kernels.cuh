@@ -109,6 +109,15 @@ struct SecBase<double> {
   using T = uint64_t;
 };
 
+// The weight of a value from the factors coord() collected under a run-time
+// Korobov weight: FP32 raises their product to the power alpha once
+// (korobov_weight_rt); FP64 factors are already the normalised weights.
+template <typename R>
+__device__ __forceinline__ R korobov_weight(R w, int alpha) {
+  if constexpr (sizeof(R) == 4) return korobov_weight_rt(w, alpha);
+  else return w;
+}
+
 template <typename R, int TR, int ALPHA>
 __device__ __forceinline__ R coord(typename FixT<R>::T X, const R* kor, int alpha, R& w) {
   if constexpr (sizeof(R) == 4) return coord_f32<TR, ALPHA>(X, kor, alpha, w);
@@ -412,12 +421,12 @@ struct SepState {
       lin[kk] = fma_(P.sep_c[i], z, lin[kk]);
     }
   }
-  __device__ __forceinline__ R value(int kk) const {
+  __device__ __forceinline__ R value(const RuleParams<R>& P, int kk) const {
     R v;
     if constexpr (FK == FK_SEPEXP) v = prod[kk] * exp(lin[kk]);
     else if constexpr (FK == FK_TRIG) v = cospi(R(2) * lin[kk]);
     else v = R(1);
-    if constexpr (TR == TR_KOROBOV) v *= w[kk];
+    if constexpr (TR == TR_KOROBOV) v *= korobov_weight<R>(w[kk], P.alpha);
     return v;
   }
 };
@@ -451,7 +460,7 @@ __global__ void __launch_bounds__(kThreads)
     if constexpr (FK == FK_SEPEXP) v = prod * exp(lin);
     else if constexpr (FK == FK_TRIG) v = cospi(R(2) * lin);
     else v = R(1);
-    if constexpr (TR == TR_KOROBOV) v *= w;
+    if constexpr (TR == TR_KOROBOV) v *= korobov_weight<R>(w, P.alpha);
     sio.values[2 * (size_t)s] = (double)v * P.value_scale;
     sio.values[2 * (size_t)s + 1] = 0.0;
     return;
@@ -481,7 +490,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int kk = 0; kk < MC; ++kk) {
         if (kk < mk) {
-          R v = st.value(kk);
+          R v = st.value(P, kk);
           if (P.check_finite) {
             bool ok = finite_(v);
             nbad += ok ? 0u : 1u;
@@ -548,6 +557,9 @@ __device__ __forceinline__ R general_eval(const GeneralParams<R>& G, uint64_t j,
   }
   U = sparse_eval(G.U, zsh, P.d);
   F = sparse_eval(G.F, zsh, P.d);
+  if constexpr (sizeof(R) == 4) {
+    if (P.tr == TR_KOROBOV) w = korobov_weight_rt(w, P.alpha);
+  }
   return ipow(U, P.aU) * ipow(F, P.aF) * w;
 }
 

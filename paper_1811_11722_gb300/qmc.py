@@ -77,7 +77,7 @@ class qmc_eps(ctypes.Structure):
 
 class qmc_cv_config(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("K", ctypes.c_int32), ("freq_step", ctypes.c_int32), ("steps", ctypes.c_int32),
-                ("lr", ctypes.c_float), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("lr", ctypes.c_float), ("band", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 RESULT_BYTES = ctypes.sizeof(qmc_result)
@@ -116,12 +116,16 @@ def lib():
             L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
             L.qmc_batch_plan_destroy.argtypes = [vp]
             L.qmc_batch_plan_launches.argtypes = [vp, ctypes.POINTER(i32)]
+            L.qmc_batch_plan_describe.argtypes = [vp, ctypes.c_char_p, i32]
             L.qmc_batch_plan_tune.argtypes = [vp, vp, vp, ctypes.POINTER(u64)]
             L.qmc_sample_points.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, i32, vp, vp, vp, vp, vp, vp]
             P_cfg = ctypes.POINTER(qmc_cv_config)
             L.qmc_cv_train.argtypes = [i32, u64, vp, vp, qmc_transform, P_int, P_cfg, vp, vp, vp]
             L.qmc_integrate_cv.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_cfg, vp, vp, vp, vp]
             L.qmc_cv_loss_grad.argtypes = [i32, P_cfg, i32, vp, vp, vp, vp, vp, vp]
+            L.qmc_integrate_cv_to_tolerance.argtypes = [i32, i32, vp, vp, i32, vp, qmc_transform, P_int, P_cfg, vp,
+                                                        ctypes.c_double, vp, ctypes.POINTER(i32),
+                                                        ctypes.POINTER(i32), vp, vp]
             L.qmc_integrate_noalloc.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, vp, vp, vp]
             P_eps = ctypes.POINTER(qmc_eps)
             L.qmc_integrate_eps.argtypes = [i32, u64, i32, vp, vp, qmc_transform, P_int, P_eps, vp, vp, vp]
@@ -143,7 +147,8 @@ def lib():
                          "qmc_cv_loss_grad", "qmc_integrate_noalloc", "qmc_combine_shifts", "qmc_measure_peaks",
                          "qmc_integrate_to_tolerance", "qmc_integrate_eps", "qmc_eps_plan_create",
                          "qmc_sample_points_eps", "qmc_integrate_multi", "qmc_multi_plan_create", "qmc_make_lattice_embedded",
-                         "qmc_integrate_extensible", "qmc_batch_plan_create_persistent"):
+                         "qmc_integrate_extensible", "qmc_batch_plan_create_persistent",
+                         "qmc_integrate_cv_to_tolerance", "qmc_batch_plan_describe"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -388,6 +393,11 @@ class BatchPlan:
         _check(lib().qmc_batch_plan_launches(self.h, ctypes.byref(v)))
         return int(v.value)
 
+    def describe(self) -> dict:
+        buf = ctypes.create_string_buffer(256)
+        _check(lib().qmc_batch_plan_describe(self.h, buf, 256))
+        return dict(kv.split("=") for kv in buf.value.decode().split())
+
     def tune(self, stream=0) -> int:
         w = ctypes.c_uint64(0)
         _check(lib().qmc_batch_plan_tune(self.h, ctypes.cast(self.b.arr, ctypes.c_void_p), ctypes.c_void_p(stream),
@@ -592,6 +602,28 @@ def qmc_measure_peaks(stream=0) -> dict:
     out = np.zeros(2)
     _check(lib().qmc_measure_peaks(ctypes.c_void_p(stream), _ptr(out)))
     return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1])}
+
+
+def qmc_integrate_cv_to_tolerance(d, ns, gs, m, shifts, t, f: Integrand, cfg: qmc_cv_config, a, rel_tol, stream=0):
+    """The control-variate ladder with its pilot judge.  Returns (qmc_result,
+    level index, mode (1 control variate kept, 0 plain rule), judge dict,
+    reached: bool)."""
+    ns = np.ascontiguousarray(np.asarray(ns, dtype=np.uint64))
+    gs = np.ascontiguousarray(np.asarray(gs, dtype=np.uint64).reshape(len(ns), d))
+    shifts = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    res = qmc_result()
+    lvl, mode = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    judge = np.zeros(4)
+    rc = lib().qmc_integrate_cv_to_tolerance(d, len(ns), _ptr(ns), _ptr(gs), m, _ptr(shifts), t, f.ref,
+                                             ctypes.byref(cfg), _ptr(a), rel_tol, ctypes.byref(res),
+                                             ctypes.byref(lvl), ctypes.byref(mode), _ptr(judge),
+                                             ctypes.c_void_p(stream))
+    if rc not in (QMC_OK, QMC_ETIMEOUT) and rc not in WARNINGS:
+        _check(rc)
+    j = {"rel_err_cv": float(judge[0]), "rel_err_plain": float(judge[1]), "pass_s_cv": float(judge[2]),
+         "pass_s_plain": float(judge[3])}
+    return res, int(lvl.value), int(mode.value), j, rc != QMC_ETIMEOUT
 
 
 def qmc_integrate_to_tolerance(d, ns, gs, m, shifts, t, f: Integrand, rel_tol, stream=0):

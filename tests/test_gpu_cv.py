@@ -161,3 +161,81 @@ def test_cv_estimator_full_size(Q, oracle_lib, nthreads):
     dev_quad = np.max(np.abs((ps[:, 0] - ps[:, 1]) - (ref_cv - ref_plain))) / abs(gint)
     print(f"full size: plain {dev_plain:.2e}, cv {dev_cv:.2e}, surrogate quadrature {dev_quad:.2e}")
     assert dev_plain <= 2e-7 and dev_cv <= 2e-7 and dev_quad <= 5e-8
+
+
+def test_band_limited_fit_holds_high_degrees_at_zero(Q):
+    """cfg.band = 8: the fitted parameters of degrees k >= 8 are exactly zero
+    (bfloat16 zeros), the others are trained, and int g stays the product of
+    the constant terms (the estimator is unchanged)."""
+    d = 3
+    p = _problem(d, 4099, 2, "korobov", seed=41)
+    f = Q.integrand_from_problem(p, "fp32")
+    gp = Q.qmc_make_lattice(d, 4099, I.product_weights(d))
+    cfg = _cfg(Q, steps=200)
+    cfg.band = 8
+    a, losses = Q.qmc_cv_train(d, 4099, gp, I.make_shifts(I.SplitMix64(3), 1, d)[0], Q.transform("none"), f, cfg)
+    a = a.reshape(R, d, K)
+    assert np.all(a[:, :, 8:] == 0.0)
+    assert np.any(a[:, :, 1:8] != 0.0)
+    assert losses[1] < losses[0]
+    cfg.band = K + 1
+    with pytest.raises(Q.QmcError):
+        Q.qmc_cv_train(d, 4099, gp, I.make_shifts(I.SplitMix64(3), 1, d)[0], Q.transform("none"), f, cfg)
+
+
+def _ladder(Q, d, ns, gamma):
+    return np.concatenate([Q.qmc_make_lattice(d, n, gamma) for n in ns])
+
+
+def test_cv_walk_falls_back_to_the_plain_rule(Q):
+    """The control-variate walk judges the surrogate on the first lattice at
+    equal cost.  On the configuration-5 integrand under Korobov 3 a pass of
+    the control-variate estimator costs many plain passes, more than its
+    error gain on the pilot lattice, so the walk keeps the plain rule
+    (mode 0), and from then on it is exactly the plain walk: same stopping
+    level, same estimate as qmc_integrate_to_tolerance on the same ladder."""
+    p = I.config5(n=65521, m=16)
+    d = p.d
+    ns = [65521, 131071, 262139, 524287, 1048573, 2097143]
+    gs = _ladder(Q, d, ns, p.gamma)
+    f = Q.integrand_from_problem(p, "fp32")
+    t = Q.transform("korobov", 3)
+    gp = Q.qmc_make_lattice(d, I.N_PILOT, p.gamma)
+    cfg = _cfg(Q, steps=400)
+    a, _ = Q.qmc_cv_train(d, I.N_PILOT, gp, I.make_shifts(I.SplitMix64(54), 1, d)[0], Q.transform("none"), f, cfg)
+    tol = 1e-7
+    r, lvl, mode, judge, ok = Q.qmc_integrate_cv_to_tolerance(d, ns, gs, p.m, p.shifts, t, f, cfg, a, tol)
+    assert mode == 0, judge
+    assert judge["rel_err_cv"] * judge["pass_s_cv"] >= judge["rel_err_plain"] * judge["pass_s_plain"]
+    r2, lvl2, ok2 = Q.qmc_integrate_to_tolerance(d, ns, gs, p.m, p.shifts, t, f, tol)
+    assert (lvl, ok) == (lvl2, ok2)
+    if lvl > 0:
+        assert r.mean[0] == r2.mean[0] and r.err[0] == r2.err[0]
+    else:
+        assert abs(r.mean[0] - r2.mean[0]) <= 1e-12 * abs(r2.mean[0])
+
+
+def test_cv_walk_keeps_a_winning_surrogate(Q):
+    """Where the surrogate wins at equal cost the walk keeps it (mode 1): a
+    d = 1 sector without a transform, which 32 cosines fit to about 1e-9, so
+    the control variate's error is orders of magnitude below the plain
+    rule's (whose error decays only as 1/n here).  The kept estimate is the
+    control variate's, Q[f - g] + int g, with its own Eq. (3) error."""
+    d = 1
+    U = I.Poly(np.array([0.7, 1.3]), np.array([[0], [1]], dtype=np.uint8))
+    F = I.Poly(np.array([0.4, 1.9]), np.array([[0], [2]], dtype=np.uint8))
+    rng = I.SplitMix64(61)
+    p = I.Problem("d1cv", 1, 65521, 8, I.make_shifts(rng, 8, 1), "none", kind="sector", U=U, F=F, precision="fp32")
+    f = Q.integrand_from_problem(p, "fp32")
+    t = Q.transform("none")
+    ns = [10007, 20011, 40009]
+    gs = np.ones(len(ns), dtype=np.uint64)
+    gp = np.array([1], dtype=np.uint64)
+    cfg = _cfg(Q, steps=2000)
+    a, losses = Q.qmc_cv_train(d, 65537, gp, np.array([0.25]), t, f, cfg)
+    r, lvl, mode, judge, ok = Q.qmc_integrate_cv_to_tolerance(d, ns, gs, p.m, p.shifts, t, f, cfg, a, 1e-30)
+    assert mode == 1, (judge, losses)
+    assert judge["rel_err_cv"] * judge["pass_s_cv"] < judge["rel_err_plain"] * judge["pass_s_plain"]
+    assert not ok and lvl == len(ns) - 1
+    rc, _ = Q.qmc_integrate_cv(d, ns[-1], p.m, gs[-1:], p.shifts, t, f, cfg, a)
+    assert r.mean[0] == rc.mean[0] and r.err[0] == rc.err[0]

@@ -412,6 +412,77 @@ def test_config4_full_size(Q, oracle_lib, nthreads):
         assert abs(g32["mean"][part] - g64["mean"][part]) <= 0.25 * g64["err"][part], part
 
 
+@pytest.mark.slow
+def test_fp32_deformed_unbiased_at_full_size(Q):
+    """Configuration 4 at full size (n = 4194301, m = 20) in FP32 against FP64
+    on the same lattice and shifts.  The FP32 fast variant takes the sector
+    kernels' dithered fixed-point coordinates and compensated weight, and
+    factors the Jacobian as J = I + B with the identity implicit, carrying
+    det J - 1 (rounding each diagonal entry of J near 1 after every small
+    elimination update made the integral 2.0e-8 too large).  What remains is
+    rounding noise: the per-point FP32 - FP64 difference, measured here on
+    2^16 sampled points, has a root mean square s (about 1.7e-6 of |Q|), so a
+    per-shift sum over n points scatters by about s / sqrt(n) and the mean
+    over m shifts by s / sqrt(n m).  Per shift the difference must stay within
+    5 s / sqrt(n) + 1e-10 d, the mean within 5 s / sqrt(n m) + 1e-10 d
+    (about 1.4e-9, against the old 2.0e-8), and the sampled points' mean
+    difference within 5 s / sqrt(2^16) of zero."""
+    p = _c4(n=4194301)
+    g = Q.qmc_make_lattice(p.d, p.n, p.gamma)
+    _, ps64 = gpu_run(Q, p, g, "fp64")
+    _, ps32 = gpu_run(Q, p, g, "fp32")
+    c64, c32 = ps64[:, 0] + 1j * ps64[:, 1], ps32[:, 0] + 1j * ps32[:, 1]
+    q = abs(c64.mean())
+    rng = np.random.default_rng(44)
+    S = 1 << 16
+    js = rng.integers(0, p.n, S).astype(np.uint64)
+    ks = rng.integers(0, p.m, S).astype(np.int32)
+    t = Q.transform("korobov", 3)
+    v32, _, _ = Q.qmc_sample_points(p.d, p.n, p.m, g, p.shifts, t, Q.integrand_from_problem(p, "fp32"), js, ks,
+                                    want_idx=False, want_coord=False)
+    v64, _, _ = Q.qmc_sample_points(p.d, p.n, p.m, g, p.shifts, t, Q.integrand_from_problem(p, "fp64"), js, ks,
+                                    want_idx=False, want_coord=False)
+    dv = (v32[:, 0] - v64[:, 0]) + 1j * (v32[:, 1] - v64[:, 1])
+    s = float(np.sqrt(np.mean(np.abs(dv) ** 2)) / q)
+    rel = np.abs(c32 - c64) / q
+    mean_rel = abs((c32 - c64).mean()) / q
+    print(f"C4 FP32 - FP64: per point rms {s:.2e}; per shift max {rel.max():.2e}; mean {mean_rel:.2e}; "
+          f"sampled mean {abs(dv.mean()) / q:.2e}")
+    assert s < 1e-5
+    assert abs(dv.mean()) / q <= 5 * s / np.sqrt(S)
+    assert mean_rel <= 5 * s / np.sqrt(p.n * p.m) + 1e-10 * p.d
+    assert np.all(rel <= 5 * s / np.sqrt(p.n) + 1e-10 * p.d)
+
+
+def test_fp32_double_coefficients(Q, oracle_lib, nthreads):
+    """FP32EVAL rounds each polynomial coefficient to float (reading R12).
+    With coefficients that float32 cannot hold, the FP32 path integrates a
+    nearby integrand: every coefficient of U and F is positive, so rounding
+    moves U and F by at most 2^-24 relative each and U^-2 F^-1 by at most
+    3 x 2^-24 (1.8e-7).  Per shift the FP32 value stays within that bound plus
+    the FP32 evaluation bound of the other tests (2e-7) of the oracle with the
+    exact coefficients, and within 2e-7 of the oracle with the coefficients
+    rounded to float first, which places the rest of the difference in the
+    coefficients."""
+    import dataclasses
+    p = I.config2(n=100003, m=32)
+    rng = np.random.default_rng(12)
+    U = I.Poly(rng.uniform(0.1, 2.0, p.U.nterms), p.U.expo.copy())
+    F = I.Poly(rng.uniform(0.1, 2.0, p.F.nterms), p.F.expo.copy())
+    assert np.all(U.coef != U.coef.astype(np.float32)) and np.all(F.coef != F.coef.astype(np.float32))
+    p = dataclasses.replace(p, U=U, F=F)
+    pf = dataclasses.replace(p, U=I.Poly(U.coef.astype(np.float32).astype(np.float64), U.expo),
+                             F=I.Poly(F.coef.astype(np.float32).astype(np.float64), F.expo))
+    g = I.random_generating_vector(I.SplitMix64(9), 6, p.n)
+    _, ps = gpu_run(Q, p, g, "fp32")
+    q_exact = oracle_lib.integrate(p, g, nthreads=nthreads)["q"][:, 0]
+    q_round = oracle_lib.integrate(pf, g, nthreads=nthreads)["q"][:, 0]
+    coef_bound = 3 * 2.0 ** -24
+    assert np.all(np.abs(q_round - q_exact) <= coef_bound * np.abs(q_exact))
+    assert np.all(np.abs(ps[:, 0] - q_exact) <= (2e-7 + coef_bound) * np.abs(q_exact))
+    assert np.all(np.abs(ps[:, 0] - q_round) <= 2e-7 * np.abs(q_round))
+
+
 @pytest.mark.parametrize("d", [2, 3, 5])
 def test_deformed_packed_matches_one_shift_kernel(Q, oracle_lib, nthreads, monkeypatch, d):
     """The FP32 deformed kernel that evaluates two shifts per instruction
@@ -551,6 +622,55 @@ def test_persistent_batch_matches_oracle_and_graph(Q, oracle_lib, nthreads):
         assert np.all(np.abs(q[:, 0] - qg[:, 0]) <= 1e-8 * np.abs(qg[:, 0])), p.name
         ref = oracle_lib.integrate(p, g, nthreads=nthreads)
         assert np.all(np.abs(q[:, 0] - ref["q"][:, 0]) <= 4e-7 * np.abs(ref["q"][:, 0])), p.name
+
+
+def test_persistent_specialised_matches_generic(Q, monkeypatch):
+    """The persistent batch's run-time specialised kernel (per descriptor:
+    straight-line code with the lattice, shifts and nonzero coefficients as
+    constants, linked into one module) against the generic persistent kernel
+    (QMC_PERSIST_JIT=0: dense coefficients staged in shared memory) on a mixed
+    batch: d = 1..8; baker, none and Korobov 3; m = 5, 16 and 21 (descriptors
+    of 16 shifts and a ragged 5, padded to an even row count); a non-positive
+    F (the non-finite check).  Every value is computed by the same arithmetic
+    in the same order and every work item writes its fixed slots, so the
+    per-shift results must be bit-identical, and so must the non-finite
+    counts."""
+    sect = I.config3(count=9)
+    trs = [("baker", 0), ("none", 0), ("korobov", 3)]
+    ms = [5, 16, 21]
+    probs = []
+    for s, p in enumerate(sect):
+        p.n = I.prev_prime(20000 + 3000 * s)
+        p.transform, p.alpha = trs[s % 3]
+        probs.append(I.with_shifts(p, ms[s % 3], 1300 + s))
+    d1 = I.Problem("d1", 1, 10007, 4, I.make_shifts(I.SplitMix64(15), 4, 1), "korobov", alpha=3, kind="sector",
+                   U=I.random_poly(I.SplitMix64(16), 1, 1, 0), F=I.random_poly(I.SplitMix64(17), 1, 0, 1),
+                   precision="fp32", gamma=I.product_weights(1))
+    probs.append(d1)
+    neg = I.config3(count=3, seed=I.SEED_BASE + 79)[2]
+    neg.n = I.prev_prime(30000)
+    neg.F.coef[-1] = -0.05
+    probs.append(neg)
+    gs = [I.random_generating_vector(I.SplitMix64(900 + i), p.d, p.n) for i, p in enumerate(probs)]
+    tuples = [_batch_tuple(Q, p, g, "fp32") for p, g in zip(probs, gs)]
+    total_m = sum(p.m for p in probs)
+    spec = Q.BatchPlan(tuples, persistent=True, chunk=2048)
+    desc = spec.describe()
+    assert desc["specialised"] == "1" and desc["shifts_per_descriptor"] == "16", desc
+    assert int(desc["descriptors"]) == sum((p.m + 15) // 16 for p in probs)
+    ps_s = np.zeros(2 * total_m)
+    res_s = [r.as_dict() for r in spec.execute(per_shift=ps_s)]
+    spec.destroy()
+    monkeypatch.setenv("QMC_PERSIST_JIT", "0")
+    gen = Q.BatchPlan(tuples, persistent=True, chunk=2048)
+    assert gen.describe()["specialised"] == "0"
+    ps_g = np.zeros(2 * total_m)
+    res_g = [r.as_dict() for r in gen.execute(per_shift=ps_g)]
+    gen.destroy()
+    assert np.array_equal(ps_s, ps_g)
+    for a, b in zip(res_s, res_g):
+        assert a["mean"][0] == b["mean"][0] and a["nonfinite"] == b["nonfinite"] and a["status"] == b["status"]
+    assert res_s[-1]["nonfinite"] > 0 or res_s[-1]["status"] == 0
 
 
 def test_persistent_batch_tune(Q):
