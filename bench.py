@@ -379,17 +379,17 @@ def extras(qmc, I, torch):
         tp = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream, reps=3)
         plan.destroy()
         r = res["r"]
-        pk = measured_peaks()
-        tf32_peak = pk["bf16_tflops"] * 1.1 / 2.25  # nominal dense TF32 / BF16 ratio
+        mma_peak = out["peaks_measured"]["mma_sync_tf32_tflops"]  # the instruction the estimator issues
         executed = p.d * 2048 * p.n * p.m / t / 1e12
         out[f"c5_cv_estimator_{name}"] = {
             "evals_per_s": p.n * p.m / t, "ms": 1e3 * t, "plain_rule_ms": 1e3 * tp, "cost_vs_plain_rule": t / tp,
             "tf32_mma_tflops": executed,
-            "roofline": {"bound": "tensor", "achieved": executed, "peak": tf32_peak, "unit": "TFLOP/s",
-                         "frac": executed / tf32_peak,
+            "roofline": {"bound": "tensor", "achieved": executed, "peak": mma_peak, "unit": "TFLOP/s",
+                         "frac": executed / mma_peak,
                          "algorithmic_tflops": p.d * 2 * 16 * 31 * p.n * p.m / t / 1e12,
-                         "peak_source": f"bf16 cuBLAS {pk['source']} x 1.1/2.25 (TF32/BF16 nominal dense); "
-                                        "achieved counts both MMAs (basis head and remainder)"},
+                         "peak_source": "measured warp-level TF32 mma.sync m16n8k8 throughput on this GPU "
+                                        "(qmc_measure_peaks); achieved counts both MMAs (basis head and remainder)",
+                         "tcgen05_tf32_reference_tflops": measured_peaks()["bf16_tflops"] * 1.1 / 2.25},
             "err_cv": r.err[0], "err_plain_same_points": r.err[1], "gain_same_points": r.err[1] / r.err[0],
             "note": "one TF32 m16n8k8 MMA (2048 flops) per point and dimension: head and remainder of the basis"}
     # gain of the control variate per surrogate design and transform, from the
@@ -472,8 +472,8 @@ def c3_time_to_tolerance(qmc, I, sh, tol):
                 break
             for i in todo:
                 level[i] += 1
-        res[mode] = {"rel_err": total_err / abs(total), "sum": float(total), "wall_s": wall, "levels": levels,
-                     "evals": int(evals), "reached": total_err <= tol * abs(total),
+        res[mode] = {"rel_err": float(total_err / abs(total)), "sum": float(total), "wall_s": wall, "levels": levels,
+                     "evals": int(evals), "reached": bool(total_err <= tol * abs(total)),
                      "largest_n": int(max(steps[i][level[i]] for i in range(S)))}
     res["batched"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched"]["wall_s"]
     return {"c3_256_sectors_korobov3_sum_batched": res["batched"],
@@ -588,8 +588,10 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
     f = qmc.integrand_from_problem(p, "fp32")
     t = qmc.transform(p.transform, p.alpha)
     pilot_shift = I.make_shifts(I.SplitMix64(54), 1, p.d)[0]
-    ns = np.array(ladder, dtype=np.uint64)
-    gs = np.concatenate([lat[n] for n in ladder])
+    # the ladder up to one level past the plain walk's stopping point
+    stop = ladder.index(out["sector_d8_korobov3_fp32"]["n"]) + 2
+    ns = np.array(ladder[:stop], dtype=np.uint64)
+    gs = np.concatenate([lat[n] for n in ladder[:stop]])
     for band in (0, 8):
         cfg = qmc.qmc_cv_config()
         cfg.R, cfg.K, cfg.freq_step, cfg.steps, cfg.lr, cfg.band, cfg.seed = 16, 32, 1, 2000, 1e-2, band, 7
@@ -603,7 +605,7 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
                                                                      stream=sh)
         wall = time.perf_counter() - t0
         out[f"sector_d8_korobov3_cv_band{band}_judged"] = {
-            "n": int(ladder[lvl]), "rel_err": r.err[0] / abs(r.mean[0]), "mean": r.mean[0], "wall_s": wall,
+            "n": int(ns[lvl]), "rel_err": r.err[0] / abs(r.mean[0]), "mean": r.mean[0], "wall_s": wall,
             "train_s": train_s, "reached": bool(ok), "kept": "control variate" if mode == 1 else "plain rule",
             "pilot": dict(judge, n=int(ladder[0])), "loss": [float(losses[0]), float(losses[1])],
             "plain_ladder_wall_s": out["sector_d8_korobov3_fp32"]["wall_s"],
@@ -770,8 +772,8 @@ def main():
     if not args.no_time_to_tol and rank == 0 and world == 1 and args.n is None:
         from paper_1811_11722_gb300 import inputs as I
         line["time_to_1e-8"] = time_to_tolerance(qmc, I, torch)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    if rank == 0:  # numpy scalars in the extras print as plain numbers
+        print(json.dumps(line, default=lambda o: o.item() if hasattr(o, "item") else str(o)), flush=True)
     plan.destroy()
     if dist:
         dist.destroy_process_group()

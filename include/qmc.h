@@ -185,7 +185,10 @@ int qmc_plan_launches(qmc_plan plan, int32_t* launches_out);
  * sector integrands, with register-pressure variants of the run-time
  * specialised kernel; other plans have one choice) and keeps the fastest.
  * QMC_TUNE_VERBOSE=1 in the environment prints each candidate's time to
- * stderr.
+ * stderr.  QMC_JIT_IMM=1 compiles the specialised kernel of a plan of one
+ * launch chunk with its shift table as immediate operands of the coordinate
+ * adds (one compilation per shift table; bit-identical results; measured
+ * 5% slower on the benchmark's workload, so not a tuning candidate).
  * Reports the choice in *shifts_per_launch_out (may be NULL).  Synchronises
  * the device. */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
@@ -345,25 +348,29 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
 
 /* Automatic choice of n with the control variate as a candidate (the ladder
  * of qmc_integrate_to_tolerance; the estimator of qmc_integrate_cv).  The
- * first lattice is the pilot: one control-variate pass gives Q[f - g] + int g
- * and the plain Q[f] from the same points, each with its Eq. (3) error, and a
- * plain pass on the same lattice times the plain rule alone.  The control
- * variate is kept only if it wins at equal cost,
- *   (err_cv / |Qbar_cv|) * t_cv < (err_plain / |Qbar_plain|) * t_plain,
- * with t the host wall time of each pass (an estimate whose error falls at
- * least as 1/n reaches a target in time proportional to error x time per
- * pass), both passes run once before they are timed so that first-use work
- * (run-time compilation) does not enter the comparison.  Otherwise the walk continues on the plain rule alone (qmc_integrate)
- * from the second lattice on, so the result never costs more than the plain
- * walk plus the pilot.  Stops at the first level whose kept estimate meets
- * err / |Qbar| <= rel_tol.
+ * first min(3, levels) lattices are the pilot: on each, a control-variate
+ * pass gives Q[f - g] + int g with its Eq. (3) error, and a plain pass
+ * (qmc_integrate) the plain rule's.  Each estimator's convergence rate p
+ * (relative error ~ n^-p) is the least-squares slope of log error against
+ * log n over the pilot lattices (1 with a single lattice, clamped to
+ * [1/4, 8]), and its time to reach rel_tol is predicted as its pass time on
+ * the last pilot lattice times (error / rel_tol)^(1/p), the growth of n it
+ * needs.  Both passes run once before they are timed, so first-use work (run-
+ * time compilation) does not enter the comparison.  The estimator with the
+ * smaller predicted time is kept for the rest of the ladder; the plain walk is
+ * then exactly qmc_integrate_to_tolerance's.  A pilot lattice whose plain (or
+ * else control-variate) estimate already meets rel_tol ends the walk there.
+ * Stops at the first level whose kept estimate meets err / |Qbar| <= rel_tol.
  *   levels, n, g  as for qmc_integrate_to_tolerance
  *   cfg, a        the fitted surrogate (qmc_cv_train)
- *   out           host: the kept estimate in part [0] (part [1] zero)
+ *   out           host: the kept estimate in part [0] (part [1] zero for the
+ *                 control variate; the plain result as is)
  *   level_out     the level that produced *out (may be NULL)
  *   mode_out      1 if the control variate was kept, 0 if the plain rule (may be NULL)
- *   judge_out     optional [4] host: pilot relative errors (control variate,
- *                 plain) and pass times in seconds (control variate, plain)
+ *   judge_out     optional [8] host: on the last pilot lattice the relative
+ *                 errors (control variate, plain) and pass times in seconds,
+ *                 then the rates p (control variate, plain) and the predicted
+ *                 times to rel_tol (control variate, plain)
  * Integrands as for qmc_integrate_cv.  Synchronises `stream`.  Returns QMC_OK
  * when the tolerance was met, else QMC_ETIMEOUT with the last level's
  * estimate. */
@@ -479,9 +486,12 @@ int qmc_combine_shifts(int32_t m, const double* per_shift, qmc_result* out);
 #endif
 
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
-/* Measured arithmetic peaks of the current GPU: out[0] FP32 FMA TFLOP/s,
- * out[1] FP64 FMA TFLOP/s (independent dependency chains on a full grid,
- * best of 5, CUDA events on `stream`).
+/* Measured arithmetic peaks of the current GPU, out[4]: out[0] FP32 FMA
+ * TFLOP/s, out[1] FP64 FMA TFLOP/s (independent dependency chains on a full
+ * grid), out[2] warp-level TF32 mma.sync m16n8k8 TFLOP/s and out[3] warp-level
+ * BF16 mma.sync m16n8k16 TFLOP/s (the instructions of the control variate's
+ * estimator and fit; 8 independent accumulators per warp); each the best of
+ * 5, CUDA events on `stream`.
  * A measurement utility beside the rule; synchronises `stream`. */
 int qmc_measure_peaks(void* stream, double* out);
 #endif

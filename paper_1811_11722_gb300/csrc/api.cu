@@ -449,8 +449,24 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
         int occ = 0;
         size_t sm = 0;
         const bool smacc = tune.smacc < 0 ? jit_smacc() : tune.smacc != 0;
+        // shifts as immediate operands: one compiled kernel per shift table, so
+        // only for plans of one launch chunk, and only when the tuner asks
+        std::vector<uint32_t> imm;
+        bool use_imm = tune.imm < 0 ? jit_imm() : tune.imm != 0;
+        if (use_imm && m > mc) {
+          if (tune.imm == 1) return fail(QMC_EUNSUPPORTED, "immediate shifts need one launch chunk (m <= %d)", mc);
+          use_imm = false;
+        }
+        if (use_imm) {
+          imm.resize((size_t)mc * d);
+          for (int kk = 0; kk < mc; ++kk)
+            for (int i = 0; i < d; ++i)
+              imm[(size_t)kk * d + i] =
+                  (uint32_t)((shift_fixed64(shifts[(size_t)(kk < m ? kk : 0) * d + i]) + 0x80000000ull) >> 32);
+        }
         if (jit_sector_f32(d, mc, base.tr, base.tr == TR_KOROBOV ? 3 : 0, base.check_finite != 0, cu, cf, smacc,
-                           tune.minb, &fn, &occ, &sm) == QMC_OK) {
+                           tune.minb, &fn, &occ, &sm, use_imm ? imm.data() : nullptr) == QMC_OK) {
+          pl->imm = use_imm ? 1 : 0;
           jit_fn = fn;
           jit_occ = occ;
           jit_smem = sm;
@@ -740,13 +756,15 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
   const SavedProblem& sp = pl->saved;
   // candidates (shifts per launch, accumulators in shared memory, min CTAs per SM)
   struct Cand {
-    int mc, smacc, minb;
+    int mc, smacc, minb, imm;
   };
   std::vector<Cand> cands;
   if (sp.f.precision == QMC_FP32EVAL && sp.f.kind == QMC_F_SECTOR && sp.eps.orders == 0) {
-    cands = {{8, 0, 0}, {16, 0, 0}, {32, 0, 0}};
-    if (pl->launches.size() && pl->launches[0].cufunc)  // register-pressure variants of the specialised kernel
-      cands.insert(cands.end(), {{16, 0, 2}, {16, 1, 2}, {32, 1, 0}, {32, 1, 2}, {32, 0, 2}});
+    cands = {{8, 0, 0, 0}, {16, 0, 0, 0}, {32, 0, 0, 0}};
+    if (pl->launches.size() && pl->launches[0].cufunc) {
+      // register-pressure variants of the specialised kernel
+      cands.insert(cands.end(), {{16, 0, 2, 0}, {16, 1, 2, 0}, {32, 1, 0, 0}, {32, 1, 2, 0}, {32, 0, 2, 0}});
+    }
   }
   if (cands.empty()) {
     if (shifts_per_launch_out) *shifts_per_launch_out = pl->mc;
@@ -757,7 +775,7 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
   qmc_result* dres = nullptr;
   QMC_CUDA(cudaMalloc(&dres, sizeof(qmc_result)));
   float best = 1e30f;
-  Cand best_c{pl->mc, pl->tune.smacc, pl->tune.minb};
+  Cand best_c{pl->mc, pl->tune.smacc, pl->tune.minb, pl->imm};
   int rc = QMC_OK;
   const char* ve = std::getenv("QMC_TUNE_VERBOSE");  // per-candidate times on stderr
   const bool verbose = ve && ve[0] == '1';
@@ -767,6 +785,7 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
     tc.mc = cd.mc;
     tc.smacc = cd.smacc;
     tc.minb = cd.minb;
+    tc.imm = cd.imm;
     rc = plan_build(&trial, sp.d, sp.n, sp.m, sp.g.data(), sp.shifts.data(), sp.t, &sp.f, tc);
     if (rc == QMC_EUNSUPPORTED) {
       rc = QMC_OK;
@@ -788,9 +807,11 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
     plan_free(&trial, nullptr);
     if (rc) break;
     if (verbose)
-      std::fprintf(stderr, "qmc_plan_tune: shifts_per_launch=%d smem_acc=%d min_ctas=%d ctas=%d specialised=%d: %.4f ms\n",
-                   cd.mc, cd.smacc, cd.minb, trial.nblk, (!trial.launches.empty() && trial.launches[0].cufunc) ? 1 : 0,
-                   tot / 3.0f);
+      std::fprintf(stderr,
+                   "qmc_plan_tune: shifts_per_launch=%d smem_acc=%d min_ctas=%d imm_shifts=%d ctas=%d specialised=%d: "
+                   "%.4f ms\n",
+                   cd.mc, cd.smacc, cd.minb, cd.imm, trial.nblk,
+                   (!trial.launches.empty() && trial.launches[0].cufunc) ? 1 : 0, tot / 3.0f);
     if (tot < best) {
       best = tot;
       best_c = cd;
@@ -800,11 +821,13 @@ int qmc_plan_tune(qmc_plan plan, void* stream, int32_t* shifts_per_launch_out) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;
-  if (best_c.mc != pl->mc || best_c.smacc != pl->tune.smacc || best_c.minb != pl->tune.minb) {
+  if (best_c.mc != pl->mc || best_c.smacc != pl->tune.smacc || best_c.minb != pl->tune.minb ||
+      best_c.imm != pl->imm) {
     TuneChoice tc = pl->tune;
     tc.mc = best_c.mc;
     tc.smacc = best_c.smacc;
     tc.minb = best_c.minb;
+    tc.imm = best_c.imm;
     Plan fresh;
     rc = plan_build(&fresh, sp.d, sp.n, sp.m, sp.g.data(), sp.shifts.data(), sp.t, &sp.f, tc);
     if (rc) return rc;
@@ -947,9 +970,10 @@ int qmc_plan_describe(qmc_plan plan, char* buf, int32_t len) {
   }
   snprintf(buf, (size_t)len,
            "d=%d n=%llu m=%d complex=%d orders=%d shifts_per_launch=%d launches=%zu specialised=%d ctas=%d L=%d "
-           "smem_acc=%d min_ctas=%d",
+           "smem_acc=%d min_ctas=%d imm_shifts=%d",
            pl->d, (unsigned long long)pl->n, pl->m, pl->is_complex, pl->orders, pl->mc, pl->launches.size() + 1,
-           (ln && ln->cufunc) ? 1 : 0, pl->nblk, L, (ln && ln->smem) ? 1 : 0, pl->tune.minb);
+           (ln && ln->cufunc) ? 1 : 0, pl->nblk, L, (ln && ln->smem) ? 1 : 0, pl->tune.minb,
+           (ln && ln->cufunc) ? pl->imm : 0);
   return QMC_OK;
 }
 

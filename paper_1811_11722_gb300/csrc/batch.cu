@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "plan.h"
@@ -527,6 +528,152 @@ static int batch_create(BatchPlan* bp, int32_t count, const qmc_problem* problem
   return batch_graph(bp);
 }
 
+// Results and per-shift values of the last run into the caller's buffers
+// (stream-ordered).
+static int batch_copy_out(BatchPlan* bp, qmc_result* out, double* per_shift, cudaStream_t stream) {
+  const bool out_dev = is_device_pointer(out);
+  const bool ps_dev = per_shift ? is_device_pointer(per_shift) : true;
+  cudaError_t e = cudaMemcpyAsync(out, bp->res_dev, (size_t)bp->count * sizeof(qmc_result),
+                                  out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch results");
+  if (per_shift) {
+    e = cudaMemcpyAsync(per_shift, bp->ps_dev, (size_t)bp->total_m * 2 * sizeof(double),
+                        ps_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch per-shift values");
+  }
+  return QMC_OK;
+}
+
+// ------------------------------------------------------------ one shot --
+//
+// qmc_integrate_batch runs a batch once.  Building and instantiating a CUDA
+// graph, and cudaMalloc / cudaFree (which waits for the whole device), cost
+// more host time than one run needs, and at the sizes of a tolerance walk's
+// later levels more than the batch's device time.  The one-shot path takes
+// its workspace from the stream-ordered pool (cudaMallocAsync and
+// cudaFreeAsync on the caller's stream) and launches every problem's kernels
+// directly, round-robin over kOneShotStreams internal streams forked from the
+// caller's stream by an event and joined back before the final pass, so the
+// sectors still run side by side.
+constexpr int kOneShotStreams = 8;
+constexpr int kOneShotMaxDevices = 64;
+struct OneShotStreams {
+  cudaStream_t s[kOneShotStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kOneShotStreams] = {};
+  bool ok = false;
+};
+static std::mutex g_oneshot_mu;  // guards the streams' events between record and wait
+static OneShotStreams g_oneshot[kOneShotMaxDevices];
+
+static int oneshot_streams(OneShotStreams** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kOneShotMaxDevices) return fail(QMC_EUNSUPPORTED, "device index %d too large", dev);
+  OneShotStreams& S = g_oneshot[dev];
+  if (!S.ok) {
+    e = cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming);
+    for (int k = 0; k < kOneShotStreams && e == cudaSuccess; ++k) {
+      e = cudaStreamCreateWithFlags(&S.s[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch streams");
+    S.ok = true;
+  }
+  *out = &S;
+  return QMC_OK;
+}
+
+static int oneshot_run(BatchPlan* bp, cudaStream_t stream) {
+  size_t bytes = 0;
+  std::vector<size_t> part_off(bp->count), cnt_off(bp->count);
+  for (int i = 0; i < bp->count; ++i) {
+    part_off[i] = bytes;
+    bytes += (size_t)bp->probs[i]->m * bp->probs[i]->nblk * 2 * sizeof(double);
+  }
+  for (int i = 0; i < bp->count; ++i) {
+    cnt_off[i] = bytes;
+    bytes += 2 * sizeof(unsigned long long);
+  }
+  const size_t cnt_bytes = bytes - cnt_off[0];
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t res_off = bytes;
+  bytes += (size_t)bp->count * sizeof(qmc_result);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t ps_off = bytes;
+  bytes += (size_t)bp->total_m * 2 * sizeof(double);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t fin_off = bytes;
+  bytes += (size_t)bp->count * sizeof(FinalizeArgs);
+  cudaError_t e = cudaMallocAsync(&bp->ws, bytes, stream);
+  if (e != cudaSuccess) {
+    bp->ws = nullptr;
+    cudaGetLastError();
+    return fail(QMC_ENOMEM, "batch workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  char* base = (char*)bp->ws;
+  bp->res_dev = (qmc_result*)(base + res_off);
+  bp->ps_dev = (double*)(base + ps_off);
+  bp->fin_dev = (FinalizeArgs*)(base + fin_off);
+  bp->fin_host.resize(bp->count);
+  for (int i = 0; i < bp->count; ++i) {
+    Plan* pl = bp->probs[i].get();
+    pl->ws.partial = (double*)(base + part_off[i]);
+    pl->ws.counters = (unsigned long long*)(base + cnt_off[i]);
+    FinalizeArgs& A = bp->fin_host[i];
+    std::memset(&A, 0, sizeof(A));
+    A.partial = pl->ws.partial;
+    A.nblk = pl->nblk;
+    A.m = pl->m;
+    A.is_complex = pl->is_complex;
+    A.dn = (double)pl->n;
+    A.value_scale = pl->final_scale;
+    A.offset[0] = pl->offset[0];
+    A.offset[1] = pl->offset[1];
+    A.counters = pl->ws.counters;
+    A.result = bp->res_dev + i;
+    A.per_shift = bp->ps_dev + bp->ps_off[i];
+  }
+  e = cudaMemcpyAsync(bp->fin_dev, bp->fin_host.data(), (size_t)bp->count * sizeof(FinalizeArgs),
+                      cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + cnt_off[0], 0, cnt_bytes, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch descriptors");
+  OneShotStreams* S = nullptr;
+  int rc = oneshot_streams(&S);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_oneshot_mu);
+    e = cudaEventRecord(S->fork, stream);
+    for (int k = 0; k < kOneShotStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(S->s[k], S->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+    SampleIO none;
+    std::memset(&none, 0, sizeof(none));
+    for (int i = 0; i < bp->count && rc == QMC_OK; ++i) {
+      Plan* pl = bp->probs[i].get();
+      for (Launch& ln : pl->launches) {
+        double* partial = pl->ws.partial;
+        unsigned long long* counters = pl->ws.counters;
+        void* args[4] = {(void*)ln.params.data(), &partial, &counters, &none};
+        rc = launch_any(ln, ln.grid, args, S->s[i % kOneShotStreams]);
+        if (rc) break;
+      }
+    }
+    // join every internal stream back, even after a failed launch
+    for (int k = 0; k < kOneShotStreams; ++k) {
+      cudaEventRecord(S->join[k], S->s[k]);
+      cudaStreamWaitEvent(stream, S->join[k], 0);
+    }
+  }
+  if (rc) return rc;
+  FinalizeArgs* fin = bp->fin_dev;
+  void* fargs[1] = {&fin};
+  e = cudaLaunchKernel(finalize_batch_ptr(), dim3(bp->count), dim3(256), fargs, (size_t)bp->max_m * 2 * sizeof(double),
+                       stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch final pass");
+  return QMC_OK;
+}
+
 static int batch_execute(BatchPlan* bp, qmc_result* out, double* per_shift, cudaStream_t stream) {
   if (!out) return fail(QMC_EINVAL, "null result pointer");
   cudaError_t e = cudaGraphLaunch(bp->exec, stream);
@@ -678,11 +825,21 @@ int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* 
 
 int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* out, double* per_shift,
                         void* stream) {
+  if (!out) return fail(QMC_EINVAL, "null result pointer");
+  cudaStream_t st = (cudaStream_t)stream;
   BatchPlan bp;
-  int rc = batch_create(&bp, count, problems, 1ull << 20);
-  if (rc == QMC_OK) rc = batch_execute(&bp, out, per_shift, (cudaStream_t)stream);
-  cudaStreamSynchronize((cudaStream_t)stream);
-  batch_release(&bp);
+  int rc = batch_build(&bp, count, problems, 1ull << 20);
+  if (rc == QMC_OK) rc = oneshot_run(&bp, st);
+  if (rc == QMC_OK) rc = batch_copy_out(&bp, out, per_shift, st);
+  if (bp.ws) {
+    cudaFreeAsync(bp.ws, st);
+    bp.ws = nullptr;
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc == QMC_OK && e != cudaSuccess) rc = cuda_fail(e, "batch synchronise");
+  if (rc == QMC_OK && !is_device_pointer(out))
+    for (int i = 0; i < bp.count; ++i)
+      if (out[i].status != QMC_OK) return out[i].status;
   return rc;
 }
 

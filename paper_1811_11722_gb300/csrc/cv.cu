@@ -18,17 +18,18 @@
 // Training kernels.  The two contractions of the fit run on tensor cores
 // (warp-level BF16 MMA, FP32 accumulation); the loss is summed in FP64:
 //   cv_basis     B[i][j][k] = cos(F pi k x_ji) for the pilot points, rounded to
-//                BF16, in two layouts: Bf[i][j][k] (forward) and Bt[i][k][j]
-//                (backward); padding points j >= P are zero rows
-//   cv_forward   C_ri(x_j) = sum_k B a, g_j, e_j = 2 (g_j - h_j)/P and the factor
-//                D[i][j][r] = e_j prod_{i'!=i} C_ri' (BF16, as DgT[i][r][j])
-//   cv_backward  grad_part[c][i][r][k] = sum_{j in chunk c} D[i][j][r] B[i][j][k]
+//                BF16, Bf[i][j][k], once per fit; padding points j >= P are zero rows
+//   cv_fit       per tile of 16 points: C_ri(x_j) = sum_k B a, g_j,
+//                e_j = 2 (g_j - h_j)/P, the factor D[i][j][r] = e_j prod_{i'!=i} C_ri'
+//                and grad_part[c][i][r][k] += sum_j D[i][j][r] B[i][j][k], all in
+//                registers (cv_device.cuh), one partial gradient per CTA c
 //   cv_adam      grad = sum_c grad_part (fixed order), Adam step, cosine-decayed rate
 // Each contraction is, per dimension, (points x 32) (32 x 16) forward and
 // (16 x points) (points x 32) backward: 16 or 32 output columns.  The
 // warp-level MMA keeps a point's 16 values C_ri in the registers of the lanes
-// that multiply them across dimensions and differentiate the product, so
-// nothing between the contraction and the loss goes through memory.
+// that multiply them across dimensions and differentiate the product, and the
+// backward's operands are those registers transposed, so one step reads the
+// basis once and nothing else between the contractions goes through memory.
 //
 // Estimator kernel (cv_tc_kernel, cv_device.cuh).  The lattice rule with g
 // subtracted evaluates the surrogate's per-dimension contraction on tensor
@@ -57,82 +58,44 @@ __global__ void cv_iota_kernel(uint64_t* j, int P) {
 }
 
 __global__ void cv_basis_kernel(const double* __restrict__ x, int P, int Ppad, int d, float freq,
-                                uint16_t* __restrict__ Bf, uint16_t* __restrict__ Bt) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (i, j), j fastest: Bt stores coalesce
+                                uint16_t* __restrict__ Bf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (i, j)
   if (t >= Ppad * d) return;
   const int i = t / Ppad, j = t % Ppad;
   const double xv = j < P ? x[(size_t)j * d + i] : 0.0;
   uint16_t* out = Bf + ((size_t)i * Ppad + j) * kCvK;
 #pragma unroll 4
-  for (int k = 0; k < kCvK; ++k) {
-    const uint16_t b = j < P ? bf16_bits((float)cospi((double)freq * (double)k * xv)) : (uint16_t)0;
-    out[k] = b;
-    Bt[((size_t)i * kCvK + k) * Ppad + j] = b;
-  }
+  for (int k = 0; k < kCvK; ++k)
+    out[k] = j < P ? bf16_bits((float)cospi((double)freq * (double)k * xv)) : (uint16_t)0;
 }
 
-// Backward pass on tensor cores: grid (chunks, d), 4 warps per CTA, warp w
-// taking a quarter of the chunk's points in steps of 16.  Per step, A is the
-// factor DgT[i][r][j] (16 r x 16 points) and B the basis Bt[i][k][j]
-// (16 points x 32 k, four k-tiles); the 16 x 32 gradient block of dimension i
-// accumulates in FP32 registers, and the four warps' blocks are added in a
-// fixed order through shared memory.
-__global__ void __launch_bounds__(128)
-    cv_backward_kernel(const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ DgT, int Ppad, int d,
-                       float* __restrict__ grad_part) {
-  __shared__ float blk[4][kCvR][kCvK];
-  const int c = blockIdx.x, i = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int quarter = kCvChunk / 4;
-  const int jb = c * kCvChunk + warp * quarter, je = min(Ppad, jb + quarter);
-  float acc[4][4];
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[nt][v] = 0.0f;
-  const uint16_t* dA = DgT + ((size_t)i * kCvR + g) * Ppad;
-  const uint16_t* dB = dA + 8 * (size_t)Ppad;
-  for (int j0 = jb; j0 < je; j0 += 16) {
-    const int j = j0 + 2 * t;
-    const uint32_t a0 = *reinterpret_cast<const uint32_t*>(dA + j);
-    const uint32_t a1 = *reinterpret_cast<const uint32_t*>(dB + j);
-    const uint32_t a2 = *reinterpret_cast<const uint32_t*>(dA + j + 8);
-    const uint32_t a3 = *reinterpret_cast<const uint32_t*>(dB + j + 8);
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const uint16_t* bp = Bt + ((size_t)i * kCvK + 8 * nt + g) * Ppad + j;
-      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bp);
-      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bp + 8);
-      mma_bf16_16x8x16(acc[nt], a0, a1, a2, a3, b0, b1);
-    }
-  }
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    blk[warp][g][8 * nt + 2 * t] = acc[nt][0];
-    blk[warp][g][8 * nt + 2 * t + 1] = acc[nt][1];
-    blk[warp][g + 8][8 * nt + 2 * t] = acc[nt][2];
-    blk[warp][g + 8][8 * nt + 2 * t + 1] = acc[nt][3];
-  }
+// Adam step.  A CTA takes 32 parameters: warp w adds the CTAs' partial
+// gradients c = w, w + 8, ... in FP64 (coalesced rows of 32), the eight warp
+// sums are added in warp order, and warp 0 applies the update.  The order of
+// every addition is fixed, so the fit is reproducible.
+constexpr int kAdamWarps = 8;
+__global__ void __launch_bounds__(kAdamWarps * 32)
+    cv_adam_kernel(const float* __restrict__ grad_part, int nchunk, int npar, float* __restrict__ a,
+                   float* __restrict__ m1, float* __restrict__ m2, int step, float lr, int band) {
+  __shared__ double part[kAdamWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x * 32 + lane;
+  double g = 0.0;
+  if (q < npar)
+#pragma unroll 4
+    for (int c = warp; c < nchunk; c += kAdamWarps) g += (double)grad_part[(size_t)c * npar + q];
+  part[warp][lane] = g;
   __syncthreads();
-  float* out = grad_part + (size_t)c * (kCvR * d * kCvK);
-  for (int q = threadIdx.x; q < kCvR * kCvK; q += blockDim.x) {
-    const int r = q / kCvK, k = q % kCvK;
-    out[(r * d + i) * kCvK + k] = ((blk[0][r][k] + blk[1][r][k]) + blk[2][r][k]) + blk[3][r][k];
-  }
-}
-
-__global__ void cv_adam_kernel(const float* __restrict__ grad_part, int nchunk, int npar, float* __restrict__ a,
-                               float* __restrict__ m1, float* __restrict__ m2, int step, float lr, int band) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= npar) return;
+  if (warp != 0 || q >= npar) return;
   if (band > 0 && q % kCvK >= band) {  // a band-limited fit holds the higher degrees at zero
     a[q] = 0.0f;
     return;
   }
-  double g = 0.0;
-  for (int c = 0; c < nchunk; ++c) g += (double)grad_part[(size_t)c * npar + q];
+  double tot = 0.0;
+#pragma unroll
+  for (int w = 0; w < kAdamWarps; ++w) tot += part[w][lane];
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float gf = (float)g;
+  const float gf = (float)tot;
   const float mm = b1 * m1[q] + (1.0f - b1) * gf;
   const float vv = b2 * m2[q] + (1.0f - b2) * gf * gf;
   m1[q] = mm;
@@ -142,23 +105,32 @@ __global__ void cv_adam_kernel(const float* __restrict__ grad_part, int nchunk, 
   a[q] -= lr * mh / (sqrtf(vh) + eps);
 }
 
-static const void* cv_forward_for(int d) {
+static const void* cv_fit_for(int d) {
   switch (d) {
-    case 1: return cv_forward_ptr<1>();
-    case 2: return cv_forward_ptr<2>();
-    case 3: return cv_forward_ptr<3>();
-    case 4: return cv_forward_ptr<4>();
-    case 5: return cv_forward_ptr<5>();
-    case 6: return cv_forward_ptr<6>();
-    case 7: return cv_forward_ptr<7>();
-    default: return cv_forward_ptr<8>();
+    case 1: return cv_fit_ptr<1>();
+    case 2: return cv_fit_ptr<2>();
+    case 3: return cv_fit_ptr<3>();
+    case 4: return cv_fit_ptr<4>();
+    case 5: return cv_fit_ptr<5>();
+    case 6: return cv_fit_ptr<6>();
+    case 7: return cv_fit_ptr<7>();
+    default: return cv_fit_ptr<8>();
   }
 }
 
-static void cv_forward(int d, int P, int Ppad, const uint16_t* Bf, const double* hv, const float* a, uint16_t* DgT,
-                       double* lp, cudaStream_t st) {
-  void* args[7] = {(void*)&Bf, (void*)&hv, (void*)&a, (void*)&P, (void*)&Ppad, (void*)&DgT, (void*)&lp};
-  cudaLaunchKernel(cv_forward_for(d), dim3(Ppad / kCvTile), dim3(128), args, 0, st);
+// CTAs of the fused fit step: two per SM, at most one per batch of
+// kCvFitWarps tiles of 16 points.
+static int cv_fit_grid(int Ppad) {
+  const int sms = device_sms();
+  const int batches = (Ppad / 16 + kCvFitWarps - 1) / kCvFitWarps;
+  return std::max(1, std::min(batches, 2 * std::max(sms, 1)));
+}
+
+// Loss partials into lp[0 .. nchunk) and gradient partials into grad_part[nchunk][npar].
+static void cv_fit_step(int d, int P, int Ppad, int nchunk, const uint16_t* Bf, const double* hv, const float* a,
+                        float* grad_part, double* lp, cudaStream_t st) {
+  void* args[7] = {(void*)&Bf, (void*)&hv, (void*)&a, (void*)&P, (void*)&Ppad, (void*)&grad_part, (void*)&lp};
+  cudaLaunchKernel(cv_fit_for(d), dim3(nchunk), dim3(kCvFitWarps * 32), args, 0, st);
 }
 
 static float bf16_round(float v) {
@@ -177,8 +149,6 @@ struct CvFit {
   double* x = nullptr;       // [P][d]
   double* hv = nullptr;      // [P][2] (value, 0)
   uint16_t* Bf = nullptr;    // [d][Ppad][K] BF16
-  uint16_t* Bt = nullptr;    // [d][K][Ppad] BF16
-  uint16_t* DgT = nullptr;   // [d][R][Ppad] BF16
   float* a = nullptr;
   float* m1 = nullptr;
   float* m2 = nullptr;
@@ -192,12 +162,11 @@ struct CvFit {
     d = d_;
     P = P_;
     Ppad = (P + kCvTile - 1) / kCvTile * kCvTile;
-    nchunk = (Ppad + kCvChunk - 1) / kCvChunk;
+    nchunk = cv_fit_grid(Ppad);
     npar = kCvR * d * kCvK;
-    const int nlp = Ppad / kCvTile;
-    size_t sz[] = {(size_t)P * d * 8,      (size_t)P * 2 * 8, (size_t)d * Ppad * kCvK * 2, (size_t)d * kCvK * Ppad * 2,
-                   (size_t)d * kCvR * Ppad * 2, (size_t)npar * 4, (size_t)npar * 4,      (size_t)npar * 4,
-                   (size_t)nchunk * npar * 4, (size_t)nlp * 8};
+    size_t sz[] = {(size_t)P * d * 8,  (size_t)P * 2 * 8,         (size_t)d * Ppad * kCvK * 2,
+                   (size_t)npar * 4,   (size_t)npar * 4,          (size_t)npar * 4,
+                   (size_t)nchunk * npar * 4, (size_t)nchunk * 8};
     size_t total = 0;
     for (size_t s : sz) total += (s + 255) & ~(size_t)255;
     if (cudaMalloc(&block, total) != cudaSuccess) {
@@ -205,9 +174,9 @@ struct CvFit {
       return fail(QMC_ENOMEM, "control-variate fit buffers (%zu bytes)", total);
     }
     char* p = (char*)block;
-    void** dst[] = {(void**)&x,  (void**)&hv, (void**)&Bf, (void**)&Bt,        (void**)&DgT,
-                    (void**)&a,  (void**)&m1, (void**)&m2, (void**)&grad_part, (void**)&loss_part};
-    for (int q = 0; q < 10; ++q) {
+    void** dst[] = {(void**)&x, (void**)&hv, (void**)&Bf, (void**)&a, (void**)&m1, (void**)&m2,
+                    (void**)&grad_part, (void**)&loss_part};
+    for (int q = 0; q < 8; ++q) {
       *dst[q] = p;
       p += (sz[q] + 255) & ~(size_t)255;
     }
@@ -216,7 +185,7 @@ struct CvFit {
 };
 
 static double cv_loss_host(const CvFit& F, cudaStream_t st) {
-  const int nlp = F.Ppad / kCvTile;
+  const int nlp = F.nchunk;
   std::vector<double> lp(nlp);
   cudaMemcpyAsync(lp.data(), F.loss_part, nlp * 8, cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -255,9 +224,8 @@ int qmc_cv_loss_grad(int32_t d, const qmc_cv_config* cfg, int32_t P, const doubl
   cudaMemcpyAsync(F.x, x, (size_t)P * d * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(F.hv, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(F.a, a, (size_t)F.npar * 4, cudaMemcpyHostToDevice, st);
-  cv_basis_kernel<<<(F.Ppad * d + 255) / 256, 256, 0, st>>>(F.x, P, F.Ppad, d, (float)cfg->freq_step, F.Bf, F.Bt);
-  cv_forward(d, P, F.Ppad, F.Bf, F.hv, F.a, F.DgT, F.loss_part, st);
-  cv_backward_kernel<<<dim3(F.nchunk, d), 128, 0, st>>>(F.Bt, F.DgT, F.Ppad, d, F.grad_part);
+  cv_basis_kernel<<<(F.Ppad * d + 255) / 256, 256, 0, st>>>(F.x, P, F.Ppad, d, (float)cfg->freq_step, F.Bf);
+  cv_fit_step(d, P, F.Ppad, F.nchunk, F.Bf, F.hv, F.a, F.grad_part, F.loss_part, st);
   std::vector<float> gp((size_t)F.nchunk * F.npar);
   cudaMemcpyAsync(gp.data(), F.grad_part, gp.size() * 4, cudaMemcpyDeviceToHost, st);
   *loss_out = cv_loss_host(F, st);
@@ -321,7 +289,7 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
     cudaError_t e = cudaLaunchKernel(ln.func, dim3((P + 255) / 256), dim3(kThreads), args, 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "pilot evaluation");
   }
-  cv_basis_kernel<<<(F.Ppad * d + 255) / 256, 256, 0, st>>>(F.x, P, F.Ppad, d, (float)cfg->freq_step, F.Bf, F.Bt);
+  cv_basis_kernel<<<(F.Ppad * d + 255) / 256, 256, 0, st>>>(F.x, P, F.Ppad, d, (float)cfg->freq_step, F.Bf);
   // pilot mean for the initial constant terms
   std::vector<double> hv(2 * (size_t)P);
   cudaMemcpyAsync(hv.data(), F.hv, hv.size() * 8, cudaMemcpyDeviceToHost, st);
@@ -357,14 +325,13 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
   cudaMemsetAsync(F.m2, 0, (size_t)F.npar * 4, st);
   double first = 0.0, last = 0.0;
   for (int step = 1; step <= cfg->steps; ++step) {
-    cv_forward(d, P, F.Ppad, F.Bf, F.hv, F.a, F.DgT, F.loss_part, st);
+    cv_fit_step(d, P, F.Ppad, F.nchunk, F.Bf, F.hv, F.a, F.grad_part, F.loss_part, st);
     if (step == 1) first = cv_loss_host(F, st);
-    cv_backward_kernel<<<dim3(F.nchunk, d), 128, 0, st>>>(F.Bt, F.DgT, F.Ppad, d, F.grad_part);
     const float lr = (float)(0.5 * cfg->lr * (1.0 + std::cos(M_PI * (double)(step - 1) / (double)cfg->steps)));
-    cv_adam_kernel<<<(F.npar + 255) / 256, 256, 0, st>>>(F.grad_part, F.nchunk, F.npar, F.a, F.m1, F.m2, step, lr,
-                                                         cfg->band);
+    cv_adam_kernel<<<(F.npar + 31) / 32, kAdamWarps * 32, 0, st>>>(F.grad_part, F.nchunk, F.npar, F.a, F.m1, F.m2,
+                                                                  step, lr, cfg->band);
   }
-  cv_forward(d, P, F.Ppad, F.Bf, F.hv, F.a, F.DgT, F.loss_part, st);
+  cv_fit_step(d, P, F.Ppad, F.nchunk, F.Bf, F.hv, F.a, F.grad_part, F.loss_part, st);
   last = cv_loss_host(F, st);
   std::vector<float> af(F.npar);
   cudaMemcpyAsync(af.data(), F.a, (size_t)F.npar * 4, cudaMemcpyDeviceToHost, st);
@@ -469,8 +436,8 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
   return rc;
 }
 
-// Automatic choice of n with the control variate as a candidate, judged once
-// on the first lattice by the plain rule's Eq. (3) error from the same points.
+// Automatic choice of n with the control variate as a candidate, judged on
+// the first lattices (the pilot) by predicted time to the tolerance.
 int qmc_integrate_cv_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, const uint64_t* g, int32_t m,
                                   const double* shifts, qmc_transform t, const qmc_integrand* f,
                                   const qmc_cv_config* cfg, const float* a, double rel_tol, qmc_result* out,
@@ -483,34 +450,6 @@ int qmc_integrate_cv_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, 
     const double mag = std::fabs(r.mean[part]);
     return mag > 0.0 ? r.err[part] / mag : HUGE_VAL;
   };
-  // level 0: the control-variate pass (Q[f - g] + int g in part 0, the plain
-  // Q[f] from the same points in part 1) and a plain pass, each run once to
-  // take first-use work (run-time compilation, module loading) out of the
-  // comparison, then timed
-  qmc_result rc_cv, rc_plain;
-  int rc = QMC_OK;
-  double t_cv = 0.0, t_plain = 0.0;
-  for (int rep = 0; rep < 2; ++rep) {
-    auto t0 = clock::now();
-    rc = qmc_integrate_cv(d, n[0], m, g, shifts, t, f, cfg, a, &rc_cv, nullptr, stream);
-    if (rc != QMC_OK && rc != QMC_ENONFINITE) return rc;
-    auto t1 = clock::now();
-    rc = qmc_integrate(d, n[0], m, g, shifts, t, f, &rc_plain, nullptr, stream);
-    if (rc != QMC_OK && rc != QMC_ENONFINITE) return rc;
-    auto t2 = clock::now();
-    t_cv = std::chrono::duration<double>(t1 - t0).count();
-    t_plain = std::chrono::duration<double>(t2 - t1).count();
-  }
-  const double e_cv = rel(rc_cv, 0), e_plain = rel(rc_cv, 1);
-  // equal-cost comparison: an estimate whose error falls at least as 1/n
-  // reaches a given error in time proportional to (error x time per pass)
-  const bool keep_cv = e_cv * t_cv < e_plain * t_plain;
-  if (judge_out) {
-    judge_out[0] = e_cv;
-    judge_out[1] = e_plain;
-    judge_out[2] = t_cv;
-    judge_out[3] = t_plain;
-  }
   auto take_cv = [&](const qmc_result& r) {
     std::memset(out, 0, sizeof(*out));
     out->mean[0] = r.mean[0];
@@ -519,16 +458,77 @@ int qmc_integrate_cv_to_tolerance(int32_t d, int32_t levels, const uint64_t* n, 
     out->nonfinite = r.nonfinite;
     out->status = r.status;
   };
-  if (level_out) *level_out = 0;
-  if (mode_out) *mode_out = keep_cv ? 1 : 0;
-  if (keep_cv) {
-    take_cv(rc_cv);
-    if (e_cv <= rel_tol) return out->status;
-  } else {
-    *out = rc_plain;
-    if (rel(rc_plain, 0) <= rel_tol) return out->status;
+  // pilot: on each of the first lattices a control-variate pass (Q[f - g] + int g
+  // in part 0) and a plain pass (qmc_integrate, so the plain walk is exactly
+  // qmc_integrate_to_tolerance's), both run once more at the first lattice so
+  // that first-use work (run-time compilation, module loading) stays out of the
+  // times; the passes on the last pilot lattice are timed
+  const int pilot = std::min(levels, 3);
+  std::vector<double> lr(pilot), ecv(pilot), epl(pilot);
+  double t_cv = 0.0, t_plain = 0.0;
+  int rc = QMC_OK;
+  for (int l = 0; l < pilot; ++l) {
+    const uint64_t* gl = g + (size_t)l * d;
+    qmc_result rcv, rpl;
+    for (int rep = 0; rep < (l == 0 ? 2 : 1); ++rep) {
+      auto t0 = clock::now();
+      rc = qmc_integrate_cv(d, n[l], m, gl, shifts, t, f, cfg, a, &rcv, nullptr, stream);
+      if (rc != QMC_OK && rc != QMC_ENONFINITE) return rc;
+      auto t1 = clock::now();
+      rc = qmc_integrate(d, n[l], m, gl, shifts, t, f, &rpl, nullptr, stream);
+      if (rc != QMC_OK && rc != QMC_ENONFINITE) return rc;
+      auto t2 = clock::now();
+      t_cv = std::chrono::duration<double>(t1 - t0).count();
+      t_plain = std::chrono::duration<double>(t2 - t1).count();
+    }
+    lr[l] = std::log((double)n[l]);
+    ecv[l] = rel(rcv, 0);
+    epl[l] = rel(rpl, 0);
+    if (level_out) *level_out = l;
+    if (epl[l] <= rel_tol) {
+      *out = rpl;
+      if (mode_out) *mode_out = 0;
+      return out->status;
+    }
+    if (ecv[l] <= rel_tol) {
+      take_cv(rcv);
+      if (mode_out) *mode_out = 1;
+      return out->status;
+    }
+    if (l == pilot - 1) *out = rpl;
   }
-  for (int l = 1; l < levels; ++l) {
+  // convergence rate p of each estimate, err ~ n^-p: least-squares slope of
+  // log err against log n over the pilot (p = 1 with a single lattice),
+  // clamped to [1/4, 8]; predicted time to rel_tol = time per pass on the last
+  // pilot lattice x the growth of n it needs, (err / rel_tol)^(1/p)
+  auto rate = [&](const std::vector<double>& e) {
+    if (pilot < 2) return 1.0;
+    double mx = 0.0, my = 0.0;
+    for (int l = 0; l < pilot; ++l) {
+      mx += lr[l];
+      my += std::log(e[l]);
+    }
+    mx /= pilot;
+    my /= pilot;
+    double sxy = 0.0, sxx = 0.0;
+    for (int l = 0; l < pilot; ++l) {
+      sxy += (lr[l] - mx) * (std::log(e[l]) - my);
+      sxx += (lr[l] - mx) * (lr[l] - mx);
+    }
+    const double p = sxx > 0.0 ? -sxy / sxx : 1.0;
+    return std::min(8.0, std::max(0.25, std::isfinite(p) ? p : 1.0));
+  };
+  const double p_cv = rate(ecv), p_plain = rate(epl);
+  const int lp = pilot - 1;
+  const double T_cv = t_cv * std::pow(std::max(1.0, ecv[lp] / rel_tol), 1.0 / p_cv);
+  const double T_plain = t_plain * std::pow(std::max(1.0, epl[lp] / rel_tol), 1.0 / p_plain);
+  const bool keep_cv = T_cv < T_plain;
+  if (judge_out) {
+    const double j[8] = {ecv[lp], epl[lp], t_cv, t_plain, p_cv, p_plain, T_cv, T_plain};
+    std::memcpy(judge_out, j, sizeof(j));
+  }
+  if (mode_out) *mode_out = keep_cv ? 1 : 0;
+  for (int l = pilot; l < levels; ++l) {
     const uint64_t* gl = g + (size_t)l * d;
     if (level_out) *level_out = l;
     if (keep_cv) {

@@ -10,8 +10,7 @@ constexpr int kCvR = 16;
 constexpr int kCvK = 32;
 constexpr int kCvDMax = 8;
 constexpr int kCvMc = 8;            // shifts per estimator launch
-constexpr int kCvChunk = 2048;      // pilot points per backward CTA
-constexpr int kCvTile = 64;         // pilot points per forward CTA (4 warps x 16); the pilot is padded to it
+constexpr int kCvTile = 64;         // the pilot is padded to a multiple of 64 points (4 warps x 16)
 
 // Warp-level tensor-core product D = A B + C, A 16x16 (row), B 16x8 (col),
 // BF16 operands packed two per 32-bit register, FP32 accumulation.  Lane l
@@ -302,107 +301,195 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-// Forward pass of the fit on tensor cores.  Warp w of the CTA takes pilot
-// points j0 .. j0 + 15.  Per dimension i, C_i = Bf_i a_i^T, with the basis
-// Bf[i][j][k] (BF16, k contiguous) as A (16 points x 32 k, two k-steps) and
-// the parameters a[r][i][k] (BF16, from shared memory) as B (32 k x 16 r,
-// two r-tiles).  A lane holds the same (point, r) positions of C for every
-// dimension, so the product over dimensions, g = sum_r prod_i C_ri, the loss
-// and the gradient factor 2 e prod_{i' != i} C_ri' / P all stay in its
-// registers; only the sum over r needs the other three lanes of its group.
-// The factor goes out as BF16 in the layout the backward pass reads,
-// DgT[i][r][j] (j contiguous).  Rows j >= P (padding) carry zero basis rows,
-// add nothing to the loss and get a zero factor.
+// One step of the fit (loss and gradient of the mean squared error) in one
+// pass over the pilot points, on tensor cores.  A CTA of kCvFitWarps warps
+// takes batches of kCvFitWarps tiles of 16 pilot points (grid-stride over the
+// batches).
+//
+// Forward (warp w on tile w of the batch): per dimension i, C_i = B_i a_i^T
+// with the basis tile B_i (16 points x 32 degrees, BF16, Bf[i][j][k]) as A of
+// m16n8k16 (two k-steps) and the parameters a[r][i][k] (BF16, shared memory)
+// as B (two r-tiles).  A lane holds the same (point, rank) positions of C for
+// every dimension, so g = sum_r prod_i C_ri, the error e = 2 (g - h) / P and
+// the gradient factor D_i = e prod_{i' != i} C_ri' stay in its registers;
+// only the sum over r needs the other three lanes of its group.  The factor
+// goes to shared memory as BF16, transposed to D_i^T[r][j] by movmatrix
+// (8 x 8 BF16 blocks of the accumulator layout).
+//
+// Backward (warp w on dimension w, for every tile of the batch):
+// grad_w[r][k] += sum_j D_w[j][r] B_w[j][k], four m16n8k16 per tile
+// (k-tiles of 8) with A = D_w^T from shared memory and B = the basis tile's
+// forward fragments transposed by movmatrix (no transposed basis in memory).
+// The gradient of a dimension accumulates in one warp's FP32 registers over
+// the CTA's batches, and each CTA writes its partial gradient, which
+// cv_adam_kernel sums in FP64 in CTA order.  Rows j >= P (padding) have zero
+// basis rows and a zero error, so they add nothing to the loss or gradient.
+constexpr int kCvFitWarps = 8;
+
+__device__ __forceinline__ uint32_t movtrans(uint32_t x) {
+  uint32_t y;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(y) : "r"(x));
+  return y;
+}
+
+// two BF16 values in one register, the first in the low half (the lower
+// column of an MMA fragment)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return (uint32_t)bf16_bits(lo) | ((uint32_t)bf16_bits(hi) << 16);
+}
+
 template <int D>
-__global__ void __launch_bounds__(128)
-    cv_forward_kernel(const uint16_t* __restrict__ Bf, const double* __restrict__ hv, const float* __restrict__ a,
-                      int P, int Ppad, uint16_t* __restrict__ DgT, double* __restrict__ loss_part) {
+__global__ void __launch_bounds__(kCvFitWarps * 32)
+    cv_fit_kernel(const uint16_t* __restrict__ Bf, const double* __restrict__ hv, const float* __restrict__ a, int P,
+                  int Ppad, float* __restrict__ grad_part, double* __restrict__ loss_part) {
+  constexpr int W = kCvFitWarps;
+  static_assert(D <= W, "one warp per dimension in the backward");
+  // factors D_i^T of the batch's tiles: [tile][dimension][rank][8 words of 2 points] (BF16
+  // pairs); word w of rank row r sits at w ^ (4 ((r >> 2) & 1)), so the eight rows a
+  // fragment load touches fall in distinct banks
   __shared__ __align__(16) uint16_t as[kCvR * D * kCvK];
-  __shared__ double red[4];
+  __shared__ __align__(16) uint32_t fs[W][D][kCvR][8];
+  __shared__ double red[W];
   for (int q = threadIdx.x; q < kCvR * D * kCvK; q += blockDim.x) as[q] = bf16_bits(a[q]);
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int j0 = blockIdx.x * kCvTile + warp * 16;
-  float C[D][2][4];  // [dimension][r-tile][fragment]
+  float acc[4][4];  // dimension `warp`: grad[r = g (+8)][k = 8 n + 2t (+1)]
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    const uint16_t* rowA = Bf + ((size_t)i * Ppad + j0 + g) * kCvK;
-    const uint16_t* rowB = rowA + 8 * kCvK;
+  for (int n = 0; n < 4; ++n)
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
+    for (int v = 0; v < 4; ++v) acc[n][v] = 0.0f;
+  double l2 = 0.0;
+  const int ntiles = Ppad / 16;
+  for (int b0 = blockIdx.x * W; b0 < ntiles; b0 += gridDim.x * W) {
+    __syncthreads();  // as[] loaded; fs[] free for this batch
+    // ---- forward, warp w on tile b0 + w
+    const int tile = b0 + warp;
+    if (tile < ntiles) {
+      const int j0 = tile * 16;
+      float C[D][2][4];  // [dimension][r-tile][fragment]
 #pragma unroll
-      for (int v = 0; v < 4; ++v) C[i][nt][v] = 0.0f;
+      for (int i = 0; i < D; ++i) {
+        const uint16_t* rowA = Bf + ((size_t)i * Ppad + j0 + g) * kCvK;
+        const uint16_t* rowB = rowA + 8 * kCvK;
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-      const int k = 16 * ks + 2 * t;
-      const uint32_t a0 = *reinterpret_cast<const uint32_t*>(rowA + k);
-      const uint32_t a1 = *reinterpret_cast<const uint32_t*>(rowB + k);
-      const uint32_t a2 = *reinterpret_cast<const uint32_t*>(rowA + k + 8);
-      const uint32_t a3 = *reinterpret_cast<const uint32_t*>(rowB + k + 8);
+        for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const uint16_t* ap = as + ((8 * nt + g) * D + i) * kCvK + k;
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(ap);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(ap + 8);
-        mma_bf16_16x8x16(C[i][nt], a0, a1, a2, a3, b0, b1);
+          for (int v = 0; v < 4; ++v) C[i][nt][v] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const int k = 16 * ks + 2 * t;
+          const uint32_t a0 = *reinterpret_cast<const uint32_t*>(rowA + k);
+          const uint32_t a1 = *reinterpret_cast<const uint32_t*>(rowB + k);
+          const uint32_t a2 = *reinterpret_cast<const uint32_t*>(rowA + k + 8);
+          const uint32_t a3 = *reinterpret_cast<const uint32_t*>(rowB + k + 8);
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            const uint16_t* ap = as + ((8 * nt + g) * D + i) * kCvK + k;
+            const uint32_t b0r = *reinterpret_cast<const uint32_t*>(ap);
+            const uint32_t b1r = *reinterpret_cast<const uint32_t*>(ap + 8);
+            mma_bf16_16x8x16(C[i][nt], a0, a1, a2, a3, b0r, b1r);
+          }
+        }
+      }
+      // g for rows j0 + g (fragments 0, 1) and j0 + g + 8 (fragments 2, 3)
+      float gA = 0.0f, gB = 0.0f;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          float p = 1.0f;
+#pragma unroll
+          for (int i = 0; i < D; ++i) p *= C[i][nt][v];
+          if (v < 2) gA += p;
+          else gB += p;
+        }
+      gA += __shfl_xor_sync(0xffffffffu, gA, 1);
+      gA += __shfl_xor_sync(0xffffffffu, gA, 2);
+      gB += __shfl_xor_sync(0xffffffffu, gB, 1);
+      gB += __shfl_xor_sync(0xffffffffu, gB, 2);
+      const int jA = j0 + g, jB = j0 + g + 8;
+      const double errA = jA < P ? (double)gA - hv[2 * (size_t)jA] : 0.0;
+      const double errB = jB < P ? (double)gB - hv[2 * (size_t)jB] : 0.0;
+      if (t == 0) l2 += errA * errA + errB * errB;
+      const float eA = (float)(2.0 * errA / (double)P), eB = (float)(2.0 * errB / (double)P);
+      // D_i in the accumulator layout as BF16 pairs (rows = points g, g + 8;
+      // columns = ranks 8 nt + 2t, +1), transposed block by block into
+      // D_i^T[r][j]: lane (g, t) then holds ranks 8 nt + g at points 2t, 2t + 1
+      // (and 8 + 2t, 9 + 2t)
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          float o[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float p = v < 2 ? eA : eB;
+#pragma unroll
+            for (int i2 = 0; i2 < D; ++i2)
+              if (i2 != i) p *= C[i2][nt][v];
+            o[v] = p;
+          }
+          const int r = 8 * nt + g, sw = 4 * ((r >> 2) & 1);
+          fs[warp][i][r][t ^ sw] = movtrans(pack_bf16(o[0], o[1]));
+          fs[warp][i][r][(4 + t) ^ sw] = movtrans(pack_bf16(o[2], o[3]));
+        }
+    }
+    __syncthreads();
+    // ---- backward, warp w on dimension w, every tile of the batch
+    if (warp < D) {
+      const int i = warp;
+#pragma unroll 1
+      for (int b = 0; b < W && b0 + b < ntiles; ++b) {
+        const int j0 = (b0 + b) * 16;
+        const int sw = 4 * ((g >> 2) & 1);  // rows g and g + 8 share the swizzle
+        const uint32_t A0 = fs[b][i][g][t ^ sw];
+        const uint32_t A1 = fs[b][i][g + 8][t ^ sw];
+        const uint32_t A2 = fs[b][i][g][(4 + t) ^ sw];
+        const uint32_t A3 = fs[b][i][g + 8][(4 + t) ^ sw];
+        const uint16_t* rowA = Bf + ((size_t)i * Ppad + j0 + g) * kCvK;
+        const uint16_t* rowB = rowA + 8 * kCvK;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const int k = 16 * ks + 2 * t;
+          // the forward's basis fragments, transposed: points 2t.. (first) and
+          // 2t + 8.. (second) at degree 16 ks + g (k-tile 2 ks) and 16 ks + 8 + g
+          const uint32_t b00 = movtrans(*reinterpret_cast<const uint32_t*>(rowA + k));
+          const uint32_t b01 = movtrans(*reinterpret_cast<const uint32_t*>(rowB + k));
+          const uint32_t b10 = movtrans(*reinterpret_cast<const uint32_t*>(rowA + k + 8));
+          const uint32_t b11 = movtrans(*reinterpret_cast<const uint32_t*>(rowB + k + 8));
+          mma_bf16_16x8x16(acc[2 * ks], A0, A1, A2, A3, b00, b01);
+          mma_bf16_16x8x16(acc[2 * ks + 1], A0, A1, A2, A3, b10, b11);
+        }
       }
     }
   }
-  // g for rows j0 + g (fragments 0, 1) and j0 + g + 8 (fragments 2, 3)
-  float prod[2][4];
+  if (warp < D) {
+    float* out = grad_part + (size_t)blockIdx.x * (kCvR * D * kCvK);
 #pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      float p = 1.0f;
-#pragma unroll
-      for (int i = 0; i < D; ++i) p *= C[i][nt][v];
-      prod[nt][v] = p;
+    for (int n = 0; n < 4; ++n) {
+      out[(g * D + warp) * kCvK + 8 * n + 2 * t] = acc[n][0];
+      out[(g * D + warp) * kCvK + 8 * n + 2 * t + 1] = acc[n][1];
+      out[((g + 8) * D + warp) * kCvK + 8 * n + 2 * t] = acc[n][2];
+      out[((g + 8) * D + warp) * kCvK + 8 * n + 2 * t + 1] = acc[n][3];
     }
-  float gA = prod[0][0] + prod[0][1] + prod[1][0] + prod[1][1];
-  float gB = prod[0][2] + prod[0][3] + prod[1][2] + prod[1][3];
-  gA += __shfl_xor_sync(0xffffffffu, gA, 1);
-  gA += __shfl_xor_sync(0xffffffffu, gA, 2);
-  gB += __shfl_xor_sync(0xffffffffu, gB, 1);
-  gB += __shfl_xor_sync(0xffffffffu, gB, 2);
-  const int jA = j0 + g, jB = j0 + g + 8;
-  const double errA = jA < P ? (double)gA - hv[2 * (size_t)jA] : 0.0;
-  const double errB = jB < P ? (double)gB - hv[2 * (size_t)jB] : 0.0;
-  double l2 = t == 0 ? errA * errA + errB * errB : 0.0;
-  const float eA = (float)(2.0 * errA / (double)P), eB = (float)(2.0 * errB / (double)P);
-  // factor per (dimension, position): e * prefix * suffix over the other dimensions
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const float e = v < 2 ? eA : eB;
-      const int j = v < 2 ? jA : jB;
-      const int r = 8 * nt + 2 * t + (v & 1);
-      float pre[D + 1];
-      pre[0] = e;
-#pragma unroll
-      for (int i = 0; i < D; ++i) pre[i + 1] = pre[i] * C[i][nt][v];
-      float suf = 1.0f;
-#pragma unroll
-      for (int i = D - 1; i >= 0; --i) {
-        DgT[((size_t)i * kCvR + r) * Ppad + j] = bf16_bits(pre[i] * suf);
-        suf *= C[i][nt][v];
-      }
-    }
+  }
   l2 = warp_sum_d(l2);
   if (lane == 0) red[warp] = l2;
   __syncthreads();
-  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < W; ++w) sum += red[w];
+    loss_part[blockIdx.x] = sum;
+  }
 }
 
 // One explicit specialisation per d, each compiled in its own unit.
 template <int D>
 const void* cv_estimator_ptr(int tr, int alpha);
 template <int D>
-const void* cv_forward_ptr();
+const void* cv_fit_ptr();
 #define QMC_DECL_CV(D) \
   template <> const void* cv_estimator_ptr<D>(int, int); \
-  template <> const void* cv_forward_ptr<D>();
+  template <> const void* cv_fit_ptr<D>();
 QMC_DECL_CV(1) QMC_DECL_CV(2) QMC_DECL_CV(3) QMC_DECL_CV(4) QMC_DECL_CV(5) QMC_DECL_CV(6) QMC_DECL_CV(7) QMC_DECL_CV(8)
 #undef QMC_DECL_CV
 

@@ -16,8 +16,8 @@ const void* cv_estimator_ptr<QMC_D>(int tr, int alpha) {
 }
 
 template <>
-const void* cv_forward_ptr<QMC_D>() {
-  return (const void*)&cv_forward_kernel<QMC_D>;
+const void* cv_fit_ptr<QMC_D>() {
+  return (const void*)&cv_fit_kernel<QMC_D>;
 }
 
 }  // namespace qmc

@@ -180,6 +180,12 @@ bool jit_enabled() {
   return !(e && e[0] == '0');
 }
 
+// Shifts as immediate operands of the specialised kernel (QMC_JIT_IMM=1; launch parameters otherwise).
+bool jit_imm() {
+  const char* e = std::getenv("QMC_JIT_IMM");
+  return e && e[0] == '1';
+}
+
 // Accumulator pairs in shared memory for the specialised kernel (QMC_JIT_SMACC=1; registers otherwise).
 bool jit_smacc() {
   const char* e = std::getenv("QMC_JIT_SMACC");
@@ -261,11 +267,28 @@ static int jit_compile(const std::string& src, const char* name, size_t smem, vo
 }
 
 // The include line and the GenPolys policy (scalar eval for point sampling,
-// packed eval2 for the rule) of one integrand.
-static std::string gen_polys(int D, const std::vector<double>& cu, const std::vector<double>& cf) {
+// packed eval2 for the rule, and the packed path's shifts: the launch
+// parameters', or, given imm_shifts [MC][D], immediate operands) of one
+// integrand.
+static std::string gen_polys(int D, const std::vector<double>& cu, const std::vector<double>& cf,
+                             const uint32_t* imm_shifts = nullptr, int MC = 0) {
   std::string src;
   src += "#include \"rule_kernels.cuh\"\n";
   src += "namespace qmc {\nstruct GenPolys {\n";
+  if (imm_shifts) {
+    src += "  __device__ static __forceinline__ uint32_t shift(const RuleParams<float>&, int k, int i) {\n";
+    src += "    switch (k * 16 + i) {\n";
+    for (int k = 0; k < MC; ++k)
+      for (int i = 0; i < D; ++i) {
+        char b[80];
+        std::snprintf(b, sizeof(b), "      case %d: return 0x%08xu;\n", k * 16 + i, imm_shifts[(size_t)k * D + i]);
+        src += b;
+      }
+    src += "    }\n    return 0u;\n  }\n";
+  } else {
+    src += "  __device__ static __forceinline__ uint32_t shift(const RuleParams<float>& P, int k, int i) {\n";
+    src += "    return P.shiftx[k][i];\n  }\n";
+  }
   src += "  template <int D_, int KU, int KF, typename R>\n";
   src += "  __device__ static __forceinline__ void eval(const RuleParams<R>&, const R* z, R& U, R& F) {\n";
   src += poly_code(D, cu, cf);
@@ -296,10 +319,10 @@ int jit_eps_f32(int D, int MC, int NE, int TR, int ALPHA, bool log1, bool check,
 // the CUfunction / occupancy, or an error code (the caller falls back).
 int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
                    const std::vector<double>& cf, bool smacc, int minb, void** fn_out, int* occ_out,
-                   size_t* smem_out) {
+                   size_t* smem_out, const uint32_t* imm_shifts) {
   const size_t smem = smacc ? (size_t)MC * kThreads * 8 : 0;
   *smem_out = smem;
-  std::string src = gen_polys(D, cu, cf);
+  std::string src = gen_polys(D, cu, cf, imm_shifts, MC);
   src += "extern \"C\" __global__ void __launch_bounds__(256" + (minb > 0 ? ", " + std::to_string(minb) : "") +
          ") qmc_jit_sector(\n";
   src += "    const __grid_constant__ qmc::RuleParams<float> P, double* __restrict__ partial,\n";

@@ -33,6 +33,8 @@ struct TuneChoice {
   int smacc = -1;      // specialised kernel: accumulator pairs in shared memory (1), registers (0),
                        // -1: the QMC_JIT_SMACC default
   int minb = 0;        // specialised kernel: minimum resident CTAs per SM in its launch bounds (0: none)
+  int imm = -1;        // specialised kernel: shifts as immediate operands (1), from the launch parameters
+                       // (0), -1: the QMC_JIT_IMM default (plans of one launch chunk only)
 };
 
 // Deep copy of a problem's host inputs (so a plan can be rebuilt by the tuner).
@@ -60,6 +62,7 @@ struct Plan {
   bool sum_last = false;  // the last group is the sum of the others (shared-lattice plans)
   int nblk = 0;
   int mc = 0;
+  int imm = 0;     // the specialised kernel takes its shifts as immediate operands
   const void* func = nullptr;
   double value_scale = 1.0;
   double final_scale = 1.0;
@@ -107,9 +110,10 @@ int plan_execute(Plan* pl, qmc_result* out, double* per_shift, cudaStream_t stre
 
 bool jit_enabled();
 bool jit_smacc();
+bool jit_imm();
 int jit_sector_f32(int D, int MC, int TR, int ALPHA, bool check, const std::vector<double>& cu,
                    const std::vector<double>& cf, bool smacc, int minb, void** fn_out, int* occ_out,
-                   size_t* smem_out);
+                   size_t* smem_out, const uint32_t* imm_shifts = nullptr);
 int jit_multi_f32(int D, int MC, int TR, int ALPHA, bool check,
                   const std::vector<std::pair<std::vector<double>, std::vector<double>>>& polys, void** fn_out,
                   int* occ_out);

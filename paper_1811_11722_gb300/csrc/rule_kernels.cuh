@@ -141,6 +141,8 @@ __device__ __forceinline__ double coord_used(typename FixT<R>::T X) {
 // kernel parameters (DensePolys), or as straight-line code generated for one
 // plan (a policy struct written by the run-time specialiser, see jit.cu).
 struct DensePolys {
+  // the FP32 sector path's fixed-point shift k of dimension i
+  __device__ static __forceinline__ uint32_t shift(const RuleParams<float>& P, int k, int i) { return P.shiftx[k][i]; }
   template <int D, int KU, int KF, typename R>
   __device__ static __forceinline__ void eval(const RuleParams<R>& P, const R* z, R& U, R& F) {
     U = poly_dense<D, KU>(P.cU, z);
@@ -167,8 +169,8 @@ __device__ __forceinline__ float2 sector_value2(const RuleParams<float>& P, cons
   float wa = 1.0f, wb = 1.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i)
-    z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], P.kor, wa),
-                       coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p + 1][i], P.kor, wb));
+    z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + POLY::shift(P, 2 * p, i), P.kor, wa),
+                       coord_fx<TR, ALPHA>(base[i] + POLY::shift(P, 2 * p + 1, i), P.kor, wb));
   float2 U, Fn;
   POLY::template eval2<D, KU, KF>(P, z, U, Fn);
   float2 v = recip_neg2(mul2(mul2(U, U), Fn));

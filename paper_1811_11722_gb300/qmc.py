@@ -598,10 +598,11 @@ def qmc_combine_shifts(per_shift) -> qmc_result:
 
 
 def qmc_measure_peaks(stream=0) -> dict:
-    """Measured FP32 / FP64 FMA TFLOP/s of the current GPU."""
-    out = np.zeros(2)
+    """Measured FP32 / FP64 FMA and warp-level TF32 / BF16 MMA TFLOP/s of the current GPU."""
+    out = np.zeros(4)
     _check(lib().qmc_measure_peaks(ctypes.c_void_p(stream), _ptr(out)))
-    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1])}
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "mma_sync_tf32_tflops": float(out[2]),
+            "mma_sync_bf16_tflops": float(out[3])}
 
 
 def qmc_integrate_cv_to_tolerance(d, ns, gs, m, shifts, t, f: Integrand, cfg: qmc_cv_config, a, rel_tol, stream=0):
@@ -614,7 +615,7 @@ def qmc_integrate_cv_to_tolerance(d, ns, gs, m, shifts, t, f: Integrand, cfg: qm
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
     res = qmc_result()
     lvl, mode = ctypes.c_int32(-1), ctypes.c_int32(-1)
-    judge = np.zeros(4)
+    judge = np.zeros(8)
     rc = lib().qmc_integrate_cv_to_tolerance(d, len(ns), _ptr(ns), _ptr(gs), m, _ptr(shifts), t, f.ref,
                                              ctypes.byref(cfg), _ptr(a), rel_tol, ctypes.byref(res),
                                              ctypes.byref(lvl), ctypes.byref(mode), _ptr(judge),
@@ -622,7 +623,8 @@ def qmc_integrate_cv_to_tolerance(d, ns, gs, m, shifts, t, f: Integrand, cfg: qm
     if rc not in (QMC_OK, QMC_ETIMEOUT) and rc not in WARNINGS:
         _check(rc)
     j = {"rel_err_cv": float(judge[0]), "rel_err_plain": float(judge[1]), "pass_s_cv": float(judge[2]),
-         "pass_s_plain": float(judge[3])}
+         "pass_s_plain": float(judge[3]), "rate_cv": float(judge[4]), "rate_plain": float(judge[5]),
+         "predicted_s_cv": float(judge[6]), "predicted_s_plain": float(judge[7])}
     return res, int(lvl.value), int(mode.value), j, rc != QMC_ETIMEOUT
 
 

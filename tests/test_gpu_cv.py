@@ -188,12 +188,12 @@ def _ladder(Q, d, ns, gamma):
 
 
 def test_cv_walk_falls_back_to_the_plain_rule(Q):
-    """The control-variate walk judges the surrogate on the first lattice at
-    equal cost.  On the configuration-5 integrand under Korobov 3 a pass of
-    the control-variate estimator costs many plain passes, more than its
-    error gain on the pilot lattice, so the walk keeps the plain rule
-    (mode 0), and from then on it is exactly the plain walk: same stopping
-    level, same estimate as qmc_integrate_to_tolerance on the same ladder."""
+    """The control-variate walk judges the surrogate on the first three
+    lattices by predicted time to the target.  On the configuration-5
+    integrand under Korobov 3 the plain rule's error falls much faster with n
+    than the control variate's, so the walk keeps the plain rule (mode 0),
+    and it is exactly the plain walk: same stopping level, same estimate as
+    qmc_integrate_to_tolerance on the same ladder."""
     p = I.config5(n=65521, m=16)
     d = p.d
     ns = [65521, 131071, 262139, 524287, 1048573, 2097143]
@@ -206,21 +206,21 @@ def test_cv_walk_falls_back_to_the_plain_rule(Q):
     tol = 1e-7
     r, lvl, mode, judge, ok = Q.qmc_integrate_cv_to_tolerance(d, ns, gs, p.m, p.shifts, t, f, cfg, a, tol)
     assert mode == 0, judge
-    assert judge["rel_err_cv"] * judge["pass_s_cv"] >= judge["rel_err_plain"] * judge["pass_s_plain"]
+    assert judge["predicted_s_cv"] >= judge["predicted_s_plain"]
+    assert judge["rate_plain"] > judge["rate_cv"]
     r2, lvl2, ok2 = Q.qmc_integrate_to_tolerance(d, ns, gs, p.m, p.shifts, t, f, tol)
     assert (lvl, ok) == (lvl2, ok2)
-    if lvl > 0:
-        assert r.mean[0] == r2.mean[0] and r.err[0] == r2.err[0]
-    else:
-        assert abs(r.mean[0] - r2.mean[0]) <= 1e-12 * abs(r2.mean[0])
+    assert r.mean[0] == r2.mean[0] and r.err[0] == r2.err[0]
 
 
 def test_cv_walk_keeps_a_winning_surrogate(Q):
-    """Where the surrogate wins at equal cost the walk keeps it (mode 1): a
-    d = 1 sector without a transform, which 32 cosines fit to about 1e-9, so
-    the control variate's error is orders of magnitude below the plain
-    rule's (whose error decays only as 1/n here).  The kept estimate is the
-    control variate's, Q[f - g] + int g, with its own Eq. (3) error."""
+    """Where the surrogate wins the walk keeps it (mode 1): a d = 1 sector
+    without a transform, which 32 cosines fit to about 1e-9, so the control
+    variate's error is orders of magnitude below the plain rule's at the
+    same rate (both decay as about 1/n here, the non-periodic integrand's
+    rate), and its predicted time to the target is far smaller.  The kept
+    estimate is the control variate's, Q[f - g] + int g, with its own Eq. (3)
+    error."""
     d = 1
     U = I.Poly(np.array([0.7, 1.3]), np.array([[0], [1]], dtype=np.uint8))
     F = I.Poly(np.array([0.4, 1.9]), np.array([[0], [2]], dtype=np.uint8))
@@ -228,14 +228,14 @@ def test_cv_walk_keeps_a_winning_surrogate(Q):
     p = I.Problem("d1cv", 1, 65521, 8, I.make_shifts(rng, 8, 1), "none", kind="sector", U=U, F=F, precision="fp32")
     f = Q.integrand_from_problem(p, "fp32")
     t = Q.transform("none")
-    ns = [10007, 20011, 40009]
+    ns = [10007, 20011, 40009, 80021]
     gs = np.ones(len(ns), dtype=np.uint64)
     gp = np.array([1], dtype=np.uint64)
     cfg = _cfg(Q, steps=2000)
     a, losses = Q.qmc_cv_train(d, 65537, gp, np.array([0.25]), t, f, cfg)
-    r, lvl, mode, judge, ok = Q.qmc_integrate_cv_to_tolerance(d, ns, gs, p.m, p.shifts, t, f, cfg, a, 1e-30)
+    r, lvl, mode, judge, ok = Q.qmc_integrate_cv_to_tolerance(d, ns, gs, p.m, p.shifts, t, f, cfg, a, 1e-11)
     assert mode == 1, (judge, losses)
-    assert judge["rel_err_cv"] * judge["pass_s_cv"] < judge["rel_err_plain"] * judge["pass_s_plain"]
-    assert not ok and lvl == len(ns) - 1
-    rc, _ = Q.qmc_integrate_cv(d, ns[-1], p.m, gs[-1:], p.shifts, t, f, cfg, a)
+    if lvl >= 2:  # past the first lattices the judgement was made on predicted times
+        assert judge["predicted_s_cv"] < judge["predicted_s_plain"], judge
+    rc, _ = Q.qmc_integrate_cv(d, ns[lvl], p.m, gs[lvl:lvl + 1], p.shifts, t, f, cfg, a)
     assert r.mean[0] == rc.mean[0] and r.err[0] == rc.err[0]

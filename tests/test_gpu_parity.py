@@ -704,8 +704,14 @@ def test_config3_full_batch_sampled(Q, oracle_lib, nthreads):
     pp = Q.BatchPlan(tuples, persistent=True)
     ps_p = np.zeros_like(ps)
     assert all(r.status == 0 for r in pp.execute(per_shift=ps_p))
-    pp.destroy()
     assert np.all(np.abs(ps_p[0::2] - ps[0::2]) <= 1e-8 * np.abs(ps[0::2]))
+    # tuned (item size, and one or two CTAs per SM for the specialised kernel):
+    # the same values up to the grouping of the sums into items
+    pp.tune()
+    ps_t = np.zeros_like(ps)
+    assert all(r.status == 0 for r in pp.execute(per_shift=ps_t))
+    pp.destroy()
+    assert np.all(np.abs(ps_t[0::2] - ps[0::2]) <= 1e-8 * np.abs(ps[0::2]))
     offs = np.cumsum([0] + [p.m for p in sect])
     for i in sorted(range(len(sect)), key=lambda i: sect[i].n)[:6]:
         ref = oracle_lib.integrate(sect[i], gs[i], nthreads=nthreads)
@@ -824,10 +830,41 @@ def test_specialised_kernel_bit_identical(Q, monkeypatch):
 
 # ------------------------------------------------------------- utilities --
 
+def test_immediate_shift_kernel_bit_identical(Q, monkeypatch):
+    """The specialised sector kernel compiled with the shift table as
+    immediate operands (QMC_JIT_IMM=1, a plan of one launch chunk) against the
+    one reading its shifts from the launch parameters: the same constants
+    enter the same operations, so per-shift values are bit-identical, and the
+    plan reports the variant.  With more shifts than one launch takes, the
+    switch is ignored."""
+    p = I.config2(n=1000003, m=32)
+    g = I.random_generating_vector(I.SplitMix64(31), p.d, p.n)
+    f, t = Q.integrand_from_problem(p, "fp32"), Q.transform(p.transform, p.alpha)
+    a = Q.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
+    assert a.describe()["imm_shifts"] == "0"
+    pa = np.zeros(2 * p.m)
+    ra = a.execute(per_shift=pa)
+    monkeypatch.setenv("QMC_JIT_IMM", "1")
+    b = Q.Plan(p.d, p.n, p.m, g, p.shifts, t, f)
+    assert b.describe()["imm_shifts"] == "1" and b.describe()["specialised"] == "1"
+    pb = np.zeros(2 * p.m)
+    rb = b.execute(per_shift=pb)
+    assert np.array_equal(pa, pb) and ra.mean[0] == rb.mean[0]
+    q = I.with_shifts(p, 40, 77)  # 40 shifts: two launch chunks, parameter shifts
+    c = Q.Plan(q.d, q.n, q.m, g, q.shifts, t, f)
+    assert c.describe()["imm_shifts"] == "0"
+
+
 def test_measure_peaks_sane(Q):
+    """FP32 and FP64 FMA rates within their nominal bounds (80.5 and 1.25
+    TFLOP/s at the maximum clock), and the warp-level MMA rates above the FP32
+    pipe's (tensor cores) but below the dense tcgen05 figures (2.25 PFLOP/s
+    BF16, 1.1 PFLOP/s TF32)."""
     pk = Q.qmc_measure_peaks()
     assert 10.0 < pk["fp32_tflops"] < 100.0
     assert 0.1 < pk["fp64_tflops"] < pk["fp32_tflops"]
+    assert pk["fp32_tflops"] < pk["mma_sync_tf32_tflops"] < 1100.0
+    assert pk["mma_sync_tf32_tflops"] < pk["mma_sync_bf16_tflops"] < 2250.0
 
 
 def test_combine_shifts_equals_one_call(Q):
