@@ -67,7 +67,7 @@ def device_max_sm_mhz(index: int) -> float:
 
 # DRAM traffic of the lattice kernel from one ncu capture of this workload;
 # valid only while the kernel sources hash to KERNEL_SHA (else reported null).
-NCU_TRAFFIC = {"kernel_sha": "da2bd60a044b9dd0", "bytes_per_launch": 90112}
+NCU_TRAFFIC = {"kernel_sha": "126ec923c5333d58", "bytes_per_launch": 90112}
 
 
 # the sources the benchmark's lattice kernel is compiled from
@@ -344,8 +344,8 @@ def extras(qmc, I, torch):
                                    "note": "generating vectors drawn at random (any valid g; throughput only)"}
     for pl in plans:
         pl.destroy()
-    # the same 256 sectors as one persistent launch (work items from a device
-    # counter, coefficients staged in shared memory, no run-time compilation)
+    # the same 256 sectors as one persistent launch: work items from a device
+    # counter, each dispatched to its sector's run-time specialised code
     t0 = time.perf_counter()
     pp = qmc.BatchPlan(tuples, persistent=True)
     pbuild_s = time.perf_counter() - t0
@@ -356,8 +356,25 @@ def extras(qmc, I, torch):
     out["c3_batch_256_sectors_persistent"] = {
         "evals_per_s": evals / tpp, "ms": 1e3 * tpp, "points_per_item": pw, "plan_build_s": pbuild_s,
         "launches": pp.launches(), "ms_graph": 1e3 * t, "graph_plan_build_s": build_s,
-        "max_rel_diff_vs_graph": max(abs(a["mean"][0] - b["mean"][0]) / abs(b["mean"][0]) for a, b in zip(rp, rg))}
+        "max_rel_diff_vs_graph": max(abs(a["mean"][0] - b["mean"][0]) / abs(b["mean"][0]) for a, b in zip(rp, rg)),
+        "plan": pp.describe()}
     pp.destroy()
+    # the generic persistent kernel (no run-time compilation: every sector's
+    # dense coefficient slots staged in shared memory), tuned the same way
+    saved_env = os.environ.get("QMC_PERSIST_JIT")
+    os.environ["QMC_PERSIST_JIT"] = "0"
+    try:
+        pg = qmc.BatchPlan(tuples, persistent=True)
+        pgw = pg.tune(sh)
+        tpg = device_time(lambda: pg.execute(out=dev_res, stream=sh), stream, reps=3)
+        out["c3_batch_256_sectors_persistent_generic"] = {"evals_per_s": evals / tpg, "ms": 1e3 * tpg,
+                                                          "points_per_item": pgw, "plan": pg.describe()}
+        pg.destroy()
+    finally:
+        if saved_env is None:
+            del os.environ["QMC_PERSIST_JIT"]
+        else:
+            os.environ["QMC_PERSIST_JIT"] = saved_env
     bp.destroy()
     # control-variate estimator Q[f - g] + int g (surrogate contracted on tensor
     # cores) on the configuration-5 integrand at n = 16777213, m = 16: one fit
@@ -423,58 +440,77 @@ def _short(cfg):
     return c
 
 
-def c3_time_to_tolerance(qmc, I, sh, tol):
+def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279):
+    """The 256 Korobov-3 sectors summed to tol: every sector starts on its own
+    table prime and climbs the prime ladder (up to ladder_max) while its error
+    is above its share tol |sum| / sqrt(256) of the tolerance on the sum.
+    Batched: qmc_integrate_batch_to_tolerance, one batched launch per pass.
+    One by one: the same walk with one qmc_integrate call per sector and
+    level.  CBC vectors (d = 8, restricted to each sector's d) are host
+    precomputes and not timed."""
     import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
     sect = I.config3(transform="korobov", alpha=3)
     S = len(sect)
-    ladder = I.ladder_primes()
-    cbc = {}   # n -> d=8 CBC vector (a d-dimensional CBC vector is its first d components)
-
-    def lattice(n, d):
-        if n not in cbc:
-            cbc[n] = qmc.qmc_make_lattice(8, n, I.product_weights(8))
-        return cbc[n][:d]
-
-    steps = [[q.n] + [n for n in ladder if n > q.n] for q in sect]
+    ladder = [n for n in I.ladder_primes() if min(q.n for q in sect) < n <= ladder_max]
+    need = sorted(set(ladder) | {q.n for q in sect})
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        cbc = dict(zip(need, ex.map(lambda n: qmc.qmc_make_lattice(8, n, I.product_weights(8)), need)))
     fs = [qmc.integrand_from_problem(q) for q in sect]
     ts = [qmc.transform(q.transform, q.alpha) for q in sect]
+    tuples = [(q.d, q.n, q.m, cbc[q.n][:q.d].copy(), q.shifts, t_, f_) for q, t_, f_ in zip(sect, ts, fs)]
+    ladder_n = np.array(ladder, dtype=np.uint64)
+    ladder_g = np.stack([cbc[n] for n in ladder]).astype(np.uint64)
     # run-time compilation of every sector's kernel (independent of n): a precompute
-    qmc.qmc_integrate_batch([(q.d, 1009, q.m, lattice(1009, q.d), q.shifts, t_, f_)
+    g1009 = qmc.qmc_make_lattice(8, 1009, I.product_weights(8))
+    qmc.qmc_integrate_batch([(q.d, 1009, q.m, g1009[:q.d].copy(), q.shifts, t_, f_)
                              for q, t_, f_ in zip(sect, ts, fs)], stream=sh)
     res = {}
-    for mode in ("batched", "one_by_one"):
-        level = [0] * S
-        mean = np.zeros(S)
-        err = np.zeros(S)
-        todo = list(range(S))
-        wall, levels, evals = 0.0, 0, 0
-        while True:
-            for i in todo:  # lattices are host precomputes (not timed)
-                lattice(steps[i][level[i]], sect[i].d)
-            t0 = time.perf_counter()
-            if mode == "batched":
-                tuples = [(sect[i].d, steps[i][level[i]], sect[i].m, lattice(steps[i][level[i]], sect[i].d),
-                           sect[i].shifts, ts[i], fs[i]) for i in todo]
-                rs, _ = qmc.qmc_integrate_batch(tuples, stream=sh)
-            else:
-                rs = [qmc.qmc_integrate(sect[i].d, steps[i][level[i]], sect[i].m,
-                                        lattice(steps[i][level[i]], sect[i].d), sect[i].shifts, ts[i], fs[i],
-                                        stream=sh)[0] for i in todo]
-            wall += time.perf_counter() - t0
-            levels += 1
-            for i, r in zip(todo, rs):
-                mean[i], err[i] = r.mean[0], r.err[0]
-                evals += steps[i][level[i]] * sect[i].m
-            total, total_err = mean.sum(), math.sqrt(float(np.sum(err ** 2)))
-            share = tol * abs(total) / math.sqrt(S)
-            todo = [i for i in range(S) if err[i] > share and level[i] + 1 < len(steps[i])]
-            if total_err <= tol * abs(total) or not todo:
-                break
-            for i in todo:
-                level[i] += 1
-        res[mode] = {"rel_err": float(total_err / abs(total)), "sum": float(total), "wall_s": wall, "levels": levels,
-                     "evals": int(evals), "reached": bool(total_err <= tol * abs(total)),
-                     "largest_n": int(max(steps[i][level[i]] for i in range(S)))}
+    # batched: the library's walk (best of 3 runs; the first also warms the allocator)
+    walls = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        rs, lv, passes, reached = qmc.qmc_integrate_batch_to_tolerance(tuples, ladder_n, ladder_g, tol,
+                                                                       qmc.WALK_SUM, stream=sh)
+        walls.append(time.perf_counter() - t0)
+    mean = np.array([r.mean[0] for r in rs])
+    err = np.array([r.err[0] for r in rs])
+    ns = [q.n if l < 0 else ladder[l] for q, l in zip(sect, lv)]
+    evals = 0
+    for q, l in zip(sect, lv):  # every lattice a sector visited
+        evals += q.n * q.m + sum(ladder[k] * q.m for k in range(int(np.searchsorted(ladder_n, q.n, "right")), l + 1))
+    total, total_err = mean.sum(), math.sqrt(float(np.sum(err ** 2)))
+    res["batched"] = {"rel_err": float(total_err / abs(total)), "sum": float(total), "wall_s": min(walls),
+                      "wall_s_runs": walls, "passes": int(passes), "evals": int(evals), "reached": bool(reached),
+                      "largest_n": int(max(ns)), "api": "qmc_integrate_batch_to_tolerance"}
+    # one by one: the same decisions, one rule call per sector and level
+    steps = [[q.n] + [n for n in ladder if n > q.n] for q in sect]
+    level = [0] * S
+    mean = np.zeros(S)
+    err = np.zeros(S)
+    todo = list(range(S))
+    wall, passes, evals = 0.0, 0, 0
+    while True:
+        t0 = time.perf_counter()
+        rs = [qmc.qmc_integrate(sect[i].d, steps[i][level[i]], sect[i].m, cbc[steps[i][level[i]]][:sect[i].d].copy(),
+                                sect[i].shifts, ts[i], fs[i], stream=sh)[0] for i in todo]
+        wall += time.perf_counter() - t0
+        passes += 1
+        for i, r in zip(todo, rs):
+            mean[i], err[i] = r.mean[0], r.err[0]
+            evals += steps[i][level[i]] * sect[i].m
+        total, total_err = mean.sum(), math.sqrt(float(np.sum(err ** 2)))
+        if total_err <= tol * abs(total):
+            break
+        share = tol * abs(total) / math.sqrt(S)
+        todo = [i for i in range(S) if err[i] > share and level[i] + 1 < len(steps[i])]
+        if not todo:
+            break
+        for i in todo:
+            level[i] += 1
+    res["one_by_one"] = {"rel_err": float(total_err / abs(total)), "sum": float(total), "wall_s": wall,
+                         "passes": passes, "evals": int(evals), "reached": bool(total_err <= tol * abs(total)),
+                         "largest_n": int(max(steps[i][level[i]] for i in range(S))), "api": "qmc_integrate per call"}
     res["batched"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched"]["wall_s"]
     return {"c3_256_sectors_korobov3_sum_batched": res["batched"],
             "c3_256_sectors_korobov3_sum_one_by_one": res["one_by_one"]}
@@ -571,11 +607,12 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
     # configuration 3's 256 sectors (Korobov 3 variant), their sum to 1e-8
     # relative error: every sector walks its own ladder (its table prime, then
     # the ladder primes above it, CBC vectors from the library, untimed).  A
-    # level refines only the sectors whose Eq. (3) error exceeds their share
+    # pass refines only the sectors whose Eq. (3) error exceeds their share
     # tol |sum| / sqrt(256) of the total's budget; the total error is the
-    # quadrature sum of the sectors'.  Batched: each level is one
-    # qmc_integrate_batch call over the refined sectors; one by one: one
-    # qmc_integrate call per refined sector.  Same lattices, shifts and points.
+    # quadrature sum of the sectors'.  Batched: the library's walk
+    # (qmc_integrate_batch_to_tolerance, one batched launch per pass); one by
+    # one: one qmc_integrate call per refined sector.  Same lattices, shifts
+    # and decisions.
     out.update(c3_time_to_tolerance(qmc, I, sh, tol))
     # control variate on the d=8 sector (pilot n=65537, 2000 Adam steps).  The
     # library's judged walk (qmc_integrate_cv_to_tolerance): the first ladder

@@ -221,17 +221,57 @@ typedef struct {
 
 /* Many independent rules (e.g. the sectors of one integral: uneven d, n,
  * integrand) evaluated together.  Every problem keeps the kernel it would get
- * from qmc_integrate; the batch runs them as independent nodes of one CUDA
- * graph (the GPU schedules them side by side) followed by one final-pass
- * launch for all problems.
+ * from qmc_integrate, with at most ceil(n m / 2^20) CTAs (at most 4 per SM);
+ * the problems' launches go round-robin to internal streams forked from
+ * `stream` (the GPU runs the sectors side by side), followed by one
+ * final-pass launch for all problems.  The workspace comes from the
+ * stream-ordered allocator (cudaMallocAsync / cudaFreeAsync on `stream`).
  *   count      number of problems (1..65536)
  *   problems   [count] descriptors (host); each as for qmc_integrate
  *   out        [count] results (host or device); out[i].status per problem
  *   per_shift  optional; problem i writes 2*m_i doubles at offset 2*sum_{p<i} m_p
- * Returns the first non-OK per-problem status when `out` is host memory. */
+ * Synchronises `stream`.  Returns the first non-OK per-problem status when
+ * `out` is host memory. */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* out,
                         double* per_shift, void* stream);
+#endif
+
+/* Automatic choice of n for a batch (the sectors of one integral), each pass
+ * one batched launch.  Problem i is first evaluated on its own lattice
+ * (problems[i].n, .g), then on the ladder's lattices with n above its own, in
+ * order; a ladder lattice serves every problem through its first d
+ * components (a component-by-component vector of ladder_dim components
+ * restricted to d is the d-dimensional one).  Each pass evaluates, as
+ * qmc_integrate_batch would at their current lattices (bit for bit), only the
+ * problems that move up; the others keep their last result.  Kernels,
+ * shifts and coefficients are prepared once, so a pass costs its launches,
+ * one final pass and one copy of the results.
+ *   criterion QMC_WALK_SUM: stop when the sum's error estimate,
+ *       sqrt(sum_i err_i^2), is <= rel_tol |sum_i Qbar_i|; else move up every
+ *       problem whose err_i is above its share rel_tol |sum_i Qbar_i| / sqrt(count)
+ *     QMC_WALK_EACH: stop when every problem meets err_i <= rel_tol |Qbar_i|;
+ *       else move up every problem that does not
+ *   (modulus of (re, im) for complex integrands).  Stops too when no problem
+ *   that should move up has a further lattice.
+ *   levels          ladder lattices (0..64), increasing n in [2, 2^31)
+ *   ladder_n        [levels];  ladder_g  [levels * ladder_dim], g in [1, n)
+ *   ladder_dim      components per ladder vector, >= every problem's d
+ *   out             [count] results at the final lattices (host)
+ *   level_out       optional [count]: ladder index of problem i's final
+ *                   lattice, -1 for its own
+ *   passes_out      optional: passes run
+ * Synchronises `stream`.  Returns QMC_OK when the tolerance was met, else
+ * QMC_ETIMEOUT with the last results (QMC_WALK_EACH: out[i].status =
+ * QMC_ETIMEOUT for the problems that miss it); per-problem non-finite or
+ * deformation warnings stay in out[i].status. */
+#define QMC_WALK_SUM 0
+#define QMC_WALK_EACH 1
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+int qmc_integrate_batch_to_tolerance(int32_t count, const qmc_problem* problems, int32_t levels,
+                                     const uint64_t* ladder_n, const uint64_t* ladder_g, int32_t ladder_dim,
+                                     double rel_tol, int32_t criterion, qmc_result* out, int32_t* level_out,
+                                     int32_t* passes_out, void* stream);
 #endif
 
 /* Planned batch: validates and packs once and builds the CUDA graph; every

@@ -309,27 +309,53 @@ static int device_sm_count() {
 
 int device_sms() { return device_sm_count(); }
 
-// Grid: one resident wave (SMs x CTAs per SM), each CTA one tile of
-// kThreads * L points, L from the point count.
-int choose_grid(const void* func, size_t smem, uint64_t n, int& nblk, int& L, uint64_t& tiles,
-                int occupancy_override) {
-  int sms = device_sm_count();
-  if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
-  int occ = 0;
+// CTAs of `func` resident per SM (at least 1), capped by occupancy_override
+// when > 0; a run-time compiled kernel (func null) takes the caller's figure.
+int grid_occupancy(const void* func, size_t smem, int occupancy_override, int& occ) {
+  occ = 0;
   if (func) {
     QMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, kThreads, smem));
     if (occ < 1) occ = 1;
     if (occupancy_override > 0) occ = std::min(occ, occupancy_override);
   } else {
-    occ = std::max(1, occupancy_override);  // a run-time compiled kernel: the caller's occupancy
+    occ = std::max(1, occupancy_override);
   }
-  uint64_t want = (uint64_t)sms * occ;
-  uint64_t per = (n + want * kThreads - 1) / (want * kThreads);
+  return QMC_OK;
+}
+
+// Grid: one resident wave (SMs x occ CTAs), each CTA one tile of kThreads * L
+// points, L from the point count; then at most max_ctas CTAs (> 0) and a
+// fixed L (> 0) if asked.
+int grid_shape(int occ, uint64_t n, int max_ctas, int fixed_L, int& nblk, int& L, uint64_t& tiles) {
+  const int sms = device_sm_count();
+  if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
   const uint64_t Lmax = 512;
+  const uint64_t want = (uint64_t)sms * (uint64_t)std::max(occ, 1);
+  uint64_t per = (n + want * kThreads - 1) / (want * kThreads);
   L = (int)std::max<uint64_t>(1, std::min(per, Lmax));
   tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
   nblk = (int)std::min<uint64_t>(want, tiles);
+  if (max_ctas > 0 && nblk > max_ctas) {
+    nblk = max_ctas;
+    per = (n + (uint64_t)nblk * kThreads - 1) / ((uint64_t)nblk * kThreads);
+    L = (int)std::max<uint64_t>(1, std::min(per, Lmax));
+    tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
+    nblk = (int)std::min<uint64_t>((uint64_t)nblk, tiles);
+  }
+  if (fixed_L > 0) {
+    L = fixed_L;
+    tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
+    nblk = (int)std::min<uint64_t>((uint64_t)nblk, tiles);
+  }
   return QMC_OK;
+}
+
+int choose_grid(const void* func, size_t smem, uint64_t n, int& nblk, int& L, uint64_t& tiles,
+                int occupancy_override) {
+  int occ = 0;
+  int rc = grid_occupancy(func, smem, occupancy_override, occ);
+  if (rc) return rc;
+  return grid_shape(occ, n, 0, 0, nblk, L, tiles);
 }
 
 static int pick_mc(int m, bool fp32) {
@@ -506,25 +532,19 @@ static int build_rule_plan(Plan* pl, int32_t d, uint64_t n, int32_t m, const uin
   if (fp32 && (general || !(f->kind == QMC_F_SECTOR || eps)) && base.tr == TR_KOROBOV)
     base.value_scale = std::pow((double)base.kor[7] / std::pow(4.0, (double)base.alpha), (double)d);
 
-  int nblk = 0, L = 0;
+  int nblk = 0, L = 0, occ = 0;
   uint64_t tiles = 0;
   // a run-time specialised kernel has its own occupancy (registers, shared memory), not the template's
-  int rc = choose_grid(jit_fn ? nullptr : func, 0, n, nblk, L, tiles,
-                       jit_fn ? (tune.occupancy > 0 ? std::min(tune.occupancy, jit_occ) : jit_occ)
-                                                          : tune.occupancy);
+  int rc = grid_occupancy(jit_fn ? nullptr : func, 0,
+                          jit_fn ? (tune.occupancy > 0 ? std::min(tune.occupancy, jit_occ) : jit_occ)
+                                 : tune.occupancy,
+                          occ);
   if (rc) return rc;
-  if (tune.max_ctas > 0 && nblk > tune.max_ctas) {
-    nblk = tune.max_ctas;
-    uint64_t per = (n + (uint64_t)nblk * kThreads - 1) / ((uint64_t)nblk * kThreads);
-    L = (int)std::max<uint64_t>(1, std::min<uint64_t>(per, 512));
-    tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
-    nblk = (int)std::min<uint64_t>((uint64_t)nblk, tiles);
-  }
-  if (tune.L > 0) {
-    L = tune.L;
-    tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
-    nblk = (int)std::min<uint64_t>((uint64_t)nblk, tiles);
-  }
+  rc = grid_shape(occ, n, tune.max_ctas, tune.L, nblk, L, tiles);
+  if (rc) return rc;
+  pl->param_kind = general ? (fp32 ? 3 : 4) : (fp32 ? 1 : 2);
+  pl->grid_occ = occ;
+  pl->grid_capped = true;
   base.L = L;
   base.tiles = tiles;
   base.nblk = nblk;
@@ -619,6 +639,44 @@ int plan_build(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t* g, co
     rc = build_rule_plan<double>(pl, d, n, m, g, shifts, t, f, tune, eps);
   }
   return rc;
+}
+
+template <typename R>
+static void rebase_rule(RuleParams<R>& P, int d, uint64_t n, const uint64_t* g, int nblk, int L, uint64_t tiles) {
+  P.n = n;
+  P.rc = reciprocal(n);
+  for (int i = 0; i < d; ++i) {
+    P.g[i] = (uint32_t)g[i];
+    P.gstep[i] = (uint32_t)(((uint64_t)kThreads * g[i]) % n);
+  }
+  P.L = L;
+  P.tiles = tiles;
+  P.nblk = nblk;
+}
+
+int plan_rebase(Plan* pl, uint64_t n, const uint64_t* g, int max_ctas) {
+  if (pl->param_kind < 1 || pl->param_kind > 4) return fail(QMC_EUNSUPPORTED, "this plan is bound to its lattice");
+  if (n < 2 || n >= (1ull << 31)) return fail(QMC_EINVAL, "n=%llu outside [2, 2^31)", (unsigned long long)n);
+  for (int i = 0; i < pl->d; ++i)
+    if (g[i] < 1 || g[i] >= n) return fail(QMC_EINVAL, "g[%d]=%llu outside [1, n)", i, (unsigned long long)g[i]);
+  int nblk = 0, L = 0;
+  uint64_t tiles = 0;
+  int rc = grid_shape(pl->grid_occ, n, pl->grid_capped ? max_ctas : 0, pl->tune.L, nblk, L, tiles);
+  if (rc) return rc;
+  for (Launch& ln : pl->launches) {
+    uint8_t* p = ln.params.data();
+    switch (pl->param_kind) {
+      case 1: rebase_rule(*reinterpret_cast<RuleParams<float>*>(p), pl->d, n, g, nblk, L, tiles); break;
+      case 2: rebase_rule(*reinterpret_cast<RuleParams<double>*>(p), pl->d, n, g, nblk, L, tiles); break;
+      case 3: rebase_rule(reinterpret_cast<GeneralParams<float>*>(p)->base, pl->d, n, g, nblk, L, tiles); break;
+      default: rebase_rule(reinterpret_cast<GeneralParams<double>*>(p)->base, pl->d, n, g, nblk, L, tiles); break;
+    }
+    ln.grid = dim3(nblk);
+  }
+  pl->n = n;
+  pl->nblk = nblk;
+  pl->tune.max_ctas = max_ctas;
+  return QMC_OK;
 }
 
 int plan_alloc(Plan* pl, cudaStream_t stream, bool async) {

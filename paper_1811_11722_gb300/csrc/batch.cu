@@ -585,6 +585,37 @@ static int oneshot_streams(OneShotStreams** out) {
   return QMC_OK;
 }
 
+// Every launch of problems idx[0..nidx) (all problems when idx is null),
+// round-robin over the internal streams forked from `stream` and joined back
+// to it.
+static int launch_side_by_side(BatchPlan* bp, const int* idx, int nidx, cudaStream_t stream) {
+  OneShotStreams* S = nullptr;
+  int rc = oneshot_streams(&S);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_oneshot_mu);
+  cudaError_t e = cudaEventRecord(S->fork, stream);
+  for (int k = 0; k < kOneShotStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(S->s[k], S->fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+  SampleIO none;
+  std::memset(&none, 0, sizeof(none));
+  for (int u = 0; u < nidx && rc == QMC_OK; ++u) {
+    Plan* pl = bp->probs[idx ? idx[u] : u].get();
+    for (Launch& ln : pl->launches) {
+      double* partial = pl->ws.partial;
+      unsigned long long* counters = pl->ws.counters;
+      void* args[4] = {(void*)ln.params.data(), &partial, &counters, &none};
+      rc = launch_any(ln, ln.grid, args, S->s[u % kOneShotStreams]);
+      if (rc) break;
+    }
+  }
+  // join every internal stream back, even after a failed launch
+  for (int k = 0; k < kOneShotStreams; ++k) {
+    cudaEventRecord(S->join[k], S->s[k]);
+    cudaStreamWaitEvent(stream, S->join[k], 0);
+  }
+  return rc;
+}
+
 static int oneshot_run(BatchPlan* bp, cudaStream_t stream) {
   size_t bytes = 0;
   std::vector<size_t> part_off(bp->count), cnt_off(bp->count);
@@ -639,32 +670,7 @@ static int oneshot_run(BatchPlan* bp, cudaStream_t stream) {
                       cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + cnt_off[0], 0, cnt_bytes, stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch descriptors");
-  OneShotStreams* S = nullptr;
-  int rc = oneshot_streams(&S);
-  if (rc) return rc;
-  {
-    std::lock_guard<std::mutex> lk(g_oneshot_mu);
-    e = cudaEventRecord(S->fork, stream);
-    for (int k = 0; k < kOneShotStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(S->s[k], S->fork, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "batch fork");
-    SampleIO none;
-    std::memset(&none, 0, sizeof(none));
-    for (int i = 0; i < bp->count && rc == QMC_OK; ++i) {
-      Plan* pl = bp->probs[i].get();
-      for (Launch& ln : pl->launches) {
-        double* partial = pl->ws.partial;
-        unsigned long long* counters = pl->ws.counters;
-        void* args[4] = {(void*)ln.params.data(), &partial, &counters, &none};
-        rc = launch_any(ln, ln.grid, args, S->s[i % kOneShotStreams]);
-        if (rc) break;
-      }
-    }
-    // join every internal stream back, even after a failed launch
-    for (int k = 0; k < kOneShotStreams; ++k) {
-      cudaEventRecord(S->join[k], S->s[k]);
-      cudaStreamWaitEvent(stream, S->join[k], 0);
-    }
-  }
+  int rc = launch_side_by_side(bp, nullptr, bp->count, stream);
   if (rc) return rc;
   FinalizeArgs* fin = bp->fin_dev;
   void* fargs[1] = {&fin};
@@ -672,6 +678,216 @@ static int oneshot_run(BatchPlan* bp, cudaStream_t stream) {
                        stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch final pass");
   return QMC_OK;
+}
+
+// ------------------------------------------------------ ladder walk --
+//
+// qmc_integrate_batch_to_tolerance.  Every problem's plan (kernel, shifts,
+// coefficients) is built once, on its own lattice; a later level only moves
+// the plan to the next lattice (plan_rebase: n, g, the reciprocal of n and
+// the launch shape), so a pass costs the launches of the problems that move
+// up, one final pass over them and one copy of the results.
+
+constexpr uint64_t kWalkWork = 1ull << 20;  // evaluations per CTA, as qmc_integrate_batch
+
+static int walk_cap(uint64_t n, int m, int sms) {
+  const uint64_t evals = n * (uint64_t)std::max(m, 1);
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>((evals + kWalkWork - 1) / kWalkWork, 4ull * sms));
+}
+
+// One pass: the listed problems' rules, their final pass, and every
+// problem's current result copied to res (host).
+static int walk_pass(BatchPlan* bp, const std::vector<int>& act, std::vector<FinalizeArgs>& fin,
+                     std::vector<qmc_result>& res, cudaStream_t stream) {
+  fin.resize(act.size());
+  for (size_t u = 0; u < act.size(); ++u) {
+    const int i = act[u];
+    const Plan* pl = bp->probs[i].get();
+    FinalizeArgs& A = fin[u];
+    std::memset(&A, 0, sizeof(A));
+    A.partial = pl->ws.partial;
+    A.nblk = pl->nblk;
+    A.m = pl->m;
+    A.is_complex = pl->is_complex;
+    A.groups = 1;
+    A.dn = (double)pl->n;
+    A.value_scale = pl->final_scale;
+    A.offset[0] = pl->offset[0];
+    A.offset[1] = pl->offset[1];
+    A.counters = pl->ws.counters;
+    A.result = bp->res_dev + i;
+    A.per_shift = bp->ps_dev + bp->ps_off[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(bp->fin_dev, fin.data(), fin.size() * sizeof(FinalizeArgs), cudaMemcpyHostToDevice,
+                                  stream);
+  if (e != cudaSuccess) return cuda_fail(e, "walk descriptors");
+  int rc = launch_side_by_side(bp, act.data(), (int)act.size(), stream);
+  if (rc) return rc;
+  FinalizeArgs* fd = bp->fin_dev;
+  void* fargs[1] = {&fd};
+  e = cudaLaunchKernel(finalize_batch_ptr(), dim3((unsigned)act.size()), dim3(256), fargs,
+                       (size_t)bp->max_m * 2 * sizeof(double), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "walk final pass");
+  e = cudaMemcpyAsync(res.data(), bp->res_dev, res.size() * sizeof(qmc_result), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "walk results");
+  return QMC_OK;
+}
+
+static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels, const uint64_t* ladder_n,
+                      const uint64_t* ladder_g, int32_t ladder_dim, double rel_tol, int32_t criterion,
+                      qmc_result* out, int32_t* level_out, int32_t* passes_out, cudaStream_t stream) {
+  if (count < 1 || count > 65536) return fail(QMC_EINVAL, "batch count=%d outside [1, 65536]", count);
+  if (!problems || !out) return fail(QMC_EINVAL, "null problems or results");
+  if (levels < 0 || levels > 64 || (levels > 0 && (!ladder_n || !ladder_g)))
+    return fail(QMC_EINVAL, "ladder of %d lattices (0..64, with n and g)", levels);
+  if (ladder_dim < 1 || ladder_dim > QMC_DMAX) return fail(QMC_EINVAL, "ladder_dim=%d outside [1, %d]", ladder_dim, QMC_DMAX);
+  if (!(rel_tol > 0.0)) return fail(QMC_EINVAL, "rel_tol must be > 0");
+  if (criterion != QMC_WALK_SUM && criterion != QMC_WALK_EACH) return fail(QMC_EINVAL, "unknown criterion %d", criterion);
+  for (int l = 0; l < levels; ++l) {
+    const uint64_t n = ladder_n[l];
+    if (n < 2 || n >= (1ull << 31) || (l > 0 && n <= ladder_n[l - 1]))
+      return fail(QMC_EINVAL, "ladder n[%d]=%llu: sizes must increase within [2, 2^31)", l, (unsigned long long)n);
+    for (int i = 0; i < ladder_dim; ++i) {
+      const uint64_t gi = ladder_g[(size_t)l * ladder_dim + i];
+      if (gi < 1 || gi >= n) return fail(QMC_EINVAL, "ladder g[%d][%d]=%llu outside [1, n)", l, i, (unsigned long long)gi);
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    if (problems[i].d > ladder_dim) return fail(QMC_EINVAL, "problem %d: d=%d above ladder_dim", i, problems[i].d);
+  if (is_device_pointer(out)) return fail(QMC_EINVAL, "the results must be host memory");
+  const int sms = device_sms();
+  if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
+  BatchPlan bp;
+  int rc = batch_build(&bp, count, problems, kWalkWork);
+  if (rc) return rc;
+  // lattices of problem i: its own, then the ladder's entries above its n
+  std::vector<int> next(count), at(count, -1);
+  for (int i = 0; i < count; ++i) {
+    int l = 0;
+    while (l < levels && ladder_n[l] <= problems[i].n) ++l;
+    next[i] = l;
+  }
+  // slots: at most one resident wave of CTAs, and at most the cap of the largest lattice
+  size_t bytes = 0;
+  std::vector<size_t> part_off(count), cnt_off(count);
+  for (int i = 0; i < count; ++i) {
+    const Plan* pl = bp.probs[i].get();
+    int slots = pl->nblk;
+    if (next[i] < levels) {
+      const int wave = sms * std::max(pl->grid_occ, 1);
+      slots = std::max(slots, pl->grid_capped ? std::min(wave, walk_cap(ladder_n[levels - 1], pl->m, sms)) : wave);
+    }
+    part_off[i] = bytes;
+    bytes += (size_t)pl->m * slots * 2 * sizeof(double);
+  }
+  for (int i = 0; i < count; ++i) {
+    cnt_off[i] = bytes;
+    bytes += 2 * sizeof(unsigned long long);
+  }
+  const size_t cnt_bytes = bytes - cnt_off[0];
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t res_off = bytes;
+  bytes += (size_t)count * sizeof(qmc_result);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t ps_off = bytes;
+  bytes += (size_t)bp.total_m * 2 * sizeof(double);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t fin_off = bytes;
+  bytes += (size_t)count * sizeof(FinalizeArgs);
+  cudaError_t e = cudaMallocAsync(&bp.ws, bytes, stream);
+  if (e != cudaSuccess) {
+    bp.ws = nullptr;
+    cudaGetLastError();
+    return fail(QMC_ENOMEM, "walk workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  char* base = (char*)bp.ws;
+  bp.res_dev = (qmc_result*)(base + res_off);
+  bp.ps_dev = (double*)(base + ps_off);
+  bp.fin_dev = (FinalizeArgs*)(base + fin_off);
+  for (int i = 0; i < count; ++i) {
+    bp.probs[i]->ws.partial = (double*)(base + part_off[i]);
+    bp.probs[i]->ws.counters = (unsigned long long*)(base + cnt_off[i]);
+  }
+  e = cudaMemsetAsync(base + cnt_off[0], 0, cnt_bytes, stream);  // the final pass resets them after each read
+  if (e != cudaSuccess) rc = cuda_fail(e, "walk counters");
+  std::vector<int> act(count);
+  for (int i = 0; i < count; ++i) act[i] = i;
+  std::vector<FinalizeArgs> fin;
+  std::vector<qmc_result> res(count);
+  int passes = 0;
+  bool reached = false;
+  while (rc == QMC_OK) {
+    if (passes > 0)
+      for (int i : act) {
+        const int l = next[i];
+        Plan* pl = bp.probs[i].get();
+        rc = plan_rebase(pl, ladder_n[l], ladder_g + (size_t)l * ladder_dim, walk_cap(ladder_n[l], pl->m, sms));
+        if (rc) break;
+        at[i] = l;
+        next[i] = l + 1;
+      }
+    if (rc) break;
+    rc = walk_pass(&bp, act, fin, res, stream);
+    if (rc) break;
+    ++passes;
+    for (int i : act)
+      if (res[i].status != QMC_OK && res[i].status != QMC_ENONFINITE && res[i].status != QMC_EDEFORM) {
+        rc = fail(res[i].status, "problem %d failed with status %d", i, res[i].status);
+        break;
+      }
+    if (rc) break;
+    // next pass: the problems whose error is above their share of the tolerance
+    act.clear();
+    if (criterion == QMC_WALK_SUM) {
+      double sre = 0.0, sim = 0.0, e2 = 0.0;
+      for (int i = 0; i < count; ++i) {
+        sre += res[i].mean[0];
+        sim += res[i].mean[1];
+        e2 += res[i].err[0] * res[i].err[0] + res[i].err[1] * res[i].err[1];
+      }
+      const double mag = std::hypot(sre, sim);
+      if (mag > 0.0 && std::sqrt(e2) <= rel_tol * mag) {
+        reached = true;
+        break;
+      }
+      const double share = rel_tol * mag / std::sqrt((double)count);
+      for (int i = 0; i < count; ++i)
+        if (std::hypot(res[i].err[0], res[i].err[1]) > share && next[i] < levels) act.push_back(i);
+    } else {
+      bool all = true;
+      for (int i = 0; i < count; ++i) {
+        const double mag = std::hypot(res[i].mean[0], res[i].mean[1]);
+        if (mag > 0.0 && std::hypot(res[i].err[0], res[i].err[1]) <= rel_tol * mag) continue;
+        all = false;
+        if (next[i] < levels) act.push_back(i);
+      }
+      if (all) {
+        reached = true;
+        break;
+      }
+    }
+    if (act.empty()) break;
+  }
+  if (bp.ws) {
+    cudaFreeAsync(bp.ws, stream);
+    bp.ws = nullptr;
+  }
+  e = cudaStreamSynchronize(stream);
+  if (rc == QMC_OK && e != cudaSuccess) rc = cuda_fail(e, "walk synchronise");
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) {
+    out[i] = res[i];
+    if (level_out) level_out[i] = at[i];
+  }
+  if (passes_out) *passes_out = passes;
+  if (reached) return QMC_OK;
+  if (criterion == QMC_WALK_EACH)
+    for (int i = 0; i < count; ++i) {
+      const double mag = std::hypot(out[i].mean[0], out[i].mean[1]);
+      if (!(mag > 0.0 && std::hypot(out[i].err[0], out[i].err[1]) <= rel_tol * mag)) out[i].status = QMC_ETIMEOUT;
+    }
+  return fail(QMC_ETIMEOUT, "relative error %.3g not reached after %d passes", rel_tol, passes);
 }
 
 static int batch_execute(BatchPlan* bp, qmc_result* out, double* per_shift, cudaStream_t stream) {
@@ -782,6 +998,8 @@ int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* 
   // a specialised persistent kernel is also built for two CTAs per SM (128 registers)
   const int max_minc = pers && bp->pj_fn ? 2 : 1;
   int rc = QMC_OK;
+  const char* ve = std::getenv("QMC_TUNE_VERBOSE");  // per-candidate times on stderr
+  const bool verbose = ve && ve[0] == '1';
   // graph mode: evaluations per CTA 2^18..2^24; persistent mode: points per work item 2^14..2^18
   for (int minc = 1; minc <= max_minc && rc == QMC_OK; ++minc)
     for (int lw = pers ? 14 : 18; lw <= (pers ? 18 : 24) && rc == QMC_OK; ++lw) {
@@ -802,6 +1020,9 @@ int qmc_batch_plan_tune(qmc_batch_plan plan, const qmc_problem* problems, void* 
       }
       cudaStreamSynchronize(st);
       const bool got = !pers || minc == 1 || trial.pj_fn;  // a failed two-CTA build fell back: not a candidate
+      if (verbose)
+        std::fprintf(stderr, "batch tune: %s work=2^%d min_ctas=%d%s ms=%.4f (mean of 3 replays)\n",
+                     pers ? "persistent" : "graph", lw, pers ? minc : 0, got ? "" : " (not built)", tot / 3.0f);
       batch_release(&trial);
       if (got && tot > 0.0f && tot < best_ms) {
         best_ms = tot;
@@ -841,6 +1062,14 @@ int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* 
     for (int i = 0; i < bp.count; ++i)
       if (out[i].status != QMC_OK) return out[i].status;
   return rc;
+}
+
+int qmc_integrate_batch_to_tolerance(int32_t count, const qmc_problem* problems, int32_t levels,
+                                     const uint64_t* ladder_n, const uint64_t* ladder_g, int32_t ladder_dim,
+                                     double rel_tol, int32_t criterion, qmc_result* out, int32_t* level_out,
+                                     int32_t* passes_out, void* stream) {
+  return batch_walk(count, problems, levels, ladder_n, ladder_g, ladder_dim, rel_tol, criterion, out, level_out,
+                    passes_out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -49,6 +50,20 @@
 #include "plan.h"
 
 namespace qmc {
+
+// Estimator engine: QMC_CV_ENGINE=tcgen05 takes cv_tc5_kernel (contraction
+// by tcgen05.mma, basis in tensor memory), anything else cv_tc_kernel
+// (warp-level mma.sync).
+static bool cv_engine_tcgen05() {
+  const char* e = std::getenv("QMC_CV_ENGINE");
+  return e && std::strcmp(e, "tcgen05") == 0;
+}
+// QMC_CV_TEST_STALL=1: the tcgen05 kernel issues no MMA, so its bounded
+// waits run out and the call returns QMC_ETIMEOUT (tests the time-out path)
+static bool cv_stall_test() {
+  const char* e = std::getenv("QMC_CV_TEST_STALL");
+  return e && e[0] == '1';
+}
 
 // -------------------------------------------------------------- training --
 
@@ -357,16 +372,16 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
       poly_degree(f->U, d) > 1 || poly_degree(f->F, d) > 2)
     return fail(QMC_EUNSUPPORTED, "control variate: FP32EVAL U^-2 F^-1 sector with deg U <= 1, deg F <= 2");
   const int tr = t.kind == QMC_TRANSFORM_KOROBOV ? TR_KOROBOV : (t.kind == QMC_TRANSFORM_BAKER ? TR_BAKER : TR_NONE);
+  const bool tc5 = cv_engine_tcgen05();
   const void* func = nullptr;
   switch (d) {
-    case 1: func = cv_estimator_ptr<1>(tr, t.alpha); break;
-    case 2: func = cv_estimator_ptr<2>(tr, t.alpha); break;
-    case 3: func = cv_estimator_ptr<3>(tr, t.alpha); break;
-    case 4: func = cv_estimator_ptr<4>(tr, t.alpha); break;
-    case 5: func = cv_estimator_ptr<5>(tr, t.alpha); break;
-    case 6: func = cv_estimator_ptr<6>(tr, t.alpha); break;
-    case 7: func = cv_estimator_ptr<7>(tr, t.alpha); break;
-    case 8: func = cv_estimator_ptr<8>(tr, t.alpha); break;
+#define QMC_CV_CASE(DD) \
+  case DD:             \
+    func = tc5 ? cv_estimator5_ptr<DD>(tr, t.alpha) : cv_estimator_ptr<DD>(tr, t.alpha); \
+    break;
+    QMC_CV_CASE(1) QMC_CV_CASE(2) QMC_CV_CASE(3) QMC_CV_CASE(4) QMC_CV_CASE(5) QMC_CV_CASE(6) QMC_CV_CASE(7)
+    QMC_CV_CASE(8)
+#undef QMC_CV_CASE
   }
   if (!func) return fail(QMC_EUNSUPPORTED, "control variate: transform must be none, baker or Korobov 3");
   std::unique_ptr<CvParams> C(new CvParams());
@@ -385,6 +400,7 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
   const int npar = kCvR * d * kCvK;
   for (int q = 0; q < npar; ++q) C->a[q] = a[q];
   C->freq = (float)cfg->freq_step;
+  C->stall_test = tc5 && cv_stall_test() ? 1 : 0;
   double gint = 0.0;
   for (int r = 0; r < kCvR; ++r) {
     double p = 1.0;
@@ -433,6 +449,12 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
   if (rc) return rc;
   rc = plan_execute(&pl, out, per_shift, st);
   plan_free(&pl, st);
+  // the tcgen05 kernel reports a bounded wait that ran out in bit 63 of the
+  // second counter (no deformation in these plans)
+  if (tc5 && !is_device_pointer(out) && (out->deform_violations & (1ull << 63))) {
+    out->status = QMC_ETIMEOUT;
+    return fail(QMC_ETIMEOUT, "control variate: a tensor-core wait timed out");
+  }
   return rc;
 }
 

@@ -114,6 +114,7 @@ struct CvParams {
   float a[kCvR * kCvDMax * kCvK];   // [r][i][k] with row stride d (packed for the actual d)
   float freq;                       // F: 1 -> cos(pi k x), 2 -> cos(2 pi k x)
   float sigma;                      // coordinate scale of the fixed-point path (z = zf sigma)
+  int32_t stall_test;               // tcgen05 kernel: 1 = issue no MMA, so every wait runs out (test hook)
 };
 
 template <int D, int TR, int ALPHA>
@@ -486,9 +487,12 @@ __global__ void __launch_bounds__(kCvFitWarps * 32)
 template <int D>
 const void* cv_estimator_ptr(int tr, int alpha);
 template <int D>
+const void* cv_estimator5_ptr(int tr, int alpha);  // tcgen05 contraction (cv_tc5.cuh)
+template <int D>
 const void* cv_fit_ptr();
 #define QMC_DECL_CV(D) \
   template <> const void* cv_estimator_ptr<D>(int, int); \
+  template <> const void* cv_estimator5_ptr<D>(int, int); \
   template <> const void* cv_fit_ptr<D>();
 QMC_DECL_CV(1) QMC_DECL_CV(2) QMC_DECL_CV(3) QMC_DECL_CV(4) QMC_DECL_CV(5) QMC_DECL_CV(6) QMC_DECL_CV(7) QMC_DECL_CV(8)
 #undef QMC_DECL_CV

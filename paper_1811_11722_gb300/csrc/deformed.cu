@@ -104,15 +104,15 @@ static int build_def(Plan* pl, int32_t d, uint64_t n, int32_t m, const uint64_t*
     base.value_scale = fast ? std::pow((double)base.kor[7], (double)d)
                             : std::pow((double)base.kor[7] / std::pow(4.0, (double)base.alpha), (double)d);
   base.check_finite = 1;
-  int nblk = 0, L = 0;
+  int nblk = 0, L = 0, occ = 0;
   uint64_t tiles = 0;
-  int rc = choose_grid(func, 0, n, nblk, L, tiles, tune.occupancy);
+  int rc = grid_occupancy(func, 0, tune.occupancy, occ);
   if (rc) return rc;
-  if (tune.L > 0) {
-    L = tune.L;
-    tiles = (n + (uint64_t)kThreads * L - 1) / ((uint64_t)kThreads * L);
-    nblk = (int)std::min<uint64_t>((uint64_t)nblk, tiles);
-  }
+  rc = grid_shape(occ, n, 0, tune.L, nblk, L, tiles);
+  if (rc) return rc;
+  pl->param_kind = sizeof(R) == 4 ? 1 : 2;
+  pl->grid_occ = occ;
+  pl->grid_capped = false;  // one resident wave whatever the caller's cap
   base.L = L;
   base.tiles = tiles;
   base.nblk = nblk;

@@ -75,6 +75,11 @@ struct Plan {
   cudaEvent_t ev_after = nullptr;
   TuneChoice tune{};
   SavedProblem saved;
+  // what plan_rebase needs to move the plan to another lattice
+  int param_kind = 0;       // launches hold RuleParams<float> (1), RuleParams<double> (2),
+                            // GeneralParams<float> (3), GeneralParams<double> (4); 0: fixed lattice
+  int grid_occ = 1;         // CTAs per SM the launch shape assumes
+  bool grid_capped = true;  // the launch shape honours a cap on CTAs (rule plans; not deformed ones)
 };
 
 int fail(int code, const char* fmt, ...);
@@ -92,6 +97,13 @@ void korobov_coefs(int alpha, double* kor);
 uint64_t shift_fixed64(double delta);
 int choose_grid(const void* func, size_t smem, uint64_t n, int& nblk, int& L, uint64_t& tiles,
                 int occupancy_override);
+int grid_occupancy(const void* func, size_t smem, int occupancy_override, int& occ);
+int grid_shape(int occ, uint64_t n, int max_ctas, int fixed_L, int& nblk, int& L, uint64_t& tiles);
+// Move a built plan to the lattice (n, g) of the same dimension: lattice
+// fields and launch shape of every launch (max_ctas as TuneChoice::max_ctas);
+// kernels, shifts and coefficients are kept.  QMC_EUNSUPPORTED for plans
+// whose launches are not rule launches (param_kind 0).
+int plan_rebase(Plan* pl, uint64_t n, const uint64_t* g, int max_ctas);
 
 template <typename R>
 void fill_common(RuleParams<R>& P, int32_t d, uint64_t n, const uint64_t* g, const qmc_transform& t,

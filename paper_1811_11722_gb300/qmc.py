@@ -111,6 +111,8 @@ def lib():
             L.qmc_integrate_to_tolerance.argtypes = [i32, i32, vp, vp, i32, vp, qmc_transform, P_int,
                                                      ctypes.c_double, vp, ctypes.POINTER(i32), vp]
             L.qmc_integrate_batch.argtypes = [i32, vp, vp, vp, vp]
+            L.qmc_integrate_batch_to_tolerance.argtypes = [i32, vp, i32, vp, vp, i32, ctypes.c_double, i32, vp, vp,
+                                                           ctypes.POINTER(i32), vp]
             L.qmc_batch_plan_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
             L.qmc_batch_plan_create_persistent.argtypes = [i32, vp, ctypes.c_uint32, ctypes.POINTER(vp)]
             L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
@@ -148,7 +150,8 @@ def lib():
                          "qmc_integrate_to_tolerance", "qmc_integrate_eps", "qmc_eps_plan_create",
                          "qmc_sample_points_eps", "qmc_integrate_multi", "qmc_multi_plan_create", "qmc_make_lattice_embedded",
                          "qmc_integrate_extensible", "qmc_batch_plan_create_persistent",
-                         "qmc_integrate_cv_to_tolerance", "qmc_batch_plan_describe"):
+                         "qmc_integrate_cv_to_tolerance", "qmc_batch_plan_describe",
+                         "qmc_integrate_batch_to_tolerance"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -359,6 +362,29 @@ def qmc_integrate_batch(problems, stream=0, want_per_shift=False):
                                    _ptr(ps), ctypes.c_void_p(stream))
     _check(rc, allow_warnings=True)
     return list(res), ps
+
+
+WALK_SUM, WALK_EACH = 0, 1
+
+
+def qmc_integrate_batch_to_tolerance(problems, ladder_n, ladder_g, rel_tol, criterion=WALK_SUM, stream=0):
+    """Per-problem ladder walk, each pass one batched launch: problem i starts
+    on its own lattice, then takes the ladder lattices (ladder_n[l],
+    ladder_g[l, :d_i]) above its n.  Returns (results, level index per problem
+    (-1: its own lattice), passes, reached: bool)."""
+    b = _Batch(problems)
+    ladder_n = np.ascontiguousarray(np.asarray(ladder_n, dtype=np.uint64))
+    ladder_g = np.ascontiguousarray(np.asarray(ladder_g, dtype=np.uint64).reshape(len(ladder_n), -1))
+    res = (qmc_result * b.count)()
+    lv = np.zeros(b.count, dtype=np.int32)
+    passes = ctypes.c_int32(0)
+    rc = lib().qmc_integrate_batch_to_tolerance(b.count, ctypes.cast(b.arr, ctypes.c_void_p), len(ladder_n),
+                                                _ptr(ladder_n), _ptr(ladder_g), ladder_g.shape[1] if len(ladder_n) else 1,
+                                                float(rel_tol), int(criterion), ctypes.cast(res, ctypes.c_void_p),
+                                                _ptr(lv), ctypes.byref(passes), ctypes.c_void_p(stream))
+    if rc != QMC_ETIMEOUT:
+        _check(rc, allow_warnings=True)
+    return list(res), lv, int(passes.value), rc != QMC_ETIMEOUT
 
 
 class BatchPlan:

@@ -275,3 +275,33 @@ def test_embedded_lattice_validation(Q, args):
     with pytest.raises(Q.QmcError) as ei:
         Q.qmc_make_lattice_embedded(d, kmin, K, np.ones(max(d, 1)))
     assert ei.value.status == Q.QMC_EINVAL
+
+
+@pytest.mark.parametrize("case", ["decreasing", "g_out_of_range", "dim_below_d", "criterion", "tol", "levels"])
+def test_batch_walk_validation(Q, case):
+    """The batched ladder walk checks its ladder and options on the host,
+    before any device work (so these run without a GPU)."""
+    d, n, m = 3, 101, 4
+    coef = np.array([1.0, 0.5])
+    expo = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.uint8)
+    f = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP32EVAL, (coef, expo), (coef, expo))
+    probs = [(d, n, m, np.arange(1, d + 1, dtype=np.uint64), np.full((m, d), 0.25), Q.transform("baker"), f)]
+    ladder_n = np.array([211, 401, 809], dtype=np.uint64)
+    ladder_g = np.tile(np.arange(1, 5, dtype=np.uint64), (3, 1))
+    tol, crit = 1e-6, Q.WALK_SUM
+    if case == "decreasing":
+        ladder_n = np.array([211, 809, 401], dtype=np.uint64)
+    elif case == "g_out_of_range":
+        ladder_g[1, 3] = 401
+    elif case == "dim_below_d":
+        ladder_g = ladder_g[:, :2].copy()
+    elif case == "criterion":
+        crit = 2
+    elif case == "tol":
+        tol = 0.0
+    elif case == "levels":
+        ladder_n = np.arange(1000, 1000 + 65, dtype=np.uint64)
+        ladder_g = np.ones((65, 4), dtype=np.uint64)
+    with pytest.raises(Q.QmcError) as ei:
+        Q.qmc_integrate_batch_to_tolerance(probs, ladder_n, ladder_g, tol, crit)
+    assert ei.value.status == Q.QMC_EINVAL

@@ -1,5 +1,6 @@
 """GPU parity of the control-variate estimator Q[f - g] + int g (tensor-core
-surrogate, cv_tc_kernel) against the oracle, for every transform it takes.
+surrogate: cv_tc_kernel with warp-level MMA, cv_tc5_kernel with tcgen05 and
+the basis in tensor memory) against the oracle, for every transform it takes.
 
 Tolerances.  h = f(z) prod w is the FP32 sector path's value (per shift the
 oracle's Q^(k)[h] within 2e-7 relative, as for the plain FP32 path).  The
@@ -28,6 +29,14 @@ def Q():
     from paper_1811_11722_gb300 import build, qmc
     build.build_library()
     return qmc
+
+
+@pytest.fixture(params=["mma", "tcgen05"])
+def engine(request, monkeypatch):
+    """The estimator's contraction: warp-level mma.sync (cv_tc_kernel) or
+    tcgen05.mma with the basis in tensor memory (cv_tc5_kernel)."""
+    monkeypatch.setenv("QMC_CV_ENGINE", request.param)
+    return request.param
 
 
 def _cfg(Q, steps=300, freq=1, seed=7):
@@ -67,7 +76,7 @@ def _transform(Q, p):
     (3, "korobov", 20011, 9),
     (1, "baker", 10007, 2),
 ])
-def test_cv_estimator_matches_oracle(Q, oracle_lib, nthreads, d, transform, n, m):
+def test_cv_estimator_matches_oracle(Q, oracle_lib, nthreads, engine, d, transform, n, m):
     p = _problem(d, n, m, transform, seed=100 + d)
     g = I.random_generating_vector(I.SplitMix64(200 + d), d, n)
     a = _params(oracle_lib, d, seed=300 + d)
@@ -85,14 +94,14 @@ def test_cv_estimator_matches_oracle(Q, oracle_lib, nthreads, d, transform, n, m
     quad_gpu = ps[:, 0] - ps[:, 1]
     quad_ref = ref_cv - ref_plain
     dev_quad = np.max(np.abs(quad_gpu - quad_ref)) / abs(gint)
-    print(f"d={d} {transform} n={n}: plain {dev_plain:.2e}, cv {dev_cv:.2e}, surrogate quadrature {dev_quad:.2e} "
+    print(f"{engine} d={d} {transform} n={n}: plain {dev_plain:.2e}, cv {dev_cv:.2e}, surrogate quadrature {dev_quad:.2e} "
           f"(int g - Q[g] ~ {np.max(np.abs(quad_ref)) / abs(gint):.1e} of int g)")
     assert dev_plain <= 2e-7
     assert dev_cv <= 2e-7
     assert dev_quad <= 5e-8
 
 
-def test_cv_estimator_freq2_and_zero_surrogate(Q, oracle_lib, nthreads):
+def test_cv_estimator_freq2_and_zero_surrogate(Q, oracle_lib, nthreads, engine):
     """The cos(2 pi k z) basis against the oracle; and a surrogate that is
     identically zero gives the plain rule's values exactly (same h, nothing
     subtracted)."""
@@ -141,7 +150,7 @@ def test_cv_gain_by_transform(Q):
 
 
 @pytest.mark.slow
-def test_cv_estimator_full_size(Q, oracle_lib, nthreads):
+def test_cv_estimator_full_size(Q, oracle_lib, nthreads, engine):
     """The estimator at the size the benchmark times it (configuration-5
     integrand, d = 8, Korobov 3, n = 16777213; two shifts, one launch): both
     per-shift sums against the oracle over all 16.7M points, and the
@@ -159,7 +168,7 @@ def test_cv_estimator_full_size(Q, oracle_lib, nthreads):
     dev_plain = np.max(np.abs(ps[:, 1] - ref_plain) / np.abs(ref_plain))
     dev_cv = np.max(np.abs(ps[:, 0] - ref_cv) / (np.abs(ref_plain) + abs(gint)))
     dev_quad = np.max(np.abs((ps[:, 0] - ps[:, 1]) - (ref_cv - ref_plain))) / abs(gint)
-    print(f"full size: plain {dev_plain:.2e}, cv {dev_cv:.2e}, surrogate quadrature {dev_quad:.2e}")
+    print(f"{engine} full size: plain {dev_plain:.2e}, cv {dev_cv:.2e}, surrogate quadrature {dev_quad:.2e}")
     assert dev_plain <= 2e-7 and dev_cv <= 2e-7 and dev_quad <= 5e-8
 
 
@@ -239,3 +248,26 @@ def test_cv_walk_keeps_a_winning_surrogate(Q):
         assert judge["predicted_s_cv"] < judge["predicted_s_plain"], judge
     rc, _ = Q.qmc_integrate_cv(d, ns[lvl], p.m, gs[lvl:lvl + 1], p.shifts, t, f, cfg, a)
     assert r.mean[0] == rc.mean[0] and r.err[0] == rc.err[0]
+
+
+def test_tcgen05_wait_runs_out_and_reports(Q, oracle_lib, monkeypatch):
+    """The tcgen05 estimator's waits are bounded.  With no MMA issued
+    (QMC_CV_TEST_STALL=1) every wait on the MMA's mbarrier runs out: the
+    kernel's groups leave together, free their tensor memory and flag the
+    launch, and the call returns QMC_ETIMEOUT.  The next call on the same
+    context gives the same values as the call before."""
+    monkeypatch.setenv("QMC_CV_ENGINE", "tcgen05")
+    d, n, m = 2, 1009, 2
+    p = _problem(d, n, m, "baker", seed=5)
+    g = I.random_generating_vector(I.SplitMix64(6), d, n)
+    a = _params(oracle_lib, d, seed=7)
+    f = Q.integrand_from_problem(p, "fp32")
+    args = (d, n, m, g, p.shifts, _transform(Q, p), f, _cfg(Q), a)
+    before = Q.qmc_integrate_cv(*args)[1]
+    monkeypatch.setenv("QMC_CV_TEST_STALL", "1")
+    with pytest.raises(Q.QmcError) as ei:
+        Q.qmc_integrate_cv(*args)
+    assert ei.value.status == Q.QMC_ETIMEOUT
+    monkeypatch.delenv("QMC_CV_TEST_STALL")
+    after = Q.qmc_integrate_cv(*args)[1]
+    assert np.array_equal(before, after)

@@ -576,6 +576,82 @@ def test_batch_plan_graph_replay_and_tune(Q):
     bp.destroy()
 
 
+def _python_batch_walk(Q, tuples, ladder_n, ladder_g, tol, criterion):
+    """The walk of qmc_integrate_batch_to_tolerance written with one
+    qmc_integrate_batch call per pass (same lattices, same decisions)."""
+    S, L = len(tuples), len(ladder_n)
+    nxt = [int(np.searchsorted(ladder_n, t[1], side="right")) for t in tuples]
+    at = [-1] * S
+    cur = list(tuples)
+    res = [None] * S
+    act, passes, reached = list(range(S)), 0, False
+    while True:
+        if passes:
+            for i in act:
+                l = nxt[i]
+                d = cur[i][0]
+                cur[i] = (d, int(ladder_n[l]), cur[i][2], ladder_g[l, :d].copy()) + tuple(cur[i][4:])
+                at[i], nxt[i] = l, l + 1
+        rs, _ = Q.qmc_integrate_batch([cur[i] for i in act])
+        for i, r in zip(act, rs):
+            res[i] = r
+        passes += 1
+        mag = [math.hypot(r.mean[0], r.mean[1]) for r in res]
+        err = [math.hypot(r.err[0], r.err[1]) for r in res]
+        if criterion == Q.WALK_SUM:
+            tot = math.hypot(sum(r.mean[0] for r in res), sum(r.mean[1] for r in res))
+            if tot > 0 and math.sqrt(sum(e * e for e in err)) <= tol * tot:
+                reached = True
+                break
+            share = tol * tot / math.sqrt(S)
+            act = [i for i in range(S) if err[i] > share and nxt[i] < L]
+        else:
+            ok = [mag[i] > 0 and err[i] <= tol * mag[i] for i in range(S)]
+            if all(ok):
+                reached = True
+                break
+            act = [i for i in range(S) if not ok[i] and nxt[i] < L]
+        if not act:
+            break
+    return res, at, passes, reached
+
+
+@pytest.mark.parametrize("criterion,tol", [("sum", 3e-8), ("each", 2e-7), ("sum", 1e-15)])
+def test_batch_walk_matches_per_pass_batches(Q, criterion, tol):
+    """The batched ladder walk (plans built once, moved to each new lattice)
+    against the same walk made of one qmc_integrate_batch per pass: the same
+    passes and final lattices, and bit-identical results.  The batch mixes
+    FP32 sectors (baker, Korobov 3), an FP64 separable problem and a deformed
+    FP64 problem (whose launch shape ignores the CTA cap); the last case's
+    tolerance cannot be met, so the ladder runs out."""
+    crit = Q.WALK_SUM if criterion == "sum" else Q.WALK_EACH
+    sect = I.config3(count=12, transform="korobov", alpha=3)
+    probs = []
+    for s, p in enumerate(sect):
+        p.n = I.prev_prime(20000 + 9000 * s)
+        if s % 3 == 0:
+            p.transform, p.alpha = "baker", 0
+        probs.append(p)
+    probs.append(I.config1())
+    probs.append(_c4(n=20011, m=8))
+    gs = [I.random_generating_vector(I.SplitMix64(800 + i), p.d, p.n) for i, p in enumerate(probs)]
+    tuples = [_batch_tuple(Q, p, g) for p, g in zip(probs, gs)]
+    ladder_n = np.array([I.prev_prime(v) for v in (40000, 90000, 200000, 450000, 1000000, 2200000)], np.uint64)
+    ladder_g = np.stack([I.random_generating_vector(I.SplitMix64(900 + l), 8, int(n))
+                         for l, n in enumerate(ladder_n)]).astype(np.uint64)
+    res, lv, passes, reached = Q.qmc_integrate_batch_to_tolerance(tuples, ladder_n, ladder_g, tol, crit)
+    ref, at, ref_passes, ref_reached = _python_batch_walk(Q, tuples, ladder_n, ladder_g, tol, crit)
+    assert passes == ref_passes and reached == ref_reached
+    assert list(lv) == at
+    assert passes >= 2  # at least one move to a ladder lattice
+    for r, q in zip(res, ref):
+        assert r.mean[0] == q.mean[0] and r.mean[1] == q.mean[1]
+        assert r.err[0] == q.err[0] and r.err[1] == q.err[1]
+        assert r.nonfinite == q.nonfinite
+    if tol < 1e-12:
+        assert not reached and passes >= 3
+
+
 def test_persistent_batch_matches_oracle_and_graph(Q, oracle_lib, nthreads):
     """One persistent launch over a mixed batch of FP32 sectors (d = 1..8;
     baker, none and Korobov 3; m = 5, 16 and 21, so shift chunks of 8 with
