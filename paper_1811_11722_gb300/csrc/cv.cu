@@ -420,7 +420,9 @@ int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const 
   pl.mc = kCvMc;
   int nblk = 0, L = 0;
   uint64_t tiles = 0;
-  rc = choose_grid(func, 0, n, nblk, L, tiles, 0);
+  // the tcgen05 kernel is built for two resident CTAs per SM (its tensor
+  // memory and shared memory admit two, not three)
+  rc = tc5 ? grid_shape(2, n, 0, 0, nblk, L, tiles) : choose_grid(func, 0, n, nblk, L, tiles, 0);
   if (rc) return rc;
   C->base.L = L;
   C->base.tiles = tiles;

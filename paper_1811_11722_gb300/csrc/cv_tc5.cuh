@@ -17,8 +17,9 @@
 //   A (tensor memory, 128 lanes x 64 columns): columns 0..31 hold the TF32
 //     heads of T_0..T_31 of the lane's point (T_0's column is zero: degree 0
 //     stays out of the contraction), columns 32..63 the remainders
-//   B (shared memory, K-major, no swizzle): B[k][r] = a_rik (k >= 1), zero
-//     for k = 0, for all d dimensions, written once per CTA
+//   B (shared memory, K-major, no swizzle): B[k][r] = s a_rik with the sign
+//     s = (-1)^floor(k/4) that the basis pairs carry (k >= 1), zero for k = 0,
+//     for all d dimensions, written once per CTA
 //   D (tensor memory, 32 columns): the head products (ranks 0..15) and the
 //     remainder products (ranks 16..31 of the columns), each accumulated over
 //     four MMAs of K = 8 (N = 16)
@@ -51,6 +52,7 @@ constexpr int kTc5AHead = 0, kTc5ARem = 32, kTc5D = 64;
 constexpr int kTc5PadBytes = 40 * 1024;  // with the rest (~50 KB): two CTAs fit an SM, three do not
 constexpr unsigned long long kTc5TimeoutFlag = 1ull << 63;
 constexpr long long kTc5WaitCycles = 4ll << 30;  // about two seconds at 2 GHz
+constexpr uint32_t kTc5SuspendNs = 1000000;      // a waiting thread sleeps until the phase completes (at most 1 ms)
 
 // Instruction descriptor of tcgen05.mma.kind::tf32: D FP32 (bits 4-5 = 1),
 // A and B TF32 (bits 7-9, 10-12 = 2), both K-major, N >> 3 in bits 17-22,
@@ -119,11 +121,11 @@ __device__ __forceinline__ bool tc5_try_wait(uint64_t* mbar, uint32_t parity) {
   asm volatile(
       "{\n"
       ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       "selp.u32 %0, 1, 0, p;\n"
       "}\n"
       : "=r"(ok)
-      : "r"(smem_addr(mbar)), "r"(parity)
+      : "r"(smem_addr(mbar)), "r"(parity), "n"(kTc5SuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -176,7 +178,8 @@ __global__ void __launch_bounds__(kTc5Threads, 2)
     const int i = q / 512, w = q % 512;
     const int kb = w / 64, nb = (w / 32) & 1, row = (w / 4) & 7, kk = w & 3;
     const int r = nb * 8 + row, k = kb * 4 + kk;
-    bsm[q] = k == 0 ? 0.0f : C.a[(r * D + i) * kCvK + k];
+    const float sg = ((k >> 2) & 1) ? -1.0f : 1.0f;  // the basis pairs' sign s_(k/2)
+    bsm[q] = k == 0 ? 0.0f : sg * C.a[(r * D + i) * kCvK + k];
   }
   for (int q = threadIdx.x; q < D * kCvR; q += kThreads) {
     const int i = q / kCvR, r = q % kCvR;
@@ -254,37 +257,40 @@ __global__ void __launch_bounds__(kTc5Threads, 2)
         for (int r = 0; r < kCvR; ++r) prod[r] = 1.0f;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-          // basis row of this point: T_k(c) by the two interleaved chains
-          // T_{k+2} = 2 T_2 T_k - T_{k-2}, split into TF32 head and remainder
+          // basis row of this point, degrees (2u, 2u + 1) as one packed pair
+          // Q_u = s_u (T_2u, T_2u+1) with the signs s = (+, +, -, -, +, +, ...):
+          // from T_{k+2} = 2 T_2 T_k - T_{k-2} the pairs follow
+          // Q_{u+1} = (+/-) 2 T_2 Q_u + Q_{u-1} (+ from even u, - from odd u),
+          // one FFMA2 and no negation; s_u sits in the B operand.  Each value
+          // is split into its TF32 head and the exact remainder.
           const float c = cospif(C.freq * (zf[i] * C.sigma));
-          const float t2 = __fmaf_rn(2.0f * c, c, -1.0f), tt2 = 2.0f * t2;
-          float e0 = 1.0f, e1 = t2, o0 = c, o1 = __fmaf_rn(2.0f * c, t2, -c);  // T_0, T_2, T_1, T_3
+          const float t2 = __fmaf_rn(2.0f * c, c, -1.0f);
+          const float2 p2t2 = make_float2(2.0f * t2, 2.0f * t2), m2t2 = make_float2(-2.0f * t2, -2.0f * t2);
+          const float2 mone = make_float2(-1.0f, -1.0f);
+          float2 qprev = make_float2(1.0f, c);                                  // Q_0
+          float2 qcur = make_float2(t2, __fmaf_rn(2.0f * c, t2, -c));           // Q_1
 #pragma unroll
           for (int half = 0; half < 2; ++half) {
             float hd[16], rm[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {  // degrees 16 half + 2u (even chain) and + 1 (odd chain)
-              const int k = 16 * half + 2 * u;
-              float ve, vo;
-              if (k == 0) {
-                ve = 0.0f;  // degree 0: not contracted
-                vo = o0;
-              } else if (k == 2) {
-                ve = e1;
-                vo = o1;
+            for (int u = 0; u < 8; ++u) {  // pair 8 half + u: degrees 16 half + 2u, + 1
+              const int pu = 8 * half + u;
+              float2 q;
+              if (pu == 0) {
+                q = make_float2(0.0f, c);  // degree 0: not contracted
+              } else if (pu == 1) {
+                q = qcur;
               } else {
-                const float ne = __fmaf_rn(tt2, e1, -e0), no = __fmaf_rn(tt2, o1, -o0);
-                e0 = e1;
-                e1 = ne;
-                o0 = o1;
-                o1 = no;
-                ve = ne;
-                vo = no;
+                q = fma2(((pu - 1) & 1) ? m2t2 : p2t2, qcur, qprev);
+                qprev = qcur;
+                qcur = q;
               }
-              hd[2 * u] = tf32_head(ve);
-              hd[2 * u + 1] = tf32_head(vo);
-              rm[2 * u] = __fsub_rn(ve, hd[2 * u]);
-              rm[2 * u + 1] = __fsub_rn(vo, hd[2 * u + 1]);
+              const float2 h2 = make_float2(tf32_head(q.x), tf32_head(q.y));
+              const float2 r2 = fma2(h2, mone, q);
+              hd[2 * u] = h2.x;
+              hd[2 * u + 1] = h2.y;
+              rm[2 * u] = r2.x;
+              rm[2 * u + 1] = r2.y;
             }
             tc5_st16(tlane + kTc5AHead + 16 * half, hd);
             tc5_st16(tlane + kTc5ARem + 16 * half, rm);
