@@ -388,27 +388,44 @@ def extras(qmc, I, torch):
     cfg.R, cfg.K, cfg.freq_step, cfg.steps, cfg.lr, cfg.seed = 16, 32, 1, 2000, 1e-2, 7
     a, _ = qmc.qmc_cv_train(p.d, I.N_PILOT, gp, I.make_shifts(I.SplitMix64(54), 1, p.d)[0], qmc.transform("none"),
                             f_, cfg, stream=sh)
+    # the estimator's two engines: the contraction as warp-level mma.sync
+    # (cv_tc_kernel) and as tcgen05.mma with the basis in tensor memory
+    # (cv_tc5_kernel), the same arithmetic to FP32 accuracy
+    saved_engine = os.environ.get("QMC_CV_ENGINE")
     for name, tt in (("none", qmc.transform("none")), ("korobov3", qmc.transform("korobov", 3))):
-        res = {}
-        t = device_time(lambda: res.update(r=qmc.qmc_integrate_cv(p.d, p.n, p.m, g, p.shifts, tt, f_, cfg, a,
-                                                                  stream=sh)[0]), stream, reps=3)
         plan = qmc.Plan(p.d, p.n, p.m, g, p.shifts, tt, f_)
         tp = device_time(lambda: plan.execute(out=dev_res, stream=sh), stream, reps=3)
         plan.destroy()
-        r = res["r"]
-        mma_peak = out["peaks_measured"]["mma_sync_tf32_tflops"]  # the instruction the estimator issues
-        executed = p.d * 2048 * p.n * p.m / t / 1e12
-        out[f"c5_cv_estimator_{name}"] = {
-            "evals_per_s": p.n * p.m / t, "ms": 1e3 * t, "plain_rule_ms": 1e3 * tp, "cost_vs_plain_rule": t / tp,
-            "tf32_mma_tflops": executed,
-            "roofline": {"bound": "tensor", "achieved": executed, "peak": mma_peak, "unit": "TFLOP/s",
-                         "frac": executed / mma_peak,
-                         "algorithmic_tflops": p.d * 2 * 16 * 31 * p.n * p.m / t / 1e12,
-                         "peak_source": "measured warp-level TF32 mma.sync m16n8k8 throughput on this GPU "
-                                        "(qmc_measure_peaks); achieved counts both MMAs (basis head and remainder)",
-                         "tcgen05_tf32_reference_tflops": measured_peaks()["bf16_tflops"] * 1.1 / 2.25},
-            "err_cv": r.err[0], "err_plain_same_points": r.err[1], "gain_same_points": r.err[1] / r.err[0],
-            "note": "one TF32 m16n8k8 MMA (2048 flops) per point and dimension: head and remainder of the basis"}
+        row = {}
+        for engine in ("mma", "tcgen05"):
+            os.environ["QMC_CV_ENGINE"] = engine
+            res = {}
+            t = device_time(lambda: res.update(r=qmc.qmc_integrate_cv(p.d, p.n, p.m, g, p.shifts, tt, f_, cfg, a,
+                                                                      stream=sh)[0]), stream, reps=3)
+            r = res["r"]
+            executed = p.d * 2048 * p.n * p.m / t / 1e12
+            if engine == "mma":
+                peak = out["peaks_measured"]["mma_sync_tf32_tflops"]  # the instruction this kernel issues
+                src = ("measured warp-level TF32 mma.sync m16n8k8 throughput on this GPU (qmc_measure_peaks); "
+                       "achieved counts both MMAs (basis head and remainder)")
+            else:
+                peak = measured_peaks()["bf16_tflops"] * 1.1 / 2.25
+                src = ("dense TF32 tensor peak taken as the measured cuBLAS BF16 peak x 1.1/2.25 (nominal ratio); "
+                       "achieved counts both MMAs (basis head and remainder)")
+            row[engine] = {
+                "evals_per_s": p.n * p.m / t, "ms": 1e3 * t, "cost_vs_plain_rule": t / tp,
+                "roofline": {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
+                             "frac": executed / peak,
+                             "algorithmic_tflops": p.d * 2 * 16 * 31 * p.n * p.m / t / 1e12, "peak_source": src},
+                "err_cv": r.err[0], "err_plain_same_points": r.err[1], "mean_cv": r.mean[0]}
+        out[f"c5_cv_estimator_{name}"] = dict(
+            row, plain_rule_ms=1e3 * tp, speedup_tcgen05_vs_mma=row["mma"]["ms"] / row["tcgen05"]["ms"],
+            gain_same_points=row["mma"]["err_plain_same_points"] / row["mma"]["err_cv"],
+            note="2048 TF32 MMA flops per point and dimension: head and remainder of the 32-degree basis x 16 ranks")
+    if saved_engine is None:
+        os.environ.pop("QMC_CV_ENGINE", None)
+    else:
+        os.environ["QMC_CV_ENGINE"] = saved_engine
     # gain of the control variate per surrogate design and transform, from the
     # same points (n = 1048573, m = 16): plain error / control-variate error.
     # band > 0 holds the cosine degrees k >= band at zero (band-limited fit)

@@ -379,7 +379,12 @@ int qmc_cv_train(int32_t d, uint64_t n_pilot, const uint64_t* g_pilot, const dou
  * transform none, baker or Korobov 3.  f is evaluated as by the FP32 sector
  * kernels; g's per-dimension contraction runs on tensor cores (TF32 products
  * of the parameters with a head/remainder split of each basis value, degree 0
- * added in FP32), which keeps g to FP32 accuracy. */
+ * added in FP32), which keeps g to FP32 accuracy.  Engine: tcgen05.mma with
+ * the basis written to tensor memory (one 128-point tile per MMA, M = 128,
+ * N = 16), or warp-level mma.sync when QMC_CV_ENGINE=mma is set in the
+ * environment.  The tcgen05 kernel's waits on its MMAs are bounded (about
+ * 2 s); one that runs out makes the call return QMC_ETIMEOUT (out->status
+ * too), and the context stays usable. */
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_integrate_cv(int32_t d, uint64_t n, int32_t m, const uint64_t* g, const double* shifts,
                      qmc_transform t, const qmc_integrand* f, const qmc_cv_config* cfg, const float* a,

@@ -31,11 +31,12 @@
 // backward's operands are those registers transposed, so one step reads the
 // basis once and nothing else between the contractions goes through memory.
 //
-// Estimator kernel (cv_tc_kernel, cv_device.cuh).  The lattice rule with g
-// subtracted evaluates the surrogate's per-dimension contraction on tensor
-// cores too, as TF32 warp MMAs on a head/remainder split of each basis value,
-// which keeps FP32 accuracy: a BF16 basis there would bias Q[f - g] beyond
-// the rule's error.
+// Estimator kernels.  The lattice rule with g subtracted evaluates the
+// surrogate's per-dimension contraction on tensor cores too, in TF32 on a
+// head/remainder split of each basis value, which keeps FP32 accuracy (a BF16
+// basis there would bias Q[f - g] beyond the rule's error): cv_tc5_kernel
+// (cv_tc5.cuh) with tcgen05.mma and the basis in tensor memory, or
+// cv_tc_kernel (cv_device.cuh) with warp-level mma.sync.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,12 +52,12 @@
 
 namespace qmc {
 
-// Estimator engine: QMC_CV_ENGINE=tcgen05 takes cv_tc5_kernel (contraction
-// by tcgen05.mma, basis in tensor memory), anything else cv_tc_kernel
-// (warp-level mma.sync).
+// Estimator engine: cv_tc5_kernel (contraction by tcgen05.mma, basis in
+// tensor memory; the faster one on GB300) unless QMC_CV_ENGINE=mma, which
+// takes cv_tc_kernel (warp-level mma.sync).
 static bool cv_engine_tcgen05() {
   const char* e = std::getenv("QMC_CV_ENGINE");
-  return e && std::strcmp(e, "tcgen05") == 0;
+  return !(e && std::strcmp(e, "mma") == 0);
 }
 // QMC_CV_TEST_STALL=1: the tcgen05 kernel issues no MMA, so its bounded
 // waits run out and the call returns QMC_ETIMEOUT (tests the time-out path)

@@ -52,7 +52,6 @@ constexpr int kTc5AHead = 0, kTc5ARem = 32, kTc5D = 64;
 constexpr int kTc5PadBytes = 40 * 1024;  // with the rest (~50 KB): two CTAs fit an SM, three do not
 constexpr unsigned long long kTc5TimeoutFlag = 1ull << 63;
 constexpr long long kTc5WaitCycles = 4ll << 30;  // about two seconds at 2 GHz
-constexpr uint32_t kTc5SuspendNs = 1000000;      // a waiting thread sleeps until the phase completes (at most 1 ms)
 
 // Instruction descriptor of tcgen05.mma.kind::tf32: D FP32 (bits 4-5 = 1),
 // A and B TF32 (bits 7-9, 10-12 = 2), both K-major, N >> 3 in bits 17-22,
@@ -121,11 +120,11 @@ __device__ __forceinline__ bool tc5_try_wait(uint64_t* mbar, uint32_t parity) {
   asm volatile(
       "{\n"
       ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       "selp.u32 %0, 1, 0, p;\n"
       "}\n"
       : "=r"(ok)
-      : "r"(smem_addr(mbar)), "r"(parity), "n"(kTc5SuspendNs)
+      : "r"(smem_addr(mbar)), "r"(parity)
       : "memory");
   return ok != 0;
 }

@@ -34,7 +34,7 @@ def Q():
 @pytest.fixture(params=["mma", "tcgen05"])
 def engine(request, monkeypatch):
     """The estimator's contraction: warp-level mma.sync (cv_tc_kernel) or
-    tcgen05.mma with the basis in tensor memory (cv_tc5_kernel)."""
+    tcgen05.mma with the basis in tensor memory (cv_tc5_kernel, the default)."""
     monkeypatch.setenv("QMC_CV_ENGINE", request.param)
     return request.param
 
