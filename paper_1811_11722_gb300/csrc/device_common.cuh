@@ -284,8 +284,41 @@ __device__ __forceinline__ float coord_fx(uint32_t X, const float* kor, float& w
       static_assert(ALPHA == 3, "the fixed-point FP32 path takes Korobov weight 3");
       const float s = a * 0x1p-32f;
       w = __fmul_rn(w, __fmaf_rn(-s, s, s));  // the product of u = s (1 - s)
-      const float zs = korobov_lower<ALPHA>(s, kor);
-      return (int32_t)X < 0 ? 1.0f - zs : zs;
+      // z = s^4 q(s) on the lower half, 1 - s^4 q(s) (one rounding) on the upper
+      float q = kor[ALPHA];
+#pragma unroll
+      for (int k = ALPHA - 1; k >= 0; --k) q = __fmaf_rn(q, s, kor[k]);
+      const float s2 = __fmul_rn(s, s);
+      const float s4 = __fmul_rn(s2, s2);
+      return (int32_t)X < 0 ? __fmaf_rn(-s4, q, 1.0f) : __fmul_rn(s4, q);
+    }
+  }
+}
+
+// coord_fx for two shifts at once: the same operations per lane (so the same
+// values bit for bit) in packed f32x2 arithmetic; w holds the two products
+// of the Korobov factors.
+template <int TR, int ALPHA>
+__device__ __forceinline__ float2 coord_fx2(uint32_t Xa, uint32_t Xb, const float* kor, float2& w) {
+  if constexpr (TR == TR_NONE) {
+    return make_float2(__uint2float_rn(Xa), __uint2float_rn(Xb));
+  } else {
+    const float2 a = make_float2(fabsf(__int2float_rn((int32_t)Xa)), fabsf(__int2float_rn((int32_t)Xb)));
+    if constexpr (TR == TR_BAKER) {
+      return a;
+    } else {
+      static_assert(ALPHA == 3, "the fixed-point FP32 path takes Korobov weight 3");
+      const float2 s = mul2(a, make_float2(0x1p-32f, 0x1p-32f));
+      const float2 ms = mul2(s, make_float2(-1.0f, -1.0f));
+      w = mul2(w, fma2(ms, s, s));  // the products of u = s (1 - s)
+      float2 q = make_float2(kor[ALPHA], kor[ALPHA]);
+#pragma unroll
+      for (int k = ALPHA - 1; k >= 0; --k) q = fma2(q, s, make_float2(kor[k], kor[k]));
+      const float2 s2 = mul2(s, s);
+      const float2 s4 = mul2(s2, s2);
+      const float2 zs = mul2(s4, q);
+      const float2 up = fma2(mul2(s4, make_float2(-1.0f, -1.0f)), q, make_float2(1.0f, 1.0f));  // 1 - s^4 q
+      return make_float2((int32_t)Xa < 0 ? up.x : zs.x, (int32_t)Xb < 0 ? up.y : zs.y);
     }
   }
 }
@@ -382,6 +415,15 @@ __device__ __forceinline__ void fast2sum_add(float& hi, float& lo, float v) {
   float e = (hi - s) + v;
   hi = s;
   lo += e;
+}
+
+// fast2sum_add on two sums at once (packed f32x2), the same operations per
+// lane: hi - s is an FFMA2 with -1, exact like the scalar subtraction's rounding.
+__device__ __forceinline__ void fast2sum_add2(float2& hi, float2& lo, float2 v) {
+  const float2 s = add2(hi, v);
+  const float2 e = add2(fma2(s, make_float2(-1.0f, -1.0f), hi), v);
+  hi = s;
+  lo = add2(lo, e);
 }
 
 // TwoSum (Knuth): error-free for any ordering.

@@ -25,6 +25,12 @@ __device__ __noinline__ void persist_item(const RuleParams<float>& P, uint64_t j
   float2 run2[MC / 2];
 #pragma unroll
   for (int p = 0; p < MC / 2; ++p) run2[p] = make_float2(0.0f, 0.0f);
+  // under Korobov every value is folded on its own: packed on the compensated
+  // pairs directly, as the specialised kernels do
+  constexpr bool kPackFold = TR == TR_KOROBOV;
+  float2 hi2[kPackFold ? MC / 2 : 1], lo2[kPackFold ? MC / 2 : 1];
+#pragma unroll
+  for (int p = 0; p < (kPackFold ? MC / 2 : 1); ++p) hi2[p] = lo2[p] = make_float2(0.0f, 0.0f);
   unsigned nbad = 0;
   const uint64_t jt = j0 + threadIdx.x;
   if (jt < j1) {
@@ -46,18 +52,29 @@ __device__ __noinline__ void persist_item(const RuleParams<float>& P, uint64_t j
           nbad += (okb || 2 * p + 1 >= P.m_launch) ? 0u : 1u;
           v = make_float2(oka ? v.x : 0.0f, okb ? v.y : 0.0f);
         }
-        run2[p] = add2(run2[p], v);
+        if constexpr (kPackFold) fast2sum_add2(hi2[p], lo2[p], v);
+        else run2[p] = add2(run2[p], v);
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-      if ((s & fold_mask<TR>()) == fold_mask<TR>()) {
+      if (!kPackFold && (s & fold_mask<TR>()) == fold_mask<TR>()) {
         unpack_runs<MC>(run2, acc);
 #pragma unroll
         for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
       }
     }
   }
-  unpack_runs<MC>(run2, acc);
+  if constexpr (kPackFold) {
+#pragma unroll
+    for (int p = 0; p < MC / 2; ++p) {
+      acc[2 * p].hi = hi2[p].x;
+      acc[2 * p].lo = lo2[p].x;
+      acc[2 * p + 1].hi = hi2[p].y;
+      acc[2 * p + 1].lo = lo2[p].y;
+    }
+  } else {
+    unpack_runs<MC>(run2, acc);
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int kk = 0; kk < MC; ++kk) {

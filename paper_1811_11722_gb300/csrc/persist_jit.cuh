@@ -39,6 +39,12 @@ __device__ __forceinline__ void pj_sweep(uint64_t j0, uint64_t chunk, uint32_t i
   float2 run2[MC / 2];
 #pragma unroll
   for (int p = 0; p < MC / 2; ++p) run2[p] = make_float2(0.0f, 0.0f);
+  // under Korobov every value is folded on its own: packed on the compensated
+  // pairs directly (the same operations as the scalar fold)
+  constexpr bool kPackFold = TR == TR_KOROBOV;
+  float2 hi2[kPackFold ? MC / 2 : 1], lo2[kPackFold ? MC / 2 : 1];
+#pragma unroll
+  for (int p = 0; p < (kPackFold ? MC / 2 : 1); ++p) hi2[p] = lo2[p] = make_float2(0.0f, 0.0f);
   unsigned nbad = 0;
   const uint64_t jt = j0 + threadIdx.x;
   if (jt < j1) {
@@ -54,33 +60,43 @@ __device__ __forceinline__ void pj_sweep(uint64_t j0, uint64_t chunk, uint32_t i
 #pragma unroll
       for (int p = 0; p < MC / 2; ++p) {
         float2 z[D];
-        float wa = 1.0f, wb = 1.0f;
+        float2 w = make_float2(1.0f, 1.0f);
 #pragma unroll
         for (int i = 0; i < D; ++i)
-          z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + SP::shift(2 * p, i), SP::kor(), wa),
-                             coord_fx<TR, ALPHA>(base[i] + SP::shift(2 * p + 1, i), SP::kor(), wb));
+          z[i] = coord_fx2<TR, ALPHA>(base[i] + SP::shift(2 * p, i), base[i] + SP::shift(2 * p + 1, i), SP::kor(), w);
         float2 U, Fn;
         SP::eval2(z, U, Fn);
         float2 v = recip_neg2(mul2(mul2(U, U), Fn));
-        if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(make_float2(wa, wb)));
+        if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(w));
         if constexpr (SP::CHECK) {
           const bool oka = finite_(v.x), okb = finite_(v.y);
           nbad += (oka || 2 * p >= SP::M) ? 0u : 1u;  // padded rows are not counted
           nbad += (okb || 2 * p + 1 >= SP::M) ? 0u : 1u;
           v = make_float2(oka ? v.x : 0.0f, okb ? v.y : 0.0f);
         }
-        run2[p] = add2(run2[p], v);
+        if constexpr (kPackFold) fast2sum_add2(hi2[p], lo2[p], v);
+        else run2[p] = add2(run2[p], v);
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], SP::gstep(i), (uint32_t)SP::N);
-      if ((s & fold_mask<TR>()) == fold_mask<TR>()) {
+      if (!kPackFold && (s & fold_mask<TR>()) == fold_mask<TR>()) {
         unpack_runs<MC>(run2, acc);
 #pragma unroll
         for (int kk = 0; kk < MC; ++kk) acc[kk].fold();
       }
     }
   }
-  unpack_runs<MC>(run2, acc);
+  if constexpr (kPackFold) {
+#pragma unroll
+    for (int p = 0; p < MC / 2; ++p) {
+      acc[2 * p].hi = hi2[p].x;
+      acc[2 * p].lo = lo2[p].x;
+      acc[2 * p + 1].hi = hi2[p].y;
+      acc[2 * p + 1].lo = lo2[p].y;
+    }
+  } else {
+    unpack_runs<MC>(run2, acc);
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int kk = 0; kk < MC; ++kk) {

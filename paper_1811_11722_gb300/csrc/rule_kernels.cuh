@@ -166,15 +166,14 @@ constexpr bool kPacked = sizeof(R) == 4 && KU == 1 && KF == 2;
 template <int D, int TR, int ALPHA, int KU, int KF, class POLY>
 __device__ __forceinline__ float2 sector_value2(const RuleParams<float>& P, const uint32_t* base, int p) {
   float2 z[D];
-  float wa = 1.0f, wb = 1.0f;
+  float2 w = make_float2(1.0f, 1.0f);
 #pragma unroll
   for (int i = 0; i < D; ++i)
-    z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + POLY::shift(P, 2 * p, i), P.kor, wa),
-                       coord_fx<TR, ALPHA>(base[i] + POLY::shift(P, 2 * p + 1, i), P.kor, wb));
+    z[i] = coord_fx2<TR, ALPHA>(base[i] + POLY::shift(P, 2 * p, i), base[i] + POLY::shift(P, 2 * p + 1, i), P.kor, w);
   float2 U, Fn;
   POLY::template eval2<D, KU, KF>(P, z, U, Fn);
   float2 v = recip_neg2(mul2(mul2(U, U), Fn));
-  if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(make_float2(wa, wb)));
+  if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(w));
   return v;
 }
 
@@ -315,6 +314,12 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
   float2 run2[kPack ? MC / 2 : 1];
 #pragma unroll
   for (int p = 0; p < (kPack ? MC / 2 : 1); ++p) run2[p] = make_float2(0.0f, 0.0f);
+  // under Korobov every value is folded on its own (fold_mask): packed on the
+  // compensated pairs directly, the same operations as the scalar fold
+  constexpr bool kPackFold = kPack && !kSm && TR == TR_KOROBOV;
+  float2 hi2[kPackFold ? MC / 2 : 1], lo2[kPackFold ? MC / 2 : 1];
+#pragma unroll
+  for (int p = 0; p < (kPackFold ? MC / 2 : 1); ++p) hi2[p] = lo2[p] = make_float2(0.0f, 0.0f);
   extern __shared__ float2 accsm[];  // [MC][kThreads] (hi, lo), used when kSm
   if constexpr (kSm) {
 #pragma unroll
@@ -344,7 +349,8 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
             nbad += (okb || 2 * p + 1 >= P.m_launch) ? 0u : 1u;
             v = make_float2(oka ? v.x : 0.0f, okb ? v.y : 0.0f);
           }
-          run2[p] = add2(run2[p], v);
+          if constexpr (kPackFold) fast2sum_add2(hi2[p], lo2[p], v);
+          else run2[p] = add2(run2[p], v);
         }
       } else {
 #pragma unroll
@@ -360,7 +366,7 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-      if constexpr (sizeof(R) == 4) {
+      if constexpr (sizeof(R) == 4 && !kPackFold) {
         if ((s & fold_mask<TR>()) == fold_mask<TR>()) {
           if constexpr (kPack) unpack_runs<MC>(run2, acc);
 #pragma unroll
@@ -378,7 +384,17 @@ __device__ __forceinline__ void sector_body(const RuleParams<R>& P, double* __re
       }
     }
   }
-  if constexpr (kPack) unpack_runs<MC>(run2, acc);  // the last partial run
+  if constexpr (kPackFold) {
+#pragma unroll
+    for (int p = 0; p < MC / 2; ++p) {
+      acc[2 * p].hi = hi2[p].x;
+      acc[2 * p].lo = lo2[p].x;
+      acc[2 * p + 1].hi = hi2[p].y;
+      acc[2 * p + 1].lo = lo2[p].y;
+    }
+  } else if constexpr (kPack) {
+    unpack_runs<MC>(run2, acc);  // the last partial run
+  }
   if constexpr (kSm) {
 #pragma unroll
     for (int kk = 0; kk < MC; ++kk) {
@@ -823,11 +839,10 @@ __device__ __forceinline__ void eps_body2(const RuleParams<float>& P, double* __
 #pragma unroll
       for (int p = 0; p < MC / 2; ++p) {
         float2 z[D];
-        float wa = 1.0f, wb = 1.0f;
+        float2 wk = make_float2(1.0f, 1.0f);
 #pragma unroll
         for (int i = 0; i < D; ++i)
-          z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], P.kor, wa),
-                             coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p + 1][i], P.kor, wb));
+          z[i] = coord_fx2<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], base[i] + P.shiftx[2 * p + 1][i], P.kor, wk);
         float2 U, Fn;
         POLY::template eval2<D, 1, 2>(P, z, U, Fn);
         const float2 uu = mul2(U, U);
@@ -840,7 +855,7 @@ __device__ __forceinline__ void eps_body2(const RuleParams<float>& P, double* __
           L = make_float2(P.eps_b[0] * log_(U.x) + P.eps_b[1] * log_(-Fn.x),
                           P.eps_b[0] * log_(U.y) + P.eps_b[1] * log_(-Fn.y));
         }
-        if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(make_float2(wa, wb)));
+        if constexpr (TR == TR_KOROBOV) v = mul2(v, korobov_weight_fx2(wk));
 #pragma unroll
         for (int o = 0; o < NE; ++o) {
           if constexpr (CHECK) {
@@ -969,12 +984,11 @@ __device__ __forceinline__ void multi_body(const MultiParams& M, double* __restr
 #pragma unroll
       for (int p = 0; p < MC / 2; ++p) {
         float2 z[D];
-        float wa = 1.0f, wb = 1.0f;
+        float2 wk = make_float2(1.0f, 1.0f);
 #pragma unroll
         for (int i = 0; i < D; ++i)
-          z[i] = make_float2(coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], P.kor, wa),
-                             coord_fx<TR, ALPHA>(base[i] + P.shiftx[2 * p + 1][i], P.kor, wb));
-        float2 w = make_float2(wa, wb);
+          z[i] = coord_fx2<TR, ALPHA>(base[i] + P.shiftx[2 * p][i], base[i] + P.shiftx[2 * p + 1][i], P.kor, wk);
+        float2 w = wk;
         if constexpr (TR == TR_KOROBOV) w = korobov_weight_fx2(w);
 #pragma unroll
         for (int s = 0; s < SC; ++s) {
