@@ -361,6 +361,15 @@ def extras(qmc, I, torch):
     pp.destroy()
     # the generic persistent kernel (no run-time compilation: every sector's
     # dense coefficient slots staged in shared memory), tuned the same way
+    # the same batch under Korobov 3 (the transform of the walks to 1e-8)
+    sect_k = I.config3(transform="korobov", alpha=3)
+    tuples_k = [(q.d, q.n, q.m, gg, q.shifts, qmc.transform(q.transform, q.alpha), qmc.integrand_from_problem(q))
+                for q, gg in zip(sect_k, gs)]
+    bk = qmc.BatchPlan(tuples_k)
+    wk = bk.tune(sh)
+    tk = device_time(lambda: bk.execute(out=dev_res, stream=sh), stream, reps=3)
+    out["c3_batch_256_sectors_korobov3"] = {"evals_per_s_graph": evals / tk, "ms_graph": 1e3 * tk, "work_per_cta": wk}
+    bk.destroy()
     saved_env = os.environ.get("QMC_PERSIST_JIT")
     os.environ["QMC_PERSIST_JIT"] = "0"
     try:
@@ -457,25 +466,31 @@ def _short(cfg):
     return c
 
 
-def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279):
-    """The 256 Korobov-3 sectors summed to tol: every sector starts on its own
-    table prime and climbs the prime ladder (up to ladder_max) while its error
-    is above its share tol |sum| / sqrt(256) of the tolerance on the sum.
-    Batched: qmc_integrate_batch_to_tolerance, one batched launch per pass.
-    One by one: the same walk with one qmc_integrate call per sector and
-    level.  CBC vectors (d = 8, restricted to each sector's d) are host
-    precomputes and not timed."""
+def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279, start="own"):
+    """The 256 Korobov-3 sectors summed to tol.  Every sector starts on its own
+    table prime (start="own") or on the ladder's first prime (start="ladder")
+    and climbs the prime ladder (up to ladder_max) while its error is above
+    its share tol |sum| / sqrt(256) of the tolerance on the sum.  Batched:
+    qmc_integrate_batch_to_tolerance, one batched launch per pass.  One by
+    one: the same walk with one qmc_integrate call per sector and level.  CBC
+    vectors (d = 8, restricted to each sector's d) are host precomputes and
+    not timed."""
     import numpy as np
     from concurrent.futures import ThreadPoolExecutor
     sect = I.config3(transform="korobov", alpha=3)
     S = len(sect)
     ladder = [n for n in I.ladder_primes() if min(q.n for q in sect) < n <= ladder_max]
-    need = sorted(set(ladder) | {q.n for q in sect})
+    if start == "ladder":
+        n0 = [ladder[0]] * S
+        ladder = ladder[1:]
+    else:
+        n0 = [q.n for q in sect]
+    need = sorted(set(ladder) | set(n0))
     with ThreadPoolExecutor(max_workers=4) as ex:
         cbc = dict(zip(need, ex.map(lambda n: qmc.qmc_make_lattice(8, n, I.product_weights(8)), need)))
     fs = [qmc.integrand_from_problem(q) for q in sect]
     ts = [qmc.transform(q.transform, q.alpha) for q in sect]
-    tuples = [(q.d, q.n, q.m, cbc[q.n][:q.d].copy(), q.shifts, t_, f_) for q, t_, f_ in zip(sect, ts, fs)]
+    tuples = [(q.d, n, q.m, cbc[n][:q.d].copy(), q.shifts, t_, f_) for q, n, t_, f_ in zip(sect, n0, ts, fs)]
     ladder_n = np.array(ladder, dtype=np.uint64)
     ladder_g = np.stack([cbc[n] for n in ladder]).astype(np.uint64)
     # run-time compilation of every sector's kernel (independent of n): a precompute
@@ -492,16 +507,16 @@ def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279):
         walls.append(time.perf_counter() - t0)
     mean = np.array([r.mean[0] for r in rs])
     err = np.array([r.err[0] for r in rs])
-    ns = [q.n if l < 0 else ladder[l] for q, l in zip(sect, lv)]
+    ns = [n if l < 0 else ladder[l] for n, l in zip(n0, lv)]
     evals = 0
-    for q, l in zip(sect, lv):  # every lattice a sector visited
-        evals += q.n * q.m + sum(ladder[k] * q.m for k in range(int(np.searchsorted(ladder_n, q.n, "right")), l + 1))
+    for q, n, l in zip(sect, n0, lv):  # every lattice a sector visited
+        evals += n * q.m + sum(ladder[k] * q.m for k in range(int(np.searchsorted(ladder_n, n, "right")), l + 1))
     total, total_err = mean.sum(), math.sqrt(float(np.sum(err ** 2)))
     res["batched"] = {"rel_err": float(total_err / abs(total)), "sum": float(total), "wall_s": min(walls),
                       "wall_s_runs": walls, "passes": int(passes), "evals": int(evals), "reached": bool(reached),
                       "largest_n": int(max(ns)), "api": "qmc_integrate_batch_to_tolerance"}
     # one by one: the same decisions, one rule call per sector and level
-    steps = [[q.n] + [n for n in ladder if n > q.n] for q in sect]
+    steps = [[n] + [m_ for m_ in ladder if m_ > n] for n in n0]
     level = [0] * S
     mean = np.zeros(S)
     err = np.zeros(S)
@@ -529,8 +544,8 @@ def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279):
                          "passes": passes, "evals": int(evals), "reached": bool(total_err <= tol * abs(total)),
                          "largest_n": int(max(steps[i][level[i]] for i in range(S))), "api": "qmc_integrate per call"}
     res["batched"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched"]["wall_s"]
-    return {"c3_256_sectors_korobov3_sum_batched": res["batched"],
-            "c3_256_sectors_korobov3_sum_one_by_one": res["one_by_one"]}
+    tag = "c3_256_sectors_korobov3_sum" + ("_from_ladder_start" if start == "ladder" else "")
+    return {f"{tag}_batched": res["batched"], f"{tag}_one_by_one": res["one_by_one"]}
 
 
 def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
@@ -631,6 +646,9 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
     # one: one qmc_integrate call per refined sector.  Same lattices, shifts
     # and decisions.
     out.update(c3_time_to_tolerance(qmc, I, sh, tol))
+    # the same sum with every sector started on the ladder's first prime: the
+    # walk then chooses each sector's n from the bottom of the ladder
+    out.update(c3_time_to_tolerance(qmc, I, sh, tol, start="ladder"))
     # control variate on the d=8 sector (pilot n=65537, 2000 Adam steps).  The
     # library's judged walk (qmc_integrate_cv_to_tolerance): the first ladder
     # lattice is the pilot where the control variate and the plain rule meet at

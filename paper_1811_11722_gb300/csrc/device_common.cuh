@@ -290,7 +290,11 @@ __device__ __forceinline__ float coord_fx(uint32_t X, const float* kor, float& w
       for (int k = ALPHA - 1; k >= 0; --k) q = __fmaf_rn(q, s, kor[k]);
       const float s2 = __fmul_rn(s, s);
       const float s4 = __fmul_rn(s2, s2);
-      return (int32_t)X < 0 ? __fmaf_rn(-s4, q, 1.0f) : __fmul_rn(s4, q);
+      // one FMA for both halves: s^4 q + 0, or -s^4 q + 1 (the sign and the
+      // addend from X's sign bit by integer operations)
+      const float s4x = __uint_as_float(__float_as_uint(s4) ^ (X & 0x80000000u));
+      const float c = __int_as_float(((int32_t)X >> 31) & 0x3F800000);
+      return __fmaf_rn(s4x, q, c);
     }
   }
 }
@@ -309,16 +313,17 @@ __device__ __forceinline__ float2 coord_fx2(uint32_t Xa, uint32_t Xb, const floa
     } else {
       static_assert(ALPHA == 3, "the fixed-point FP32 path takes Korobov weight 3");
       const float2 s = mul2(a, make_float2(0x1p-32f, 0x1p-32f));
-      const float2 ms = mul2(s, make_float2(-1.0f, -1.0f));
-      w = mul2(w, fma2(ms, s, s));  // the products of u = s (1 - s)
+      w = mul2(w, fma2(make_float2(-s.x, -s.y), s, s));  // the products of u = s (1 - s)
       float2 q = make_float2(kor[ALPHA], kor[ALPHA]);
 #pragma unroll
       for (int k = ALPHA - 1; k >= 0; --k) q = fma2(q, s, make_float2(kor[k], kor[k]));
       const float2 s2 = mul2(s, s);
       const float2 s4 = mul2(s2, s2);
-      const float2 zs = mul2(s4, q);
-      const float2 up = fma2(mul2(s4, make_float2(-1.0f, -1.0f)), q, make_float2(1.0f, 1.0f));  // 1 - s^4 q
-      return make_float2((int32_t)Xa < 0 ? up.x : zs.x, (int32_t)Xb < 0 ? up.y : zs.y);
+      const float2 s4x = make_float2(__uint_as_float(__float_as_uint(s4.x) ^ (Xa & 0x80000000u)),
+                                     __uint_as_float(__float_as_uint(s4.y) ^ (Xb & 0x80000000u)));
+      const float2 c = make_float2(__int_as_float(((int32_t)Xa >> 31) & 0x3F800000),
+                                   __int_as_float(((int32_t)Xb >> 31) & 0x3F800000));
+      return fma2(s4x, q, c);  // s^4 q, or 1 - s^4 q on the upper half
     }
   }
 }
