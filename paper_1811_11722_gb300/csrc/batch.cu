@@ -556,6 +556,10 @@ static int batch_copy_out(BatchPlan* bp, qmc_result* out, double* per_shift, cud
 // caller's stream by an event and joined back before the final pass, so the
 // sectors still run side by side.
 constexpr int kOneShotStreams = 8;
+// evaluations per CTA of a one-shot batch (a problem gets ceil(n m / W) CTAs,
+// at most 4 per SM): the graph tuner's choice for the batched-sector workload
+// under Korobov 3, whose sectors cost about three times baker's per point
+constexpr uint64_t kOneShotWork = 1ull << 18;
 constexpr int kOneShotMaxDevices = 64;
 struct OneShotStreams {
   cudaStream_t s[kOneShotStreams] = {};
@@ -688,7 +692,7 @@ static int oneshot_run(BatchPlan* bp, cudaStream_t stream) {
 // the launch shape), so a pass costs the launches of the problems that move
 // up, one final pass over them and one copy of the results.
 
-constexpr uint64_t kWalkWork = 1ull << 20;  // evaluations per CTA, as qmc_integrate_batch
+constexpr uint64_t kWalkWork = kOneShotWork;  // evaluations per CTA, as qmc_integrate_batch
 
 static int walk_cap(uint64_t n, int m, int sms) {
   const uint64_t evals = n * (uint64_t)std::max(m, 1);
@@ -1049,7 +1053,7 @@ int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* 
   if (!out) return fail(QMC_EINVAL, "null result pointer");
   cudaStream_t st = (cudaStream_t)stream;
   BatchPlan bp;
-  int rc = batch_build(&bp, count, problems, 1ull << 20);
+  int rc = batch_build(&bp, count, problems, kOneShotWork);
   if (rc == QMC_OK) rc = oneshot_run(&bp, st);
   if (rc == QMC_OK) rc = batch_copy_out(&bp, out, per_shift, st);
   if (bp.ws) {
