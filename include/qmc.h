@@ -221,7 +221,7 @@ typedef struct {
 
 /* Many independent rules (e.g. the sectors of one integral: uneven d, n,
  * integrand) evaluated together.  Every problem keeps the kernel it would get
- * from qmc_integrate, with at most ceil(n m / 2^18) CTAs (at most 4 per SM);
+ * from qmc_integrate, with at most ceil(n m / 2^16) CTAs (at most 4 per SM);
  * the problems' launches go round-robin to internal streams forked from
  * `stream` (the GPU runs the sectors side by side), followed by one
  * final-pass launch for all problems.  The workspace comes from the

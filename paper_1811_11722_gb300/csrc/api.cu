@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cmath>
 #include <cstdarg>
@@ -300,10 +301,16 @@ void fill_common(RuleParams<R>& P, int32_t d, uint64_t n, const uint64_t* g, con
 
 // ------------------------------------------------------------------- plan --
 
+// SM count of the current device, read once per device (plans query it for
+// every launch shape, a walk for every sector and pass).
 static int device_sm_count() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (dev >= 0 && dev < kMaxDevices && (sms = cache[dev].load(std::memory_order_relaxed)) > 0) return sms;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (dev >= 0 && dev < kMaxDevices) cache[dev].store(sms, std::memory_order_relaxed);
   return sms;
 }
 

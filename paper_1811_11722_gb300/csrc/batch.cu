@@ -557,9 +557,11 @@ static int batch_copy_out(BatchPlan* bp, qmc_result* out, double* per_shift, cud
 // sectors still run side by side.
 constexpr int kOneShotStreams = 8;
 // evaluations per CTA of a one-shot batch (a problem gets ceil(n m / W) CTAs,
-// at most 4 per SM): the graph tuner's choice for the batched-sector workload
-// under Korobov 3, whose sectors cost about three times baker's per point
-constexpr uint64_t kOneShotWork = 1ull << 18;
+// at most 4 per SM).  Sectors run side by side on 8 streams, so a pass of
+// many medium sectors fills the GPU only if each gets enough CTAs: the C3
+// walks to 1e-8 under Korobov 3 took 52 / 51 / 50 ms at W = 2^18 / 2^17 /
+// 2^16 (49 / 44 / 42 ms when started at the ladder's bottom)
+constexpr uint64_t kOneShotWork = 1ull << 16;
 constexpr int kOneShotMaxDevices = 64;
 struct OneShotStreams {
   cudaStream_t s[kOneShotStreams] = {};
