@@ -325,9 +325,11 @@ def extras(qmc, I, torch):
     mp.destroy()
     for pl in singles:
         pl.destroy()
-    # configuration 3: 256 sectors in one graph replay vs the same plans one after another
+    # configuration 3: 256 sectors in one graph replay vs the same plans one after another,
+    # each sector on the CBC vector of its table prime (d = 8, restricted to its d)
     sect = I.config3()
-    gs = [I.random_generating_vector(I.SplitMix64(900 + i), q.d, q.n) for i, q in enumerate(sect)]
+    cbc = cbc8(qmc, I, {q.n for q in sect})
+    gs = [cbc[q.n][:q.d].copy() for q in sect]
     tuples = [(q.d, q.n, q.m, gg, q.shifts, qmc.transform(q.transform, q.alpha), qmc.integrand_from_problem(q))
               for q, gg in zip(sect, gs)]
     evals = sum(q.n * q.m for q in sect)
@@ -341,7 +343,7 @@ def extras(qmc, I, torch):
     out["c3_batch_256_sectors"] = {"evals": evals, "evals_per_s_graph": evals / t, "ms_graph": 1e3 * t,
                                    "ms_one_by_one": 1e3 * t1, "speedup_vs_one_by_one": t1 / t,
                                    "work_per_cta": w, "plan_build_s": build_s, "launches": bp.launches(),
-                                   "note": "generating vectors drawn at random (any valid g; throughput only)"}
+                                   "note": "CBC generating vectors (product weights 1/i^2, d = 8, restricted)"}
     for pl in plans:
         pl.destroy()
     # the same 256 sectors as one persistent launch: work items from a device
@@ -466,6 +468,19 @@ def _short(cfg):
     return c
 
 
+_CBC8 = {}  # n -> the d = 8 CBC vector (product weights 1/i^2); its first d components are the d-dim one
+
+
+def cbc8(qmc, I, ns):
+    """CBC vectors for the primes ns (host precompute, computed once per n)."""
+    from concurrent.futures import ThreadPoolExecutor
+    need = sorted(n for n in ns if n not in _CBC8)
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        for n, g in zip(need, ex.map(lambda n: qmc.qmc_make_lattice(8, n, I.product_weights(8)), need)):
+            _CBC8[n] = g
+    return _CBC8
+
+
 def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279, start="own"):
     """The 256 Korobov-3 sectors summed to tol.  Every sector starts on its own
     table prime (start="own") or on the ladder's first prime (start="ladder")
@@ -476,7 +491,6 @@ def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279, start="own"):
     vectors (d = 8, restricted to each sector's d) are host precomputes and
     not timed."""
     import numpy as np
-    from concurrent.futures import ThreadPoolExecutor
     sect = I.config3(transform="korobov", alpha=3)
     S = len(sect)
     ladder = [n for n in I.ladder_primes() if min(q.n for q in sect) < n <= ladder_max]
@@ -485,9 +499,7 @@ def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279, start="own"):
         ladder = ladder[1:]
     else:
         n0 = [q.n for q in sect]
-    need = sorted(set(ladder) | set(n0))
-    with ThreadPoolExecutor(max_workers=4) as ex:
-        cbc = dict(zip(need, ex.map(lambda n: qmc.qmc_make_lattice(8, n, I.product_weights(8)), need)))
+    cbc = cbc8(qmc, I, set(ladder) | set(n0))
     fs = [qmc.integrand_from_problem(q) for q in sect]
     ts = [qmc.transform(q.transform, q.alpha) for q in sect]
     tuples = [(q.d, n, q.m, cbc[n][:q.d].copy(), q.shifts, t_, f_) for q, n, t_, f_ in zip(sect, n0, ts, fs)]

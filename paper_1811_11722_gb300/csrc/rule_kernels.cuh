@@ -960,6 +960,14 @@ __device__ __forceinline__ void multi_body(const MultiParams& M, double* __restr
   float2 run2[SC][MC / 2];
   Acc<float> acc[SC][MC];
   unsigned nbad[SC];
+  // under Korobov every value is folded on its own: packed on the compensated
+  // pairs directly (the same operations as the scalar fold)
+  constexpr bool kPackFold = TR == TR_KOROBOV;
+  float2 hi2[SC][kPackFold ? MC / 2 : 1], lo2[SC][kPackFold ? MC / 2 : 1];
+#pragma unroll
+  for (int s = 0; s < SC; ++s)
+#pragma unroll
+    for (int p = 0; p < (kPackFold ? MC / 2 : 1); ++p) hi2[s][p] = lo2[s][p] = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int s = 0; s < SC; ++s) {
     nbad[s] = 0;
@@ -1002,12 +1010,13 @@ __device__ __forceinline__ void multi_body(const MultiParams& M, double* __restr
             nbad[s] += (okb || 2 * p + 1 >= P.m_launch) ? 0u : 1u;
             v = make_float2(oka ? v.x : 0.0f, okb ? v.y : 0.0f);
           }
-          run2[s][p] = add2(run2[s][p], v);
+          if constexpr (kPackFold) fast2sum_add2(hi2[s][p], lo2[s][p], v);
+          else run2[s][p] = add2(run2[s][p], v);
         }
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], P.gstep[i], n);
-      if ((st & fold_mask<TR>()) == fold_mask<TR>()) {
+      if (!kPackFold && (st & fold_mask<TR>()) == fold_mask<TR>()) {
 #pragma unroll
         for (int s = 0; s < SC; ++s) {
           unpack_runs<MC>(run2[s], acc[s]);
@@ -1022,7 +1031,17 @@ __device__ __forceinline__ void multi_body(const MultiParams& M, double* __restr
   unsigned long long bad_all = 0;
 #pragma unroll
   for (int s = 0; s < SC; ++s) {
-    unpack_runs<MC>(run2[s], acc[s]);
+    if constexpr (kPackFold) {
+#pragma unroll
+      for (int p = 0; p < MC / 2; ++p) {
+        acc[s][2 * p].hi = hi2[s][p].x;
+        acc[s][2 * p].lo = lo2[s][p].x;
+        acc[s][2 * p + 1].hi = hi2[s][p].y;
+        acc[s][2 * p + 1].lo = lo2[s][p].y;
+      }
+    } else {
+      unpack_runs<MC>(run2[s], acc[s]);
+    }
 #pragma unroll
     for (int kk = 0; kk < MC; ++kk) {
       double t = acc[s][kk].warp_total();
