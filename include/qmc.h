@@ -256,7 +256,7 @@ int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* 
  *   that should move up has a further lattice.
  *   levels          ladder lattices (0..64), increasing n in [2, 2^31)
  *   ladder_n        [levels];  ladder_g  [levels * ladder_dim], g in [1, n)
- *   ladder_dim      components per ladder vector, >= every problem's d
+ *   ladder_dim      components per ladder vector, >= every problem's d (when levels > 0)
  *   out             [count] results at the final lattices (host)
  *   level_out       optional [count]: ladder index of problem i's final
  *                   lattice, -1 for its own

@@ -759,7 +759,7 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
       if (gi < 1 || gi >= n) return fail(QMC_EINVAL, "ladder g[%d][%d]=%llu outside [1, n)", l, i, (unsigned long long)gi);
     }
   }
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count && levels > 0; ++i)
     if (problems[i].d > ladder_dim) return fail(QMC_EINVAL, "problem %d: d=%d above ladder_dim", i, problems[i].d);
   if (is_device_pointer(out)) return fail(QMC_EINVAL, "the results must be host memory");
   const int sms = device_sms();

@@ -374,12 +374,15 @@ def qmc_integrate_batch_to_tolerance(problems, ladder_n, ladder_g, rel_tol, crit
     (-1: its own lattice), passes, reached: bool)."""
     b = _Batch(problems)
     ladder_n = np.ascontiguousarray(np.asarray(ladder_n, dtype=np.uint64))
-    ladder_g = np.ascontiguousarray(np.asarray(ladder_g, dtype=np.uint64).reshape(len(ladder_n), -1))
+    if len(ladder_n) == 0:  # no ladder: every problem is evaluated on its own lattice only
+        ladder_g = np.zeros((0, 8), dtype=np.uint64)
+    else:
+        ladder_g = np.ascontiguousarray(np.asarray(ladder_g, dtype=np.uint64).reshape(len(ladder_n), -1))
     res = (qmc_result * b.count)()
     lv = np.zeros(b.count, dtype=np.int32)
     passes = ctypes.c_int32(0)
     rc = lib().qmc_integrate_batch_to_tolerance(b.count, ctypes.cast(b.arr, ctypes.c_void_p), len(ladder_n),
-                                                _ptr(ladder_n), _ptr(ladder_g), ladder_g.shape[1] if len(ladder_n) else 1,
+                                                _ptr(ladder_n), _ptr(ladder_g), ladder_g.shape[1],
                                                 float(rel_tol), int(criterion), ctypes.cast(res, ctypes.c_void_p),
                                                 _ptr(lv), ctypes.byref(passes), ctypes.c_void_p(stream))
     if rc != QMC_ETIMEOUT:

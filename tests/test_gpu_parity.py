@@ -652,6 +652,23 @@ def test_batch_walk_matches_per_pass_batches(Q, criterion, tol):
         assert not reached and passes >= 3
 
 
+def test_batch_walk_without_ladder_is_one_batch(Q):
+    """A walk with no ladder lattices evaluates every problem once, on its own
+    lattice, exactly as qmc_integrate_batch does, and reports whether the sum
+    met the tolerance."""
+    sect = I.config3(count=6)
+    for s, p in enumerate(sect):
+        p.n = I.prev_prime(30000 + 5000 * s)
+    gs = [I.random_generating_vector(I.SplitMix64(40 + i), p.d, p.n) for i, p in enumerate(sect)]
+    tuples = [_batch_tuple(Q, p, g) for p, g in zip(sect, gs)]
+    ref, _ = Q.qmc_integrate_batch(tuples)
+    for tol, want in ((1e-15, False), (1.0, True)):
+        res, lv, passes, reached = Q.qmc_integrate_batch_to_tolerance(tuples, [], np.zeros((0, 8), np.uint64), tol)
+        assert passes == 1 and reached == want and list(lv) == [-1] * len(sect)
+        for r, q in zip(res, ref):
+            assert r.mean[0] == q.mean[0] and r.err[0] == q.err[0]
+
+
 def test_persistent_batch_matches_oracle_and_graph(Q, oracle_lib, nthreads):
     """One persistent launch over a mixed batch of FP32 sectors (d = 1..8;
     baker, none and Korobov 3; m = 5, 16 and 21, so shift chunks of 8 with
