@@ -254,6 +254,13 @@ int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* 
  *       else move up every problem that does not
  *   (modulus of (re, im) for complex integrands).  Stops too when no problem
  *   that should move up has a further lattice.
+ *   QMC_WALK_PERSISTENT (or-ed into criterion): each pass is one launch of a
+ *   persistent kernel over work items of 2^15 points from all the problems
+ *   it refines.  The kernel is specialised at run time per (problem, chunk of
+ *   16 shifts) with the lattice as launch data, so one module serves every
+ *   pass (built on first use, then cached).  Problems as for
+ *   qmc_batch_plan_create_persistent (else QMC_EUNSUPPORTED); a problem's
+ *   results equal that plan's at the same lattice, bit for bit.
  *   levels          ladder lattices (0..64), increasing n in [2, 2^31)
  *   ladder_n        [levels];  ladder_g  [levels * ladder_dim], g in [1, n)
  *   ladder_dim      components per ladder vector, >= every problem's d (when levels > 0)
@@ -267,6 +274,7 @@ int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* 
  * deformation warnings stay in out[i].status. */
 #define QMC_WALK_SUM 0
 #define QMC_WALK_EACH 1
+#define QMC_WALK_PERSISTENT 0x10
 #ifndef __CUDACC_RTC__  /* function declarations are host-only */
 int qmc_integrate_batch_to_tolerance(int32_t count, const qmc_problem* problems, int32_t levels,
                                      const uint64_t* ladder_n, const uint64_t* ladder_g, int32_t ladder_dim,

@@ -451,12 +451,15 @@ static bool persist_jit_enabled() {
   return jit_enabled() && !(e && e[0] == '0');
 }
 
-// The specialised persistent kernel for the descriptors persist_build made
-// (kPjMc shift rows each); false if it cannot be built (the caller falls back).
-static bool persist_specialise(BatchPlan* bp) {
-  std::vector<PjSector> secs(bp->count);
+// The run-time specialisation's view of the descriptors persist_build made:
+// one PjSector per problem (its lattice, dense slots, Korobov coefficients)
+// and one PjDesc per descriptor (its shift rows).
+static void persist_descriptors(const BatchPlan* bp, std::vector<PjSector>* secs_out, std::vector<PjDesc>* descs_out) {
+  std::vector<PjSector>& secs = *secs_out;
+  std::vector<PjDesc>& descs = *descs_out;
+  secs.assign(bp->count, PjSector());
+  descs.assign(bp->pdesc.size(), PjDesc());
   std::vector<bool> have(bp->count, false);
-  std::vector<PjDesc> descs(bp->pdesc.size());
   for (size_t q = 0; q < bp->pdesc.size(); ++q) {
     const RuleParams<float>& P = bp->pdesc[q].P;
     const int s = bp->pdesc_sector[q];
@@ -491,6 +494,14 @@ static bool persist_specialise(BatchPlan* bp) {
       for (int t = 0; t < bp->count; ++t) std::memcpy(secs[t].kor, secs[s].kor, sizeof(secs[s].kor));
       break;
     }
+}
+
+// The specialised persistent kernel for the descriptors persist_build made
+// (kPjMc shift rows each); false if it cannot be built (the caller falls back).
+static bool persist_specialise(BatchPlan* bp) {
+  std::vector<PjSector> secs;
+  std::vector<PjDesc> descs;
+  persist_descriptors(bp, &secs, &descs);
   void* fn = nullptr;
   int occ = 0;
   if (jit_persist(secs, descs, bp->pj_min_ctas, &fn, &occ) != QMC_OK) return false;
@@ -740,6 +751,143 @@ static int walk_pass(BatchPlan* bp, const std::vector<int>& act, std::vector<Fin
   return QMC_OK;
 }
 
+// Persistent passes (QMC_WALK_PERSISTENT): every pass is one launch of the
+// run-time specialised persistent kernel built with run-time lattices
+// (qmc_jit_walk): each (sector, chunk of 16 shifts) keeps its compiled shifts
+// and coefficients, and the pass hands each descriptor its sector's current
+// lattice and slots.  Work items of kWalkChunk points from all refined
+// sectors, the costliest sectors' first, feed one wave of CTAs, so small and
+// large sectors share the GPU in a single launch.  The module is compiled for
+// one CTA per SM (255 registers): with the lattice in registers (n, its
+// reciprocal, g and gstep per dimension) it ran faster so than at two CTAs
+// per SM and 128 registers.
+constexpr uint32_t kWalkChunk = 1u << 15;
+
+struct WalkPersist {
+  void* fn = nullptr;                       // qmc_jit_walk (CUfunction)
+  int occ = 0;
+  int sms = 0;
+  std::vector<std::vector<int>> descs_of;   // sector -> its descriptors
+  std::vector<int> desc_mc;                 // descriptor -> shift rows evaluated
+  std::vector<double> weight;               // sector -> cost of a point per shift row
+  std::vector<PjLattice> lat;               // descriptor -> lattice and slots (host copy)
+  std::vector<double*> part;                // sector -> slots
+  std::vector<unsigned long long*> cnt;     // sector -> counters
+  std::vector<int> nitems;                  // sector -> items at its current lattice
+  PjLattice* lat_dev = nullptr;
+  PersistItem* items_dev = nullptr;
+  unsigned* next_dev = nullptr;
+};
+
+// Descriptors, the run-time lattice module and the host tables; slots are
+// placed by the caller.
+static int walk_persist_build(BatchPlan* bp, WalkPersist* W, int32_t count, const qmc_problem* problems) {
+  int rc = persist_build(bp, count, problems, kWalkChunk, kPjMc);
+  if (rc) return rc;
+  std::vector<PjSector> secs;
+  std::vector<PjDesc> descs;
+  persist_descriptors(bp, &secs, &descs);
+  if (!jit_enabled()) return fail(QMC_EUNSUPPORTED, "persistent walk passes need run-time compilation (QMC_JIT)");
+  rc = jit_persist(secs, descs, 1, &W->fn, &W->occ, true);
+  if (rc) return fail(rc == QMC_EUNSUPPORTED ? QMC_EUNSUPPORTED : rc, "the persistent walk kernel could not be built");
+  W->sms = device_sms();
+  if (W->sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
+  W->descs_of.assign(count, std::vector<int>());
+  W->desc_mc.resize(descs.size());
+  for (size_t q = 0; q < descs.size(); ++q) {
+    W->descs_of[descs[q].sector].push_back((int)q);
+    W->desc_mc[q] = descs[q].mc;
+  }
+  W->weight.resize(count);
+  for (int s = 0; s < count; ++s)
+    W->weight[s] = (double)(poly_slots(problems[s].d, 1) + poly_slots(problems[s].d, 2) + 2 * problems[s].d);
+  W->lat.assign(descs.size(), PjLattice());
+  W->part.assign(count, nullptr);
+  W->cnt.assign(count, nullptr);
+  W->nitems.assign(count, 0);
+  return QMC_OK;
+}
+
+// One persistent pass over the listed sectors, each on its lattice (n[i],
+// g[i]); every problem's current result copied to res (host).
+static int walk_pass_persistent(BatchPlan* bp, WalkPersist* W, const std::vector<int>& act,
+                                const std::vector<uint64_t>& n, const std::vector<const uint64_t*>& g,
+                                const qmc_problem* problems, std::vector<FinalizeArgs>& fin,
+                                std::vector<qmc_result>& res, cudaStream_t stream) {
+  // work items, the costliest sectors' first (a point's cost times the shift
+  // rows): every item but a sector's last has kWalkChunk points
+  std::vector<int> order(act);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return W->weight[a] > W->weight[b]; });
+  std::vector<PersistItem> items;
+  for (int i : order) {
+    const uint64_t ni = n[i];
+    const int d = problems[i].d;
+    const Recip rc = reciprocal(ni);
+    W->nitems[i] = (int)((ni + kWalkChunk - 1) / kWalkChunk);
+    for (int q : W->descs_of[i]) {
+      PjLattice& L = W->lat[q];
+      std::memset(&L, 0, sizeof(L));
+      L.n = ni;
+      L.rhi = rc.rhi;
+      L.rlo = rc.rlo;
+      for (int dd = 0; dd < d; ++dd) {
+        L.g[dd] = (uint32_t)g[i][dd];
+        L.gstep[dd] = (uint32_t)(((uint64_t)kThreads * g[i][dd]) % ni);
+      }
+      L.partial = W->part[i];
+      L.counters = W->cnt[i];
+      L.nitems = W->nitems[i];
+      for (int it = 0; it < W->nitems[i]; ++it) items.push_back(PersistItem{(uint32_t)q, (uint32_t)it});
+    }
+  }
+  fin.resize(act.size());
+  for (size_t u = 0; u < act.size(); ++u) {
+    const int i = act[u];
+    FinalizeArgs& A = fin[u];
+    std::memset(&A, 0, sizeof(A));
+    A.partial = W->part[i];
+    A.nblk = W->nitems[i];
+    A.m = problems[i].m;
+    A.groups = 1;
+    A.dn = (double)n[i];
+    A.value_scale = bp->psec[i].final_scale;
+    A.counters = W->cnt[i];
+    A.result = bp->res_dev + i;
+    A.per_shift = bp->ps_dev + bp->ps_off[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(W->lat_dev, W->lat.data(), W->lat.size() * sizeof(PjLattice), cudaMemcpyHostToDevice,
+                                  stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(W->items_dev, items.data(), items.size() * sizeof(PersistItem), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bp->fin_dev, fin.data(), fin.size() * sizeof(FinalizeArgs), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(W->next_dev, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "walk pass tables");
+  PersistArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.items = W->items_dev;
+  A.nitems = (uint32_t)items.size();
+  A.chunk = kWalkChunk;
+  A.next = W->next_dev;
+  A.lats = W->lat_dev;
+  Launch ln;
+  ln.cufunc = W->fn;
+  const uint64_t wave = (uint64_t)W->sms * (uint64_t)std::max(W->occ, 1);
+  ln.grid = dim3((unsigned)std::max<uint64_t>(1, std::min<uint64_t>(wave, items.size())));
+  void* args[1] = {&A};
+  int rc = launch_any(ln, ln.grid, args, stream);
+  if (rc) return rc;
+  FinalizeArgs* fd = bp->fin_dev;
+  void* fargs[1] = {&fd};
+  e = cudaLaunchKernel(finalize_batch_ptr(), dim3((unsigned)act.size()), dim3(256), fargs,
+                       (size_t)bp->max_m * 2 * sizeof(double), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "walk final pass");
+  e = cudaMemcpyAsync(res.data(), bp->res_dev, res.size() * sizeof(qmc_result), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "walk results");
+  return QMC_OK;
+}
+
 static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels, const uint64_t* ladder_n,
                       const uint64_t* ladder_g, int32_t ladder_dim, double rel_tol, int32_t criterion,
                       qmc_result* out, int32_t* level_out, int32_t* passes_out, cudaStream_t stream) {
@@ -749,6 +897,8 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
     return fail(QMC_EINVAL, "ladder of %d lattices (0..64, with n and g)", levels);
   if (ladder_dim < 1 || ladder_dim > QMC_DMAX) return fail(QMC_EINVAL, "ladder_dim=%d outside [1, %d]", ladder_dim, QMC_DMAX);
   if (!(rel_tol > 0.0)) return fail(QMC_EINVAL, "rel_tol must be > 0");
+  const bool pers = (criterion & QMC_WALK_PERSISTENT) != 0;
+  criterion &= ~QMC_WALK_PERSISTENT;
   if (criterion != QMC_WALK_SUM && criterion != QMC_WALK_EACH) return fail(QMC_EINVAL, "unknown criterion %d", criterion);
   for (int l = 0; l < levels; ++l) {
     const uint64_t n = ladder_n[l];
@@ -765,27 +915,41 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
   const int sms = device_sms();
   if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
   BatchPlan bp;
-  int rc = batch_build(&bp, count, problems, kWalkWork);
+  WalkPersist W;
+  int rc = pers ? walk_persist_build(&bp, &W, count, problems) : batch_build(&bp, count, problems, kWalkWork);
   if (rc) return rc;
   // lattices of problem i: its own, then the ladder's entries above its n
   std::vector<int> next(count), at(count, -1);
+  std::vector<uint64_t> cur_n(count);
+  std::vector<const uint64_t*> cur_g(count);
   for (int i = 0; i < count; ++i) {
     int l = 0;
     while (l < levels && ladder_n[l] <= problems[i].n) ++l;
     next[i] = l;
+    cur_n[i] = problems[i].n;
+    cur_g[i] = problems[i].g;
   }
-  // slots: at most one resident wave of CTAs, and at most the cap of the largest lattice
+  // slots: the sector kernels' CTAs (at most one resident wave, and at most
+  // the cap of the largest lattice), or the persistent passes' work items
   size_t bytes = 0;
   std::vector<size_t> part_off(count), cnt_off(count);
+  size_t max_items = 0;
   for (int i = 0; i < count; ++i) {
-    const Plan* pl = bp.probs[i].get();
-    int slots = pl->nblk;
-    if (next[i] < levels) {
-      const int wave = sms * std::max(pl->grid_occ, 1);
-      slots = std::max(slots, pl->grid_capped ? std::min(wave, walk_cap(ladder_n[levels - 1], pl->m, sms)) : wave);
+    const uint64_t n_max = next[i] < levels ? ladder_n[levels - 1] : problems[i].n;
+    int slots = 0;
+    if (pers) {
+      slots = (int)((n_max + kWalkChunk - 1) / kWalkChunk);
+      max_items += (size_t)slots * W.descs_of[i].size();
+    } else {
+      const Plan* pl = bp.probs[i].get();
+      slots = pl->nblk;
+      if (next[i] < levels) {
+        const int wave = sms * std::max(pl->grid_occ, 1);
+        slots = std::max(slots, pl->grid_capped ? std::min(wave, walk_cap(n_max, pl->m, sms)) : wave);
+      }
     }
     part_off[i] = bytes;
-    bytes += (size_t)pl->m * slots * 2 * sizeof(double);
+    bytes += (size_t)problems[i].m * slots * 2 * sizeof(double);
   }
   for (int i = 0; i < count; ++i) {
     cnt_off[i] = bytes;
@@ -801,6 +965,18 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
   bytes = (bytes + 255) & ~(size_t)255;
   const size_t fin_off = bytes;
   bytes += (size_t)count * sizeof(FinalizeArgs);
+  size_t lat_off = 0, items_off = 0, next_off = 0;
+  if (pers) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    lat_off = bytes;
+    bytes += W.lat.size() * sizeof(PjLattice);
+    bytes = (bytes + 255) & ~(size_t)255;
+    items_off = bytes;
+    bytes += std::max<size_t>(max_items, 1) * sizeof(PersistItem);
+    bytes = (bytes + 255) & ~(size_t)255;
+    next_off = bytes;
+    bytes += 16;
+  }
   cudaError_t e = cudaMallocAsync(&bp.ws, bytes, stream);
   if (e != cudaSuccess) {
     bp.ws = nullptr;
@@ -812,8 +988,18 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
   bp.ps_dev = (double*)(base + ps_off);
   bp.fin_dev = (FinalizeArgs*)(base + fin_off);
   for (int i = 0; i < count; ++i) {
-    bp.probs[i]->ws.partial = (double*)(base + part_off[i]);
-    bp.probs[i]->ws.counters = (unsigned long long*)(base + cnt_off[i]);
+    if (pers) {
+      W.part[i] = (double*)(base + part_off[i]);
+      W.cnt[i] = (unsigned long long*)(base + cnt_off[i]);
+    } else {
+      bp.probs[i]->ws.partial = (double*)(base + part_off[i]);
+      bp.probs[i]->ws.counters = (unsigned long long*)(base + cnt_off[i]);
+    }
+  }
+  if (pers) {
+    W.lat_dev = (PjLattice*)(base + lat_off);
+    W.items_dev = (PersistItem*)(base + items_off);
+    W.next_dev = (unsigned*)(base + next_off);
   }
   e = cudaMemsetAsync(base + cnt_off[0], 0, cnt_bytes, stream);  // the final pass resets them after each read
   if (e != cudaSuccess) rc = cuda_fail(e, "walk counters");
@@ -827,14 +1013,19 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
     if (passes > 0)
       for (int i : act) {
         const int l = next[i];
-        Plan* pl = bp.probs[i].get();
-        rc = plan_rebase(pl, ladder_n[l], ladder_g + (size_t)l * ladder_dim, walk_cap(ladder_n[l], pl->m, sms));
-        if (rc) break;
+        cur_n[i] = ladder_n[l];
+        cur_g[i] = ladder_g + (size_t)l * ladder_dim;
+        if (!pers) {
+          Plan* pl = bp.probs[i].get();
+          rc = plan_rebase(pl, cur_n[i], cur_g[i], walk_cap(cur_n[i], pl->m, sms));
+          if (rc) break;
+        }
         at[i] = l;
         next[i] = l + 1;
       }
     if (rc) break;
-    rc = walk_pass(&bp, act, fin, res, stream);
+    rc = pers ? walk_pass_persistent(&bp, &W, act, cur_n, cur_g, problems, fin, res, stream)
+              : walk_pass(&bp, act, fin, res, stream);
     if (rc) break;
     ++passes;
     for (int i : act)

@@ -432,7 +432,7 @@ int nvrtc_rdc(const std::string& src, const std::string& name, int max_regs, std
 // descriptor) and the dispatching kernel.  QMC_EUNSUPPORTED when the nonzero
 // coefficient pairs exceed what the module's constant bank holds.
 int persist_sources(const std::vector<PjSector>& secs, const std::vector<PjDesc>& descs, int ngroups, int min_ctas,
-                    std::vector<std::string>* gsrc_out, std::string* msrc_out) {
+                    bool rt, std::vector<std::string>* gsrc_out, std::string* msrc_out) {
   const int nsec = (int)secs.size();
   std::vector<std::string>& gsrc = *gsrc_out;
   gsrc.assign(ngroups, std::string());
@@ -467,16 +467,17 @@ int persist_sources(const std::vector<PjSector>& secs, const std::vector<PjDesc>
            ", ALPHA = " + std::to_string(S.tr == TR_KOROBOV ? 3 : 0) + ", MC = " + std::to_string(Dq.mc) +
            ", M = " + std::to_string(Dq.m) + ", KBASE = " + std::to_string(Dq.kbase) + ";\n";
     src += std::string("  static constexpr bool CHECK = ") + (S.check ? "true" : "false") + ";\n";
-    src += "  static constexpr unsigned long long N = " + hex64(S.n) + ", RHI = " + hex64(S.rc.rhi) +
-           ", RLO = " + hex64(S.rc.rlo) + ";\n";
-    auto table = [&](const char* fname, const char* arg, int count, auto value) {
-      src += std::string("  __device__ static __forceinline__ unsigned ") + fname + "(" + arg + ") {\n    switch (" +
-             (std::strchr(arg, ',') ? "k * 16 + i" : "i") + ") {\n";
-      for (int c = 0; c < count; ++c) src += "      case " + std::to_string(c) + ": return " + value(c) + ";\n";
-      src += "    }\n    return 0u;\n  }\n";
-    };
-    table("g", "int i", S.d, [&](int i) { return hex32(S.g[i]); });
-    table("gstep", "int i", S.d, [&](int i) { return hex32(S.gstep[i]); });
+    if (!rt) {  // the lattice as constants (with run-time lattices it comes from the launch)
+      src += "  static constexpr unsigned long long N = " + hex64(S.n) + ", RHI = " + hex64(S.rc.rhi) +
+             ", RLO = " + hex64(S.rc.rlo) + ";\n";
+      auto table = [&](const char* fname, int count, auto value) {
+        src += std::string("  __device__ static __forceinline__ unsigned ") + fname + "(int i) {\n    switch (i) {\n";
+        for (int c = 0; c < count; ++c) src += "      case " + std::to_string(c) + ": return " + value(c) + ";\n";
+        src += "    }\n    return 0u;\n  }\n";
+      };
+      table("g", S.d, [&](int i) { return hex32(S.g[i]); });
+      table("gstep", S.d, [&](int i) { return hex32(S.gstep[i]); });
+    }
     {
       src += "  __device__ static __forceinline__ unsigned shift(int k, int i) {\n    switch (k * 16 + i) {\n";
       for (int k = 0; k < Dq.mc; ++k)
@@ -491,18 +492,20 @@ int persist_sources(const std::vector<PjSector>& secs, const std::vector<PjDesc>
     src += "  }\n};\n";
     src += "extern \"C\" __device__ void qmc_pd_" + std::to_string(q) +
            "(unsigned long long j0, unsigned long long chunk, unsigned item, int nitems, double* partial, "
-           "unsigned long long* counters, double (*red)[qmc::kPjMc]) {\n";
-    src += "  qmc::pj_sweep<" + nm + ">(j0, chunk, item, nitems, partial, counters, red);\n}\n";
+           "unsigned long long* counters, double (*red)[qmc::kPjMc], const qmc::PjLattice* lat) {\n";
+    src += "  qmc::pj_sweep<" + nm + (rt ? ", true" : ", false") +
+           ">(j0, chunk, item, nitems, partial, counters, red, lat);\n}\n";
   }
   std::string& msrc = *msrc_out;
   msrc = "#include \"persist_jit.cuh\"\n";
   for (size_t q = 0; q < descs.size(); ++q)
     msrc += "extern \"C\" __device__ void qmc_pd_" + std::to_string(q) +
             "(unsigned long long, unsigned long long, unsigned, int, double*, unsigned long long*, "
-            "double (*)[qmc::kPjMc]);\n";
+            "double (*)[qmc::kPjMc], const qmc::PjLattice*);\n";
   msrc +=
-      "extern \"C\" __global__ void __launch_bounds__(256, " + std::to_string(min_ctas) +
-      ") qmc_jit_persist(const __grid_constant__ qmc::PersistArgs A) {\n"
+      "extern \"C\" __global__ void __launch_bounds__(256, " + std::to_string(min_ctas) + ") " +
+      std::string(rt ? "qmc_jit_walk" : "qmc_jit_persist") +
+      "(const __grid_constant__ qmc::PersistArgs A) {\n"
       "  __shared__ double red[qmc::kThreads / 32][qmc::kPjMc];\n"
       "  __shared__ unsigned cur;\n"
       "  for (;;) {\n"
@@ -511,15 +514,24 @@ int persist_sources(const std::vector<PjSector>& secs, const std::vector<PjDesc>
       "    const unsigned it = cur;\n"
       "    if (it >= A.nitems) break;  // the same for every thread of the CTA\n"
       "    const qmc::PersistItem wi = A.items[it];\n"
-      "    const qmc::PersistDesc* ds = A.descs + wi.desc;\n"
-      "    const unsigned long long j0 = (unsigned long long)wi.item * A.chunk;\n"
-      "    double* partial = ds->partial;\n"
-      "    unsigned long long* counters = ds->counters;\n"
-      "    const int nitems = ds->nitems;\n"
-      "    switch (wi.desc) {\n";
+      "    const unsigned long long j0 = (unsigned long long)wi.item * A.chunk;\n";
+  if (rt)
+    msrc +=
+        "    const qmc::PjLattice* lat = A.lats + wi.desc;\n"
+        "    double* partial = lat->partial;\n"
+        "    unsigned long long* counters = lat->counters;\n"
+        "    const int nitems = lat->nitems;\n";
+  else
+    msrc +=
+        "    const qmc::PersistDesc* ds = A.descs + wi.desc;\n"
+        "    const qmc::PjLattice* lat = nullptr;\n"
+        "    double* partial = ds->partial;\n"
+        "    unsigned long long* counters = ds->counters;\n"
+        "    const int nitems = ds->nitems;\n";
+  msrc += "    switch (wi.desc) {\n";
   for (size_t q = 0; q < descs.size(); ++q)
     msrc += "      case " + std::to_string(q) + ": qmc_pd_" + std::to_string(q) +
-            "(j0, A.chunk, wi.item, nitems, partial, counters, red); break;\n";
+            "(j0, A.chunk, wi.item, nitems, partial, counters, red, lat); break;\n";
   msrc +=
       "    }\n"
       "    __syncthreads();  // red and cur are rewritten for the next item\n"
@@ -528,7 +540,7 @@ int persist_sources(const std::vector<PjSector>& secs, const std::vector<PjDesc>
 }
 
 int jit_persist(const std::vector<PjSector>& secs, const std::vector<PjDesc>& descs, int min_ctas, void** fn_out,
-                int* occ_out) {
+                int* occ_out, bool runtime_lattice) {
   if (secs.empty() || descs.empty() || min_ctas < 1 || min_ctas > 2) return QMC_EINVAL;
   const int max_regs = min_ctas == 2 ? 128 : 255;
   int dev = 0;
@@ -545,7 +557,7 @@ int jit_persist(const std::vector<PjSector>& secs, const std::vector<PjDesc>& de
                                                 std::min(32u, std::max(1u, std::thread::hardware_concurrency()))));
   std::vector<std::string> gsrc;
   std::string msrc;
-  int rc = persist_sources(secs, descs, ngroups, min_ctas, &gsrc, &msrc);
+  int rc = persist_sources(secs, descs, ngroups, min_ctas, runtime_lattice, &gsrc, &msrc);
   if (rc) return rc;
   std::string key = std::to_string(dev) + "\npersist " + std::to_string(max_regs) + "\n" + msrc;
   for (const std::string& g : gsrc) key += g;
@@ -601,7 +613,7 @@ int jit_persist(const std::vector<PjSector>& secs, const std::vector<PjDesc>& de
   const bool loaded = drv.moduleLoadData(&e.mod, image) == CUDA_SUCCESS;
   drv.linkDestroy(ls);  // owns the linked image; the module keeps its own copy
   if (!loaded) return QMC_EUNSUPPORTED;
-  if (drv.moduleGetFunction(&e.fn, e.mod, "qmc_jit_persist") != CUDA_SUCCESS) {
+  if (drv.moduleGetFunction(&e.fn, e.mod, runtime_lattice ? "qmc_jit_walk" : "qmc_jit_persist") != CUDA_SUCCESS) {
     drv.moduleUnload(e.mod);
     return QMC_EUNSUPPORTED;
   }

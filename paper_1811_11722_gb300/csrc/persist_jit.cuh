@@ -16,8 +16,9 @@
 // SP provides
 //   static constexpr int D, TR, ALPHA, MC (even, <= kPjMc), M (shift rows
 //     written back, <= MC), KBASE (first shift of the chunk); bool CHECK
-//   static constexpr uint64_t N, RHI, RLO
-//   static uint32_t g(int i), gstep(int i), shift(int k, int i)
+//   static constexpr uint64_t N, RHI, RLO and static uint32_t g(int i),
+//     gstep(int i) (not read with run-time lattices)
+//   static uint32_t shift(int k, int i)
 //   static const float* kor()
 //   static void eval2(const float2* z, float2& U, float2& Fn)
 #pragma once
@@ -26,13 +27,37 @@
 
 namespace qmc {
 
-template <class SP>
+// RT: the lattice (n, its reciprocal, g, gstep) comes from *lat at run time
+// instead of SP's constants (the batched ladder walk moves a descriptor from
+// lattice to lattice); everything else stays compiled in, and the arithmetic
+// is the same.
+template <class SP, bool RT = false>
 __device__ __forceinline__ void pj_sweep(uint64_t j0, uint64_t chunk, uint32_t item, int32_t nitems,
                                          double* __restrict__ partial, unsigned long long* __restrict__ counters,
-                                         double (*red)[kPjMc]) {
+                                         double (*red)[kPjMc], const PjLattice* __restrict__ lat = nullptr) {
   constexpr int D = SP::D, MC = SP::MC, TR = SP::TR, ALPHA = SP::ALPHA;
   static_assert(MC % 2 == 0 && MC <= kPjMc && SP::M <= MC, "shift rows of a descriptor");
-  const uint64_t j1 = j0 + chunk < SP::N ? j0 + chunk : SP::N;
+  uint64_t N;
+  Recip rc;
+  uint32_t gg[D], gs[D];
+  if constexpr (RT) {
+    N = lat->n;
+    rc = Recip{lat->rhi, lat->rlo};
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      gg[i] = lat->g[i];
+      gs[i] = lat->gstep[i];
+    }
+  } else {
+    N = SP::N;
+    rc = Recip{SP::RHI, SP::RLO};
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      gg[i] = SP::g(i);
+      gs[i] = SP::gstep(i);
+    }
+  }
+  const uint64_t j1 = j0 + chunk < N ? j0 + chunk : N;
   Acc<float> acc[MC];
 #pragma unroll
   for (int kk = 0; kk < MC; ++kk) acc[kk].init();
@@ -49,10 +74,9 @@ __device__ __forceinline__ void pj_sweep(uint64_t j0, uint64_t chunk, uint32_t i
   const uint64_t jt = j0 + threadIdx.x;
   if (jt < j1) {
     const int steps = (int)((j1 - jt + kThreads - 1) / kThreads);
-    const Recip rc{SP::RHI, SP::RLO};
     uint32_t idx[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) idx[i] = lattice_index(jt, SP::g(i), SP::N);
+    for (int i = 0; i < D; ++i) idx[i] = lattice_index(jt, gg[i], N);
     for (int s = 0; s < steps; ++s) {
       uint32_t base[D];
 #pragma unroll
@@ -78,7 +102,7 @@ __device__ __forceinline__ void pj_sweep(uint64_t j0, uint64_t chunk, uint32_t i
         else run2[p] = add2(run2[p], v);
       }
 #pragma unroll
-      for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], SP::gstep(i), (uint32_t)SP::N);
+      for (int i = 0; i < D; ++i) idx[i] = index_step(idx[i], gs[i], (uint32_t)N);
       if (!kPackFold && (s & fold_mask<TR>()) == fold_mask<TR>()) {
         unpack_runs<MC>(run2, acc);
 #pragma unroll

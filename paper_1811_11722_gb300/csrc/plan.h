@@ -152,9 +152,11 @@ struct PjDesc {
 // cores as relocatable code and linked); QMC_OK with the CUfunction and its
 // occupancy, else an error code (the caller keeps the generic kernel).
 // min_ctas: resident CTAs per SM the kernel is built for (1, or 2 with every
-// function held to 128 registers).
+// function held to 128 registers).  runtime_lattice: the kernel (qmc_jit_walk)
+// reads each descriptor's lattice and slots from PersistArgs::lats instead of
+// compiling the lattice in (the batched ladder walk).
 int jit_persist(const std::vector<PjSector>& secs, const std::vector<PjDesc>& descs, int min_ctas, void** fn_out,
-                int* occ_out);
+                int* occ_out, bool runtime_lattice = false);
 
 int device_sms();
 int launch_any(const Launch& ln, dim3 grid, void** args, cudaStream_t stream);

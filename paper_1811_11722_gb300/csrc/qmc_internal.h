@@ -170,12 +170,25 @@ struct PersistItem {
   uint32_t desc;  // descriptor
   uint32_t item;  // j-chunk of its sector: points [item * chunk, min(n, (item + 1) * chunk))
 };
+// One descriptor of a persistent launch whose lattices are run-time values
+// (the batched ladder walk): its sector's current lattice and result slots.
+struct PjLattice {
+  uint64_t n;
+  uint64_t rhi, rlo;                 // 2^128 / n
+  uint32_t g[QMC_DMAX];
+  uint32_t gstep[QMC_DMAX];          // (kThreads g_i) mod n
+  double* partial;                   // the sector's slots [m][nitems][2]
+  unsigned long long* counters;      // the sector's counters
+  int32_t nitems;                    // work items of the sector at this lattice
+  int32_t pad;
+};
 struct PersistArgs {
   const PersistDesc* descs;
   const PersistItem* items;
   uint32_t nitems;
   uint32_t chunk;   // points per item, a multiple of kThreads
   unsigned* next;   // item counter, zero at launch
+  const PjLattice* lats;  // per descriptor, for kernels with run-time lattices (else null)
 };
 
 // Sparse monomial table for the general kernel (any degree, d <= QMC_DMAX).

@@ -652,6 +652,42 @@ def test_batch_walk_matches_per_pass_batches(Q, criterion, tol):
         assert not reached and passes >= 3
 
 
+def test_batch_walk_persistent_passes(Q):
+    """The walk with persistent passes (one launch of the run-time-lattice
+    kernel per pass) against the walk with one kernel per sector: the same
+    passes and final lattices, results within the grouping of the sums; and
+    every problem's final result equal, bit for bit, to the persistent batch
+    plan at its final lattice (the same work items of 2^15 points)."""
+    sect = I.config3(count=12, transform="korobov", alpha=3)
+    for s, p in enumerate(sect):
+        p.n = I.prev_prime(20000 + 9000 * s)
+        if s % 3 == 0:
+            p.transform, p.alpha = "baker", 0
+    gs = [I.random_generating_vector(I.SplitMix64(800 + i), p.d, p.n) for i, p in enumerate(sect)]
+    tuples = [_batch_tuple(Q, p, g) for p, g in zip(sect, gs)]
+    ladder_n = np.array([I.prev_prime(v) for v in (40000, 90000, 200000, 450000, 1000000, 2200000)], np.uint64)
+    ladder_g = np.stack([I.random_generating_vector(I.SplitMix64(900 + l), 8, int(n))
+                         for l, n in enumerate(ladder_n)]).astype(np.uint64)
+    tol = 3e-8
+    res, lv, passes, reached = Q.qmc_integrate_batch_to_tolerance(tuples, ladder_n, ladder_g, tol,
+                                                                  Q.WALK_SUM | Q.WALK_PERSISTENT)
+    ref, lv_ref, passes_ref, reached_ref = Q.qmc_integrate_batch_to_tolerance(tuples, ladder_n, ladder_g, tol)
+    assert passes == passes_ref and reached == reached_ref and list(lv) == list(lv_ref)
+    assert passes >= 2
+    # the same FP32 values, summed in other groups (items of 2^15 points
+    # against CTA tiles): baker's FP32 runs of 8 values round differently, a
+    # few 1e-10 of the mean at these n (measured up to 1.5e-10)
+    for r, q in zip(res, ref):
+        assert abs(r.mean[0] - q.mean[0]) <= 2e-9 * abs(q.mean[0]) and r.nonfinite == q.nonfinite
+    final = [(t[0], int(ladder_n[l]) if l >= 0 else t[1], t[2], ladder_g[l, :t[0]].copy() if l >= 0 else t[3])
+             + tuple(t[4:]) for t, l in zip(tuples, lv)]
+    pp = Q.BatchPlan(final, persistent=True, chunk=1 << 15)
+    want = pp.execute()
+    pp.destroy()
+    for r, q in zip(res, want):
+        assert r.mean[0] == q.mean[0] and r.err[0] == q.err[0] and r.nonfinite == q.nonfinite
+
+
 def test_batch_walk_without_ladder_is_one_batch(Q):
     """A walk with no ladder lattices evaluates every problem once, on its own
     lattice, exactly as qmc_integrate_batch does, and reports whether the sum
