@@ -759,7 +759,7 @@ static int walk_pass(BatchPlan* bp, const std::vector<int>& act, std::vector<Fin
 // sectors, the costliest sectors' first, feed one wave of CTAs, so small and
 // large sectors share the GPU in a single launch.  The module is compiled for
 // one CTA per SM (255 registers): with the lattice in registers (n, its
-// reciprocal, g and gstep per dimension) it ran faster so than at two CTAs
+// reciprocal, g and gstep per dimension) it ran faster that way than at two CTAs
 // per SM and 128 registers.
 constexpr uint32_t kWalkChunk = 1u << 15;
 
