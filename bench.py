@@ -560,6 +560,83 @@ def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279, start="own"):
     return {f"{tag}_batched": res["batched"], f"{tag}_one_by_one": res["one_by_one"]}
 
 
+def c3_time_to_tolerance_embedded(qmc, I, sh, tol, log2_n0=16, log2_nmax=24):
+    """The 256 Korobov-3 sectors summed to tol on embedded base-2 lattices:
+    every sector starts with 2^log2_n0 points and doubles (up to
+    2^log2_nmax) while its error is above its share tol |sum| / sqrt(256);
+    a doubling evaluates only the new half of the points.  Batched:
+    qmc_integrate_batch_extensible, one batched launch per pass.  One by one:
+    the same walk with one qmc_integrate call per sector and pass on the new
+    points, per-shift values averaged and combined (qmc_combine_shifts) on
+    the host.  The embedded vector (d = 8, restricted to each sector's d) is
+    a host precompute and not timed."""
+    import numpy as np
+    sect = I.config3(transform="korobov", alpha=3)
+    S = len(sect)
+    levels = log2_nmax - log2_n0
+    g = qmc.qmc_make_lattice_embedded(8, log2_n0, log2_nmax, I.product_weights(8))
+    n0 = 1 << log2_n0
+    fs = [qmc.integrand_from_problem(q) for q in sect]
+    ts = [qmc.transform(q.transform, q.alpha) for q in sect]
+    tuples = [(q.d, n0, q.m, g[:q.d] % np.uint64(n0), q.shifts, t_, f_) for q, t_, f_ in zip(sect, ts, fs)]
+    qmc.qmc_integrate_batch(tuples, stream=sh)  # run-time compilation of every sector's kernel: a precompute
+    res = {}
+    walls = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        rs, lv, passes, reached = qmc.qmc_integrate_batch_extensible(tuples, levels, g, tol, qmc.WALK_SUM, stream=sh)
+        walls.append(time.perf_counter() - t0)
+    mean = np.array([r.mean[0] for r in rs])
+    err = np.array([r.err[0] for r in rs])
+    total, total_err = mean.sum(), math.sqrt(float(np.sum(err ** 2)))
+    res["batched"] = {"rel_err": float(total_err / abs(total)), "sum": float(total), "wall_s": min(walls),
+                      "wall_s_runs": walls, "passes": int(passes), "reached": bool(reached),
+                      "evals": int(sum((n0 << int(l)) * q.m for q, l in zip(sect, lv))),
+                      "largest_n": int(n0 << int(max(lv))), "api": "qmc_integrate_batch_extensible"}
+    # one by one: the same decisions, one rule call per sector and pass
+    size = [n0] * S
+    dbl = [0] * S
+    q = [None] * S
+    mean = np.zeros(S)
+    err = np.zeros(S)
+    todo = list(range(S))
+    wall, passes, evals = 0.0, 0, 0
+    while True:
+        t0 = time.perf_counter()
+        for i in todo:
+            p, n = sect[i], size[i]
+            shifts = p.shifts
+            if passes:
+                v = p.shifts + (g[:p.d] % np.uint64(2 * n)).astype(np.float64) / float(2 * n)
+                shifts = np.where(v >= 1.0, v - 1.0, v)
+            _, ps = qmc.qmc_integrate(p.d, n, p.m, g[:p.d] % np.uint64(n), shifts, ts[i], fs[i], stream=sh,
+                                      want_per_shift=True)
+            if passes:
+                q[i] = 0.5 * (q[i] + ps)
+                size[i] *= 2
+                dbl[i] += 1
+            else:
+                q[i] = ps
+            r = qmc.qmc_combine_shifts(q[i])
+            mean[i], err[i] = r.mean[0], r.err[0]
+            evals += n * p.m
+        wall += time.perf_counter() - t0
+        passes += 1
+        total, total_err = mean.sum(), math.sqrt(float(np.sum(err ** 2)))
+        if total_err <= tol * abs(total):
+            break
+        share = tol * abs(total) / math.sqrt(S)
+        todo = [i for i in range(S) if err[i] > share and dbl[i] < levels]
+        if not todo:
+            break
+    res["one_by_one"] = {"rel_err": float(total_err / abs(total)), "sum": float(total), "wall_s": wall,
+                         "passes": passes, "evals": int(evals), "reached": bool(total_err <= tol * abs(total)),
+                         "largest_n": int(max(size)), "api": "qmc_integrate per call"}
+    res["batched"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched"]["wall_s"]
+    tag = "c3_256_sectors_korobov3_sum_embedded"
+    return {f"{tag}_batched": res["batched"], f"{tag}_one_by_one": res["one_by_one"]}
+
+
 def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
     """Wall time until err/|Qbar| <= tol walking the lattice ladder (largest prime
     <= 2^(e/2)), each level a fresh rule with its CBC vector; lattice
@@ -661,6 +738,13 @@ def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):
     # the same sum with every sector started on the ladder's first prime: the
     # walk then chooses each sector's n from the bottom of the ladder
     out.update(c3_time_to_tolerance(qmc, I, sh, tol, start="ladder"))
+    # the same sum on embedded base-2 lattices: every sector starts at 2^16
+    # points and doubles, each doubling evaluating only the new half
+    out.update(c3_time_to_tolerance_embedded(qmc, I, sh, tol))
+    lad = out.get("c3_256_sectors_korobov3_sum_from_ladder_start_batched")
+    if lad:
+        emb = out["c3_256_sectors_korobov3_sum_embedded_batched"]
+        emb["speedup_vs_prime_ladder_batched"] = lad["wall_s"] / emb["wall_s"]
     # control variate on the d=8 sector (pilot n=65537, 2000 Adam steps).  The
     # library's judged walk (qmc_integrate_cv_to_tolerance): the first ladder
     # lattice is the pilot where the control variate and the plain rule meet at

@@ -282,6 +282,30 @@ int qmc_integrate_batch_to_tolerance(int32_t count, const qmc_problem* problems,
                                      int32_t* passes_out, void* stream);
 #endif
 
+/* Automatic choice of n for a batch on embedded base-2 lattices (Eq. 2 and
+ * Eq. 3 as for qmc_integrate_extensible, the walk's passes and criterion as
+ * for qmc_integrate_batch_to_tolerance).  Problem i starts with the rule of
+ * problems[i].n = 2^k points whose vector is g mod 2^k (its first d
+ * components; problems[i].g is not read).  A pass doubles the size of every
+ * problem it refines and evaluates only the new points: the previous size's
+ * lattice on shifts Delta_k + (g mod 2n) / (2n), averaged per shift with the
+ * previous values, so each result is exactly the size-2n rule and no point is
+ * evaluated twice.  All refined problems of a pass run as one batched launch.
+ *   levels     most doublings per problem (0..30); no size exceeds 2^30
+ *   g          [g_dim] odd components (qmc_make_lattice_embedded), host
+ *   g_dim      >= every problem's d
+ *   criterion  QMC_WALK_SUM or QMC_WALK_EACH
+ *   level_out  optional [count]: doublings taken (final n = problems[i].n << level)
+ * Problems as for qmc_integrate_batch, with m >= 2 and n a power of two in
+ * [2, 2^30].  Synchronises `stream`.  Returns as
+ * qmc_integrate_batch_to_tolerance; out[i].nonfinite and deform_violations
+ * count every pass. */
+#ifndef __CUDACC_RTC__  /* function declarations are host-only */
+int qmc_integrate_batch_extensible(int32_t count, const qmc_problem* problems, int32_t levels, const uint64_t* g,
+                                   int32_t g_dim, double rel_tol, int32_t criterion, qmc_result* out,
+                                   int32_t* level_out, int32_t* passes_out, void* stream);
+#endif
+
 /* Planned batch: validates and packs once and builds the CUDA graph; every
  * execute replays it (one cudaGraphLaunch). */
 typedef struct qmc_batch_plan_s* qmc_batch_plan;

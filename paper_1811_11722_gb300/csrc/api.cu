@@ -686,6 +686,33 @@ int plan_rebase(Plan* pl, uint64_t n, const uint64_t* g, int max_ctas) {
   return QMC_OK;
 }
 
+template <typename R>
+static void reshift_rule(RuleParams<R>& P, int d, int mc, const double* shifts) {
+  // rows m_launch..mc-1 repeat the launch's first row, as at build time
+  for (int kk = 0; kk < mc; ++kk)
+    for (int i = 0; i < d; ++i) {
+      const int src = kk < P.m_launch ? P.k_base + kk : P.k_base;
+      set_shift(P, kk, i, shift_fixed64(shifts[(size_t)src * d + i]));
+    }
+}
+
+int plan_reshift(Plan* pl, const double* shifts) {
+  if (pl->param_kind < 1 || pl->param_kind > 4) return fail(QMC_EUNSUPPORTED, "this plan is bound to its shifts");
+  if (pl->imm) return fail(QMC_EUNSUPPORTED, "this plan has its shifts compiled into its kernel");
+  for (size_t u = 0; u < (size_t)pl->m * pl->d; ++u)
+    if (!(shifts[u] >= 0.0 && shifts[u] < 1.0)) return fail(QMC_EINVAL, "shift value %zu outside [0, 1)", u);
+  for (Launch& ln : pl->launches) {
+    uint8_t* p = ln.params.data();
+    switch (pl->param_kind) {
+      case 1: reshift_rule(*reinterpret_cast<RuleParams<float>*>(p), pl->d, pl->mc, shifts); break;
+      case 2: reshift_rule(*reinterpret_cast<RuleParams<double>*>(p), pl->d, pl->mc, shifts); break;
+      case 3: reshift_rule(reinterpret_cast<GeneralParams<float>*>(p)->base, pl->d, pl->mc, shifts); break;
+      default: reshift_rule(reinterpret_cast<GeneralParams<double>*>(p)->base, pl->d, pl->mc, shifts); break;
+    }
+  }
+  return QMC_OK;
+}
+
 int plan_alloc(Plan* pl, cudaStream_t stream, bool async) {
   const size_t G = (size_t)pl->orders;
   size_t partial_bytes = G * pl->m * pl->nblk * 2 * sizeof(double);

@@ -713,9 +713,10 @@ static int walk_cap(uint64_t n, int m, int sms) {
 }
 
 // One pass: the listed problems' rules, their final pass, and every
-// problem's current result copied to res (host).
+// problem's current result copied to res (host), and with ps every
+// problem's per-shift values ([total_m][2], host).
 static int walk_pass(BatchPlan* bp, const std::vector<int>& act, std::vector<FinalizeArgs>& fin,
-                     std::vector<qmc_result>& res, cudaStream_t stream) {
+                     std::vector<qmc_result>& res, cudaStream_t stream, double* ps = nullptr) {
   fin.resize(act.size());
   for (size_t u = 0; u < act.size(); ++u) {
     const int i = act[u];
@@ -746,6 +747,8 @@ static int walk_pass(BatchPlan* bp, const std::vector<int>& act, std::vector<Fin
                        (size_t)bp->max_m * 2 * sizeof(double), stream);
   if (e != cudaSuccess) return cuda_fail(e, "walk final pass");
   e = cudaMemcpyAsync(res.data(), bp->res_dev, res.size() * sizeof(qmc_result), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess && ps)
+    e = cudaMemcpyAsync(ps, bp->ps_dev, (size_t)bp->total_m * 2 * sizeof(double), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(e, "walk results");
   return QMC_OK;
@@ -1087,6 +1090,210 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
   return fail(QMC_ETIMEOUT, "relative error %.3g not reached after %d passes", rel_tol, passes);
 }
 
+// ------------------------------------------------ embedded doubling walk --
+//
+// qmc_integrate_batch_extensible.  Problem i starts with the rule of n_i = 2^k
+// points on the embedded vector g (g mod n_i).  A later pass doubles n_i and
+// evaluates only the new points: they are the size-n_i lattice shifted by
+// (g mod 2n_i) / (2n_i), so the plan moves to that lattice (plan_rebase) and
+// takes the shifted shifts (plan_reshift).  The new per-shift values are
+// averaged with the previous ones on the host, so every estimate is exactly
+// the rule of its size and no point is evaluated twice.
+
+static int batch_extensible(int32_t count, const qmc_problem* problems, int32_t levels, const uint64_t* g,
+                            int32_t g_dim, double rel_tol, int32_t criterion, qmc_result* out, int32_t* level_out,
+                            int32_t* passes_out, cudaStream_t stream) {
+  if (count < 1 || count > 65536) return fail(QMC_EINVAL, "batch count=%d outside [1, 65536]", count);
+  if (!problems || !out || !g) return fail(QMC_EINVAL, "null problems, generating vector or results");
+  if (levels < 0 || levels > 30) return fail(QMC_EINVAL, "levels=%d outside [0, 30]", levels);
+  if (g_dim < 1 || g_dim > QMC_DMAX) return fail(QMC_EINVAL, "g_dim=%d outside [1, %d]", g_dim, QMC_DMAX);
+  if (!(rel_tol > 0.0)) return fail(QMC_EINVAL, "rel_tol must be > 0");
+  if (criterion != QMC_WALK_SUM && criterion != QMC_WALK_EACH) return fail(QMC_EINVAL, "unknown criterion %d", criterion);
+  for (int c = 0; c < g_dim; ++c)
+    if ((g[c] & 1) == 0) return fail(QMC_EINVAL, "g[%d]=%llu must be odd", c, (unsigned long long)g[c]);
+  std::vector<int> maxd(count);  // doublings each problem may take
+  for (int i = 0; i < count; ++i) {
+    const qmc_problem& q = problems[i];
+    if (q.d < 1 || q.d > g_dim) return fail(QMC_EINVAL, "problem %d: d=%d outside [1, g_dim]", i, q.d);
+    if (q.n < 2 || q.n > (1ull << 30) || (q.n & (q.n - 1)) != 0)
+      return fail(QMC_EINVAL, "problem %d: n=%llu is not a power of two in [2, 2^30]", i, (unsigned long long)q.n);
+    if (q.m < 2 || !q.shifts) return fail(QMC_EINVAL, "problem %d: m=%d shifts (the estimate needs m >= 2)", i, q.m);
+    int k = 0;
+    while ((1ull << k) < q.n) ++k;
+    maxd[i] = std::min(levels, 30 - k);
+  }
+  if (is_device_pointer(out)) return fail(QMC_EINVAL, "the results must be host memory");
+  const int sms = device_sms();
+  if (sms <= 0) return fail(QMC_ECUDA, "no CUDA device");
+  // the problems at their first size
+  std::vector<qmc_problem> pr(problems, problems + count);
+  std::vector<uint64_t> gm((size_t)count * g_dim);
+  for (int i = 0; i < count; ++i) {
+    for (int c = 0; c < pr[i].d; ++c) gm[(size_t)i * g_dim + c] = g[c] % pr[i].n;  // odd, so >= 1
+    pr[i].g = gm.data() + (size_t)i * g_dim;
+  }
+  BatchPlan bp;
+  int rc = batch_build(&bp, count, pr.data(), kWalkWork);
+  if (rc) return rc;
+  // slots: one resident wave, at most the cap of the largest rule evaluated
+  // (half the last size)
+  size_t bytes = 0;
+  std::vector<size_t> part_off(count), cnt_off(count);
+  for (int i = 0; i < count; ++i) {
+    const Plan* pl = bp.probs[i].get();
+    int slots = pl->nblk;
+    if (maxd[i] > 0) {
+      const uint64_t n_max = pr[i].n << (maxd[i] - 1);
+      const int wave = sms * std::max(pl->grid_occ, 1);
+      slots = std::max(slots, pl->grid_capped ? std::min(wave, walk_cap(n_max, pl->m, sms)) : wave);
+    }
+    part_off[i] = bytes;
+    bytes += (size_t)pl->m * slots * 2 * sizeof(double);
+  }
+  for (int i = 0; i < count; ++i) {
+    cnt_off[i] = bytes;
+    bytes += 2 * sizeof(unsigned long long);
+  }
+  const size_t cnt_bytes = bytes - cnt_off[0];
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t res_off = bytes;
+  bytes += (size_t)count * sizeof(qmc_result);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t ps_off = bytes;
+  bytes += (size_t)bp.total_m * 2 * sizeof(double);
+  bytes = (bytes + 255) & ~(size_t)255;
+  const size_t fin_off = bytes;
+  bytes += (size_t)count * sizeof(FinalizeArgs);
+  cudaError_t e = cudaMallocAsync(&bp.ws, bytes, stream);
+  if (e != cudaSuccess) {
+    bp.ws = nullptr;
+    cudaGetLastError();
+    return fail(QMC_ENOMEM, "walk workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  char* base = (char*)bp.ws;
+  bp.res_dev = (qmc_result*)(base + res_off);
+  bp.ps_dev = (double*)(base + ps_off);
+  bp.fin_dev = (FinalizeArgs*)(base + fin_off);
+  for (int i = 0; i < count; ++i) {
+    bp.probs[i]->ws.partial = (double*)(base + part_off[i]);
+    bp.probs[i]->ws.counters = (unsigned long long*)(base + cnt_off[i]);
+  }
+  e = cudaMemsetAsync(base + cnt_off[0], 0, cnt_bytes, stream);  // the final pass resets them after each read
+  if (e != cudaSuccess) rc = cuda_fail(e, "walk counters");
+  const size_t tm2 = (size_t)bp.total_m * 2;
+  std::vector<double> q(tm2), ps(tm2), sh;
+  std::vector<uint64_t> size(count), gl(QMC_DMAX);
+  std::vector<int> dbl(count, 0);
+  std::vector<unsigned long long> nonfinite(count, 0), deform(count, 0);
+  std::vector<qmc_result> res(count), est(count);
+  std::vector<FinalizeArgs> fin;
+  std::vector<int> act(count);
+  for (int i = 0; i < count; ++i) {
+    act[i] = i;
+    size[i] = pr[i].n;
+  }
+  int passes = 0;
+  bool reached = false;
+  while (rc == QMC_OK) {
+    if (passes > 0)
+      for (int i : act) {
+        // the new points of size 2n: the size-n rule on shifts Delta + (g mod 2n) / (2n)
+        const qmc_problem& qp = problems[i];
+        const uint64_t n = size[i];
+        for (int c = 0; c < qp.d; ++c) gl[c] = g[c] % n;
+        Plan* pl = bp.probs[i].get();
+        rc = plan_rebase(pl, n, gl.data(), walk_cap(n, pl->m, sms));
+        if (rc) break;
+        sh.resize((size_t)qp.m * qp.d);
+        const double two_n = (double)(2 * n);
+        for (int k = 0; k < qp.m; ++k)
+          for (int c = 0; c < qp.d; ++c) {
+            const double v = qp.shifts[(size_t)k * qp.d + c] + (double)(g[c] % (2 * n)) / two_n;
+            sh[(size_t)k * qp.d + c] = v >= 1.0 ? v - 1.0 : v;
+          }
+        rc = plan_reshift(pl, sh.data());
+        if (rc) break;
+      }
+    if (rc) break;
+    rc = walk_pass(&bp, act, fin, res, stream, ps.data());
+    if (rc) break;
+    for (int i : act) {
+      if (res[i].status != QMC_OK && res[i].status != QMC_ENONFINITE && res[i].status != QMC_EDEFORM) {
+        rc = fail(res[i].status, "problem %d failed with status %d", i, res[i].status);
+        break;
+      }
+      double* qi = q.data() + bp.ps_off[i];
+      const double* pi = ps.data() + bp.ps_off[i];
+      const size_t m2 = (size_t)problems[i].m * 2;
+      if (passes == 0) {
+        std::memcpy(qi, pi, m2 * sizeof(double));
+      } else {
+        for (size_t u = 0; u < m2; ++u) qi[u] = 0.5 * (qi[u] + pi[u]);
+        size[i] *= 2;
+        ++dbl[i];
+      }
+      nonfinite[i] += res[i].nonfinite;
+      deform[i] += res[i].deform_violations;
+      rc = qmc_combine_shifts(problems[i].m, qi, &est[i]);  // Eq. (3) on the size-size[i] rule's per-shift values
+      if (rc) break;
+      est[i].nonfinite = nonfinite[i];
+      est[i].deform_violations = deform[i];
+      est[i].status = nonfinite[i] ? QMC_ENONFINITE : (deform[i] ? QMC_EDEFORM : QMC_OK);
+    }
+    if (rc) break;
+    ++passes;
+    // next pass: the problems whose error is above their share of the tolerance
+    act.clear();
+    if (criterion == QMC_WALK_SUM) {
+      double sre = 0.0, sim = 0.0, e2 = 0.0;
+      for (int i = 0; i < count; ++i) {
+        sre += est[i].mean[0];
+        sim += est[i].mean[1];
+        e2 += est[i].err[0] * est[i].err[0] + est[i].err[1] * est[i].err[1];
+      }
+      const double mag = std::hypot(sre, sim);
+      if (mag > 0.0 && std::sqrt(e2) <= rel_tol * mag) {
+        reached = true;
+        break;
+      }
+      const double share = rel_tol * mag / std::sqrt((double)count);
+      for (int i = 0; i < count; ++i)
+        if (std::hypot(est[i].err[0], est[i].err[1]) > share && dbl[i] < maxd[i]) act.push_back(i);
+    } else {
+      bool all = true;
+      for (int i = 0; i < count; ++i) {
+        const double mag = std::hypot(est[i].mean[0], est[i].mean[1]);
+        if (mag > 0.0 && std::hypot(est[i].err[0], est[i].err[1]) <= rel_tol * mag) continue;
+        all = false;
+        if (dbl[i] < maxd[i]) act.push_back(i);
+      }
+      if (all) {
+        reached = true;
+        break;
+      }
+    }
+    if (act.empty()) break;
+  }
+  if (bp.ws) {
+    cudaFreeAsync(bp.ws, stream);
+    bp.ws = nullptr;
+  }
+  e = cudaStreamSynchronize(stream);
+  if (rc == QMC_OK && e != cudaSuccess) rc = cuda_fail(e, "walk synchronise");
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) {
+    out[i] = est[i];
+    if (level_out) level_out[i] = dbl[i];
+  }
+  if (passes_out) *passes_out = passes;
+  if (reached) return QMC_OK;
+  if (criterion == QMC_WALK_EACH)
+    for (int i = 0; i < count; ++i) {
+      const double mag = std::hypot(out[i].mean[0], out[i].mean[1]);
+      if (!(mag > 0.0 && std::hypot(out[i].err[0], out[i].err[1]) <= rel_tol * mag)) out[i].status = QMC_ETIMEOUT;
+    }
+  return fail(QMC_ETIMEOUT, "relative error %.3g not reached after %d passes", rel_tol, passes);
+}
 static int batch_execute(BatchPlan* bp, qmc_result* out, double* per_shift, cudaStream_t stream) {
   if (!out) return fail(QMC_EINVAL, "null result pointer");
   cudaError_t e = cudaGraphLaunch(bp->exec, stream);
@@ -1267,6 +1474,13 @@ int qmc_integrate_batch_to_tolerance(int32_t count, const qmc_problem* problems,
                                      int32_t* passes_out, void* stream) {
   return batch_walk(count, problems, levels, ladder_n, ladder_g, ladder_dim, rel_tol, criterion, out, level_out,
                     passes_out, (cudaStream_t)stream);
+}
+
+int qmc_integrate_batch_extensible(int32_t count, const qmc_problem* problems, int32_t levels, const uint64_t* g,
+                                   int32_t g_dim, double rel_tol, int32_t criterion, qmc_result* out,
+                                   int32_t* level_out, int32_t* passes_out, void* stream) {
+  return batch_extensible(count, problems, levels, g, g_dim, rel_tol, criterion, out, level_out, passes_out,
+                          (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -104,6 +104,10 @@ int grid_shape(int occ, uint64_t n, int max_ctas, int fixed_L, int& nblk, int& L
 // kernels, shifts and coefficients are kept.  QMC_EUNSUPPORTED for plans
 // whose launches are not rule launches (param_kind 0).
 int plan_rebase(Plan* pl, uint64_t n, const uint64_t* g, int max_ctas);
+// Give a built plan new shifts [m][d] in [0, 1) (host), encoded as at build
+// time; lattice, kernels and coefficients are kept.  QMC_EUNSUPPORTED for
+// plans that are not rule plans or have their shifts compiled in.
+int plan_reshift(Plan* pl, const double* shifts);
 
 template <typename R>
 void fill_common(RuleParams<R>& P, int32_t d, uint64_t n, const uint64_t* g, const qmc_transform& t,

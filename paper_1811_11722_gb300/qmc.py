@@ -113,6 +113,8 @@ def lib():
             L.qmc_integrate_batch.argtypes = [i32, vp, vp, vp, vp]
             L.qmc_integrate_batch_to_tolerance.argtypes = [i32, vp, i32, vp, vp, i32, ctypes.c_double, i32, vp, vp,
                                                            ctypes.POINTER(i32), vp]
+            L.qmc_integrate_batch_extensible.argtypes = [i32, vp, i32, vp, i32, ctypes.c_double, i32, vp, vp,
+                                                         ctypes.POINTER(i32), vp]
             L.qmc_batch_plan_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
             L.qmc_batch_plan_create_persistent.argtypes = [i32, vp, ctypes.c_uint32, ctypes.POINTER(vp)]
             L.qmc_batch_plan_execute.argtypes = [vp, vp, vp, vp]
@@ -151,7 +153,7 @@ def lib():
                          "qmc_sample_points_eps", "qmc_integrate_multi", "qmc_multi_plan_create", "qmc_make_lattice_embedded",
                          "qmc_integrate_extensible", "qmc_batch_plan_create_persistent",
                          "qmc_integrate_cv_to_tolerance", "qmc_batch_plan_describe",
-                         "qmc_integrate_batch_to_tolerance"):
+                         "qmc_integrate_batch_to_tolerance", "qmc_integrate_batch_extensible"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -385,6 +387,24 @@ def qmc_integrate_batch_to_tolerance(problems, ladder_n, ladder_g, rel_tol, crit
                                                 _ptr(ladder_n), _ptr(ladder_g), ladder_g.shape[1],
                                                 float(rel_tol), int(criterion), ctypes.cast(res, ctypes.c_void_p),
                                                 _ptr(lv), ctypes.byref(passes), ctypes.c_void_p(stream))
+    if rc != QMC_ETIMEOUT:
+        _check(rc, allow_warnings=True)
+    return list(res), lv, int(passes.value), rc != QMC_ETIMEOUT
+
+
+def qmc_integrate_batch_extensible(problems, levels, g, rel_tol, criterion=WALK_SUM, stream=0):
+    """Per-problem doubling walk on embedded base-2 lattices, each pass one
+    batched launch: problem i starts with the rule of its n = 2^k points on
+    g[:d_i] mod n (its own g is not read).  Returns (results, doublings per
+    problem, passes, reached: bool)."""
+    b = _Batch(problems)
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.uint64))
+    res = (qmc_result * b.count)()
+    lv = np.zeros(b.count, dtype=np.int32)
+    passes = ctypes.c_int32(0)
+    rc = lib().qmc_integrate_batch_extensible(b.count, ctypes.cast(b.arr, ctypes.c_void_p), int(levels), _ptr(g),
+                                              len(g), float(rel_tol), int(criterion), ctypes.cast(res, ctypes.c_void_p),
+                                              _ptr(lv), ctypes.byref(passes), ctypes.c_void_p(stream))
     if rc != QMC_ETIMEOUT:
         _check(rc, allow_warnings=True)
     return list(res), lv, int(passes.value), rc != QMC_ETIMEOUT

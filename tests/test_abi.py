@@ -305,3 +305,36 @@ def test_batch_walk_validation(Q, case):
     with pytest.raises(Q.QmcError) as ei:
         Q.qmc_integrate_batch_to_tolerance(probs, ladder_n, ladder_g, tol, crit)
     assert ei.value.status == Q.QMC_EINVAL
+
+
+@pytest.mark.parametrize("case", ["n_not_power_of_two", "n_above_2_30", "even_g", "dim_below_d", "criterion", "tol",
+                                  "levels", "one_shift"])
+def test_batch_extensible_validation(Q, case):
+    """The batched embedded-lattice walk checks its sizes, vector and options
+    on the host, before any device work (so these run without a GPU)."""
+    d, n, m = 3, 1024, 4
+    coef = np.array([1.0, 0.5])
+    expo = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.uint8)
+    f = Q.Integrand(Q.QMC_F_SECTOR, d, Q.QMC_FP32EVAL, (coef, expo), (coef, expo))
+    g = np.array([1, 433, 12345, 999], dtype=np.uint64)
+    levels, tol, crit = 4, 1e-6, Q.WALK_SUM
+    if case == "n_not_power_of_two":
+        n = 1000
+    elif case == "n_above_2_30":
+        n = 1 << 31
+    elif case == "even_g":
+        g[2] = 12346
+    elif case == "dim_below_d":
+        g = g[:2].copy()
+    elif case == "criterion":
+        crit = Q.WALK_SUM | Q.WALK_PERSISTENT
+    elif case == "tol":
+        tol = -1.0
+    elif case == "levels":
+        levels = 31
+    elif case == "one_shift":
+        m = 1
+    probs = [(d, n, m, g[:d] % n, np.full((m, d), 0.25), Q.transform("baker"), f)]
+    with pytest.raises(Q.QmcError) as ei:
+        Q.qmc_integrate_batch_extensible(probs, levels, g, tol, crit)
+    assert ei.value.status == Q.QMC_EINVAL

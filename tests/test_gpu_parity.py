@@ -688,6 +688,134 @@ def test_batch_walk_persistent_passes(Q):
         assert r.mean[0] == q.mean[0] and r.err[0] == q.err[0] and r.nonfinite == q.nonfinite
 
 
+def _embedded_g(seed, d=8):
+    """An odd generating vector for embedded base-2 lattices (g_1 = 1)."""
+    rng = I.SplitMix64(seed)
+    return np.array([1] + [2 * rng.randint(0, (1 << 29) - 1) + 1 for _ in range(d - 1)], dtype=np.uint64)
+
+
+def _extensible_problems(Q, seed=0):
+    """FP32 sectors (baker, Korobov 3) of d = 2..8, an FP64 separable problem
+    and a deformed FP64 problem, each starting at its own power of two."""
+    sect = I.config3(count=10, transform="korobov", alpha=3)
+    probs = []
+    for s, p in enumerate(sect):
+        p.n = 1 << (12 + s % 4)
+        if s % 3 == 0:
+            p.transform, p.alpha = "baker", 0
+        probs.append(p)
+    c1 = I.config1()
+    c1.n = 1 << 13
+    probs.append(c1)
+    probs.append(_c4(n=1 << 14, m=8))
+    return probs
+
+
+def _shifted_tuple(t, g, n, new_points):
+    """Problem tuple t at size n on g mod n; with new_points, the points of
+    size 2n that are not in size n (shifts moved by (g mod 2n) / (2n))."""
+    d = t[0]
+    sh = np.asarray(t[4], dtype=np.float64)
+    if new_points:
+        v = sh + (g[:d] % np.uint64(2 * n)).astype(np.float64) / float(2 * n)
+        sh = np.where(v >= 1.0, v - 1.0, v)
+    return (d, n, t[2], g[:d] % np.uint64(n), np.ascontiguousarray(sh)) + tuple(t[5:])
+
+
+def _python_batch_extensible(Q, tuples, g, levels, tol, criterion):
+    """The walk of qmc_integrate_batch_extensible written with one
+    qmc_integrate_batch call per pass (same points, same decisions), the
+    per-shift values averaged and combined on the host."""
+    S = len(tuples)
+    size = [t[1] for t in tuples]
+    maxd = [min(levels, 30 - int(t[1]).bit_length() + 1) for t in tuples]
+    dbl = [0] * S
+    q = [None] * S
+    res = [None] * S
+    act, passes, reached = list(range(S)), 0, False
+    while True:
+        rs, ps = Q.qmc_integrate_batch([_shifted_tuple(tuples[i], g, size[i], passes > 0) for i in act],
+                                       want_per_shift=True)
+        off = 0
+        for i, r in zip(act, rs):
+            m = tuples[i][2]
+            qn = ps[2 * off: 2 * (off + m)].reshape(m, 2)
+            off += m
+            if passes == 0:
+                q[i] = qn.copy()
+            else:
+                q[i] = 0.5 * (q[i] + qn)
+                size[i] *= 2
+                dbl[i] += 1
+            res[i] = Q.qmc_combine_shifts(q[i])
+        passes += 1
+        mag = [math.hypot(r.mean[0], r.mean[1]) for r in res]
+        err = [math.hypot(r.err[0], r.err[1]) for r in res]
+        if criterion == Q.WALK_SUM:
+            tot = math.hypot(sum(r.mean[0] for r in res), sum(r.mean[1] for r in res))
+            if tot > 0 and math.sqrt(sum(e * e for e in err)) <= tol * tot:
+                reached = True
+                break
+            share = tol * tot / math.sqrt(S)
+            act = [i for i in range(S) if err[i] > share and dbl[i] < maxd[i]]
+        else:
+            ok = [mag[i] > 0 and err[i] <= tol * mag[i] for i in range(S)]
+            if all(ok):
+                reached = True
+                break
+            act = [i for i in range(S) if not ok[i] and dbl[i] < maxd[i]]
+        if not act:
+            break
+    return res, dbl, passes, reached
+
+
+@pytest.mark.parametrize("criterion,tol,levels", [("sum", 3e-8, 8), ("each", 2e-7, 8), ("sum", 1e-15, 3)])
+def test_batch_extensible_matches_per_pass_batches(Q, criterion, tol, levels):
+    """The batched embedded-lattice walk (plans built once, moved to each
+    size and shifted to its new points) against the same walk made of one
+    qmc_integrate_batch per pass: the same passes and doublings, and
+    bit-identical results.  The last case's tolerance cannot be met, so every
+    problem takes its three doublings."""
+    crit = Q.WALK_SUM if criterion == "sum" else Q.WALK_EACH
+    probs = _extensible_problems(Q)
+    g = _embedded_g(31)
+    tuples = [_batch_tuple(Q, p, g[:p.d] % np.uint64(p.n)) for p in probs]
+    res, lv, passes, reached = Q.qmc_integrate_batch_extensible(tuples, levels, g, tol, crit)
+    ref, dbl, ref_passes, ref_reached = _python_batch_extensible(Q, tuples, g, levels, tol, crit)
+    assert passes == ref_passes and reached == ref_reached
+    assert list(lv) == dbl
+    assert passes >= 2
+    for r, q in zip(res, ref):
+        assert r.mean[0] == q.mean[0] and r.mean[1] == q.mean[1]
+        assert r.err[0] == q.err[0] and r.err[1] == q.err[1]
+    if tol < 1e-12:
+        assert not reached and passes == levels + 1 and all(v == levels for v in lv)
+
+
+def test_batch_extensible_is_the_rule_of_its_size(Q, oracle_lib, nthreads):
+    """Each result of the batched embedded-lattice walk is the rule of its
+    final size 2^k on g mod 2^k: per problem against qmc_integrate at that
+    size (FP32 within its rounding, FP64 within 1e-12), and the FP64
+    separable problem against the oracle."""
+    probs = _extensible_problems(Q)
+    g = _embedded_g(32)
+    tuples = [_batch_tuple(Q, p, g[:p.d] % np.uint64(p.n)) for p in probs]
+    res, lv, passes, reached = Q.qmc_integrate_batch_extensible(tuples, 3, g, 1e-15, Q.WALK_SUM)
+    assert not reached and all(v == 3 for v in lv)
+    for p, t, r, l in zip(probs, tuples, res, lv):
+        n = p.n << int(l)
+        direct, _ = Q.qmc_integrate(p.d, n, p.m, g[:p.d] % np.uint64(n), p.shifts, t[5], t[6])
+        tol = 2e-7 if p.precision == "fp32" else 1e-12
+        mag = math.hypot(direct.mean[0], direct.mean[1])
+        assert math.hypot(r.mean[0] - direct.mean[0], r.mean[1] - direct.mean[1]) <= tol * mag, p.name
+        assert math.hypot(r.err[0] - direct.err[0], r.err[1] - direct.err[1]) <= 10 * tol * mag, p.name
+        assert r.nonfinite == direct.nonfinite
+    p, r = probs[-2], res[-2]
+    p.n = p.n << int(lv[-2])
+    ref = oracle_lib.integrate(p, g[:p.d] % np.uint64(p.n), nthreads=nthreads)
+    assert abs(r.mean[0] - ref["mean"][0]) <= 1e-12 * abs(ref["mean"][0])
+
+
 def test_batch_walk_without_ladder_is_one_batch(Q):
     """A walk with no ladder lattices evaluates every problem once, on its own
     lattice, exactly as qmc_integrate_batch does, and reports whether the sum
