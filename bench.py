@@ -527,6 +527,21 @@ def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279, start="own"):
     res["batched"] = {"rel_err": float(total_err / abs(total)), "sum": float(total), "wall_s": min(walls),
                       "wall_s_runs": walls, "passes": int(passes), "evals": int(evals), "reached": bool(reached),
                       "largest_n": int(max(ns)), "api": "qmc_integrate_batch_to_tolerance"}
+    # the same walk with QMC_WALK_JUMP: a sector moves up as far as an error
+    # falling like n^-4 would need, skipping the lattices in between
+    walls = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        rj, lvj, pj, okj = qmc.qmc_integrate_batch_to_tolerance(tuples, ladder_n, ladder_g, tol,
+                                                                qmc.WALK_SUM | qmc.WALK_JUMP, stream=sh)
+        walls.append(time.perf_counter() - t0)
+    mj = np.array([r.mean[0] for r in rj])
+    ej = np.array([r.err[0] for r in rj])
+    res["batched_jump"] = {"rel_err": float(math.sqrt(float(np.sum(ej ** 2))) / abs(mj.sum())), "sum": float(mj.sum()),
+                           "wall_s": min(walls), "wall_s_runs": walls, "passes": int(pj), "reached": bool(okj),
+                           "largest_n": int(max(n if l < 0 else ladder[l] for n, l in zip(n0, lvj))),
+                           "speedup_vs_batched": res["batched"]["wall_s"] / min(walls),
+                           "api": "qmc_integrate_batch_to_tolerance, QMC_WALK_JUMP"}
     # one by one: the same decisions, one rule call per sector and level
     steps = [[n] + [m_ for m_ in ladder if m_ > n] for n in n0]
     level = [0] * S
@@ -556,8 +571,10 @@ def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279, start="own"):
                          "passes": passes, "evals": int(evals), "reached": bool(total_err <= tol * abs(total)),
                          "largest_n": int(max(steps[i][level[i]] for i in range(S))), "api": "qmc_integrate per call"}
     res["batched"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched"]["wall_s"]
+    res["batched_jump"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched_jump"]["wall_s"]
     tag = "c3_256_sectors_korobov3_sum" + ("_from_ladder_start" if start == "ladder" else "")
-    return {f"{tag}_batched": res["batched"], f"{tag}_one_by_one": res["one_by_one"]}
+    return {f"{tag}_batched": res["batched"], f"{tag}_batched_jump": res["batched_jump"],
+            f"{tag}_one_by_one": res["one_by_one"]}
 
 
 def c3_time_to_tolerance_embedded(qmc, I, sh, tol, log2_n0=16, log2_nmax=24):
@@ -593,6 +610,19 @@ def c3_time_to_tolerance_embedded(qmc, I, sh, tol, log2_n0=16, log2_nmax=24):
                       "wall_s_runs": walls, "passes": int(passes), "reached": bool(reached),
                       "evals": int(sum((n0 << int(l)) * q.m for q, l in zip(sect, lv))),
                       "largest_n": int(n0 << int(max(lv))), "api": "qmc_integrate_batch_extensible"}
+    walls = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        rj, lvj, pj, okj = qmc.qmc_integrate_batch_extensible(tuples, levels, g, tol, qmc.WALK_SUM | qmc.WALK_JUMP,
+                                                              stream=sh)
+        walls.append(time.perf_counter() - t0)
+    mj = np.array([r.mean[0] for r in rj])
+    ej = np.array([r.err[0] for r in rj])
+    res["batched_jump"] = {"rel_err": float(math.sqrt(float(np.sum(ej ** 2))) / abs(mj.sum())), "sum": float(mj.sum()),
+                           "wall_s": min(walls), "wall_s_runs": walls, "passes": int(pj), "reached": bool(okj),
+                           "largest_n": int(n0 << int(max(lvj))),
+                           "speedup_vs_batched": res["batched"]["wall_s"] / min(walls),
+                           "api": "qmc_integrate_batch_extensible, QMC_WALK_JUMP"}
     # one by one: the same decisions, one rule call per sector and pass
     size = [n0] * S
     dbl = [0] * S
@@ -633,8 +663,10 @@ def c3_time_to_tolerance_embedded(qmc, I, sh, tol, log2_n0=16, log2_nmax=24):
                          "passes": passes, "evals": int(evals), "reached": bool(total_err <= tol * abs(total)),
                          "largest_n": int(max(size)), "api": "qmc_integrate per call"}
     res["batched"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched"]["wall_s"]
+    res["batched_jump"]["speedup_vs_one_by_one"] = res["one_by_one"]["wall_s"] / res["batched_jump"]["wall_s"]
     tag = "c3_256_sectors_korobov3_sum_embedded"
-    return {f"{tag}_batched": res["batched"], f"{tag}_one_by_one": res["one_by_one"]}
+    return {f"{tag}_batched": res["batched"], f"{tag}_batched_jump": res["batched_jump"],
+            f"{tag}_one_by_one": res["one_by_one"]}
 
 
 def time_to_tolerance(qmc, I, torch, tol=1e-8, budget_s=60.0):

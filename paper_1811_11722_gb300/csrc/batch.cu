@@ -891,6 +891,42 @@ static int walk_pass_persistent(BatchPlan* bp, WalkPersist* W, const std::vector
   return QMC_OK;
 }
 
+// QMC_WALK_JUMP.  A problem whose error err exceeds its target t (its share
+// rel_tol |sum| / sqrt(count) of the sum's tolerance, or rel_tol |Qbar_i|)
+// moves up to the first size n' with (n'/n)^4 >= err / t: as far as an
+// error falling like n^-4 would need to reach the target.  The rates the
+// paper reports for its integrals lie between n^-1 and n^-4, so for such
+// problems the jump does not pass the size they need, and it skips the
+// passes in between.  Without a target (|Qbar| = 0) the problem
+// moves one step.
+static void walk_targets(const std::vector<qmc_result>& r, int criterion, double rel_tol, std::vector<double>& t) {
+  const size_t count = r.size();
+  t.resize(count);
+  if (criterion == QMC_WALK_SUM) {
+    double sre = 0.0, sim = 0.0;
+    for (size_t i = 0; i < count; ++i) {
+      sre += r[i].mean[0];
+      sim += r[i].mean[1];
+    }
+    const double share = rel_tol * std::hypot(sre, sim) / std::sqrt((double)count);
+    for (size_t i = 0; i < count; ++i) t[i] = share;
+  } else {
+    for (size_t i = 0; i < count; ++i) t[i] = rel_tol * std::hypot(r[i].mean[0], r[i].mean[1]);
+  }
+}
+
+// err / target, 1 (one step) without a target
+static double walk_excess(const qmc_result& r, double target) {
+  return target > 0.0 ? std::hypot(r.err[0], r.err[1]) / target : 1.0;
+}
+
+// whether a size ratio q = n'/n is still short of an excess e: q^4 < e
+static bool jump_short(double q, double e) {
+  q = q * q;
+  q = q * q;
+  return q < e;
+}
+
 static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels, const uint64_t* ladder_n,
                       const uint64_t* ladder_g, int32_t ladder_dim, double rel_tol, int32_t criterion,
                       qmc_result* out, int32_t* level_out, int32_t* passes_out, cudaStream_t stream) {
@@ -901,7 +937,8 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
   if (ladder_dim < 1 || ladder_dim > QMC_DMAX) return fail(QMC_EINVAL, "ladder_dim=%d outside [1, %d]", ladder_dim, QMC_DMAX);
   if (!(rel_tol > 0.0)) return fail(QMC_EINVAL, "rel_tol must be > 0");
   const bool pers = (criterion & QMC_WALK_PERSISTENT) != 0;
-  criterion &= ~QMC_WALK_PERSISTENT;
+  const bool jump = (criterion & QMC_WALK_JUMP) != 0;
+  criterion &= ~(QMC_WALK_PERSISTENT | QMC_WALK_JUMP);
   if (criterion != QMC_WALK_SUM && criterion != QMC_WALK_EACH) return fail(QMC_EINVAL, "unknown criterion %d", criterion);
   for (int l = 0; l < levels; ++l) {
     const uint64_t n = ladder_n[l];
@@ -1068,6 +1105,16 @@ static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels
       }
     }
     if (act.empty()) break;
+    if (jump) {
+      std::vector<double> tgt;
+      walk_targets(res, criterion, rel_tol, tgt);
+      for (int i : act) {
+        const double ex = walk_excess(res[i], tgt[i]);
+        int l = next[i];
+        while (l + 1 < levels && jump_short((double)ladder_n[l] / (double)cur_n[i], ex)) ++l;
+        next[i] = l;
+      }
+    }
   }
   if (bp.ws) {
     cudaFreeAsync(bp.ws, stream);
@@ -1108,6 +1155,8 @@ static int batch_extensible(int32_t count, const qmc_problem* problems, int32_t 
   if (levels < 0 || levels > 30) return fail(QMC_EINVAL, "levels=%d outside [0, 30]", levels);
   if (g_dim < 1 || g_dim > QMC_DMAX) return fail(QMC_EINVAL, "g_dim=%d outside [1, %d]", g_dim, QMC_DMAX);
   if (!(rel_tol > 0.0)) return fail(QMC_EINVAL, "rel_tol must be > 0");
+  const bool jump = (criterion & QMC_WALK_JUMP) != 0;
+  criterion &= ~QMC_WALK_JUMP;
   if (criterion != QMC_WALK_SUM && criterion != QMC_WALK_EACH) return fail(QMC_EINVAL, "unknown criterion %d", criterion);
   for (int c = 0; c < g_dim; ++c)
     if ((g[c] & 1) == 0) return fail(QMC_EINVAL, "g[%d]=%llu must be odd", c, (unsigned long long)g[c]);
@@ -1143,7 +1192,7 @@ static int batch_extensible(int32_t count, const qmc_problem* problems, int32_t 
     const Plan* pl = bp.probs[i].get();
     int slots = pl->nblk;
     if (maxd[i] > 0) {
-      const uint64_t n_max = pr[i].n << (maxd[i] - 1);
+      const uint64_t n_max = pr[i].n << (jump ? maxd[i] : maxd[i] - 1);
       const int wave = sms * std::max(pl->grid_occ, 1);
       slots = std::max(slots, pl->grid_capped ? std::min(wave, walk_cap(n_max, pl->m, sms)) : wave);
     }
@@ -1183,7 +1232,7 @@ static int batch_extensible(int32_t count, const qmc_problem* problems, int32_t 
   const size_t tm2 = (size_t)bp.total_m * 2;
   std::vector<double> q(tm2), ps(tm2), sh;
   std::vector<uint64_t> size(count), gl(QMC_DMAX);
-  std::vector<int> dbl(count, 0);
+  std::vector<int> dbl(count, 0), step(count, 1);  // step: doublings of the next pass
   std::vector<unsigned long long> nonfinite(count, 0), deform(count, 0);
   std::vector<qmc_result> res(count), est(count);
   std::vector<FinalizeArgs> fin;
@@ -1197,11 +1246,20 @@ static int batch_extensible(int32_t count, const qmc_problem* problems, int32_t 
   while (rc == QMC_OK) {
     if (passes > 0)
       for (int i : act) {
-        // the new points of size 2n: the size-n rule on shifts Delta + (g mod 2n) / (2n)
         const qmc_problem& qp = problems[i];
+        Plan* pl = bp.probs[i].get();
+        if (step[i] > 1) {
+          // a jump of several doublings: the whole rule of the new size
+          const uint64_t n = size[i] << step[i];
+          for (int c = 0; c < qp.d; ++c) gl[c] = g[c] % n;
+          rc = plan_rebase(pl, n, gl.data(), walk_cap(n, pl->m, sms));
+          if (rc == QMC_OK) rc = plan_reshift(pl, qp.shifts);
+          if (rc) break;
+          continue;
+        }
+        // the new points of size 2n: the size-n rule on shifts Delta + (g mod 2n) / (2n)
         const uint64_t n = size[i];
         for (int c = 0; c < qp.d; ++c) gl[c] = g[c] % n;
-        Plan* pl = bp.probs[i].get();
         rc = plan_rebase(pl, n, gl.data(), walk_cap(n, pl->m, sms));
         if (rc) break;
         sh.resize((size_t)qp.m * qp.d);
@@ -1227,6 +1285,10 @@ static int batch_extensible(int32_t count, const qmc_problem* problems, int32_t 
       const size_t m2 = (size_t)problems[i].m * 2;
       if (passes == 0) {
         std::memcpy(qi, pi, m2 * sizeof(double));
+      } else if (step[i] > 1) {
+        std::memcpy(qi, pi, m2 * sizeof(double));
+        size[i] <<= step[i];
+        dbl[i] += step[i];
       } else {
         for (size_t u = 0; u < m2; ++u) qi[u] = 0.5 * (qi[u] + pi[u]);
         size[i] *= 2;
@@ -1273,6 +1335,16 @@ static int batch_extensible(int32_t count, const qmc_problem* problems, int32_t 
       }
     }
     if (act.empty()) break;
+    if (jump) {
+      std::vector<double> tgt;
+      walk_targets(est, criterion, rel_tol, tgt);
+      for (int i : act) {
+        const double ex = walk_excess(est[i], tgt[i]);
+        int k = 1;
+        while (k < maxd[i] - dbl[i] && jump_short((double)(1ull << k), ex)) ++k;
+        step[i] = k;
+      }
+    }
   }
   if (bp.ws) {
     cudaFreeAsync(bp.ws, stream);

@@ -366,7 +366,7 @@ def qmc_integrate_batch(problems, stream=0, want_per_shift=False):
     return list(res), ps
 
 
-WALK_SUM, WALK_EACH, WALK_PERSISTENT = 0, 1, 0x10
+WALK_SUM, WALK_EACH, WALK_PERSISTENT, WALK_JUMP = 0, 1, 0x10, 0x20
 
 
 def qmc_integrate_batch_to_tolerance(problems, ladder_n, ladder_g, rel_tol, criterion=WALK_SUM, stream=0):

@@ -576,7 +576,26 @@ def test_batch_plan_graph_replay_and_tune(Q):
     bp.destroy()
 
 
-def _python_batch_walk(Q, tuples, ladder_n, ladder_g, tol, criterion):
+def _walk_targets(Q, res, tol, criterion):
+    """Each problem's error target: its share of the sum's tolerance, or its own."""
+    if criterion == Q.WALK_SUM:
+        tot = math.hypot(sum(r.mean[0] for r in res), sum(r.mean[1] for r in res))
+        return [tol * tot / math.sqrt(len(res))] * len(res)
+    return [tol * math.hypot(r.mean[0], r.mean[1]) for r in res]
+
+
+def _jump_short(q, excess):
+    """QMC_WALK_JUMP's test: a size ratio q still short of the excess, q^4 < excess."""
+    q = q * q
+    q = q * q
+    return q < excess
+
+
+def _excess(r, target):
+    return math.hypot(r.err[0], r.err[1]) / target if target > 0 else 1.0
+
+
+def _python_batch_walk(Q, tuples, ladder_n, ladder_g, tol, criterion, jump=False):
     """The walk of qmc_integrate_batch_to_tolerance written with one
     qmc_integrate_batch call per pass (same lattices, same decisions)."""
     S, L = len(tuples), len(ladder_n)
@@ -613,17 +632,27 @@ def _python_batch_walk(Q, tuples, ladder_n, ladder_g, tol, criterion):
             act = [i for i in range(S) if not ok[i] and nxt[i] < L]
         if not act:
             break
+        if jump:
+            tgt = _walk_targets(Q, res, tol, criterion)
+            for i in act:
+                ex = _excess(res[i], tgt[i])
+                l = nxt[i]
+                while l + 1 < L and _jump_short(float(ladder_n[l]) / float(cur[i][1]), ex):
+                    l += 1
+                nxt[i] = l
     return res, at, passes, reached
 
 
-@pytest.mark.parametrize("criterion,tol", [("sum", 3e-8), ("each", 2e-7), ("sum", 1e-15)])
-def test_batch_walk_matches_per_pass_batches(Q, criterion, tol):
+@pytest.mark.parametrize("criterion,tol,jump", [("sum", 3e-8, False), ("each", 2e-7, False), ("sum", 1e-15, False),
+                                                ("sum", 3e-8, True), ("each", 2e-7, True)])
+def test_batch_walk_matches_per_pass_batches(Q, criterion, tol, jump):
     """The batched ladder walk (plans built once, moved to each new lattice)
     against the same walk made of one qmc_integrate_batch per pass: the same
     passes and final lattices, and bit-identical results.  The batch mixes
     FP32 sectors (baker, Korobov 3), an FP64 separable problem and a deformed
-    FP64 problem (whose launch shape ignores the CTA cap); the last case's
-    tolerance cannot be met, so the ladder runs out."""
+    FP64 problem (whose launch shape ignores the CTA cap); the third case's
+    tolerance cannot be met, so the ladder runs out.  With QMC_WALK_JUMP a
+    problem may skip ladder lattices; the replica takes the same jumps."""
     crit = Q.WALK_SUM if criterion == "sum" else Q.WALK_EACH
     sect = I.config3(count=12, transform="korobov", alpha=3)
     probs = []
@@ -639,8 +668,9 @@ def test_batch_walk_matches_per_pass_batches(Q, criterion, tol):
     ladder_n = np.array([I.prev_prime(v) for v in (40000, 90000, 200000, 450000, 1000000, 2200000)], np.uint64)
     ladder_g = np.stack([I.random_generating_vector(I.SplitMix64(900 + l), 8, int(n))
                          for l, n in enumerate(ladder_n)]).astype(np.uint64)
-    res, lv, passes, reached = Q.qmc_integrate_batch_to_tolerance(tuples, ladder_n, ladder_g, tol, crit)
-    ref, at, ref_passes, ref_reached = _python_batch_walk(Q, tuples, ladder_n, ladder_g, tol, crit)
+    res, lv, passes, reached = Q.qmc_integrate_batch_to_tolerance(tuples, ladder_n, ladder_g, tol,
+                                                                  crit | (Q.WALK_JUMP if jump else 0))
+    ref, at, ref_passes, ref_reached = _python_batch_walk(Q, tuples, ladder_n, ladder_g, tol, crit, jump)
     assert passes == ref_passes and reached == ref_reached
     assert list(lv) == at
     assert passes >= 2  # at least one move to a ladder lattice
@@ -722,20 +752,27 @@ def _shifted_tuple(t, g, n, new_points):
     return (d, n, t[2], g[:d] % np.uint64(n), np.ascontiguousarray(sh)) + tuple(t[5:])
 
 
-def _python_batch_extensible(Q, tuples, g, levels, tol, criterion):
+def _python_batch_extensible(Q, tuples, g, levels, tol, criterion, jump=False):
     """The walk of qmc_integrate_batch_extensible written with one
     qmc_integrate_batch call per pass (same points, same decisions), the
-    per-shift values averaged and combined on the host."""
+    per-shift values averaged and combined on the host.  A jump of k > 1
+    doublings evaluates the whole rule of the new size."""
     S = len(tuples)
     size = [t[1] for t in tuples]
     maxd = [min(levels, 30 - int(t[1]).bit_length() + 1) for t in tuples]
     dbl = [0] * S
+    step = [1] * S
     q = [None] * S
     res = [None] * S
     act, passes, reached = list(range(S)), 0, False
     while True:
-        rs, ps = Q.qmc_integrate_batch([_shifted_tuple(tuples[i], g, size[i], passes > 0) for i in act],
-                                       want_per_shift=True)
+        batch = []
+        for i in act:
+            if passes > 0 and step[i] > 1:
+                batch.append(_shifted_tuple(tuples[i], g, size[i] << step[i], False))
+            else:
+                batch.append(_shifted_tuple(tuples[i], g, size[i], passes > 0))
+        rs, ps = Q.qmc_integrate_batch(batch, want_per_shift=True)
         off = 0
         for i, r in zip(act, rs):
             m = tuples[i][2]
@@ -743,6 +780,10 @@ def _python_batch_extensible(Q, tuples, g, levels, tol, criterion):
             off += m
             if passes == 0:
                 q[i] = qn.copy()
+            elif step[i] > 1:
+                q[i] = qn.copy()
+                size[i] <<= step[i]
+                dbl[i] += step[i]
             else:
                 q[i] = 0.5 * (q[i] + qn)
                 size[i] *= 2
@@ -766,22 +807,35 @@ def _python_batch_extensible(Q, tuples, g, levels, tol, criterion):
             act = [i for i in range(S) if not ok[i] and dbl[i] < maxd[i]]
         if not act:
             break
+        if jump:
+            tgt = _walk_targets(Q, res, tol, criterion)
+            for i in act:
+                ex = _excess(res[i], tgt[i])
+                k = 1
+                while k < maxd[i] - dbl[i] and _jump_short(float(1 << k), ex):
+                    k += 1
+                step[i] = k
     return res, dbl, passes, reached
 
 
-@pytest.mark.parametrize("criterion,tol,levels", [("sum", 3e-8, 8), ("each", 2e-7, 8), ("sum", 1e-15, 3)])
-def test_batch_extensible_matches_per_pass_batches(Q, criterion, tol, levels):
+@pytest.mark.parametrize("criterion,tol,levels,jump", [("sum", 3e-8, 8, False), ("each", 2e-7, 8, False),
+                                                       ("sum", 1e-15, 3, False), ("sum", 3e-8, 8, True),
+                                                       ("each", 2e-7, 8, True), ("sum", 1e-15, 5, True)])
+def test_batch_extensible_matches_per_pass_batches(Q, criterion, tol, levels, jump):
     """The batched embedded-lattice walk (plans built once, moved to each
     size and shifted to its new points) against the same walk made of one
     qmc_integrate_batch per pass: the same passes and doublings, and
-    bit-identical results.  The last case's tolerance cannot be met, so every
-    problem takes its three doublings."""
-    crit = Q.WALK_SUM if criterion == "sum" else Q.WALK_EACH
+    bit-identical results.  The third case's tolerance cannot be met, so
+    every problem takes its three doublings.  With QMC_WALK_JUMP a problem
+    may take several doublings in one pass (the whole rule of its new size);
+    in the last case every problem jumps to its limit."""
+    crit = (Q.WALK_SUM if criterion == "sum" else Q.WALK_EACH) | (Q.WALK_JUMP if jump else 0)
+    base_crit = Q.WALK_SUM if criterion == "sum" else Q.WALK_EACH
     probs = _extensible_problems(Q)
     g = _embedded_g(31)
     tuples = [_batch_tuple(Q, p, g[:p.d] % np.uint64(p.n)) for p in probs]
     res, lv, passes, reached = Q.qmc_integrate_batch_extensible(tuples, levels, g, tol, crit)
-    ref, dbl, ref_passes, ref_reached = _python_batch_extensible(Q, tuples, g, levels, tol, crit)
+    ref, dbl, ref_passes, ref_reached = _python_batch_extensible(Q, tuples, g, levels, tol, base_crit, jump)
     assert passes == ref_passes and reached == ref_reached
     assert list(lv) == dbl
     assert passes >= 2
@@ -789,7 +843,8 @@ def test_batch_extensible_matches_per_pass_batches(Q, criterion, tol, levels):
         assert r.mean[0] == q.mean[0] and r.mean[1] == q.mean[1]
         assert r.err[0] == q.err[0] and r.err[1] == q.err[1]
     if tol < 1e-12:
-        assert not reached and passes == levels + 1 and all(v == levels for v in lv)
+        assert not reached and all(v == levels for v in lv)
+        assert passes == (2 if jump else levels + 1)
 
 
 def test_batch_extensible_is_the_rule_of_its_size(Q, oracle_lib, nthreads):
