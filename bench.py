@@ -528,7 +528,7 @@ def c3_time_to_tolerance(qmc, I, sh, tol, ladder_max=11863279, start="own"):
                       "wall_s_runs": walls, "passes": int(passes), "evals": int(evals), "reached": bool(reached),
                       "largest_n": int(max(ns)), "api": "qmc_integrate_batch_to_tolerance"}
     # the same walk with QMC_WALK_JUMP: a sector moves up as far as an error
-    # falling like n^-4 would need, skipping the lattices in between
+    # falling like n^-6 would need, skipping the lattices in between
     walls = []
     for _ in range(3):
         t0 = time.perf_counter()

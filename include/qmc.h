@@ -262,12 +262,13 @@ int qmc_integrate_batch(int32_t count, const qmc_problem* problems, qmc_result* 
  *   qmc_batch_plan_create_persistent (else QMC_EUNSUPPORTED); a problem's
  *   results equal that plan's at the same lattice, bit for bit.
  *   QMC_WALK_JUMP (or-ed into criterion): a problem that moves up goes to the
- *   first ladder lattice n' with (n'/n)^4 >= err_i / t_i, t_i its target
+ *   first ladder lattice n' with (n'/n)^6 >= err_i / t_i, t_i its target
  *   (the share above, or rel_tol |Qbar_i|): as far as an error falling like
- *   n^-4 would need, instead of one lattice.  Errors that fall no faster
- *   than n^-4 (the rates the paper reports lie between n^-1 and n^-4) then
- *   never take a problem past the lattice it needs; the lattices in between
- *   are skipped.  With t_i = 0 the problem moves one lattice.
+ *   n^-6 would need, instead of one lattice.  Errors that fall no faster
+ *   than that (the rates the paper reports lie between n^-1 and n^-4) then
+ *   never take a problem past the lattice it needs, and the lattices in
+ *   between are skipped; estimates that fall faster can overshoot.  With
+ *   t_i = 0 the problem moves one lattice.
  *   levels          ladder lattices (0..64), increasing n in [2, 2^31)
  *   ladder_n        [levels];  ladder_g  [levels * ladder_dim], g in [1, n)
  *   ladder_dim      components per ladder vector, >= every problem's d (when levels > 0)
@@ -303,8 +304,8 @@ int qmc_integrate_batch_to_tolerance(int32_t count, const qmc_problem* problems,
  *   g          [g_dim] odd components (qmc_make_lattice_embedded), host
  *   g_dim      >= every problem's d
  *   criterion  QMC_WALK_SUM or QMC_WALK_EACH, optionally | QMC_WALK_JUMP: a
- *              problem then takes the k >= 1 doublings with 16^k >= err_i / t_i
- *              in one pass, evaluating the whole rule of its new size when
+ *              problem then takes the fewest k >= 1 doublings with
+ *              64^k >= err_i / t_i in one pass, evaluating the whole rule of its new size when
  *              k > 1 (the points it had, at most a quarter of them, are
  *              evaluated again)
  *   level_out  optional [count]: doublings taken (final n = problems[i].n << level)

@@ -893,12 +893,12 @@ static int walk_pass_persistent(BatchPlan* bp, WalkPersist* W, const std::vector
 
 // QMC_WALK_JUMP.  A problem whose error err exceeds its target t (its share
 // rel_tol |sum| / sqrt(count) of the sum's tolerance, or rel_tol |Qbar_i|)
-// moves up to the first size n' with (n'/n)^4 >= err / t: as far as an
-// error falling like n^-4 would need to reach the target.  The rates the
+// moves up to the first size n' with (n'/n)^6 >= err / t: as far as an
+// error falling like n^-6 would need to reach the target.  The rates the
 // paper reports for its integrals lie between n^-1 and n^-4, so for such
 // problems the jump does not pass the size they need, and it skips the
-// passes in between.  Without a target (|Qbar| = 0) the problem
-// moves one step.
+// passes in between; error estimates that fall faster can be taken past
+// it.  Without a target (|Qbar| = 0) the problem moves one step.
 static void walk_targets(const std::vector<qmc_result>& r, int criterion, double rel_tol, std::vector<double>& t) {
   const size_t count = r.size();
   t.resize(count);
@@ -920,11 +920,14 @@ static double walk_excess(const qmc_result& r, double target) {
   return target > 0.0 ? std::hypot(r.err[0], r.err[1]) / target : 1.0;
 }
 
-// whether a size ratio q = n'/n is still short of an excess e: q^4 < e
+// the rate bound of the jumps: errors assumed to fall no faster than n^-kJumpPow
+constexpr int kJumpPow = 6;
+
+// whether a size ratio q = n'/n is still short of an excess e: q^kJumpPow < e
 static bool jump_short(double q, double e) {
-  q = q * q;
-  q = q * q;
-  return q < e;
+  double p = 1.0;
+  for (int t = 0; t < kJumpPow; ++t) p *= q;
+  return p < e;
 }
 
 static int batch_walk(int32_t count, const qmc_problem* problems, int32_t levels, const uint64_t* ladder_n,

@@ -585,10 +585,12 @@ def _walk_targets(Q, res, tol, criterion):
 
 
 def _jump_short(q, excess):
-    """QMC_WALK_JUMP's test: a size ratio q still short of the excess, q^4 < excess."""
-    q = q * q
-    q = q * q
-    return q < excess
+    """QMC_WALK_JUMP's test: a size ratio q still short of the excess,
+    q^6 < excess (the product taken in the library's order)."""
+    p = 1.0
+    for _ in range(6):
+        p *= q
+    return p < excess
 
 
 def _excess(r, target):
