@@ -1188,7 +1188,7 @@ static int batch_extensible(int32_t count, const qmc_problem* problems, int32_t 
   int rc = batch_build(&bp, count, pr.data(), kWalkWork);
   if (rc) return rc;
   // slots: one resident wave, at most the cap of the largest rule evaluated
-  // (half the last size)
+  // (half the last size; with jumps the last size itself)
   size_t bytes = 0;
   std::vector<size_t> part_off(count), cnt_off(count);
   for (int i = 0; i < count; ++i) {
